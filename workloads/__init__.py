@@ -1,0 +1,261 @@
+"""Seeded synthetic SDP instances shared by the oracle and the CUDA path.
+
+This module only *generates inputs*: graphs, sampled matrix entries and the
+primal SDP data (C, A, b) in the exchange format of the C-ABI, plus seeded
+starting factors.  It holds none of the solver's arithmetic (no gradient, no
+line search, no multiplier update), so that the oracle and the GPU library can
+both consume it without sharing any part of the method.
+
+Exchange format (the primal SDP of Eq. (1.1): min <C,X> s.t. <A_k,X> = b_k, X psd):
+
+* ``rowptr`` int64 (n+1), ``colind`` int32, ``val`` float64: C as a full
+  symmetric CSR matrix with sorted column indices in every row.
+* constraint triplets ``con, row, col`` int32 and ``aval`` float64 with
+  ``row <= col``; constraint k is  <A_k, X> = sum a * X_ij * (1 if i == j else 2).
+* ``b`` float64 (m).
+
+Workloads (Sec. 4.2 MaxCut SDP and Sec. 4.3 matrix-completion SDP):
+
+* MaxCut: C = -L/4 with L the weighted graph Laplacian, constraints X_ii = 1
+  (one diagonal triplet per row, b = 1).  The reported SDP value is -<C,X>.
+* Matrix completion: X has order n1 + n2, C = I, constraint k <-> (i, j) in
+  Omega is  X_{i,n1+j} + X_{n1+j,i} = 2 M_ij  (one off-diagonal triplet).
+
+Random numbers come from numpy's PCG64 (``numpy.random.default_rng(seed)``).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "SDPInstance", "er_graph", "torus_graph", "complete_graph", "cycle_graph",
+    "bipartite_torus_graph", "maxcut_instance", "mc_instance", "initial_factor",
+    "rank_log2", "config_instance",
+]
+
+
+@dataclass
+class SDPInstance:
+    """Primal SDP data in the C-ABI exchange format (all arrays host, contiguous)."""
+
+    n: int
+    rowptr: np.ndarray          # int64 (n+1)
+    colind: np.ndarray          # int32 (nnz)
+    val: np.ndarray             # float64 (nnz)
+    m: int
+    con: np.ndarray             # int32 (nnz_a)
+    row: np.ndarray             # int32 (nnz_a), row <= col
+    col: np.ndarray             # int32 (nnz_a)
+    aval: np.ndarray            # float64 (nnz_a)
+    b: np.ndarray               # float64 (m)
+    kind: str = "generic"
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+
+def _sym_csr(n: int, i: np.ndarray, j: np.ndarray, w: np.ndarray, diag: np.ndarray):
+    """Full symmetric CSR from upper off-diagonal entries (i<j, w) and a dense diagonal.
+
+    Every diagonal slot is stored (also when its value is 0) so that the row
+    structure does not depend on the weights.
+    """
+    i = np.asarray(i, dtype=np.int64)
+    j = np.asarray(j, dtype=np.int64)
+    rows = np.concatenate([i, j, np.arange(n, dtype=np.int64)])
+    cols = np.concatenate([j, i, np.arange(n, dtype=np.int64)])
+    vals = np.concatenate([w, w, diag]).astype(np.float64)
+    key = rows * n + cols
+    order = np.argsort(key, kind="stable")
+    key = key[order]
+    vals = vals[order]
+    # merge duplicates (none expected from the generators, kept for safety)
+    uniq, start = np.unique(key, return_index=True)
+    vals = np.add.reduceat(vals, start) if len(uniq) != len(key) else vals
+    rows = (uniq // n).astype(np.int64)
+    cols = (uniq % n).astype(np.int32)
+    counts = np.bincount(rows, minlength=n).astype(np.int64)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    return rowptr, cols, np.ascontiguousarray(vals, dtype=np.float64)
+
+
+# ----------------------------------------------------------------------------- graphs
+
+def _weights(rng, count: int, weights: str) -> np.ndarray:
+    if weights == "unit":
+        return np.ones(count, dtype=np.float64)
+    if weights == "pm1":
+        return rng.integers(0, 2, size=count).astype(np.float64) * 2.0 - 1.0
+    raise ValueError(f"unknown weights {weights!r}")
+
+
+def er_graph(n: int, n_edges: int, seed: int, weights: str = "unit"):
+    """Erdos-Renyi G(n, M): ``n_edges`` distinct undirected edges drawn uniformly.
+
+    Returns (i, j, w) with i < j, sorted by (i, j).
+    """
+    if n_edges > n * (n - 1) // 2:
+        raise ValueError("too many edges")
+    rng = np.random.default_rng(seed)
+    keys = np.empty(0, dtype=np.int64)
+    need = n_edges
+    while need > 0:
+        draw = int(need * 1.05) + 16
+        a = rng.integers(0, n, size=draw, dtype=np.int64)
+        c = rng.integers(0, n, size=draw, dtype=np.int64)
+        ok = a != c
+        lo = np.minimum(a[ok], c[ok])
+        hi = np.maximum(a[ok], c[ok])
+        keys = np.unique(np.concatenate([keys, lo * n + hi]))
+        if len(keys) > n_edges:
+            # keep a uniformly random subset of the distinct pairs
+            pick = rng.choice(len(keys), size=n_edges, replace=False)
+            keys = np.sort(keys[pick])
+        need = n_edges - len(keys)
+    i = (keys // n).astype(np.int64)
+    j = (keys % n).astype(np.int64)
+    return i, j, _weights(rng, len(i), weights)
+
+
+def torus_graph(side: int, seed: int, weights: str = "pm1"):
+    """2D toroidal grid side x side (4-regular with wraparound)."""
+    rng = np.random.default_rng(seed)
+    idx = np.arange(side * side, dtype=np.int64).reshape(side, side)
+    right = np.roll(idx, -1, axis=1)
+    down = np.roll(idx, -1, axis=0)
+    a = np.concatenate([idx.ravel(), idx.ravel()])
+    c = np.concatenate([right.ravel(), down.ravel()])
+    lo = np.minimum(a, c)
+    hi = np.maximum(a, c)
+    keys = np.unique(lo * (side * side) + hi)
+    n = side * side
+    i = keys // n
+    j = keys % n
+    return i, j, _weights(rng, len(i), weights)
+
+
+def bipartite_torus_graph(side: int):
+    """Even torus with unit weights (bipartite when side is even)."""
+    i, j, _ = torus_graph(side, seed=0, weights="unit")
+    return i, j, np.ones(len(i))
+
+
+def complete_graph(n: int):
+    i, j = np.triu_indices(n, k=1)
+    return i.astype(np.int64), j.astype(np.int64), np.ones(len(i))
+
+
+def cycle_graph(n: int):
+    i = np.arange(n, dtype=np.int64)
+    j = (i + 1) % n
+    lo = np.minimum(i, j)
+    hi = np.maximum(i, j)
+    order = np.lexsort((hi, lo))
+    return lo[order], hi[order], np.ones(n)
+
+
+# ----------------------------------------------------------------------------- instances
+
+def maxcut_instance(n: int, edges) -> SDPInstance:
+    """MaxCut SDP of Sec. 4.2 written as a minimisation: C = -L(G,w)/4, X_ii = 1."""
+    i, j, w = edges
+    deg = np.zeros(n, dtype=np.float64)
+    np.add.at(deg, i, w)
+    np.add.at(deg, j, w)
+    # L_ij = -w_ij, L_ii = sum_k w_ik  ->  C = -L/4
+    rowptr, colind, val = _sym_csr(n, i, j, w / 4.0, -deg / 4.0)
+    k = np.arange(n, dtype=np.int32)
+    return SDPInstance(
+        n=n, rowptr=rowptr, colind=colind, val=val, m=n,
+        con=k.copy(), row=k.copy(), col=k.copy(), aval=np.ones(n),
+        b=np.ones(n), kind="maxcut",
+        meta={"edges": (np.asarray(i), np.asarray(j), np.asarray(w, dtype=np.float64))},
+    )
+
+
+def mc_instance(n1: int, n2: int, rank: int, n_samples: int, seed: int) -> SDPInstance:
+    """Matrix-completion SDP of Sec. 4.3 with M = U V^T, U, V iid N(0,1) of rank ``rank``.
+
+    Omega is drawn uniformly without replacement.  X = [[W1, Y^T-block], ...] has
+    order n1 + n2; constraint k <-> (i, j): X_{i, n1+j} + X_{n1+j, i} = 2 M_ij.
+    """
+    rng = np.random.default_rng(seed)
+    U = rng.standard_normal((n1, rank))
+    V = rng.standard_normal((n2, rank))
+    total = n1 * n2
+    if n_samples > total:
+        raise ValueError("too many samples")
+    if n_samples > total // 2:
+        flat = rng.choice(total, size=n_samples, replace=False)
+    else:
+        flat = np.empty(0, dtype=np.int64)
+        while len(flat) < n_samples:
+            draw = rng.integers(0, total, size=int((n_samples - len(flat)) * 1.1) + 16)
+            flat = np.unique(np.concatenate([flat, draw]))
+        flat = rng.permutation(flat)[:n_samples]
+    flat = np.sort(flat)
+    si = (flat // n2).astype(np.int64)
+    sj = (flat % n2).astype(np.int64)
+    mvals = np.einsum("kr,kr->k", U[si], V[sj])
+    n = n1 + n2
+    rowptr, colind, val = _sym_csr(n, np.empty(0, np.int64), np.empty(0, np.int64),
+                                   np.empty(0), np.ones(n))
+    m = n_samples
+    return SDPInstance(
+        n=n, rowptr=rowptr, colind=colind, val=val, m=m,
+        con=np.arange(m, dtype=np.int32), row=si.astype(np.int32),
+        col=(n1 + sj).astype(np.int32), aval=np.ones(m), b=2.0 * mvals,
+        kind="mc", meta={"n1": n1, "n2": n2, "U": U, "V": V},
+    )
+
+
+def rank_log2(k: int) -> int:
+    """ceil(log2 k): the logarithmic starting rank of App. A.1."""
+    return max(1, int(math.ceil(math.log2(max(k, 2)))))
+
+
+def initial_factor(inst: SDPInstance, r: int, seed: int) -> np.ndarray:
+    """Seeded starting factor R0 (n x r), rows iid N(0, I_r).
+
+    Rows of MaxCut instances are scaled to unit norm (feasible for X_ii = 1).
+    Matrix-completion factors are scaled so that ||R0||_F^2 = ||b||_1 / 2.
+    """
+    rng = np.random.default_rng(seed)
+    R = rng.standard_normal((inst.n, r))
+    if inst.kind == "maxcut":
+        R /= np.linalg.norm(R, axis=1, keepdims=True)
+    elif inst.kind == "mc":
+        target = 0.5 * float(np.abs(inst.b).sum())
+        R *= math.sqrt(max(target, 1.0) / float((R * R).sum()))
+    return np.ascontiguousarray(R)
+
+
+def config_instance(name: str, seed: int = 0):
+    """The named synthetic workloads (shapes and distributions of the paper's workloads).
+
+    Returns (instance, r0).
+    """
+    if name == "maxcut_er_1e3":          # ER n=1000, avg degree 8, unit weights
+        n = 1000
+        inst = maxcut_instance(n, er_graph(n, 4 * n, seed, "unit"))
+        return inst, rank_log2(n)
+    if name == "maxcut_torus_1e6":       # 1000x1000 torus, weights in {-1,+1}
+        side = 1000
+        inst = maxcut_instance(side * side, torus_graph(side, seed, "pm1"))
+        return inst, rank_log2(side * side)
+    if name == "mc_5e4_rank3":           # 50000 x 50000, rank 3, |Omega| = ceil(5 n ln n)
+        n = 50000
+        k = int(math.ceil(5 * n * math.log(n)))
+        inst = mc_instance(n, n, 3, k, seed)
+        return inst, rank_log2(inst.m)
+    if name == "maxcut_er_1e7":          # ER n=1e7, avg degree 4, weights in {-1,+1}
+        n = 10_000_000
+        inst = maxcut_instance(n, er_graph(n, 2 * n, seed, "pm1"))
+        return inst, 24
+    raise KeyError(name)
