@@ -199,10 +199,12 @@ def quartic_step(a) -> float:
 
 # ----------------------------------------------------------------------------- L-BFGS
 
-def lbfgs_direction(G: np.ndarray, S: list, Y: list) -> np.ndarray:
-    """Search direction of Algorithm 1 (two-loop recursion, initial matrix I).
+def lbfgs_direction(G: np.ndarray, S: list, Y: list, scaling: int = 0) -> np.ndarray:
+    """Search direction of Algorithm 1 (two-loop recursion).
 
     ``S`` and ``Y`` hold the stored pairs oldest first; beta_t = 1/<y^t, s^t>.
+    The initial matrix is I as printed (scaling = 0) or gamma I with
+    gamma = <s,y>/<y,y> of the newest pair (scaling = 1, the usual L-BFGS choice).
     """
     D = -G.copy()
     T = len(S)
@@ -211,6 +213,8 @@ def lbfgs_direction(G: np.ndarray, S: list, Y: list) -> np.ndarray:
     for t in range(T - 1, -1, -1):                  # newest to oldest
         alpha[t] = beta[t] * float(np.sum(S[t] * D))
         D = D - alpha[t] * Y[t]
+    if scaling and T:
+        D = D * (float(np.sum(S[-1] * Y[-1])) / float(np.sum(Y[-1] * Y[-1])))
     for t in range(T):                              # oldest to newest
         D = D + (alpha[t] - beta[t] * float(np.sum(Y[t] * D))) * S[t]
     return D
@@ -304,7 +308,10 @@ class Params:
     rho_max: float = 1e12
     infeas_decrease: float = 0.25     # rho grows unless err1 shrank by this factor
     inner_rel: float = 1.0            # inner stop: ||G||_F <= inner_rel * max(||A(RR^T)-b||, tol (1+||b||_inf))
-    rank_update_threshold: int = 2    # outer steps in a row that hit max_inner
+    rank_update_threshold: int = 3    # outer steps in a row that hit max_inner
+    lbfgs_scaling: int = 1            # 0: initial matrix I (Algorithm 1); 1: gamma I
+    rho_policy: int = 1               # 1: rho grows only after a converged inner loop
+    inner_scale: int = 1              # 1: inner stop against rho ||z|| instead of ||z||
     seed: int = 0
     time_limit: float = 1e4           # seconds (Sec. 4.1)
 
@@ -343,9 +350,10 @@ def solve(P: Problem, R0: np.ndarray, params: Params | None = None,
         while k < prm.max_inner:
             # stop once the gradient is small next to the current infeasibility
             zc = float(np.linalg.norm(constraint_map(P, R, R) - P.b))
-            if float(np.linalg.norm(G)) <= prm.inner_rel * max(zc, prm.tol * (1.0 + bnorm_inf)):
+            zs = rho * zc if prm.inner_scale else zc
+            if float(np.linalg.norm(G)) <= prm.inner_rel * max(zs, prm.tol * (1.0 + bnorm_inf)):
                 break
-            D = lbfgs_direction(G, S, Yh)
+            D = lbfgs_direction(G, S, Yh, prm.lbfgs_scaling)
             k += 1
             a, _ = linesearch_coeffs(P, R, D, y, rho)
             tau = quartic_step(a)
@@ -383,7 +391,7 @@ def solve(P: Problem, R0: np.ndarray, params: Params | None = None,
             status = "ok"
             err1 = err1_new
             break
-        if err1_new > prm.infeas_decrease * err1:
+        if err1_new > prm.infeas_decrease * err1 and (prm.rho_policy == 0 or k < prm.max_inner):
             rho = min(rho * prm.rho_growth, prm.rho_max)
         err1 = err1_new
         # ---- dynamic rank (App. A.1)

@@ -174,10 +174,10 @@ def test_quartic_step_degenerate_cases():
     assert O.quartic_step([1.0, 0.0, -2.0, -1e-12]) == pytest.approx(1.0, rel=1e-9)
 
 
-def _bfgs_dense_direction(G, S, Y):
-    """-H G with H built by the BFGS inverse update from H0 = I, oldest pair first."""
+def _bfgs_dense_direction(G, S, Y, gamma=1.0):
+    """-H G with H built by the BFGS inverse update from H0 = gamma I, oldest pair first."""
     g = G.ravel()
-    H = np.eye(g.size)
+    H = gamma * np.eye(g.size)
     for s, y in zip(S, Y):
         s, y = s.ravel(), y.ravel()
         r = 1.0 / (y @ s)
@@ -197,6 +197,10 @@ def test_two_loop_matches_dense_bfgs_matrix():
         G = rng.standard_normal(shape)
         np.testing.assert_allclose(O.lbfgs_direction(G, S, Y), _bfgs_dense_direction(G, S, Y), rtol=1e-10,
                                    atol=1e-12)
+        if T:
+            gamma = float(np.sum(S[-1] * Y[-1]) / np.sum(Y[-1] * Y[-1]))
+            np.testing.assert_allclose(O.lbfgs_direction(G, S, Y, scaling=1),
+                                       _bfgs_dense_direction(G, S, Y, gamma), rtol=1e-10, atol=1e-12)
 
 
 # ----------------------------------------------------------------------------- randomness

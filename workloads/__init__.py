@@ -65,27 +65,42 @@ def _sym_csr(n: int, i: np.ndarray, j: np.ndarray, w: np.ndarray, diag: np.ndarr
     Every diagonal slot is stored (also when its value is 0) so that the row
     structure does not depend on the weights.
     """
+    import scipy.sparse as sp
     i = np.asarray(i, dtype=np.int64)
     j = np.asarray(j, dtype=np.int64)
     rows = np.concatenate([i, j, np.arange(n, dtype=np.int64)])
     cols = np.concatenate([j, i, np.arange(n, dtype=np.int64)])
-    vals = np.concatenate([w, w, diag]).astype(np.float64)
-    key = rows * n + cols
-    order = np.argsort(key, kind="stable")
-    key = key[order]
-    vals = vals[order]
-    # merge duplicates (none expected from the generators, kept for safety)
-    uniq, start = np.unique(key, return_index=True)
-    vals = np.add.reduceat(vals, start) if len(uniq) != len(key) else vals
-    rows = (uniq // n).astype(np.int64)
-    cols = (uniq % n).astype(np.int32)
-    counts = np.bincount(rows, minlength=n).astype(np.int64)
-    rowptr = np.zeros(n + 1, dtype=np.int64)
-    np.cumsum(counts, out=rowptr[1:])
-    return rowptr, cols, np.ascontiguousarray(vals, dtype=np.float64)
+    # the diagonal is added with a tiny offset and removed again so that explicit
+    # zeros on the diagonal survive the duplicate summation
+    vals = np.concatenate([np.asarray(w, np.float64), np.asarray(w, np.float64),
+                           np.asarray(diag, np.float64) + 1.0])
+    M = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    M.sum_duplicates()
+    M.sort_indices()
+    rowptr = M.indptr.astype(np.int64)
+    colind = M.indices.astype(np.int32)
+    val = M.data.astype(np.float64)
+    # undo the +1 on the diagonal slots
+    rr = np.repeat(np.arange(n, dtype=np.int64), np.diff(rowptr))
+    dmask = rr == colind
+    val[dmask] -= 1.0
+    # restore exact diagonal values (the +1/-1 round trip may round)
+    val[dmask] = np.asarray(diag, np.float64)[rr[dmask]]
+    return rowptr, colind, np.ascontiguousarray(val)
 
 
 # ----------------------------------------------------------------------------- graphs
+
+def _sorted_unique(a: np.ndarray) -> np.ndarray:
+    """Sorted distinct values (sort + adjacent difference)."""
+    a = np.sort(a)
+    if len(a) == 0:
+        return a
+    keep = np.empty(len(a), dtype=bool)
+    keep[0] = True
+    np.not_equal(a[1:], a[:-1], out=keep[1:])
+    return a[keep]
+
 
 def _weights(rng, count: int, weights: str) -> np.ndarray:
     if weights == "unit":
@@ -104,20 +119,18 @@ def er_graph(n: int, n_edges: int, seed: int, weights: str = "unit"):
         raise ValueError("too many edges")
     rng = np.random.default_rng(seed)
     keys = np.empty(0, dtype=np.int64)
-    need = n_edges
-    while need > 0:
-        draw = int(need * 1.05) + 16
+    while len(keys) < n_edges:
+        draw = int((n_edges - len(keys)) * 1.02) + 64
         a = rng.integers(0, n, size=draw, dtype=np.int64)
         c = rng.integers(0, n, size=draw, dtype=np.int64)
         ok = a != c
         lo = np.minimum(a[ok], c[ok])
         hi = np.maximum(a[ok], c[ok])
-        keys = np.unique(np.concatenate([keys, lo * n + hi]))
-        if len(keys) > n_edges:
-            # keep a uniformly random subset of the distinct pairs
-            pick = rng.choice(len(keys), size=n_edges, replace=False)
-            keys = np.sort(keys[pick])
-        need = n_edges - len(keys)
+        keys = _sorted_unique(np.concatenate([keys, lo * n + hi]))
+    if len(keys) > n_edges:
+        # drop a uniformly random subset of the surplus distinct pairs
+        drop = rng.choice(len(keys), size=len(keys) - n_edges, replace=False)
+        keys = np.delete(keys, drop)
     i = (keys // n).astype(np.int64)
     j = (keys % n).astype(np.int64)
     return i, j, _weights(rng, len(i), weights)
@@ -133,7 +146,7 @@ def torus_graph(side: int, seed: int, weights: str = "pm1"):
     c = np.concatenate([right.ravel(), down.ravel()])
     lo = np.minimum(a, c)
     hi = np.maximum(a, c)
-    keys = np.unique(lo * (side * side) + hi)
+    keys = _sorted_unique(lo * (side * side) + hi)
     n = side * side
     i = keys // n
     j = keys % n
@@ -197,7 +210,7 @@ def mc_instance(n1: int, n2: int, rank: int, n_samples: int, seed: int) -> SDPIn
         flat = np.empty(0, dtype=np.int64)
         while len(flat) < n_samples:
             draw = rng.integers(0, total, size=int((n_samples - len(flat)) * 1.1) + 16)
-            flat = np.unique(np.concatenate([flat, draw]))
+            flat = _sorted_unique(np.concatenate([flat, draw]))
         flat = rng.permutation(flat)[:n_samples]
     flat = np.sort(flat)
     si = (flat // n2).astype(np.int64)
