@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Time to relative KKT 1e-5 of the GPU LoRADS solve on the MaxCut SDP of an
+Erdos-Renyi graph with n = 10^7 vertices (average degree 4, weights in {-1,+1},
+rank r = 24), plus the roofline of its dominant kernel.
+
+A step is one full solve (init + L-BFGS/ALM iterations to rel. KKT <= 1e-5)
+from the same seeded R0 with the problem already resident in HBM; `e2e`
+repeats it through the public C ABI from host buffers (upload of C, A, b and
+R0 inside the timed region, download of R and y at the end).
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (L-BFGS iterations of the n = 10^7 solve), scaled to a time to
+tolerance with the iteration count of the solve.
+
+Multi-GPU (torchrun): replicas only -- every rank solves its own copy of the
+workload (the single-instance path has no exchange step); value is the max
+over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "time to rel. KKT 1e-5 (MaxCut n=1e7); SpMM+A(RRᵀ) HBM GB/s vs 8 TB/s"
+WORKLOADS = {
+    "maxcut_er_1e7": dict(n=10_000_000, edges=20_000_000, weights="pm1", r=24, seed=0,
+                          desc="MaxCut SDP, Erdos-Renyi n=1e7, M=2e7 edges (avg degree 4), w in {-1,+1}, r=24"),
+    "maxcut_er_1e5": dict(n=100_000, edges=200_000, weights="pm1", r=17, seed=0,
+                          desc="MaxCut SDP, Erdos-Renyi n=1e5, M=2e5 edges (avg degree 4), w in {-1,+1}, r=17"),
+}
+# iterations to tolerance used to scale the reference arm's per-iteration time when no
+# GPU run of the same invocation provides it (measured on the GPU solve of maxcut_er_1e7)
+DEFAULT_ITERS_TO_TOL = {"maxcut_er_1e7": 3000, "maxcut_er_1e5": 2000}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", default="maxcut_er_1e7", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed", "fp32"])
+    ap.add_argument("--e2e-steps", type=int, default=None, help="end-to-end steps (default: --steps)")
+    ap.add_argument("--cpu-iters", type=int, default=2, help="oracle L-BFGS iterations per CPU sample")
+    ap.add_argument("--iters-to-tol", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-profile", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def build_instance(name):
+    import workloads as W
+    cfg = WORKLOADS[name]
+    t = time.perf_counter()
+    edges = W.er_graph(cfg["n"], cfg["edges"], cfg["seed"], cfg["weights"])
+    inst = W.maxcut_instance(cfg["n"], edges)
+    R0 = W.initial_factor(inst, cfg["r"], cfg["seed"] + 1)
+    return inst, R0, time.perf_counter() - t
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        loaded = [s for s, p in zip(sm, power) if p > 0.5 * max(power)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+def kernel_bytes(fam: str, n: int, ld: int, nnz: int, m: int, wR: int, wD: int, T: int) -> float:
+    """Algorithmic bytes of one launch (each operand read or written once)."""
+    nl = n * ld
+    row_meta = 4 + 8 + 8 + 8                      # dk, da, y, b per row
+    if fam == "k_spmm_c(CD,ls)":
+        return nnz * (4 + (8 if wD == 8 else 4)) + (n + 1) * 8 + nl * (2 * wD + wR) + n * row_meta
+    if fam == "k_spmm_c(CR,obj)":
+        return nnz * (4 + (8 if wR == 8 else 4)) + (n + 1) * 8 + nl * 2 * wR
+    if fam == "k_dir":
+        return nl * wD * (2 + 2 * T)
+    if fam == "k_update(step)":
+        return nl * (4 * wR + 6 * wD + 2 * (T - 1) * wD) + n * row_meta
+    if fam == "k_update(grad)":
+        return nl * (2 * wR + wD) + n * row_meta
+    if fam == "k_cons(yupd)":
+        return nl * wR + m * (4 + 4 + 8 + 4 + 8 + 8 + 8)
+    return float("nan")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted((ROOT / "paper_2407_15049_gb300" / "csrc").glob("*")):
+        h.update(f.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernels are unchanged."""
+    p = ROOT / "profiles" / "traffic.json"
+    if not p.exists():
+        return None
+    d = json.loads(p.read_text())
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("kernels", {}).get(kernel)
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(inst, R0, iters: int):
+    """Seconds per L-BFGS iteration of the FP64 oracle on the full instance."""
+    from oracle import lorads_oracle as O
+    P = O.Problem(inst)
+    t = time.perf_counter()
+    O.solve(P, R0, O.Params(max_outer=1, max_inner=iters, tol=1e-300))
+    return (time.perf_counter() - t) / iters
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    inst, R0, gen_s = build_instance(args.workload)
+    iters_to_tol = args.iters_to_tol or DEFAULT_ITERS_TO_TOL[args.workload]
+    for _ in range(args.warmup):
+        oracle_sample(inst, R0, 1)
+    per = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        per.append(oracle_sample(inst, R0, args.cpu_iters))
+    wall = time.perf_counter() - t0
+    s_iter = statistics.mean(per)
+    value = s_iter * iters_to_tol
+    cores = 1
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config(args),
+        "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.cpu_iters} L-BFGS iterations of the n=1e7 solve per step "
+                                   f"({s_iter:.2f} s/iteration), scaled by {iters_to_tol} iterations to tolerance"},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(args):
+    cfg = WORKLOADS[args.workload]
+    return {"workload": args.workload, "description": cfg["desc"], "n": cfg["n"], "m": cfg["n"],
+            "nnz_C": cfg["n"] + 2 * cfg["edges"], "rank": cfg["r"], "solver_precision": args.prec,
+            "start": "cold (seeded unit-norm Gaussian rows)", "tolerance": 1e-5,
+            "l2_policy": "inputs larger than L2 (R alone is 1.9 GB at FP64)",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+# ----------------------------------------------------------------------------- native
+
+def run_native(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_2407_15049_gb300 as L
+    from paper_2407_15049_gb300 import _native as N
+
+    L.load()
+    prec_code = {"fp64": L.LORADS_FP64, "mixed": L.LORADS_MIXED, "fp32": L.LORADS_FP32}[args.prec]
+    inst, R0, gen_s = build_instance(args.workload)
+    cfg = WORKLOADS[args.workload]
+    stream = torch.cuda.Stream()
+    params = L.default_params(prec=prec_code)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        t = time.perf_counter()
+        ctx = L.lorads_create(inst, params, stream=stream.cuda_stream)
+        create_s = time.perf_counter() - t
+        R0_dev = torch.as_tensor(R0, device="cuda")
+        results = []
+        for _ in range(args.warmup):
+            results.append(L.lorads_solve(ctx, R0_dev, on_device=True))
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            barrier()
+            ev0.record(stream)
+            timed = [L.lorads_solve(ctx, R0_dev, on_device=True) for _ in range(args.steps)]
+            ev1.record(stream)
+            barrier()
+        elapsed = ev0.elapsed_time(ev1) / 1e3
+        last = timed[-1]
+        launches = sum(r["kernel_launches"] for r in timed)
+        # per-kernel durations: one host-stepped solve with CUDA events around every launch
+        prof = {}
+        if not args.no_profile:
+            pctx = L.lorads_create(inst, L.default_params(prec=prec_code, verbose=2), stream=stream.cuda_stream)
+            pres = L.lorads_solve(pctx, R0_dev, on_device=True)
+            prof = L.lorads_kernel_times(pctx)
+            L.lorads_destroy(pctx)
+        L.lorads_destroy(ctx)
+        del R0_dev
+        # end to end through the C ABI from host buffers
+        e2e_steps = args.e2e_steps if args.e2e_steps is not None else args.steps
+        R0_pinned = torch.from_numpy(R0).pin_memory().numpy()
+        e2e_times = []
+        h2d = (inst.rowptr.nbytes + inst.colind.nbytes + inst.val.nbytes + inst.con.nbytes + inst.row.nbytes
+               + inst.col.nbytes + inst.aval.nbytes + inst.b.nbytes + R0.nbytes)
+        d2h = 0
+        for _ in range(e2e_steps):
+            barrier()
+            t = time.perf_counter()
+            c2 = L.lorads_create(inst, params, stream=stream.cuda_stream)
+            rr = L.lorads_solve(c2, R0_pinned)
+            Rh, yh = L.lorads_get_solution(c2, inst.n, inst.m)
+            L.lorads_destroy(c2)
+            barrier()
+            e2e_times.append(time.perf_counter() - t)
+            d2h = Rh.nbytes + yh.nbytes
+
+    per_step = elapsed / args.steps
+    if world > 1:
+        tt = torch.tensor([per_step, statistics.mean(e2e_times) if e2e_times else 0.0], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        per_step, e2e_mean = tt.tolist()
+    else:
+        e2e_mean = statistics.mean(e2e_times) if e2e_times else None
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel (largest total time in the profiled solve)
+    wR = 8 if args.prec in ("fp64", "mixed") else 4
+    wD = 8 if args.prec == "fp64" else 4
+    ld = N.padded_ld(cfg["r"])
+    peak, peak_kind = measured_peaks()
+    kernels = {}
+    for name, (ms, cnt) in prof.items():
+        b = kernel_bytes(name, inst.n, ld, inst.nnz, inst.m, wR, wD, params.lbfgs_mem)
+        kernels[name] = {"avg_ms": ms, "launches": cnt, "share": None,
+                         "algorithmic_bytes": None if math.isnan(b) else b,
+                         "GBps": None if math.isnan(b) else b / (ms * 1e-3) / 1e9}
+    tot = sum(v["avg_ms"] * v["launches"] for v in kernels.values()) or 1.0
+    for v in kernels.values():
+        v["share"] = v["avg_ms"] * v["launches"] / tot
+    roofline = None
+    hot = [k for k in kernels if kernels[k]["GBps"] is not None]
+    if hot:
+        dom = max(hot, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["launches"])
+        ach = kernels[dom]["GBps"]
+        tr = ncu_traffic(dom)
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "peak_kind": peak_kind,
+                    "traffic": None if tr is None else tr.get("dram_bytes_per_launch_scaled"),
+                    "algorithmic_bytes_per_launch": kernels[dom]["algorithmic_bytes"],
+                    "avg_launch_ms": kernels[dom]["avg_ms"]}
+        spmm = kernels.get("k_spmm_c(CD,ls)")
+        if spmm:
+            roofline["spmm"] = {"achieved": spmm["GBps"], "frac": spmm["GBps"] / peak,
+                                "frac_of_8TBps": spmm["GBps"] / 8000.0, "avg_launch_ms": spmm["avg_ms"]}
+    cpu = None
+    if not args.no_cpu_baseline:
+        s_iter = oracle_sample(inst, R0, args.cpu_iters)
+        iters = last["inner_iters"]
+        cpu = {"value": s_iter * iters, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_iters} L-BFGS iterations of the same n=1e7 solve ({s_iter:.2f} s/iteration, "
+                         f"numpy/scipy single thread), scaled by the {iters} iterations this solve needed"}
+    line = {
+        "metric": METRIC, "value": per_step, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f64+f32", "fp32": "f32"}[args.prec],
+        "data": "synthetic", "config": _config(args),
+        "e2e": {"value": e2e_mean, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
+        "solve": {k: last[k] for k in ("status_name", "primal_obj", "dual_obj", "err1", "err3", "rho", "rank",
+                                       "outer_iters", "inner_iters", "seconds")},
+        "sdp_value": -last["primal_obj"],
+        "kernels": kernels, "setup_s": {"generate": gen_s, "create": create_s},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,221 @@
+/*
+ * lorads.h - C ABI of the GB300 (sm_103a) LoRADS hot path.
+ *
+ * Problem (Eq. (1.1) of arXiv 2407.15049):
+ *     min <C, X>  s.t.  <A_k, X> = b_k (k = 0..m-1),  X positive semidefinite,
+ * solved through the Burer-Monteiro factorisation X = R R^T (Sec. 1, Sec. 2.1):
+ * an augmented-Lagrangian outer loop, the L-BFGS inner solver of Algorithm 1,
+ * the exact quartic line search of App. A.2 and the dynamic rank rule of
+ * App. A.1.
+ *
+ * Sign convention.  y is the standard dual multiplier (y = -lambda of the
+ * paper's Eq. (1.2)):
+ *     L_rho(R, y) = <C, RR^T> - y^T (A(RR^T) - b) + rho/2 ||A(RR^T) - b||^2,
+ *     grad_R L    = 2 (C - A*(y~)) R  with  y~ = y - rho (A(RR^T) - b),
+ * and the multiplier step of Sec. 2.1 is y <- y~.  The error measures of
+ * Sec. 4.1 (err1, err2, err3) are written with the dual slack C - A*(y).
+ *
+ * Constraint convention (single-entry constraints).  Constraint k is one
+ * triplet (i <= j, a):  <A_k, X> = a X_ii  (i == j)  or  2 a X_ij  (i < j).
+ * This covers the MaxCut SDP of Sec. 4.2 (X_ii = 1) and the matrix-completion
+ * SDP of Sec. 4.3.  Constraints with several triplets (general SDPs, Sec. 4.4)
+ * are rejected with LORADS_ERR_UNSUPPORTED.
+ *
+ * Layout.  Every n x r factor (R, D, U, V, outputs) is row-major with a
+ * leading dimension `ld` (elements): element (i, c) lives at p[i*ld + c].
+ * `ld` must be a multiple of 4 (at most 512), and every device pointer must be
+ * 16-byte aligned.  The kernels process all `ld` columns; the caller keeps
+ * columns r..ld-1 at zero (they stay zero: C*0 = 0), `r` is informational.
+ *
+ * Precision (argument `prec`): LORADS_FP64 - double in, double out;
+ * LORADS_FP32 - float in, float out (products in FP32, reductions in FP64);
+ * LORADS_BF16 - bfloat16 in, float out.  Scalars and multipliers are double.
+ *
+ * Streams and ownership.  lorads_create copies every host input to device
+ * memory owned by the context and allocates all scratch space; the caller may
+ * free its buffers when it returns.  All entry points run on the context's
+ * CUDA stream (the one given to lorads_create; NULL = legacy default stream).
+ * Entry points taking device pointers do not allocate; pointers stay owned by
+ * the caller and must stay valid until the stream has finished the call.
+ *
+ * Errors.  Every call returns a status; nothing throws or exits.  The message
+ * of the last failure is available from lorads_last_error (per context, not
+ * thread-safe).  A CUDA failure returns LORADS_ERR_CUDA; after a sticky CUDA
+ * error the context is unusable and should be destroyed.
+ */
+#ifndef LORADS_H
+#define LORADS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lorads_ctx lorads_ctx;
+
+typedef enum {
+    LORADS_OK = 0,
+    LORADS_ERR_INVALID_ARG = 1,   /* bad size, pointer, index, layout or non-finite value */
+    LORADS_ERR_NOT_SYMMETRIC = 2, /* C is not a symmetric CSR matrix */
+    LORADS_ERR_OOM = 3,           /* device or host allocation failed */
+    LORADS_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    LORADS_ERR_NUMERIC = 5,       /* NaN/Inf reached the iteration */
+    LORADS_ERR_MAXITER = 6,       /* max_outer reached before the tolerance */
+    LORADS_ERR_TIMEOUT = 7,       /* time_limit reached */
+    LORADS_ERR_UNSUPPORTED = 8    /* valid input outside what this library implements */
+} lorads_status;
+
+typedef enum {
+    LORADS_FP64 = 0,
+    LORADS_FP32 = 1,
+    LORADS_BF16 = 2,
+    LORADS_MIXED = 3,  /* solve only: double-float R and C*R, FP32 direction/gradient/history */
+    LORADS_DF64 = 4    /* solve only: double-float (hi, lo float pairs, ~48-bit) everywhere */
+} lorads_prec;
+
+/* Solver constants.  The paper fixes tol (Sec. 4.1), the time limit (Sec. 4.1)
+ * and the rank rule (App. A.1); the remaining values are this library's
+ * readings of what the paper leaves open. */
+typedef struct {
+    double  tol;               /* 1e-5: err1 (1+||b||_inf normalisation) and |err3| */
+    double  time_limit;        /* seconds, 1e4 */
+    int32_t lbfgs_mem;         /* T of Algorithm 1, 1..4 (default 4) */
+    int32_t max_inner;         /* K of Algorithm 1 per outer step (default 500) */
+    int32_t max_outer;         /* default 200 */
+    int32_t rank_update_threshold; /* outer steps in a row hitting max_inner before r grows (3) */
+    double  rho0;              /* <= 0: 1 / mean |C_ij| over the stored entries */
+    double  rho_growth;        /* 2 */
+    double  rho_max;           /* 1e12 */
+    double  infeas_decrease;   /* 0.25: rho grows unless err1 shrank by this factor */
+    double  inner_rel;         /* 1.0: inner stop ||G||_F <= inner_rel*max(s ||A(RR^T)-b||, tol(1+||b||_inf)), s = rho or 1 */
+    int32_t prec;              /* lorads_prec of the solve: FP64, MIXED, DF64 or FP32 */
+    int32_t check_every;       /* iterations between host polls of the device status (16) */
+    uint64_t seed;             /* seed of the rank-update columns (SplitMix64 + Box-Muller) */
+    int32_t compute_err2;      /* 1: evaluate err2 (Lanczos on C - A*(y)) at the end */
+    int32_t lanczos_steps;     /* Krylov dimension of that Lanczos run (default 200) */
+    int32_t verbose;           /* 1: progress line per outer step on stderr; 2: per-kernel CUDA-event timing */
+    int32_t lbfgs_scaling;     /* 0: initial matrix I (Algorithm 1 as printed); 1 (default): gamma I, gamma = <s,y>/<y,y> */
+    int32_t rho_policy;        /* 0: grow rho when err1 did not shrink enough; 1 (default): only after a converged inner loop */
+    int32_t inner_scale;       /* 0: inner stop against ||z||; 1 (default): against rho ||z|| (z = A(RR^T) - b) */
+    int32_t reserved;
+} lorads_params;
+
+typedef struct {
+    double  primal_obj;        /* <C, R R^T> */
+    double  dual_obj;          /* b^T y */
+    double  err1;              /* ||A(RR^T) - b||_2 / (1 + ||b||_inf) */
+    double  err2;              /* |min(0, sigma_min(C - A*(y)))| / (1 + ||vec C||_1), -1 if not evaluated */
+    double  err3;              /* (<C,X> - b^T y) / (1 + |<C,X>| + |b^T y|) */
+    double  sigma_min;         /* Lanczos estimate of sigma_min(C - A*(y)) */
+    double  rho;               /* final penalty */
+    double  seconds;           /* wall time of lorads_solve */
+    int32_t rank;              /* final r */
+    int32_t outer_iters;
+    int32_t inner_iters;       /* L-BFGS directions computed, all outer steps */
+    int32_t status;            /* lorads_status of the solve */
+    int64_t kernel_launches;   /* kernels this library launched during the solve (graph nodes included) */
+} lorads_result;
+
+/* Fills *p with the defaults listed above. */
+void lorads_default_params(lorads_params* p);
+
+/* Uploads the primal SDP of Eq. (1.1).
+ *   n                          order of X (>= 1)
+ *   c_rowptr[n+1], c_colind[nnz], c_val[nnz]   C as a full symmetric CSR matrix, host,
+ *                              rowptr[0] = 0, nondecreasing, column indices sorted and
+ *                              distinct within each row, values finite; C must equal C^T.
+ *   m                          number of constraints (>= 1)
+ *   nnz_a, a_con, a_row, a_col, a_val          constraint triplets, host; a_con in [0,m),
+ *                              a_row <= a_col < n, exactly one triplet per constraint and
+ *                              at most one constraint per entry (i, j).
+ *   b[m]                       right-hand side, host.
+ *   p                          parameters (NULL = defaults), copied.
+ *   cuda_stream                cudaStream_t the context uses (NULL = default stream).
+ * On success *out receives a new context (free with lorads_destroy).  On failure *out
+ * is NULL and the status says why (INVALID_ARG, NOT_SYMMETRIC, UNSUPPORTED, OOM, CUDA). */
+lorads_status lorads_create(lorads_ctx** out, int64_t n,
+                            const int64_t* c_rowptr, const int32_t* c_colind, const double* c_val,
+                            int64_t m, int64_t nnz_a,
+                            const int32_t* a_con, const int32_t* a_row, const int32_t* a_col,
+                            const double* a_val, const double* b,
+                            const lorads_params* p, void* cuda_stream);
+
+/* out = (C - A*(v)) R  (the sparse-times-tall-skinny product of the gradient, Sec. 2;
+ * Eq. (3.1) with the multiplier folded into the values of the fixed pattern).
+ *   R, out      device, n x ld (prec: FP64 double->double, FP32 float->float,
+ *               BF16 bf16->float); out must not alias R.
+ *   v           device double[m] or NULL (NULL: out = C R).
+ * Asynchronous on the context stream. */
+lorads_status lorads_spmm(lorads_ctx* ctx, const void* R, int32_t r, int32_t ld,
+                          const double* v, void* out, int32_t prec);
+
+/* out_k = <A_k, U V^T>  for k = 0..m-1 (the constraint map evaluated as one gathered
+ * row dot per constraint: Sec. 3.4's compressed outer product; diag(RR^T) for MaxCut).
+ *   U, V        device, n x ld, element type by prec (FP64, FP32 or BF16); may be equal.
+ *   out         device double[m].  Products in the element precision, sum in FP64
+ *               for FP64 and in FP32 otherwise, output FP64.
+ * Asynchronous on the context stream. */
+lorads_status lorads_constraint_eval(lorads_ctx* ctx, const void* U, const void* V,
+                                     int32_t r, int32_t ld, double* out, int32_t prec);
+
+/* Exact line search along D at R (App. A.2), lambda := y:
+ *   p1 = <C, RD^T + DR^T>, p2 = <C, DD^T>, q0 = b - A(RR^T), q1 = A(RD^T + DR^T), q2 = A(DD^T)
+ *   a1 = rho/2 ||q2||^2, a2 = rho q1^T q2, a3 = p2 - (y + rho q0)^T q2 + rho/2 ||q1||^2,
+ *   a4 = p1 - (y + rho q0)^T q1
+ * and tau* = the positive real root of 4a1 t^3 + 3a2 t^2 + 2a3 t + a4 with the lowest
+ * quartic value (0 if none lowers it).
+ *   R, D        device, n x ld, element type by prec (FP64, FP32 or BF16).
+ *   y           device double[m].
+ *   a_out[4]    host, receives a1..a4 (FP64 reductions).   tau_out: host, may be NULL.
+ * Synchronous: returns after the stream has produced the results. */
+lorads_status lorads_linesearch_coeffs(lorads_ctx* ctx, const void* R, const void* D,
+                                       int32_t r, int32_t ld, const double* y, double rho,
+                                       double* a_out, double* tau_out, int32_t prec);
+
+/* Runs the solver (Sec. 2.1 ALM + Algorithm 1 + App. A.1/A.2) from R0 and y0.
+ *   R0          n x r0 row-major (leading dimension r0), FP64; host if r0_on_device == 0,
+ *               device otherwise; NULL: rows drawn on the device (SplitMix64 normals,
+ *               unit rows for diagonal constraints) with r0 = ceil(log2 m) if r0 <= 0.
+ *   y0          host double[m] or NULL (zeros).
+ *   res         host, receives the result (also on failure, with res->status).
+ * The solution stays in the context (lorads_get_solution). Synchronous. */
+lorads_status lorads_solve(lorads_ctx* ctx, const double* R0, int32_t r0, int32_t r0_on_device,
+                           const double* y0, lorads_result* res);
+
+/* Copies the last solution to the host.  R_host (n x rank, leading dimension rank) and
+ * y_host (m) may be NULL; R_capacity is the number of doubles R_host can hold.
+ * *rank_out (may be NULL) receives the rank.  Synchronous. */
+lorads_status lorads_get_solution(lorads_ctx* ctx, double* R_host, int64_t R_capacity,
+                                  int32_t* rank_out, double* y_host);
+
+/* Message of the last failure on this context ("" if none).  Valid until the next call. */
+const char* lorads_last_error(const lorads_ctx* ctx);
+
+/* Message of the last lorads_create failure in this thread. */
+const char* lorads_create_error(void);
+
+/* Frees the context and everything it owns.  NULL-safe. */
+void lorads_destroy(lorads_ctx* ctx);
+
+/* Sizes of the uploaded problem: n, m, nnz(C), number of diagonal and off-diagonal
+ * constraints.  Any pointer may be NULL. */
+lorads_status lorads_problem_info(const lorads_ctx* ctx, int64_t* n, int64_t* m, int64_t* nnz_c,
+                                  int64_t* m_diag, int64_t* m_offdiag);
+
+/* Average duration (ms) of each kernel family launched by the last lorads_solve that ran
+ * with params.verbose >= 2.  That solve runs host-stepped (no CUDA graph, same kernels and
+ * decisions) with a CUDA event pair around every launch on the solve stream.  names/ms
+ * have `cap` entries (names are static strings); returns the number written, 0 when no
+ * profiled solve has run. */
+int32_t lorads_kernel_times(const lorads_ctx* ctx, const char** names, double* ms, int32_t cap);
+
+/* Launch counts of the same profiled solve, by kernel family (same order as
+ * lorads_kernel_times). */
+int32_t lorads_kernel_counts(const lorads_ctx* ctx, const char** names, int64_t* counts, int32_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LORADS_H */

@@ -1,0 +1,24 @@
+"""GB300 (sm_103a) LoRADS hot path: C-ABI CUDA library + thin Python binding.
+
+The compute path is ``liblorads.so`` (built by ``builder.py`` from ``csrc/``);
+``_native`` only marshals arguments.  Importing this package does not load the
+library; the first call does, and fails loudly when it is missing.
+"""
+from . import _native
+from ._native import (  # noqa: F401
+    LoradsError, default_params, lorads_create, lorads_destroy, lorads_spmm, lorads_constraint_eval,
+    lorads_linesearch_coeffs, lorads_solve, lorads_get_solution, lorads_problem_info, padded_ld,
+    lorads_kernel_times,
+    LORADS_FP64, LORADS_FP32, LORADS_BF16, LORADS_MIXED, LORADS_DF64, load, SIGNATURES,
+)
+
+__all__ = [
+    "LoradsError", "default_params", "lorads_create", "lorads_destroy", "lorads_spmm",
+    "lorads_constraint_eval", "lorads_linesearch_coeffs", "lorads_solve", "lorads_get_solution",
+    "lorads_problem_info", "padded_ld", "load", "build",
+]
+
+
+def build(verbose: bool = False):
+    from .builder import build as _b
+    return _b(verbose=verbose)

@@ -1,0 +1,248 @@
+"""ctypes binding of liblorads.so (include/lorads.h), argument marshalling only.
+
+Every numerical step runs in the CUDA library; this module converts torch
+tensors and numpy arrays to pointers and sizes and turns status codes into
+exceptions.  It raises at import of the library when ``liblorads.so`` has not
+been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+LIB_PATH = Path(os.environ.get("LORADS_LIB", _HERE / "liblorads.so"))
+
+LORADS_OK = 0
+STATUS_NAMES = {
+    0: "LORADS_OK", 1: "LORADS_ERR_INVALID_ARG", 2: "LORADS_ERR_NOT_SYMMETRIC", 3: "LORADS_ERR_OOM",
+    4: "LORADS_ERR_CUDA", 5: "LORADS_ERR_NUMERIC", 6: "LORADS_ERR_MAXITER", 7: "LORADS_ERR_TIMEOUT",
+    8: "LORADS_ERR_UNSUPPORTED",
+}
+LORADS_FP64, LORADS_FP32, LORADS_BF16, LORADS_MIXED, LORADS_DF64 = 0, 1, 2, 3, 4
+
+
+class LoradsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class lorads_params(C.Structure):
+    _fields_ = [
+        ("tol", C.c_double), ("time_limit", C.c_double), ("lbfgs_mem", C.c_int32),
+        ("max_inner", C.c_int32), ("max_outer", C.c_int32), ("rank_update_threshold", C.c_int32),
+        ("rho0", C.c_double), ("rho_growth", C.c_double), ("rho_max", C.c_double),
+        ("infeas_decrease", C.c_double), ("inner_rel", C.c_double), ("prec", C.c_int32),
+        ("check_every", C.c_int32), ("seed", C.c_uint64), ("compute_err2", C.c_int32),
+        ("lanczos_steps", C.c_int32), ("verbose", C.c_int32), ("lbfgs_scaling", C.c_int32),
+        ("rho_policy", C.c_int32), ("inner_scale", C.c_int32), ("reserved", C.c_int32),
+    ]
+
+
+class lorads_result(C.Structure):
+    _fields_ = [
+        ("primal_obj", C.c_double), ("dual_obj", C.c_double), ("err1", C.c_double),
+        ("err2", C.c_double), ("err3", C.c_double), ("sigma_min", C.c_double), ("rho", C.c_double),
+        ("seconds", C.c_double), ("rank", C.c_int32), ("outer_iters", C.c_int32),
+        ("inner_iters", C.c_int32), ("status", C.c_int32), ("kernel_launches", C.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_VP, _DP, _I64P, _I32P = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int32)
+
+# exported symbol -> (restype, argtypes)
+SIGNATURES = {
+    "lorads_default_params": (None, [C.POINTER(lorads_params)]),
+    "lorads_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int64, _I64P, _I32P, _DP, C.c_int64, C.c_int64,
+                                _I32P, _I32P, _I32P, _DP, _DP, C.POINTER(lorads_params), C.c_void_p]),
+    "lorads_spmm": (C.c_int, [_VP, _VP, C.c_int32, C.c_int32, _VP, _VP, C.c_int32]),
+    "lorads_constraint_eval": (C.c_int, [_VP, _VP, _VP, C.c_int32, C.c_int32, _VP, C.c_int32]),
+    "lorads_linesearch_coeffs": (C.c_int, [_VP, _VP, _VP, C.c_int32, C.c_int32, _VP, C.c_double, _DP, _DP,
+                                           C.c_int32]),
+    "lorads_solve": (C.c_int, [_VP, _VP, C.c_int32, C.c_int32, _VP, C.POINTER(lorads_result)]),
+    "lorads_get_solution": (C.c_int, [_VP, _DP, C.c_int64, _I32P, _DP]),
+    "lorads_last_error": (C.c_char_p, [_VP]),
+    "lorads_create_error": (C.c_char_p, []),
+    "lorads_destroy": (None, [_VP]),
+    "lorads_problem_info": (C.c_int, [_VP, _I64P, _I64P, _I64P, _I64P, _I64P]),
+    "lorads_kernel_times": (C.c_int32, [_VP, C.POINTER(C.c_char_p), _DP, C.c_int32]),
+    "lorads_kernel_counts": (C.c_int32, [_VP, C.POINTER(C.c_char_p), _I64P, C.c_int32]),
+}
+
+_lib = None
+
+
+def load(path: str | os.PathLike | None = None) -> C.CDLL:
+    """Loads liblorads.so (raises when it is missing: build it with builder.py)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = Path(path) if path else LIB_PATH
+    if not p.exists():
+        raise ImportError(f"{p} not found: build the CUDA library first "
+                          "(python paper_2407_15049_gb300/builder.py)")
+    lib = C.CDLL(str(p))
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def default_params(**overrides) -> lorads_params:
+    p = lorads_params()
+    load().lorads_default_params(C.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _check(ctx, status: int):
+    if status != LORADS_OK:
+        msg = load().lorads_last_error(ctx).decode() if ctx else ""
+        raise LoradsError(status, msg)
+
+
+def _dptr(t) -> int:
+    """Device address of a torch tensor (or an int address)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _prec_of(t) -> int:
+    import torch
+    if t.dtype == torch.float64:
+        return LORADS_FP64
+    if t.dtype == torch.float32:
+        return LORADS_FP32
+    if t.dtype == torch.bfloat16:
+        return LORADS_BF16
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def lorads_create(inst, params: lorads_params | None = None, stream: int | None = None) -> C.c_void_p:
+    """Uploads an SDP instance (object with n, rowptr, colind, val, m, con, row, col, aval, b)."""
+    lib = load()
+    rowptr = np.ascontiguousarray(inst.rowptr, dtype=np.int64)
+    colind = np.ascontiguousarray(inst.colind, dtype=np.int32)
+    val = np.ascontiguousarray(inst.val, dtype=np.float64)
+    con = np.ascontiguousarray(inst.con, dtype=np.int32)
+    row = np.ascontiguousarray(inst.row, dtype=np.int32)
+    col = np.ascontiguousarray(inst.col, dtype=np.int32)
+    aval = np.ascontiguousarray(inst.aval, dtype=np.float64)
+    b = np.ascontiguousarray(inst.b, dtype=np.float64)
+    ctx = C.c_void_p()
+    st = lib.lorads_create(C.byref(ctx), int(inst.n), _ptr(rowptr, C.c_int64), _ptr(colind, C.c_int32),
+                           _ptr(val, C.c_double), int(inst.m), int(len(con)), _ptr(con, C.c_int32),
+                           _ptr(row, C.c_int32), _ptr(col, C.c_int32), _ptr(aval, C.c_double),
+                           _ptr(b, C.c_double), C.byref(params) if params is not None else None,
+                           C.c_void_p(stream) if stream else None)
+    if st != LORADS_OK:
+        raise LoradsError(st, lib.lorads_create_error().decode())
+    return ctx
+
+
+def lorads_destroy(ctx) -> None:
+    if ctx:
+        load().lorads_destroy(ctx)
+
+
+def lorads_spmm(ctx, R, v, out, r: int | None = None) -> None:
+    """out = (C - A*(v)) R on device tensors (R, out: n x ld; v: float64[m] or None)."""
+    ld = R.shape[1]
+    _check(ctx, load().lorads_spmm(ctx, _dptr(R), int(r or ld), int(ld), _dptr(v), _dptr(out), _prec_of(R)))
+
+
+def lorads_constraint_eval(ctx, U, V, out, r: int | None = None) -> None:
+    """out_k = <A_k, U V^T> (out: float64[m] device tensor)."""
+    ld = U.shape[1]
+    _check(ctx, load().lorads_constraint_eval(ctx, _dptr(U), _dptr(V), int(r or ld), int(ld), _dptr(out),
+                                              _prec_of(U)))
+
+
+def lorads_linesearch_coeffs(ctx, R, D, y, rho: float, r: int | None = None):
+    """Returns (a[4] as numpy, tau)."""
+    ld = R.shape[1]
+    a = np.zeros(4)
+    tau = C.c_double()
+    _check(ctx, load().lorads_linesearch_coeffs(ctx, _dptr(R), _dptr(D), int(r or ld), int(ld), _dptr(y),
+                                                float(rho), _ptr(a, C.c_double), C.byref(tau), _prec_of(R)))
+    return a, tau.value
+
+
+def lorads_solve(ctx, R0=None, y0: np.ndarray | None = None, r0: int = 0, on_device: bool = False,
+                 raise_on_status: bool = False) -> dict:
+    """Runs the solver.  R0: host numpy (n x r0) or device float64 tensor, or None."""
+    lib = load()
+    res = lorads_result()
+    keep = []
+    if R0 is None:
+        rp, r0v, dev = None, int(r0), 0
+    elif on_device or not isinstance(R0, np.ndarray):
+        rp, r0v, dev = C.c_void_p(_dptr(R0)), int(R0.shape[1]), 1
+    else:
+        R0 = np.ascontiguousarray(R0, dtype=np.float64)
+        keep.append(R0)
+        rp, r0v, dev = C.c_void_p(R0.ctypes.data), int(R0.shape[1]), 0
+    yp = None
+    if y0 is not None:
+        y0 = np.ascontiguousarray(y0, dtype=np.float64)
+        keep.append(y0)
+        yp = C.c_void_p(y0.ctypes.data)
+    st = lib.lorads_solve(ctx, rp, r0v, dev, yp, C.byref(res))
+    out = res.as_dict()
+    out["status_name"] = STATUS_NAMES.get(res.status, str(res.status))
+    if st not in (LORADS_OK, 5, 6, 7) or (raise_on_status and st != LORADS_OK):
+        _check(ctx, st)
+    return out
+
+
+def lorads_get_solution(ctx, n: int, m: int):
+    """Returns (R as numpy n x rank, y as numpy m)."""
+    lib = load()
+    rank = C.c_int32()
+    _check(ctx, lib.lorads_get_solution(ctx, None, 0, C.byref(rank), None))
+    R = np.zeros((n, rank.value))
+    y = np.zeros(m)
+    _check(ctx, lib.lorads_get_solution(ctx, _ptr(R, C.c_double), R.size, C.byref(rank), _ptr(y, C.c_double)))
+    return R, y
+
+
+def lorads_problem_info(ctx) -> dict:
+    vals = [C.c_int64() for _ in range(5)]
+    _check(ctx, load().lorads_problem_info(ctx, *[C.byref(v) for v in vals]))
+    return dict(zip(["n", "m", "nnz_c", "m_diag", "m_offdiag"], [v.value for v in vals]))
+
+
+def lorads_kernel_times(ctx) -> dict:
+    """{kernel family: (average ms, launches)} of the last profiled (verbose >= 2) solve."""
+    lib = load()
+    names = (C.c_char_p * 32)()
+    ms = (C.c_double * 32)()
+    counts = (C.c_int64 * 32)()
+    k = lib.lorads_kernel_times(ctx, names, ms, 32)
+    lib.lorads_kernel_counts(ctx, names, counts, 32)
+    return {names[i].decode(): (ms[i], counts[i]) for i in range(k)}
+
+
+def padded_ld(r: int) -> int:
+    """Row width the kernels use for rank r (r rounded up to a multiple of 4)."""
+    return (int(r) + 3) // 4 * 4

@@ -1,0 +1,1120 @@
+// C ABI of the LoRADS GB300 library (include/lorads.h): input validation and
+// upload, the standalone hot-path entry points, and the device-resident solve
+// loop (one captured CUDA graph per L-BFGS iteration + ALM outer step, gated
+// by a device control block; the host only polls a status copy).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/lorads.h"
+#include "common.cuh"
+#include "control.h"
+#include "kernels.cuh"
+#include "launch_decl.h"
+
+using namespace lorads;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+enum { PART_DIR = 0, PART_LS, PART_CONS_LS, PART_UPD, PART_CONS, PART_OBJ, PART_YTIL, PART_MISC, NPART };
+constexpr int kPartStride = 32;         // doubles per block per region (>= every NQ)
+
+struct SolverState {
+    int prec = -1;
+    int r = 0, ld = 0;
+    Shape sh{1, 1};
+    size_t esR = 0, esD = 0;
+    int rtype = 0;                      // storage of R: 0 double, 1 double-float, 2 float
+    void* R = nullptr;
+    void* CR = nullptr;
+    void* D = nullptr;
+    void* CD = nullptr;
+    void* G = nullptr;
+    void* W = nullptr;
+    void* hist = nullptr;
+    int64_t slot_stride = 0;
+    double* y = nullptr;
+    double* ytil = nullptr;
+    double* zrow = nullptr;             // A(RR^T)_k - b_k of the diagonal constraint of each row
+    double* zk = nullptr;               // same for the off-diagonal constraints (by constraint)
+    cudaGraphExec_t exec = nullptr;
+    bool have_solution = false;
+};
+
+// Per-kernel-family CUDA-event timing of the host-stepped (verbose >= 2) solve.
+enum { FAM_DIR = 0, FAM_SPMM_LS, FAM_CONS_LS, FAM_ROOT, FAM_STEP, FAM_CONS_YTIL, FAM_SPMM_A, FAM_UPDATE, FAM_HIST,
+       FAM_CONS_YUPD, FAM_SPMM_CR, FAM_OUTER, FAM_GRAD, FAM_MISC, NFAM };
+const char* const kFamNames[NFAM] = {"k_dir", "k_spmm_c(CD,ls)", "k_cons(ls)", "k_ctrl_root", "k_step",
+                                     "k_cons(ytil)", "k_spmm_a", "k_update(step)", "k_ctrl_hist",
+                                     "k_cons(yupd)", "k_spmm_c(CR,obj)", "k_ctrl_outer", "k_update(grad)",
+                                     "setup"};
+struct Prof {
+    static constexpr int kPool = 64;
+    cudaEvent_t ev[kPool][2];
+    int fam[kPool];
+    int used = 0;
+    double total_ms[NFAM] = {0};
+    int64_t count[NFAM] = {0};
+};
+
+}  // namespace
+
+struct lorads_ctx {
+    int64_t n = 0, m = 0, nnz_c = 0, m_diag = 0, m_off = 0, nnz_aoff = 0;
+    cudaStream_t stream = nullptr;       // caller's stream (entry points)
+    cudaStream_t solve_stream = nullptr; // owned, capture-capable
+    cudaEvent_t ev_sync = nullptr;
+    cudaEvent_t ev_poll[2] = {nullptr, nullptr};
+    int device = 0, num_sms = 0, max_blocks = 0;
+    lorads_params prm{};
+    std::string err;
+    double bnorm_inf = 0, bnorm1 = 0, cnorm1 = 0, mean_abs_c = 1;
+    // device problem arrays
+    int64_t* c_rowptr = nullptr;
+    int32_t* c_col = nullptr;
+    double* c_val = nullptr;
+    float* c_val32 = nullptr;
+    dfloat* c_valdf = nullptr;
+    int32_t* dk = nullptr;
+    double* da = nullptr;
+    int64_t* a_rowptr = nullptr;
+    int32_t* a_col = nullptr;
+    int32_t* a_k = nullptr;
+    double* a_a = nullptr;
+    int32_t* k_row = nullptr;
+    int32_t* k_col = nullptr;
+    double* k_a = nullptr;
+    int32_t* k_id = nullptr;
+    double* b = nullptr;
+    ProbDev pd{};
+    // scratch
+    double* part = nullptr;
+    double* small = nullptr;            // 64 doubles of scratch results
+    double* h_small = nullptr;          // pinned mirror
+    Ctrl* ctrl = nullptr;
+    Ctrl* h_ctrl = nullptr;             // pinned, 2 slots
+    SolverState st;
+    Prof* prof = nullptr;
+    bool prof_valid = false;
+    bool prof_active = false;
+    int64_t launches = 0;          // kernels launched by the current solve
+    int64_t graph_nodes = 0;       // kernel nodes of the captured iteration graph
+};
+
+// ============================================================== helpers
+namespace {
+
+bool set_err(lorads_ctx* c, const std::string& msg) {
+    if (c) c->err = msg;
+    return false;
+}
+
+#define CK(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                 \
+            return LORADS_ERR_CUDA;                                                        \
+        }                                                                                  \
+    } while (0)
+
+template <typename T>
+lorads_status dalloc(lorads_ctx* ctx, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return LORADS_OK;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->err = std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) + " bytes: " +
+                   cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? LORADS_ERR_OOM : LORADS_ERR_CUDA;
+    }
+    return LORADS_OK;
+}
+
+template <typename T>
+lorads_status upload(lorads_ctx* ctx, T** p, const T* host, size_t count) {
+    lorads_status s = dalloc(ctx, p, count);
+    if (s != LORADS_OK || count == 0) return s;
+    CK(cudaMemcpy(*p, host, count * sizeof(T), cudaMemcpyHostToDevice));
+    return LORADS_OK;
+}
+
+void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+int row_blocks(const lorads_ctx* c, int64_t rows, int L) {
+    const int64_t per_block = kThreads / L;
+    int64_t b = (rows + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    return (int)std::min<int64_t>(b, c->max_blocks);
+}
+
+int flat_blocks(const lorads_ctx* c, int64_t items) {
+    int64_t b = (items + kThreads - 1) / kThreads;
+    if (b < 1) b = 1;
+    return (int)std::min<int64_t>(b, c->max_blocks);
+}
+
+double* part_of(const lorads_ctx* c, int region) {
+    return c->part + (size_t)region * c->max_blocks * kPartStride;
+}
+
+lorads_status check_launch(lorads_ctx* ctx, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+        return LORADS_ERR_CUDA;
+    }
+    return LORADS_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+size_t elem_size(int prec) {
+    switch (prec) {
+        case LORADS_FP64: return 8;
+        case LORADS_FP32: return 4;
+        case LORADS_BF16: return 2;
+        default: return 0;
+    }
+}
+
+lorads_status check_factor_args(lorads_ctx* ctx, int32_t r, int32_t ld, int prec, Shape* sh) {
+    if (elem_size(prec) == 0) return set_err(ctx, "prec must be LORADS_FP64, LORADS_FP32 or LORADS_BF16"), LORADS_ERR_INVALID_ARG;
+    if (r < 1 || ld < r) return set_err(ctx, "need 1 <= r <= ld"), LORADS_ERR_INVALID_ARG;
+    if (!shape_for_ld(ld, sh))
+        return set_err(ctx, "ld=" + std::to_string(ld) + " is not a supported row width (a multiple of 4, at most " +
+                                std::to_string(kMaxLd) + ")"),
+               LORADS_ERR_INVALID_ARG;
+    return LORADS_OK;
+}
+
+}  // namespace
+
+// ============================================================== params
+extern "C" void lorads_default_params(lorads_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->tol = 1e-5;
+    p->time_limit = 1e4;
+    p->lbfgs_mem = 4;
+    p->max_inner = 500;
+    p->max_outer = 200;
+    p->rank_update_threshold = 3;
+    p->rho0 = 0.0;
+    p->rho_growth = 2.0;
+    p->rho_max = 1e12;
+    p->infeas_decrease = 0.25;
+    p->inner_rel = 1.0;
+    p->prec = LORADS_FP64;
+    p->check_every = 16;
+    p->seed = 0;
+    p->compute_err2 = 0;
+    p->lanczos_steps = 200;
+    p->verbose = 0;
+    p->lbfgs_scaling = 1;
+    p->rho_policy = 1;
+    p->inner_scale = 1;
+}
+
+extern "C" const char* lorads_create_error(void) { return g_create_error.c_str(); }
+
+extern "C" const char* lorads_last_error(const lorads_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+// ============================================================== destroy
+namespace {
+void free_state(SolverState& st) {
+    if (st.exec) cudaGraphExecDestroy(st.exec);
+    dfree(st.R); dfree(st.CR); dfree(st.D); dfree(st.CD); dfree(st.G); dfree(st.W); dfree(st.hist);
+    dfree(st.y); dfree(st.ytil); dfree(st.zrow); dfree(st.zk);
+    st = SolverState();
+}
+}  // namespace
+
+extern "C" void lorads_destroy(lorads_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->solve_stream) cudaStreamSynchronize(ctx->solve_stream);
+    free_state(ctx->st);
+    dfree(ctx->c_rowptr); dfree(ctx->c_col); dfree(ctx->c_val); dfree(ctx->c_val32); dfree(ctx->c_valdf);
+    dfree(ctx->dk); dfree(ctx->da);
+    dfree(ctx->a_rowptr); dfree(ctx->a_col); dfree(ctx->a_k); dfree(ctx->a_a);
+    dfree(ctx->k_row); dfree(ctx->k_col); dfree(ctx->k_a); dfree(ctx->k_id); dfree(ctx->b);
+    dfree(ctx->part); dfree(ctx->small); dfree(ctx->ctrl);
+    if (ctx->h_small) cudaFreeHost(ctx->h_small);
+    if (ctx->h_ctrl) cudaFreeHost(ctx->h_ctrl);
+    if (ctx->ev_sync) cudaEventDestroy(ctx->ev_sync);
+    for (auto& e : ctx->ev_poll) if (e) cudaEventDestroy(e);
+    if (ctx->prof) {
+        for (int q = 0; q < Prof::kPool; ++q)
+            for (int e = 0; e < 2; ++e)
+                if (ctx->prof->ev[q][e]) cudaEventDestroy(ctx->prof->ev[q][e]);
+        delete ctx->prof;
+    }
+    if (ctx->solve_stream) cudaStreamDestroy(ctx->solve_stream);
+    delete ctx;
+}
+
+// ============================================================== create
+namespace {
+
+lorads_status validate_and_build(lorads_ctx* ctx, int64_t n, const int64_t* rp, const int32_t* ci,
+                                 const double* cv, int64_t m, int64_t nnz_a, const int32_t* acon,
+                                 const int32_t* arow, const int32_t* acol, const double* aval,
+                                 const double* b) {
+    if (n < 1 || n > INT32_MAX) return set_err(ctx, "n must be in [1, 2^31)"), LORADS_ERR_INVALID_ARG;
+    if (m < 1 || m > INT32_MAX) return set_err(ctx, "m must be in [1, 2^31)"), LORADS_ERR_INVALID_ARG;
+    if (!rp || !ci || !cv || !acon || !arow || !acol || !aval || !b)
+        return set_err(ctx, "null input pointer"), LORADS_ERR_INVALID_ARG;
+    if (rp[0] != 0) return set_err(ctx, "c_rowptr[0] must be 0"), LORADS_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < n; ++i)
+        if (rp[i + 1] < rp[i]) return set_err(ctx, "c_rowptr must be nondecreasing"), LORADS_ERR_INVALID_ARG;
+    const int64_t nnz = rp[n];
+    double sum_abs = 0.0;
+    int64_t cnt_nz = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t s = rp[i]; s < rp[i + 1]; ++s) {
+            const int32_t j = ci[s];
+            if (j < 0 || j >= n) return set_err(ctx, "C column index out of range at row " + std::to_string(i)), LORADS_ERR_INVALID_ARG;
+            if (s > rp[i] && ci[s - 1] >= j)
+                return set_err(ctx, "C column indices must be sorted and distinct within row " + std::to_string(i)),
+                       LORADS_ERR_INVALID_ARG;
+            if (!std::isfinite(cv[s])) return set_err(ctx, "non-finite value in C"), LORADS_ERR_INVALID_ARG;
+            if (cv[s] != 0.0) { sum_abs += std::fabs(cv[s]); ++cnt_nz; }
+        }
+    }
+    // symmetry: (i, j, v) needs (j, i, v)
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t s = rp[i]; s < rp[i + 1]; ++s) {
+            const int32_t j = ci[s];
+            const int32_t* lo = ci + rp[j];
+            const int32_t* hi = ci + rp[j + 1];
+            const int32_t* f = std::lower_bound(lo, hi, (int32_t)i);
+            if (f == hi || *f != i || cv[f - ci] != cv[s])
+                return set_err(ctx, "C is not symmetric at (" + std::to_string(i) + "," + std::to_string(j) + ")"),
+                       LORADS_ERR_NOT_SYMMETRIC;
+        }
+    }
+    ctx->cnorm1 = sum_abs;
+    ctx->mean_abs_c = cnt_nz ? sum_abs / (double)cnt_nz : 1.0;
+    // constraints
+    if (nnz_a != m)
+        return set_err(ctx, "every constraint must be a single triplet (nnz_a == m); constraints with several "
+                            "entries are not supported"),
+               LORADS_ERR_UNSUPPORTED;
+    std::vector<int32_t> seen(m, 0);
+    std::vector<int32_t> trip_of(m, -1);
+    for (int64_t t = 0; t < nnz_a; ++t) {
+        const int32_t k = acon[t], i = arow[t], j = acol[t];
+        if (k < 0 || k >= m) return set_err(ctx, "a_con out of range"), LORADS_ERR_INVALID_ARG;
+        if (i < 0 || j < 0 || i >= n || j >= n || i > j)
+            return set_err(ctx, "constraint triplet needs 0 <= a_row <= a_col < n"), LORADS_ERR_INVALID_ARG;
+        if (!std::isfinite(aval[t]) || aval[t] == 0.0)
+            return set_err(ctx, "constraint coefficient must be finite and nonzero"), LORADS_ERR_INVALID_ARG;
+        if (seen[k]++) return set_err(ctx, "constraint with several triplets"), LORADS_ERR_UNSUPPORTED;
+        trip_of[k] = (int32_t)t;
+    }
+    double bmax = 0.0, b1 = 0.0;
+    for (int64_t k = 0; k < m; ++k) {
+        if (!std::isfinite(b[k])) return set_err(ctx, "non-finite b"), LORADS_ERR_INVALID_ARG;
+        bmax = std::max(bmax, std::fabs(b[k]));
+        b1 += std::fabs(b[k]);
+    }
+    ctx->bnorm_inf = bmax;
+    ctx->bnorm1 = b1;
+    // diagonal constraints by row
+    std::vector<int32_t> dk(n, -1);
+    std::vector<double> da(n, 0.0);
+    int64_t m_diag = 0;
+    std::vector<int64_t> offkeys;
+    for (int64_t k = 0; k < m; ++k) {
+        const int32_t t = trip_of[k];
+        const int32_t i = arow[t], j = acol[t];
+        if (i == j) {
+            if (dk[i] >= 0) return set_err(ctx, "two constraints on the same diagonal entry"), LORADS_ERR_UNSUPPORTED;
+            dk[i] = (int32_t)k;
+            da[i] = aval[t];
+            ++m_diag;
+        }
+    }
+    const int64_t m_off = m - m_diag;
+    // ordered constraint list: diagonal constraints by row, then off-diagonal by (row, col)
+    std::vector<int32_t> order;
+    order.reserve(m);
+    for (int64_t i = 0; i < n; ++i)
+        if (dk[i] >= 0) order.push_back(dk[i]);
+    {
+        std::vector<std::pair<int64_t, int32_t>> off;
+        off.reserve(m_off);
+        for (int64_t k = 0; k < m; ++k) {
+            const int32_t t = trip_of[k];
+            if (arow[t] != acol[t]) off.emplace_back((int64_t)arow[t] * n + acol[t], (int32_t)k);
+        }
+        std::sort(off.begin(), off.end());
+        for (size_t q = 1; q < off.size(); ++q)
+            if (off[q].first == off[q - 1].first)
+                return set_err(ctx, "two constraints on the same off-diagonal entry"), LORADS_ERR_UNSUPPORTED;
+        for (auto& pr : off) order.push_back(pr.second);
+    }
+    std::vector<int32_t> k_row(m), k_col(m), k_id(m);
+    std::vector<double> k_a(m);
+    for (int64_t q = 0; q < m; ++q) {
+        const int32_t k = order[q];
+        const int32_t t = trip_of[k];
+        k_row[q] = arow[t];
+        k_col[q] = acol[t];
+        k_a[q] = aval[t];
+        k_id[q] = k;
+    }
+    // off-diagonal constraint pattern (symmetric, sorted by column within a row)
+    std::vector<int64_t> a_rp(n + 1, 0);
+    std::vector<int32_t> a_col, a_k;
+    std::vector<double> a_a;
+    if (m_off > 0) {
+        for (int64_t q = m_diag; q < m; ++q) {
+            a_rp[k_row[q] + 1]++;
+            a_rp[k_col[q] + 1]++;
+        }
+        for (int64_t i = 0; i < n; ++i) a_rp[i + 1] += a_rp[i];
+        const int64_t nz = a_rp[n];
+        a_col.resize(nz);
+        a_k.resize(nz);
+        a_a.resize(nz);
+        std::vector<int64_t> fill(a_rp.begin(), a_rp.end() - 1);
+        for (int64_t q = m_diag; q < m; ++q) {
+            const int32_t i = k_row[q], j = k_col[q];
+            int64_t s = fill[i]++;
+            a_col[s] = j; a_k[s] = k_id[q]; a_a[s] = k_a[q];
+            s = fill[j]++;
+            a_col[s] = i; a_k[s] = k_id[q]; a_a[s] = k_a[q];
+        }
+        // sort each row by column
+        std::vector<int64_t> idx;
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t s0 = a_rp[i], s1 = a_rp[i + 1];
+            if (s1 - s0 < 2) continue;
+            idx.resize(s1 - s0);
+            for (int64_t q = 0; q < s1 - s0; ++q) idx[q] = s0 + q;
+            std::sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return a_col[x] < a_col[y]; });
+            std::vector<int32_t> tc(s1 - s0), tk(s1 - s0);
+            std::vector<double> ta(s1 - s0);
+            for (int64_t q = 0; q < s1 - s0; ++q) { tc[q] = a_col[idx[q]]; tk[q] = a_k[idx[q]]; ta[q] = a_a[idx[q]]; }
+            for (int64_t q = 0; q < s1 - s0; ++q) { a_col[s0 + q] = tc[q]; a_k[s0 + q] = tk[q]; a_a[s0 + q] = ta[q]; }
+        }
+        ctx->nnz_aoff = nz;
+    }
+    ctx->n = n; ctx->m = m; ctx->nnz_c = nnz; ctx->m_diag = m_diag; ctx->m_off = m_off;
+    // device (queried only once the host-side checks have passed)
+    cudaError_t ce = cudaGetDevice(&ctx->device);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        ctx->err = std::string("CUDA device query: ") + cudaGetErrorString(ce);
+        return LORADS_ERR_CUDA;
+    }
+    ctx->max_blocks = ctx->num_sms * 8;
+    // upload
+    lorads_status s;
+    std::vector<float> cv32(cv, cv + nnz);
+    std::vector<dfloat> cvdf(nnz);
+    for (int64_t q = 0; q < nnz; ++q) {
+        const float h = (float)cv[q];
+        cvdf[q] = dfloat(h, (float)(cv[q] - (double)h));
+    }
+    if ((s = upload(ctx, &ctx->c_rowptr, rp, n + 1))) return s;
+    if ((s = upload(ctx, &ctx->c_col, ci, nnz))) return s;
+    if ((s = upload(ctx, &ctx->c_val, cv, nnz))) return s;
+    if ((s = upload(ctx, &ctx->c_val32, cv32.data(), nnz))) return s;
+    if ((s = upload(ctx, &ctx->c_valdf, cvdf.data(), nnz))) return s;
+    if (m_diag > 0) {
+        if ((s = upload(ctx, &ctx->dk, dk.data(), n))) return s;
+        if ((s = upload(ctx, &ctx->da, da.data(), n))) return s;
+    }
+    if (m_off > 0) {
+        if ((s = upload(ctx, &ctx->a_rowptr, a_rp.data(), n + 1))) return s;
+        if ((s = upload(ctx, &ctx->a_col, a_col.data(), a_col.size()))) return s;
+        if ((s = upload(ctx, &ctx->a_k, a_k.data(), a_k.size()))) return s;
+        if ((s = upload(ctx, &ctx->a_a, a_a.data(), a_a.size()))) return s;
+    }
+    if ((s = upload(ctx, &ctx->k_row, k_row.data(), m))) return s;
+    if ((s = upload(ctx, &ctx->k_col, k_col.data(), m))) return s;
+    if ((s = upload(ctx, &ctx->k_a, k_a.data(), m))) return s;
+    if ((s = upload(ctx, &ctx->k_id, k_id.data(), m))) return s;
+    if ((s = upload(ctx, &ctx->b, b, m))) return s;
+    ProbDev& p = ctx->pd;
+    p.n = n; p.m = m;
+    p.c_rowptr = ctx->c_rowptr; p.c_col = ctx->c_col; p.c_val = ctx->c_val; p.c_val32 = ctx->c_val32;
+    p.c_valdf = ctx->c_valdf;
+    p.dk = ctx->dk; p.da = ctx->da;
+    p.a_rowptr = ctx->a_rowptr; p.a_col = ctx->a_col; p.a_k = ctx->a_k; p.a_a = ctx->a_a;
+    p.k_row = ctx->k_row; p.k_col = ctx->k_col; p.k_a = ctx->k_a; p.k_id = ctx->k_id;
+    p.m_diag = m_diag; p.m_off = m_off;
+    p.b = ctx->b;
+    return LORADS_OK;
+}
+
+}  // namespace
+
+extern "C" lorads_status lorads_create(lorads_ctx** out, int64_t n, const int64_t* c_rowptr,
+                                       const int32_t* c_colind, const double* c_val, int64_t m, int64_t nnz_a,
+                                       const int32_t* a_con, const int32_t* a_row, const int32_t* a_col,
+                                       const double* a_val, const double* b, const lorads_params* p,
+                                       void* cuda_stream) {
+    g_create_error.clear();
+    if (!out) {
+        g_create_error = "out is NULL";
+        return LORADS_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    lorads_ctx* ctx = new (std::nothrow) lorads_ctx();
+    if (!ctx) {
+        g_create_error = "host allocation failed";
+        return LORADS_ERR_OOM;
+    }
+    lorads_default_params(&ctx->prm);
+    if (p) ctx->prm = *p;
+    if (ctx->prm.lbfgs_mem < 1 || ctx->prm.lbfgs_mem > kMaxMem) {
+        g_create_error = "lbfgs_mem must be in [1, 4]";
+        delete ctx;
+        return LORADS_ERR_INVALID_ARG;
+    }
+    if (ctx->prm.check_every < 1) ctx->prm.check_every = 1;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    lorads_status s = validate_and_build(ctx, n, c_rowptr, c_colind, c_val, m, nnz_a, a_con, a_row, a_col, a_val, b);
+    if (s == LORADS_OK) s = dalloc(ctx, &ctx->part, (size_t)NPART * ctx->max_blocks * kPartStride);
+    if (s == LORADS_OK) s = dalloc(ctx, &ctx->small, 64);
+    if (s == LORADS_OK) s = dalloc(ctx, &ctx->ctrl, 1);
+    if (s == LORADS_OK) {
+        if (cudaMallocHost(&ctx->h_small, 64 * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost(&ctx->h_ctrl, 2 * sizeof(Ctrl)) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&ctx->solve_stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_sync, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_poll[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_poll[1], cudaEventDisableTiming) != cudaSuccess) {
+            ctx->err = "pinned memory / stream / event creation failed";
+            s = LORADS_ERR_CUDA;
+        }
+    }
+    if (s != LORADS_OK) {
+        g_create_error = ctx->err;
+        if (s == LORADS_ERR_INVALID_ARG || s == LORADS_ERR_NOT_SYMMETRIC || s == LORADS_ERR_UNSUPPORTED) {
+            delete ctx;          // nothing was allocated on the device
+        } else {
+            lorads_destroy(ctx);
+        }
+        return s;
+    }
+    *out = ctx;
+    return LORADS_OK;
+}
+
+extern "C" lorads_status lorads_problem_info(const lorads_ctx* ctx, int64_t* n, int64_t* m, int64_t* nnz_c,
+                                             int64_t* m_diag, int64_t* m_offdiag) {
+    if (!ctx) return LORADS_ERR_INVALID_ARG;
+    if (n) *n = ctx->n;
+    if (m) *m = ctx->m;
+    if (nnz_c) *nnz_c = ctx->nnz_c;
+    if (m_diag) *m_diag = ctx->m_diag;
+    if (m_offdiag) *m_offdiag = ctx->m_off;
+    return LORADS_OK;
+}
+
+// ============================================================== standalone entry points
+extern "C" lorads_status lorads_spmm(lorads_ctx* ctx, const void* R, int32_t r, int32_t ld, const double* v,
+                                     void* out, int32_t prec) {
+    if (!ctx) return LORADS_ERR_INVALID_ARG;
+    Shape sh;
+    lorads_status s = check_factor_args(ctx, r, ld, prec, &sh);
+    if (s) return s;
+    if (!R || !out || !aligned16(R) || !aligned16(out)) return set_err(ctx, "R and out must be 16-byte aligned device pointers"), LORADS_ERR_INVALID_ARG;
+    if (R == out) return set_err(ctx, "out must not alias R"), LORADS_ERR_INVALID_ARG;
+    const int nb = row_blocks(ctx, ctx->n, sh.L);
+    SpmmCArgs a{ctx->pd, R, out, ld, sh, v, 1, EPI_NONE, nullptr, nullptr, nullptr, nullptr, 0.0, nullptr,
+                nb, nullptr, PH_ALWAYS, ctx->stream};
+    SpmmAArgs aa{ctx->pd, R, out, ld, sh, v, -1.0, 1, nb, nullptr, PH_ALWAYS, ctx->stream};
+    switch (prec) {
+        case LORADS_FP64:
+            launch_spmm_c<double, double, double>(a);
+            if (v && ctx->m_off) launch_spmm_a<double, double>(aa);
+            break;
+        case LORADS_FP32:
+            launch_spmm_c<float, float, float>(a);
+            if (v && ctx->m_off) launch_spmm_a<float, float>(aa);
+            break;
+        default:
+            launch_spmm_c<bf16, float, bf16>(a);
+            if (v && ctx->m_off) launch_spmm_a<bf16, float>(aa);
+            break;
+    }
+    return check_launch(ctx, "lorads_spmm launch");
+}
+
+extern "C" lorads_status lorads_constraint_eval(lorads_ctx* ctx, const void* U, const void* V, int32_t r,
+                                                int32_t ld, double* out, int32_t prec) {
+    if (!ctx) return LORADS_ERR_INVALID_ARG;
+    Shape sh;
+    lorads_status s = check_factor_args(ctx, r, ld, prec, &sh);
+    if (s) return s;
+    if (!U || !V || !out || !aligned16(U) || !aligned16(V))
+        return set_err(ctx, "U, V must be 16-byte aligned device pointers and out non-NULL"), LORADS_ERR_INVALID_ARG;
+    ConsArgs a{ctx->pd, CONS_EVAL, 0, ctx->m, U, V, ld, sh, nullptr, out, nullptr, nullptr, 0.0, nullptr,
+               row_blocks(ctx, ctx->m, sh.L), nullptr, PH_ALWAYS, ctx->stream};
+    switch (prec) {
+        case LORADS_FP64: launch_cons<double, double>(a); break;
+        case LORADS_FP32: launch_cons<float, float>(a); break;
+        default: launch_cons<bf16, bf16>(a); break;
+    }
+    return check_launch(ctx, "lorads_constraint_eval launch");
+}
+
+extern "C" lorads_status lorads_linesearch_coeffs(lorads_ctx* ctx, const void* R, const void* D, int32_t r,
+                                                  int32_t ld, const double* y, double rho, double* a_out,
+                                                  double* tau_out, int32_t prec) {
+    if (!ctx) return LORADS_ERR_INVALID_ARG;
+    Shape sh;
+    lorads_status s = check_factor_args(ctx, r, ld, prec, &sh);
+    if (s) return s;
+    if (!R || !D || !y || !a_out || !aligned16(R) || !aligned16(D))
+        return set_err(ctx, "R, D, y must be device pointers (R, D 16-byte aligned) and a_out non-NULL"),
+               LORADS_ERR_INVALID_ARG;
+    if (!std::isfinite(rho) || rho < 0) return set_err(ctx, "rho must be finite and >= 0"), LORADS_ERR_INVALID_ARG;
+    const int nb = row_blocks(ctx, ctx->n, sh.L);
+    const int nbc = row_blocks(ctx, std::max<int64_t>(ctx->m_off, 1), sh.L);
+    double* pl = part_of(ctx, PART_LS);
+    double* pc = part_of(ctx, PART_CONS_LS);
+    SpmmCArgs a{ctx->pd, D, nullptr, ld, sh, nullptr, 0, EPI_LS, R, y, nullptr, nullptr, rho, pl,
+                nb, nullptr, PH_ALWAYS, ctx->stream};
+    ConsArgs ca{ctx->pd, CONS_LS, ctx->m_diag, ctx->m, R, D, ld, sh, const_cast<double*>(y), nullptr, nullptr, nullptr, rho,
+                pc, nbc, nullptr, PH_ALWAYS, ctx->stream};
+    switch (prec) {
+        case LORADS_FP64:
+            launch_spmm_c<double, double, double>(a);
+            launch_cons<double, double>(ca);
+            break;
+        case LORADS_FP32:
+            launch_spmm_c<float, float, float>(a);
+            launch_cons<float, float>(ca);
+            break;
+        default:
+            launch_spmm_c<bf16, float, bf16>(a);
+            launch_cons<bf16, bf16>(ca);
+            break;
+    }
+    ls_finish(ctx->stream, pl, nb, ctx->m_off ? pc : nullptr, nbc, rho, ctx->small);
+    if ((s = check_launch(ctx, "lorads_linesearch_coeffs launch"))) return s;
+    CK(cudaMemcpyAsync(ctx->h_small, ctx->small, 5 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int q = 0; q < 4; ++q) a_out[q] = ctx->h_small[q];
+    if (tau_out) *tau_out = ctx->h_small[4];
+    return LORADS_OK;
+}
+
+// ============================================================== solver
+namespace {
+
+template <typename TR, typename TD>
+struct Driver {
+    lorads_ctx* c;
+    SolverState& st;
+    cudaStream_t s;
+    int nb_rows, nb_flat, nb_off, nb_all;
+    int64_t nunits;
+
+    Driver(lorads_ctx* ctx) : c(ctx), st(ctx->st), s(ctx->solve_stream) { refresh(); }
+
+    void refresh() {
+        nb_rows = row_blocks(c, c->n, st.sh.L);
+        nunits = c->n * (int64_t)st.ld / 4;
+        nb_flat = flat_blocks(c, nunits);
+        nb_off = row_blocks(c, std::max<int64_t>(c->m_off, 1), st.sh.L);
+        nb_all = row_blocks(c, c->m, st.sh.L);
+    }
+
+    const ProbDev& p() const { return c->pd; }
+
+    // Launch with an event pair around it when profiling.
+    template <class F>
+    void timed(int fam, F&& launch) {
+        c->launches += 1;
+        Prof* pf = c->prof;
+        if (pf && pf->used < Prof::kPool) {
+            const int q = pf->used++;
+            pf->fam[q] = fam;
+            cudaEventRecord(pf->ev[q][0], s);
+            launch();
+            cudaEventRecord(pf->ev[q][1], s);
+        } else {
+            launch();
+        }
+    }
+
+    // G = grad L at the current R (outer tail and start): [y~, W], update, reset
+    void outer_gradient(int ph) {
+        if (c->m_off) {
+            ConsArgs yt{p(), CONS_YTIL, c->m_diag, c->m, st.R, st.R, st.ld, st.sh, st.y, st.ytil, st.zk, c->ctrl, 0.0,
+                        part_of(c, PART_YTIL), nb_off, c->ctrl, ph, s};
+            timed(FAM_CONS_YTIL, [&] { launch_cons<TR, TR>(yt); });
+            SpmmAArgs w{p(), st.R, st.W, st.ld, st.sh, st.ytil, 1.0, 0, nb_rows, c->ctrl, ph, s};
+            timed(FAM_SPMM_A, [&] { launch_spmm_a<TR, TD>(w); });
+        }
+        UpdateArgs u{p(), false, false, st.R, st.CR, st.D, st.CD, st.G, c->m_off ? st.W : nullptr, st.hist,
+                     st.slot_stride, st.ld, st.sh, st.y, st.zrow, c->ctrl, part_of(c, PART_UPD), nb_rows, c->ctrl, ph, s};
+        timed(FAM_GRAD, [&] { launch_update<TR, TD>(u); });
+        timed(FAM_HIST, [&] {
+            ctrl_hist(s, c->ctrl, HIST_RESET, part_of(c, PART_UPD), nb_rows,
+                      c->m_off ? part_of(c, PART_YTIL) : nullptr, nb_off);
+        });
+    }
+
+    void spmm_CR(int ph) {
+        SpmmCArgs a{p(), st.R, st.CR, st.ld, st.sh, nullptr, 1, EPI_OBJ, st.R, st.y, nullptr, c->ctrl, 0.0,
+                    part_of(c, PART_OBJ), nb_rows, c->ctrl, ph, s};
+        timed(FAM_SPMM_CR, [&] { launch_spmm_c<TR, TR, TR>(a); });
+    }
+
+    void enqueue_init() {
+        spmm_CR(PH_ALWAYS);
+        ConsArgs zz{p(), CONS_ZZ, 0, c->m, st.R, st.R, st.ld, st.sh, st.y, nullptr, nullptr, c->ctrl, 0.0,
+                    part_of(c, PART_CONS), nb_all, c->ctrl, PH_ALWAYS, s};
+        timed(FAM_MISC, [&] { launch_cons<TR, TR>(zz); });
+        timed(FAM_MISC, [&] { ctrl_init(s, c->ctrl, part_of(c, PART_CONS), nb_all, part_of(c, PART_OBJ), nb_rows); });
+        outer_gradient(PH_OUTER);
+    }
+
+    void enqueue_resume() {
+        timed(FAM_MISC, [&] { ctrl_resume(s, c->ctrl); });
+        spmm_CR(PH_OUTER);
+        outer_gradient(PH_OUTER);
+    }
+
+    void enqueue_inner() {
+        DirArgs d{nunits, st.G, st.D, st.hist, st.slot_stride, c->ctrl, part_of(c, PART_DIR), nb_flat, c->ctrl,
+                  PH_INNER, s};
+        timed(FAM_DIR, [&] { launch_dir<TD>(d); });
+        SpmmCArgs ls{p(), st.D, st.CD, st.ld, st.sh, nullptr, 1, EPI_LS, st.R, st.y, st.zrow, c->ctrl, 0.0,
+                     part_of(c, PART_LS), nb_rows, c->ctrl, PH_INNER, s};
+        timed(FAM_SPMM_LS, [&] { launch_spmm_c<TD, TD, TR>(ls); });
+        if (c->m_off) {
+            ConsArgs cl{p(), CONS_LS, c->m_diag, c->m, st.R, st.D, st.ld, st.sh, st.y, nullptr, st.zk, c->ctrl, 0.0,
+                        part_of(c, PART_CONS_LS), nb_off, c->ctrl, PH_INNER, s};
+            timed(FAM_CONS_LS, [&] { launch_cons<TR, TD>(cl); });
+        }
+        timed(FAM_ROOT, [&] {
+            ctrl_root(s, c->ctrl, part_of(c, PART_DIR), nb_flat, part_of(c, PART_LS), nb_rows,
+                      c->m_off ? part_of(c, PART_CONS_LS) : nullptr, nb_off);
+        });
+        if (c->m_off) {
+            StepArgs sa{nunits, st.R, st.CR, st.D, st.CD, c->ctrl, nb_flat, c->ctrl, PH_STEP, s};
+            timed(FAM_STEP, [&] { launch_step<TR, TD>(sa); });
+            ConsArgs yt{p(), CONS_YTIL, c->m_diag, c->m, st.R, st.R, st.ld, st.sh, st.y, st.ytil, st.zk, c->ctrl, 0.0,
+                        part_of(c, PART_YTIL), nb_off, c->ctrl, PH_STEP, s};
+            timed(FAM_CONS_YTIL, [&] { launch_cons<TR, TR>(yt); });
+            SpmmAArgs w{p(), st.R, st.W, st.ld, st.sh, st.ytil, 1.0, 0, nb_rows, c->ctrl, PH_STEP, s};
+            timed(FAM_SPMM_A, [&] { launch_spmm_a<TR, TD>(w); });
+        }
+        UpdateArgs u{p(), c->m_off == 0, true, st.R, st.CR, st.D, st.CD, st.G, c->m_off ? st.W : nullptr, st.hist,
+                     st.slot_stride, st.ld, st.sh, st.y, st.zrow, c->ctrl, part_of(c, PART_UPD), nb_rows, c->ctrl, PH_STEP, s};
+        timed(FAM_UPDATE, [&] { launch_update<TR, TD>(u); });
+        timed(FAM_HIST, [&] {
+            ctrl_hist(s, c->ctrl, HIST_STEP, part_of(c, PART_UPD), nb_rows,
+                      c->m_off ? part_of(c, PART_YTIL) : nullptr, nb_off);
+        });
+    }
+
+    // ALM outer step (Sec. 2.1) once the inner loop has finished
+    void enqueue_outer() {
+        ConsArgs yu{p(), CONS_YUPD, 0, c->m, st.R, st.R, st.ld, st.sh, st.y, nullptr, nullptr, c->ctrl, 0.0,
+                    part_of(c, PART_CONS), nb_all, c->ctrl, PH_OUTER, s};
+        timed(FAM_CONS_YUPD, [&] { launch_cons<TR, TR>(yu); });
+        spmm_CR(PH_OUTER);
+        timed(FAM_OUTER, [&] {
+            ctrl_outer(s, c->ctrl, part_of(c, PART_CONS), nb_all, part_of(c, PART_OBJ), nb_rows);
+        });
+        outer_gradient(PH_OUTER);
+    }
+
+    void enqueue_iteration() {
+        enqueue_inner();
+        enqueue_outer();
+    }
+};
+
+template <typename TR, typename TD>
+lorads_status alloc_state(lorads_ctx* ctx, int prec, int r) {
+    SolverState& st = ctx->st;
+    const int ld = padded_ld(r);
+    Shape sh;
+    if (!shape_for_ld(ld, &sh))
+        return set_err(ctx, "rank " + std::to_string(r) + " exceeds the supported row width"), LORADS_ERR_UNSUPPORTED;
+    if (st.prec == prec && st.ld == ld && st.R) {
+        st.r = r;
+        return LORADS_OK;
+    }
+    free_state(st);
+    st.prec = prec;
+    st.r = r;
+    st.ld = ld;
+    st.sh = sh;
+    st.esR = sizeof(TR);
+    st.esD = sizeof(TD);
+    st.rtype = std::is_same<TR, double>::value ? 0 : (std::is_same<TR, dfloat>::value ? 1 : 2);
+    const size_t nl = (size_t)ctx->n * ld;
+    lorads_status s;
+    const int T = ctx->prm.lbfgs_mem;
+    if ((s = dalloc(ctx, reinterpret_cast<TR**>(&st.R), nl))) return s;
+    if ((s = dalloc(ctx, reinterpret_cast<TR**>(&st.CR), nl))) return s;
+    if ((s = dalloc(ctx, reinterpret_cast<TD**>(&st.D), nl))) return s;
+    if ((s = dalloc(ctx, reinterpret_cast<TD**>(&st.CD), nl))) return s;
+    if ((s = dalloc(ctx, reinterpret_cast<TD**>(&st.G), nl))) return s;
+    if ((s = dalloc(ctx, reinterpret_cast<TD**>(&st.hist), nl * 2 * T))) return s;
+    st.slot_stride = (int64_t)nl;
+    if (ctx->m_off) {
+        if ((s = dalloc(ctx, reinterpret_cast<TD**>(&st.W), nl))) return s;
+        if ((s = dalloc(ctx, &st.ytil, ctx->m))) return s;
+    }
+    if ((s = dalloc(ctx, &st.y, ctx->m))) return s;
+    if ((s = dalloc(ctx, &st.zrow, ctx->n))) return s;
+    if ((s = dalloc(ctx, &st.zk, ctx->m))) return s;
+    CK(cudaMemset(st.R, 0, nl * sizeof(TR)));
+    CK(cudaMemset(st.CR, 0, nl * sizeof(TR)));
+    CK(cudaMemset(st.D, 0, nl * sizeof(TD)));
+    CK(cudaMemset(st.CD, 0, nl * sizeof(TD)));
+    CK(cudaMemset(st.G, 0, nl * sizeof(TD)));
+    CK(cudaMemset(st.hist, 0, nl * 2 * T * sizeof(TD)));
+    if (st.W) CK(cudaMemset(st.W, 0, nl * sizeof(TD)));
+    return LORADS_OK;
+}
+
+template <typename TR, typename TD>
+lorads_status capture(lorads_ctx* ctx) {
+    SolverState& st = ctx->st;
+    if (st.exec) {
+        cudaGraphExecDestroy(st.exec);
+        st.exec = nullptr;
+    }
+    Driver<TR, TD> drv(ctx);
+    cudaGraph_t g = nullptr;
+    const int64_t before = ctx->launches;
+    CK(cudaStreamBeginCapture(ctx->solve_stream, cudaStreamCaptureModeThreadLocal));
+    drv.enqueue_iteration();
+    ctx->graph_nodes = ctx->launches - before;
+    ctx->launches = before;
+    cudaError_t e = cudaStreamEndCapture(ctx->solve_stream, &g);
+    if (e != cudaSuccess) {
+        ctx->err = std::string("graph capture: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        return LORADS_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&st.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        ctx->err = std::string("graph instantiate: ") + cudaGetErrorString(e);
+        return LORADS_ERR_CUDA;
+    }
+    return LORADS_OK;
+}
+
+// Grows the rank (App. A.1): new columns N(0, (1e-3 ||R||_F / sqrt(n r))^2).
+template <typename TR, typename TD>
+lorads_status grow_rank(lorads_ctx* ctx, int prec, int outer_done) {
+    SolverState& st = ctx->st;
+    const int r_old = st.r;
+    const int r_cap = (int)std::ceil(std::sqrt(2.0 * (double)ctx->m));
+    const int r_new = std::min((int)std::ceil(1.5 * r_old), r_cap);
+    if (r_new <= r_old) return LORADS_OK;
+    cudaStream_t s = ctx->solve_stream;
+    // ||R||_F^2
+    double* pm = part_of(ctx, PART_MISC);
+    const int nb = flat_blocks(ctx, ctx->n * (int64_t)r_old);
+    sumsq<TR>(s, ctx->n, st.ld, r_old, st.R, pm, nb);
+    fold_to(s, pm, nb, 1, ctx->small);
+    CK(cudaMemcpyAsync(ctx->h_small, ctx->small, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double scale = 1e-3 * std::sqrt(ctx->h_small[0]) / std::sqrt((double)ctx->n * r_old);
+    // keep R and y, rebuild everything else at the new width
+    const int ld_old = st.ld;
+    TR* R_old = nullptr;
+    lorads_status rs;
+    if ((rs = dalloc(ctx, &R_old, (size_t)ctx->n * ld_old))) return rs;
+    CK(cudaMemcpyAsync(R_old, st.R, (size_t)ctx->n * ld_old * sizeof(TR), cudaMemcpyDeviceToDevice, s));
+    double* y_keep = nullptr;
+    if ((rs = dalloc(ctx, &y_keep, ctx->m))) return rs;
+    CK(cudaMemcpyAsync(y_keep, st.y, ctx->m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    st.prec = -1;                                   // force reallocation
+    if ((rs = alloc_state<TR, TD>(ctx, prec, r_new))) return rs;
+    convert<TR, TR>(s, ctx->n, ld_old, st.ld, r_old, R_old, st.R, flat_blocks(ctx, ctx->n * (int64_t)st.ld));
+    rank_columns<TR>(s, ctx->n, st.ld, r_old, r_new, scale, ctx->prm.seed, (uint64_t)(outer_done - 1), st.R,
+                     flat_blocks(ctx, ctx->n * (int64_t)(r_new - r_old)));
+    ctx->launches += 4;                     // sumsq, fold, convert, columns
+    CK(cudaMemcpyAsync(st.y, y_keep, ctx->m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    cudaFree(R_old);
+    cudaFree(y_keep);
+    return check_launch(ctx, "rank update");
+}
+
+lorads_status fill_result(lorads_ctx* ctx, std::chrono::steady_clock::time_point t0, bool timed_out,
+                          lorads_result* res) {
+    Ctrl hc;
+    CK(cudaStreamSynchronize(ctx->solve_stream));
+    CK(cudaMemcpy(&hc, ctx->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+    ctx->st.have_solution = true;
+    const lorads_status final_status =
+        timed_out && !hc.solve_done ? LORADS_ERR_TIMEOUT : (lorads_status)hc.status;
+    if (res) {
+        res->primal_obj = hc.primal_obj;
+        res->dual_obj = hc.dual_obj;
+        res->err1 = hc.err1;
+        res->err2 = -1.0;
+        res->err3 = hc.err3;
+        res->sigma_min = 0.0;
+        res->rho = hc.rho;
+        res->rank = ctx->st.r;
+        res->outer_iters = hc.outer;
+        res->inner_iters = hc.total_inner;
+        res->status = final_status;
+        res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        res->kernel_launches = ctx->launches;
+    }
+    return final_status;
+}
+
+// Host-stepped solve with a CUDA-event pair around every launch (verbose >= 2):
+// same kernels and decisions as the graph path, one host sync per iteration.
+template <typename TR, typename TD>
+lorads_status run_profiled(lorads_ctx* ctx, int prec, std::chrono::steady_clock::time_point t0,
+                           lorads_result* res) {
+    lorads_status s;
+    if (!ctx->prof) {
+        ctx->prof = new (std::nothrow) Prof();
+        if (!ctx->prof) return set_err(ctx, "host allocation failed"), LORADS_ERR_OOM;
+        for (int q = 0; q < Prof::kPool; ++q)
+            for (int e = 0; e < 2; ++e) CK(cudaEventCreate(&ctx->prof->ev[q][e]));
+    }
+    Prof* pf = ctx->prof;
+    for (int f = 0; f < NFAM; ++f) { pf->total_ms[f] = 0; pf->count[f] = 0; }
+    cudaStream_t ss = ctx->solve_stream;
+    bool timed_out = false;
+    for (;;) {
+        Ctrl hc;
+        CK(cudaMemcpyAsync(&ctx->h_ctrl[0], ctx->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, ss));
+        CK(cudaStreamSynchronize(ss));
+        hc = ctx->h_ctrl[0];
+        if (hc.solve_done) break;
+        Driver<TR, TD> drv(ctx);
+        if (hc.pause) {
+            if ((s = grow_rank<TR, TD>(ctx, prec, hc.outer))) return s;
+            Driver<TR, TD> d2(ctx);
+            d2.enqueue_resume();
+            continue;
+        }
+        pf->used = 0;
+        if (hc.phase == PHASE_INNER) drv.enqueue_inner();
+        else drv.enqueue_outer();
+        if ((s = check_launch(ctx, "profiled iteration"))) return s;
+        CK(cudaStreamSynchronize(ss));
+        for (int q = 0; q < pf->used; ++q) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, pf->ev[q][0], pf->ev[q][1]));
+            pf->total_ms[pf->fam[q]] += ms;
+            pf->count[pf->fam[q]] += 1;
+        }
+        pf->used = 0;
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > ctx->prm.time_limit) { timed_out = true; break; }
+    }
+    ctx->prof_valid = true;
+    ctx->prof_active = false;
+    return fill_result(ctx, t0, timed_out, res);
+}
+
+template <typename TR, typename TD>
+lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0, int32_t r0_on_device,
+                        const double* y0, lorads_result* res) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const lorads_params& P = ctx->prm;
+    ctx->launches = 0;
+    lorads_status s;
+    int r = r0;
+    if (r <= 0) r = std::max(1, (int)std::ceil(std::log2((double)std::max<int64_t>(ctx->m, 2))));
+    if ((s = alloc_state<TR, TD>(ctx, prec, r))) return s;
+    SolverState& st = ctx->st;
+    cudaStream_t ss = ctx->solve_stream;
+    CK(cudaEventRecord(ctx->ev_sync, ctx->stream));
+    CK(cudaStreamWaitEvent(ss, ctx->ev_sync, 0));
+    const size_t nl = (size_t)ctx->n * st.ld;
+    // R <- R0 (padded to ld, converted to TR)
+    if (R0) {
+        double* tmp = nullptr;
+        if ((s = dalloc(ctx, &tmp, (size_t)ctx->n * r))) return s;
+        CK(cudaMemcpyAsync(tmp, R0, (size_t)ctx->n * r * sizeof(double),
+                           r0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ss));
+        convert<double, TR>(ss, ctx->n, r, st.ld, r, tmp, st.R, flat_blocks(ctx, (int64_t)nl));
+        ctx->launches += 1;
+        CK(cudaStreamSynchronize(ss));
+        cudaFree(tmp);
+    } else {
+        CK(cudaMemsetAsync(st.R, 0, nl * sizeof(TR), ss));
+        const double scale = std::sqrt(std::max(0.5 * ctx->bnorm1, 1.0) / ((double)ctx->n * r));
+        random_start<TR>(ss, ctx->n, st.ld, r, P.seed, ctx->m_diag == ctx->m ? 1 : 0, scale, st.R,
+                         flat_blocks(ctx, ctx->n));
+        ctx->launches += 1;
+    }
+    if (y0) CK(cudaMemcpyAsync(st.y, y0, ctx->m * sizeof(double), cudaMemcpyHostToDevice, ss));
+    else CK(cudaMemsetAsync(st.y, 0, ctx->m * sizeof(double), ss));
+    // control block
+    Ctrl h{};
+    h.rho = P.rho0 > 0 ? P.rho0 : 1.0 / ctx->mean_abs_c;
+    h.lbfgs_mem = P.lbfgs_mem;
+    h.max_inner = P.max_inner;
+    h.max_outer = P.max_outer;
+    h.rank_threshold = std::max(1, P.rank_update_threshold);
+    h.lbfgs_scaling = P.lbfgs_scaling;
+    h.rho_policy = P.rho_policy;
+    h.inner_scale = P.inner_scale;
+    h.tol = P.tol;
+    h.inner_rel = P.inner_rel;
+    h.bnorm1 = ctx->bnorm1;
+    h.bnorm_inf = ctx->bnorm_inf;
+    h.rho_growth = P.rho_growth;
+    h.rho_max = P.rho_max;
+    h.infeas_decrease = P.infeas_decrease;
+    h.status = LORADS_ERR_MAXITER;
+    for (int q = 0; q < kMaxMem; ++q) h.order[q] = q;
+    CK(cudaMemcpyAsync(ctx->ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, ss));
+    {
+        Driver<TR, TD> drv(ctx);
+        drv.enqueue_init();
+    }
+    if ((s = check_launch(ctx, "solve init"))) return s;
+    if (P.verbose >= 2) return run_profiled<TR, TD>(ctx, prec, t0, res);
+    if ((s = capture<TR, TD>(ctx))) return s;
+    // ---- iterate: launch the graph in batches, poll the status of the previous batch
+    int slot = 0;
+    bool pending = false;
+    int last_outer_printed = -1;
+    lorads_status final_status = LORADS_OK;
+    bool timed_out = false;
+    for (;;) {
+        for (int k = 0; k < P.check_every; ++k) CK(cudaGraphLaunch(st.exec, ss));
+        ctx->launches += (int64_t)P.check_every * ctx->graph_nodes;
+        CK(cudaMemcpyAsync(&ctx->h_ctrl[slot], ctx->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, ss));
+        CK(cudaEventRecord(ctx->ev_poll[slot], ss));
+        if (pending) {
+            CK(cudaEventSynchronize(ctx->ev_poll[slot ^ 1]));
+            const Ctrl& hc = ctx->h_ctrl[slot ^ 1];
+            if (P.verbose == 1 && hc.outer != last_outer_printed) {
+                last_outer_printed = hc.outer;
+                std::fprintf(stderr, "[lorads] outer %d inner %d rho %.3g err1 %.3e err3 %.3e obj %.10g r %d t %.3fs\n",
+                             hc.outer, hc.total_inner, hc.last_iter_rho, hc.err1, hc.err3, hc.primal_obj, st.r,
+                             std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+            }
+            if (hc.solve_done || hc.pause) {
+                CK(cudaStreamSynchronize(ss));
+                const Ctrl& now = ctx->h_ctrl[slot];
+                if (now.solve_done) break;
+                // pause: grow the rank, then continue with the outer tail
+                if ((s = grow_rank<TR, TD>(ctx, prec, now.outer))) return s;
+                Driver<TR, TD> drv(ctx);
+                drv.enqueue_resume();
+                if ((s = check_launch(ctx, "resume"))) return s;
+                if ((s = capture<TR, TD>(ctx))) return s;
+                pending = false;
+                slot = 0;
+                continue;
+            }
+        }
+        pending = true;
+        slot ^= 1;
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > P.time_limit) {
+            CK(cudaStreamSynchronize(ss));
+            timed_out = true;
+            break;
+        }
+    }
+    return fill_result(ctx, t0, timed_out, res);
+}
+
+}  // namespace
+
+extern "C" lorads_status lorads_solve(lorads_ctx* ctx, const double* R0, int32_t r0, int32_t r0_on_device,
+                                      const double* y0, lorads_result* res) {
+    if (!ctx) return LORADS_ERR_INVALID_ARG;
+    if (res) std::memset(res, 0, sizeof(*res));
+    if (R0 && r0 < 1) return set_err(ctx, "r0 must be >= 1 when R0 is given"), LORADS_ERR_INVALID_ARG;
+    const int prec = ctx->prm.prec;
+    lorads_status s;
+    switch (prec) {
+        case LORADS_FP64: s = run_solve<double, double>(ctx, prec, R0, r0, r0_on_device, y0, res); break;
+        case LORADS_MIXED: s = run_solve<dfloat, float>(ctx, prec, R0, r0, r0_on_device, y0, res); break;
+        case LORADS_DF64: s = run_solve<dfloat, dfloat>(ctx, prec, R0, r0, r0_on_device, y0, res); break;
+        case LORADS_FP32: s = run_solve<float, float>(ctx, prec, R0, r0, r0_on_device, y0, res); break;
+        default:
+            return set_err(ctx, "params.prec must be FP64, MIXED, DF64 or FP32 for lorads_solve"),
+                   LORADS_ERR_INVALID_ARG;
+    }
+    if (res && res->status == 0 && s != LORADS_OK) res->status = s;
+    return s;
+}
+
+extern "C" lorads_status lorads_get_solution(lorads_ctx* ctx, double* R_host, int64_t R_capacity, int32_t* rank_out,
+                                             double* y_host) {
+    if (!ctx) return LORADS_ERR_INVALID_ARG;
+    SolverState& st = ctx->st;
+    if (!st.have_solution) return set_err(ctx, "no solution: call lorads_solve first"), LORADS_ERR_INVALID_ARG;
+    if (rank_out) *rank_out = st.r;
+    cudaStream_t s = ctx->solve_stream;
+    if (R_host) {
+        if (R_capacity < ctx->n * (int64_t)st.r) return set_err(ctx, "R_host too small"), LORADS_ERR_INVALID_ARG;
+        double* tmp = nullptr;
+        lorads_status rs;
+        if ((rs = dalloc(ctx, &tmp, (size_t)ctx->n * st.r))) return rs;
+        const int nbk = flat_blocks(ctx, ctx->n * (int64_t)st.r);
+        if (st.rtype == 0) convert<double, double>(s, ctx->n, st.ld, st.r, st.r, st.R, tmp, nbk);
+        else if (st.rtype == 1) convert<dfloat, double>(s, ctx->n, st.ld, st.r, st.r, st.R, tmp, nbk);
+        else convert<float, double>(s, ctx->n, st.ld, st.r, st.r, st.R, tmp, nbk);
+        CK(cudaMemcpyAsync(R_host, tmp, (size_t)ctx->n * st.r * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        cudaFree(tmp);
+    }
+    if (y_host) {
+        CK(cudaMemcpyAsync(y_host, st.y, ctx->m * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return LORADS_OK;
+}
+
+extern "C" int32_t lorads_kernel_times(const lorads_ctx* ctx, const char** names, double* ms, int32_t cap) {
+    if (!ctx || !ctx->prof || !ctx->prof_valid) return 0;
+    int32_t k = 0;
+    for (int f = 0; f < NFAM && k < cap; ++f) {
+        if (ctx->prof->count[f] == 0) continue;
+        if (names) names[k] = kFamNames[f];
+        if (ms) ms[k] = ctx->prof->total_ms[f] / (double)ctx->prof->count[f];
+        ++k;
+    }
+    return k;
+}
+
+extern "C" int32_t lorads_kernel_counts(const lorads_ctx* ctx, const char** names, int64_t* counts, int32_t cap) {
+    if (!ctx || !ctx->prof || !ctx->prof_valid) return 0;
+    int32_t k = 0;
+    for (int f = 0; f < NFAM && k < cap; ++f) {
+        if (ctx->prof->count[f] == 0) continue;
+        if (names) names[k] = kFamNames[f];
+        if (counts) counts[k] = ctx->prof->count[f];
+        ++k;
+    }
+    return k;
+}

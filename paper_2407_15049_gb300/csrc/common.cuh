@@ -1,0 +1,237 @@
+// Shared device helpers of the LoRADS GB300 library: vector units, block
+// reductions, the device control block and the launch-shape rules.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include "dfloat.cuh"
+
+namespace lorads {
+
+constexpr int kThreads = 256;        // threads per block of every streaming kernel
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxMem = 4;           // L-BFGS memory cap (T of Algorithm 1)
+
+// ------------------------------------------------------------------ row shapes
+// A row of ld elements is cut into Q = ld/4 units of 4 elements.  A group of
+// L lanes (the power of two >= Q, at most 32) owns a row; lane l handles units
+// c*L + l < Q for c < CPL = ceil(Q/L), so that each load instruction of a group
+// reads up to L consecutive units.  Lanes past Q idle.
+constexpr int kMaxCPL = 4;
+constexpr int kMaxLd = 4 * 32 * kMaxCPL;   // widest supported row (512 elements)
+
+struct Shape {
+    int L;     // lanes per row (power of two)
+    int CPL;   // units per lane
+    int Q;     // units per row
+};
+
+inline bool shape_for_ld(int ld, Shape* s) {
+    if (ld <= 0 || (ld % 4) != 0 || ld > kMaxLd) return false;
+    const int Q = ld / 4;
+    int L = 1;
+    while (L < Q && L < 32) L <<= 1;
+    s->L = L;
+    s->Q = Q;
+    s->CPL = (Q + L - 1) / L;
+    return s->CPL <= kMaxCPL;
+}
+
+// Row width used for rank r: r rounded up to a multiple of 4.
+inline int padded_ld(int r) { return (r + 3) / 4 * 4; }
+
+// ------------------------------------------------------------------ vector units
+template <typename T> struct Unit;      // 4 consecutive elements of type T
+
+template <> struct Unit<double> {
+    double v[4];
+    __device__ __forceinline__ void load(const double* p) {
+        double2 a = *reinterpret_cast<const double2*>(p);
+        double2 b = *reinterpret_cast<const double2*>(p + 2);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    __device__ __forceinline__ void load_stream(const double* p) {   // read once
+        double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+        double2 b = __ldcs(reinterpret_cast<const double2*>(p + 2));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    __device__ __forceinline__ void store(double* p) const {
+        *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+        *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+    }
+    __device__ __forceinline__ void store_stream(double* p) const {
+        __stcs(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
+        __stcs(reinterpret_cast<double2*>(p + 2), make_double2(v[2], v[3]));
+    }
+};
+
+template <> struct Unit<float> {
+    float v[4];
+    __device__ __forceinline__ void load(const float* p) {
+        float4 a = *reinterpret_cast<const float4*>(p);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+    __device__ __forceinline__ void load_stream(const float* p) {
+        float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+    __device__ __forceinline__ void store(float* p) const {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    __device__ __forceinline__ void store_stream(float* p) const {
+        __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+    }
+};
+
+// bf16 storage, values widened to float on load.
+template <> struct Unit<__nv_bfloat16> {
+    float v[4];
+    __device__ __forceinline__ void from_raw(uint2 a) {
+        v[0] = __uint_as_float(a.x << 16);
+        v[1] = __uint_as_float(a.x & 0xffff0000u);
+        v[2] = __uint_as_float(a.y << 16);
+        v[3] = __uint_as_float(a.y & 0xffff0000u);
+    }
+    __device__ __forceinline__ void load(const __nv_bfloat16* p) {
+        from_raw(*reinterpret_cast<const uint2*>(p));
+    }
+    __device__ __forceinline__ void load_stream(const __nv_bfloat16* p) {
+        from_raw(__ldcs(reinterpret_cast<const uint2*>(p)));
+    }
+    __device__ __forceinline__ void store(__nv_bfloat16* p) const {
+        __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+        __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+        uint2 u;
+        u.x = *reinterpret_cast<uint32_t*>(&a);
+        u.y = *reinterpret_cast<uint32_t*>(&b);
+        *reinterpret_cast<uint2*>(p) = u;
+    }
+    __device__ __forceinline__ void store_stream(__nv_bfloat16* p) const { store(p); }
+};
+
+// double-float storage: (hi, lo) pairs, 8 bytes per element
+template <> struct Unit<dfloat> {
+    dfloat v[4];
+    __device__ __forceinline__ void load(const dfloat* p) {
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        const float4 b = *reinterpret_cast<const float4*>(p + 2);
+        v[0] = dfloat(a.x, a.y); v[1] = dfloat(a.z, a.w); v[2] = dfloat(b.x, b.y); v[3] = dfloat(b.z, b.w);
+    }
+    __device__ __forceinline__ void load_stream(const dfloat* p) {
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+        const float4 b = __ldcs(reinterpret_cast<const float4*>(p + 2));
+        v[0] = dfloat(a.x, a.y); v[1] = dfloat(a.z, a.w); v[2] = dfloat(b.x, b.y); v[3] = dfloat(b.z, b.w);
+    }
+    __device__ __forceinline__ void store(dfloat* p) const {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
+        *reinterpret_cast<float4*>(p + 2) = make_float4(v[2].hi, v[2].lo, v[3].hi, v[3].lo);
+    }
+    __device__ __forceinline__ void store_stream(dfloat* p) const {
+        __stcs(reinterpret_cast<float4*>(p), make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo));
+        __stcs(reinterpret_cast<float4*>(p + 2), make_float4(v[2].hi, v[2].lo, v[3].hi, v[3].lo));
+    }
+};
+
+// arithmetic type of an element once loaded
+template <typename T> struct Arith { using type = T; };
+template <> struct Arith<__nv_bfloat16> { using type = float; };
+
+// ------------------------------------------------------------------ reductions
+// Sums NQ per-thread partials (double or double-float) over the block and
+// writes them as doubles to part[blockIdx.x * NQ + q].  Fixed order:
+// deterministic for a fixed grid.
+template <int NQ, typename PA>
+__device__ __forceinline__ void block_partials(PA (&acc)[NQ], double* part) {
+    __shared__ double red[kWarps][NQ > 0 ? NQ : 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double v = double(acc[q]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][q] = v;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) s += red[w][q];
+        part[(size_t)blockIdx.x * NQ + q] = s;
+    }
+}
+
+// Reduces a group-of-L-lanes value; every lane of the group gets the sum.
+template <typename V>
+__device__ __forceinline__ V group_sum(V v, int L) {
+    for (int o = L >> 1; o > 0; o >>= 1) v += shfl_xor(v, o);
+    return v;
+}
+
+// ------------------------------------------------------------------ control block
+// Device-resident state of one solve.  Written by the single-block control
+// kernels, read by every streaming kernel (which skip their work when the
+// phase flags say so).
+struct Ctrl {
+    // scalars of the current inner iteration
+    double rho;
+    double tau;
+    double a[4];
+    double gD;                  // <G, D>
+    double DD;                  // ||D||^2
+    double gnorm2;              // ||G||^2 at the current R
+    double znorm2;              // ||A(RR^T) - b||^2 at the current R
+    // two-loop coefficients of the next direction: D = cG G + sum cS S_u + sum cY Y_u
+    double cG, cS[kMaxMem], cY[kMaxMem];
+    // Gram data of the stored pairs, indexed by physical slot
+    double g_s[kMaxMem], g_y[kMaxMem];          // <G, S_u>, <G, Y_u>
+    double SY[kMaxMem][kMaxMem];                // <S_u, Y_v>
+    double YY[kMaxMem][kMaxMem];                // <Y_u, Y_v>
+    double SS_new;                              // ||S_new||^2 of the last step
+    int order[kMaxMem];                         // physical slot by age (0 = oldest)
+    int mem_count;
+    int new_slot;                               // slot the next pair is written to
+    int old_count;                              // pairs kept besides the new slot
+    int old_slots[kMaxMem];
+    // phase flags
+    int phase;                  // PHASE_INNER (L-BFGS) or PHASE_OUTER (multiplier step)
+    int step_ok;                // 1 if the current iteration takes a step (tau > 0)
+    int inner_done;
+    int solve_done;
+    int pause;                  // host action needed (rank update)
+    int status;                 // lorads_status of the solve
+    int inner_k;                // directions computed in this outer step
+    int outer;
+    int total_inner;
+    int hit_cap_streak;
+    int lbfgs_mem;
+    int max_inner;
+    int max_outer;
+    int rank_threshold;
+    int lbfgs_scaling;
+    int rho_policy;
+    int inner_scale;
+    // outer-loop state
+    double tol, inner_rel, bnorm1, bnorm_inf;
+    double rho_growth, rho_max, infeas_decrease;
+    double err1, err1_prev, err3, primal_obj, dual_obj;
+    double last_iter_rho;
+};
+
+// Partial-sum slots of each producing kernel.
+enum {
+    // direction kernel
+    PD_GD = 0, PD_DD, PD_N,
+    // SpMM with line-search epilogue (and constraint pass, same slots)
+    PL_P1 = 0, PL_P2, PL_YQ1, PL_YQ2, PL_Q1Q1, PL_Q1Q2, PL_Q2Q2, PL_N,
+    // constraint pass in y~ / multiplier mode
+    PC_ZZ = 0, PC_BY, PC_N,
+    // SpMM C R with objective
+    PO_CRR = 0, PO_N,
+};
+// row-update kernel: fixed slots then 5 per old pair
+enum { PU_GG = 0, PU_ZZ, PU_GSN, PU_GYN, PU_SYN, PU_YYN, PU_SSN, PU_FIXED };
+constexpr int PU_PER_OLD = 5;          // <G,S_v>, <G,Y_v>, <Snew,Y_v>, <S_v,Ynew>, <Ynew,Y_v>
+constexpr int PU_N = PU_FIXED + PU_PER_OLD * (kMaxMem - 1);
+
+}  // namespace lorads

@@ -1,0 +1,575 @@
+// Single-block control kernels of the device-resident solve loop and the
+// scalar pieces of the method: the line-search coefficients and cubic root of
+// App. A.2, the L-BFGS two-loop recursion of Algorithm 1 carried out on the
+// Gram data of the stored pairs, the multiplier/penalty step of Sec. 2.1 and
+// the error measures of Sec. 4.1.  All in FP64 on one block; the partial sums
+// of the streaming kernels are folded in a fixed order (deterministic).
+#include <math.h>
+#include "control.h"
+#include "kernels.cuh"
+
+namespace lorads {
+
+// ---------------------------------------------------------------- reductions
+// out[q] = sum over blocks of part[b*NQ + q]; warp w folds q = w, w+8, ...
+__device__ void fold_parts(const double* part, int nb, int NQ, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = warp; q < NQ; q += nw) {
+        double s = 0.0;
+        for (int b = lane; b < nb; b += 32) s += part[(size_t)b * NQ + q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[q] = s;
+    }
+}
+
+// ---------------------------------------------------------------- cubic root
+__device__ __forceinline__ double qval(const double* a, double t) {
+    return ((a[0] * t + a[1]) * t + a[2]) * t * t + a[3] * t;
+}
+__device__ __forceinline__ double qd1(const double* a, double t) {
+    return ((4.0 * a[0] * t + 3.0 * a[1]) * t + 2.0 * a[2]) * t + a[3];
+}
+__device__ __forceinline__ double qd2(const double* a, double t) {
+    return (12.0 * a[0] * t + 6.0 * a[1]) * t + 2.0 * a[2];
+}
+
+// Root of f' in [lo, hi] where f'(lo), f'(hi) have opposite signs and f' is
+// monotone: Newton steps kept inside the bracket, bisection otherwise.
+__device__ double bracketed_root(const double* a, double lo, double hi) {
+    double flo = qd1(a, lo);
+    double t = 0.5 * (lo + hi);
+    for (int it = 0; it < 200; ++it) {
+        const double f = qd1(a, t);
+        if (f == 0.0) return t;
+        if ((f < 0.0) == (flo < 0.0)) { lo = t; flo = f; } else { hi = t; }
+        const double d = qd2(a, t);
+        double tn = (d != 0.0) ? t - f / d : 0.5 * (lo + hi);
+        if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+        if (tn == t || hi - lo <= 4.0 * 2.220446049250313e-16 * fabs(t)) { t = tn; break; }
+        t = tn;
+    }
+    return t;
+}
+
+// Smallest t > 0 with f'(t) of the sign `positive` beyond `from`, by doubling.
+__device__ double grow_until(const double* a, double from, bool positive) {
+    double h = fmax(1.0, fabs(from));
+    for (int it = 0; it < 2100; ++it) {
+        const double t = from + h;
+        const double f = qd1(a, t);
+        if (positive ? (f > 0.0) : (f < 0.0)) return t;
+        h *= 2.0;
+        if (!isfinite(t)) break;
+    }
+    return from + h;
+}
+
+// Step of the exact line search (App. A.2): among the positive real roots of
+// 4a1 t^3 + 3a2 t^2 + 2a3 t + a4 the one with the lowest quartic value
+// f(t) = a1 t^4 + a2 t^3 + a3 t^2 + a4 t; 0 when no positive root lowers f.
+__device__ double quartic_step(const double* a) {
+    double cand[3];
+    int nc = 0;
+    if (a[0] != 0.0) {
+        // monotone pieces of f' split at the roots of f'' = 12a1 t^2 + 6a2 t + 2a3
+        double cuts[2];
+        int ncut = 0;
+        const double A = 12.0 * a[0], B = 6.0 * a[1], C = 2.0 * a[2];
+        const double disc = B * B - 4.0 * A * C;
+        if (disc > 0.0) {
+            const double sq = sqrt(disc);
+            const double qq = -0.5 * (B + copysign(sq, B));
+            double c1 = qq / A, c2 = (qq != 0.0) ? C / qq : -c1;
+            if (c1 > c2) { const double t = c1; c1 = c2; c2 = t; }
+            cuts[ncut++] = c1;
+            cuts[ncut++] = c2;
+        }
+        // pieces [edge_k, edge_{k+1}] clipped to t > 0
+        double edges[4];
+        int ne = 0;
+        edges[ne++] = 0.0;
+        for (int k = 0; k < ncut; ++k)
+            if (cuts[k] > 0.0) edges[ne++] = cuts[k];
+        for (int k = 0; k < ne; ++k) {
+            const double lo = edges[k];
+            const double flo = qd1(a, lo);
+            double hi;
+            bool last = (k == ne - 1);
+            if (!last) {
+                hi = edges[k + 1];
+            } else {
+                // f' -> +inf: find a finite right end with f' > 0
+                if (flo >= 0.0) continue;
+                hi = grow_until(a, lo, true);
+            }
+            const double fhi = qd1(a, hi);
+            if (flo == 0.0) {
+                if (lo > 0.0 && nc < 3) cand[nc++] = lo;
+                continue;
+            }
+            if ((flo < 0.0 && fhi > 0.0) || (flo > 0.0 && fhi < 0.0)) {
+                if (nc < 3) cand[nc++] = bracketed_root(a, lo, hi);
+            } else if (fhi == 0.0 && hi > 0.0 && last == false) {
+                if (nc < 3) cand[nc++] = hi;
+            }
+        }
+    } else if (a[1] != 0.0) {
+        // f' = 3a2 t^2 + 2a3 t + a4
+        const double A = 3.0 * a[1], B = 2.0 * a[2], C = a[3];
+        const double disc = B * B - 4.0 * A * C;
+        if (disc >= 0.0) {
+            const double sq = sqrt(disc);
+            const double qq = -0.5 * (B + copysign(sq, B));
+            if (qq != 0.0) {
+                cand[nc++] = qq / A;
+                cand[nc++] = C / qq;
+            } else {
+                cand[nc++] = 0.0;
+            }
+        }
+    } else if (a[2] != 0.0) {
+        cand[nc++] = -a[3] / (2.0 * a[2]);
+    }
+    // sort candidates ascending (ties keep the smaller)
+    for (int i = 1; i < nc; ++i)
+        for (int j = i; j > 0 && cand[j] < cand[j - 1]; --j) {
+            const double t = cand[j]; cand[j] = cand[j - 1]; cand[j - 1] = t;
+        }
+    double best = 0.0, best_f = 0.0;
+    for (int i = 0; i < nc; ++i) {
+        const double t = cand[i];
+        if (!(t > 0.0) || !isfinite(t)) continue;
+        const double f = qval(a, t);
+        if (f < best_f) { best = t; best_f = f; }
+    }
+    return best;
+}
+
+__global__ void k_quartic_step(const double* a, double* tau) { *tau = quartic_step(a); }
+
+// ---------------------------------------------------------------- memory helpers
+__device__ void mem_clear(Ctrl* c) {
+    c->mem_count = 0;
+    for (int s = 0; s < kMaxMem; ++s) {
+        c->order[s] = s;
+        c->cS[s] = 0.0;
+        c->cY[s] = 0.0;
+        c->g_s[s] = 0.0;
+        c->g_y[s] = 0.0;
+    }
+}
+
+// Two-loop recursion of Algorithm 1 (initial matrix I) carried out on
+// coefficients: D = cG G + sum cS_u S_u + sum cY_u Y_u, using only the dot
+// products <G,S_u>, <G,Y_u>, <S_u,Y_v>, <Y_u,Y_v> of the stored pairs.
+__device__ void two_loop_coeffs(Ctrl* c) {
+    const int mem = c->mem_count;
+    double alpha[kMaxMem];
+    c->cG = -1.0;
+    for (int s = 0; s < kMaxMem; ++s) { c->cS[s] = 0.0; c->cY[s] = 0.0; }
+    for (int t = mem - 1; t >= 0; --t) {                 // newest to oldest
+        const int st = c->order[t];
+        double sD = c->cG * c->g_s[st];
+        for (int u = 0; u < mem; ++u) {
+            const int su = c->order[u];
+            sD += c->cY[su] * c->SY[st][su];
+        }
+        alpha[t] = sD / c->SY[st][st];
+        c->cY[st] -= alpha[t];
+    }
+    if (c->lbfgs_scaling && mem > 0) {                   // r = gamma q
+        const int sn = c->order[mem - 1];
+        const double gamma = c->SY[sn][sn] / c->YY[sn][sn];
+        c->cG *= gamma;
+        for (int u = 0; u < mem; ++u) c->cY[c->order[u]] *= gamma;
+    }
+    for (int t = 0; t < mem; ++t) {                      // oldest to newest
+        const int st = c->order[t];
+        double yD = c->cG * c->g_y[st];
+        for (int u = 0; u < mem; ++u) {
+            const int su = c->order[u];
+            yD += c->cY[su] * c->YY[st][su] + c->cS[su] * c->SY[su][st];
+        }
+        c->cS[st] += alpha[t] - yD / c->SY[st][st];
+    }
+}
+
+// Physical slot of the next pair and the pairs it keeps.
+__device__ void plan_next_slot(Ctrl* c, int T) {
+    const int mem = c->mem_count;
+    if (mem < T) {
+        int used = 0;
+        for (int t = 0; t < mem; ++t) used |= 1 << c->order[t];
+        int ns = 0;
+        while (used & (1 << ns)) ++ns;
+        c->new_slot = ns;
+        c->old_count = mem;
+        for (int t = 0; t < mem; ++t) c->old_slots[t] = c->order[t];
+    } else {
+        c->new_slot = c->order[0];
+        c->old_count = mem - 1;
+        for (int t = 1; t < mem; ++t) c->old_slots[t - 1] = c->order[t];
+    }
+}
+
+__device__ void finish_inner_test(Ctrl* c) {
+    const double zn = sqrt(fmax(c->znorm2, 0.0));
+    const double zs = c->inner_scale ? c->rho * zn : zn;
+    const double thr = c->inner_rel * fmax(zs, c->tol * (1.0 + c->bnorm_inf));
+    const double gn = sqrt(fmax(c->gnorm2, 0.0));
+    if (!isfinite(gn) || !isfinite(zn)) {
+        c->status = 5;                          // LORADS_ERR_NUMERIC
+        c->solve_done = 1;
+        return;
+    }
+    if (gn <= thr || c->inner_k >= c->max_inner) {
+        c->inner_done = 1;
+        c->phase = PHASE_OUTER;
+        return;
+    }
+    two_loop_coeffs(c);
+    plan_next_slot(c, c->lbfgs_mem);
+}
+
+// ---------------------------------------------------------------- root kernel
+// Folds the line-search partials of the iteration, forms a1..a4 and tau.
+// a4 = <G, D> (the directional derivative; equal to p1 - y~^T q1 of App. A.2).
+__global__ void k_ctrl_root(Ctrl* c, const double* part_dir, int nb_dir, const double* part_ls, int nb_ls,
+                            const double* part_cons, int nb_cons) {
+    if (gated_off(c, PH_INNER)) return;
+    __shared__ double sd[PD_N], sl[PL_N], sc[PL_N];
+    fold_parts(part_dir, nb_dir, PD_N, sd);
+    fold_parts(part_ls, nb_ls, PL_N, sl);
+    if (part_cons != nullptr) fold_parts(part_cons, nb_cons, PL_N, sc);
+    else if (threadIdx.x < PL_N) sc[threadIdx.x] = 0.0;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double rho = c->rho;
+    const double yq2 = sl[PL_YQ2] + sc[PL_YQ2];
+    const double q1q1 = sl[PL_Q1Q1] + sc[PL_Q1Q1];
+    const double q1q2 = sl[PL_Q1Q2] + sc[PL_Q1Q2];
+    const double q2q2 = sl[PL_Q2Q2] + sc[PL_Q2Q2];
+    c->gD = sd[PD_GD];
+    c->DD = sd[PD_DD];
+    c->a[0] = 0.5 * rho * q2q2;
+    c->a[1] = rho * q1q2;
+    c->a[2] = sl[PL_P2] - yq2 + 0.5 * rho * q1q1;
+    c->a[3] = sd[PD_GD];
+    c->inner_k += 1;
+    c->total_inner += 1;
+    const double tau = quartic_step(c->a);
+    bool finite = isfinite(c->a[0]) && isfinite(c->a[1]) && isfinite(c->a[2]) && isfinite(c->a[3]);
+    if (!finite) {
+        c->status = 5;
+        c->solve_done = 1;
+        c->step_ok = 0;
+        return;
+    }
+    if (tau > 0.0) {
+        c->tau = tau;
+        c->step_ok = 1;
+    } else {
+        c->tau = 0.0;
+        c->step_ok = 0;
+        if (c->mem_count > 0) {
+            mem_clear(c);               // next direction is -G
+        } else {
+            c->inner_done = 1;          // no descent along -G: leave the inner loop
+            c->phase = PHASE_OUTER;
+        }
+    }
+}
+
+// Standalone variant for lorads_linesearch_coeffs: paper's a4 = p1 - y~^T q1.
+__global__ void k_ls_finish(const double* part_ls, int nb_ls, const double* part_cons, int nb_cons,
+                            double rho, double* out /* a[4], tau */) {
+    __shared__ double sl[PL_N], sc[PL_N];
+    fold_parts(part_ls, nb_ls, PL_N, sl);
+    if (part_cons != nullptr) fold_parts(part_cons, nb_cons, PL_N, sc);
+    else if (threadIdx.x < PL_N) sc[threadIdx.x] = 0.0;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double yq1 = sl[PL_YQ1] + sc[PL_YQ1];
+    const double yq2 = sl[PL_YQ2] + sc[PL_YQ2];
+    const double q1q1 = sl[PL_Q1Q1] + sc[PL_Q1Q1];
+    const double q1q2 = sl[PL_Q1Q2] + sc[PL_Q1Q2];
+    const double q2q2 = sl[PL_Q2Q2] + sc[PL_Q2Q2];
+    out[0] = 0.5 * rho * q2q2;
+    out[1] = rho * q1q2;
+    out[2] = sl[PL_P2] - yq2 + 0.5 * rho * q1q1;
+    out[3] = sl[PL_P1] - yq1;
+    out[4] = quartic_step(out);
+}
+
+// ---------------------------------------------------------------- history kernel
+// mode HIST_STEP: after a step, store the new pair (s = tau D, y = G' - G) if
+// its curvature <y,s> is positive enough, else clear the memory; then test the
+// inner stop and prepare the next direction.
+// mode HIST_RESET: start of an inner loop (memory empty).
+__global__ void k_ctrl_hist(Ctrl* c, int mode, const double* part_upd, int nb_upd,
+                            const double* part_ytil, int nb_ytil) {
+    const bool reset = (mode == HIST_RESET);
+    if (gated_off(c, reset ? PH_OUTER : PH_INNER)) return;
+    const bool fresh = reset || c->step_ok;
+    __shared__ double su[PU_N], sy[PC_N];
+    if (fresh) {
+        fold_parts(part_upd, nb_upd, PU_N, su);
+        if (part_ytil != nullptr) fold_parts(part_ytil, nb_ytil, PC_N, sy);
+        else if (threadIdx.x < PC_N) sy[threadIdx.x] = 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    if (fresh) {
+        c->gnorm2 = su[PU_GG];
+        c->znorm2 = su[PU_ZZ] + sy[PC_ZZ];
+    }
+    if (reset) {
+        mem_clear(c);
+        c->inner_k = 0;
+        c->inner_done = 0;
+        c->step_ok = 0;
+        c->phase = PHASE_INNER;
+    } else if (c->step_ok) {
+        const double ys = su[PU_SYN], yy = su[PU_YYN], ss = su[PU_SSN];
+        if (ys > 1e-16 * sqrt(fmax(yy, 0.0) * fmax(ss, 0.0)) && ys > 0.0) {
+            const int ns = c->new_slot;
+            for (int t = 0; t < c->old_count; ++t) {
+                const int v = c->old_slots[t];
+                const double* q = su + PU_FIXED + PU_PER_OLD * t;
+                c->g_s[v] = q[0];
+                c->g_y[v] = q[1];
+                c->SY[ns][v] = q[2];
+                c->SY[v][ns] = q[3];
+                c->YY[ns][v] = q[4];
+                c->YY[v][ns] = q[4];
+            }
+            c->SY[ns][ns] = ys;
+            c->YY[ns][ns] = yy;
+            c->g_s[ns] = su[PU_GSN];
+            c->g_y[ns] = su[PU_GYN];
+            // order: keep old slots (oldest first), append the new one
+            for (int t = 0; t < c->old_count; ++t) c->order[t] = c->old_slots[t];
+            c->order[c->old_count] = ns;
+            c->mem_count = c->old_count + 1;
+        } else {
+            mem_clear(c);
+        }
+    }
+    finish_inner_test(c);
+}
+
+// ---------------------------------------------------------------- outer kernel
+// Multiplier step of Sec. 2.1 has been applied by the constraint pass (y <- y~);
+// here: err1 = ||A(RR^T) - b|| / (1 + ||b||_inf), err3 of Sec. 4.1, stop test,
+// penalty growth when err1 did not shrink enough, and the rank-update request
+// of App. A.1 when the inner loop hit its cap in consecutive outer steps.
+__global__ void k_ctrl_outer(Ctrl* c, const double* part_cons, int nb_cons, const double* part_obj, int nb_obj) {
+    if (gated_off(c, PH_OUTER)) return;
+    __shared__ double sc[PC_N], so[PO_N];
+    fold_parts(part_cons, nb_cons, PC_N, sc);
+    fold_parts(part_obj, nb_obj, PO_N, so);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double err1 = sqrt(fmax(sc[PC_ZZ], 0.0)) / (1.0 + c->bnorm_inf);
+    const double obj = so[PO_CRR];
+    const double dual = sc[PC_BY];
+    const double err3 = (obj - dual) / (1.0 + fabs(obj) + fabs(dual));
+    c->err1 = err1;
+    c->err3 = err3;
+    c->primal_obj = obj;
+    c->dual_obj = dual;
+    c->outer += 1;
+    c->last_iter_rho = c->rho;
+    if (!isfinite(err1) || !isfinite(err3)) {
+        c->status = 5;
+        c->solve_done = 1;
+        return;
+    }
+    if (err1 <= c->tol && fabs(err3) <= c->tol) {
+        c->status = 0;
+        c->solve_done = 1;
+        return;
+    }
+    const bool capped = c->inner_k >= c->max_inner;
+    if (err1 > c->infeas_decrease * c->err1_prev && (c->rho_policy == 0 || !capped))
+        c->rho = fmin(c->rho * c->rho_growth, c->rho_max);
+    c->err1_prev = err1;
+    if (c->outer >= c->max_outer) {
+        c->status = 6;                          // LORADS_ERR_MAXITER
+        c->solve_done = 1;
+        return;
+    }
+    c->hit_cap_streak = capped ? c->hit_cap_streak + 1 : 0;
+    if (c->hit_cap_streak >= c->rank_threshold) {
+        c->hit_cap_streak = 0;
+        c->pause = 1;                           // host grows the rank
+    }
+}
+
+// Start of a solve: err1 at R0 and the outer phase for the first gradient.
+__global__ void k_ctrl_init(Ctrl* c, const double* part_cons, int nb_cons, const double* part_obj, int nb_obj) {
+    __shared__ double sc[PC_N], so[PO_N];
+    fold_parts(part_cons, nb_cons, PC_N, sc);
+    fold_parts(part_obj, nb_obj, PO_N, so);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    c->err1_prev = sqrt(fmax(sc[PC_ZZ], 0.0)) / (1.0 + c->bnorm_inf);
+    c->err1 = c->err1_prev;
+    c->primal_obj = so[PO_CRR];
+    c->phase = PHASE_OUTER;
+    c->solve_done = 0;
+    c->pause = 0;
+}
+
+// Resume after the host handled a pause (rank update): run the outer tail.
+__global__ void k_ctrl_resume(Ctrl* c) {
+    c->pause = 0;
+    c->phase = PHASE_OUTER;
+}
+
+// ---------------------------------------------------------------- misc kernels
+__global__ void k_fold_to(const double* part, int nb, int NQ, double* out) {
+    __shared__ double s[32];
+    fold_parts(part, nb, NQ, s);
+    __syncthreads();
+    if (threadIdx.x < NQ) out[threadIdx.x] = s[threadIdx.x];
+}
+
+template <typename T>
+__global__ void k_sumsq(int64_t n, int ld, int r, const T* X, double* part) {
+    double acc[1] = {0.0};
+    const int64_t total = n * (int64_t)r;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / r;
+        const int c = (int)(e - i * r);
+        const double v = double(X[i * ld + c]);
+        acc[0] += v * v;
+    }
+    block_partials<1>(acc, part);
+}
+
+__device__ __forceinline__ uint64_t splitmix_out(uint64_t state) {
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Columns r_old..r_new-1 of X get scale * N(0,1): entry (i, c) uses outputs
+// 2e and 2e+1 (e = i*k + c - r_old, k = r_new - r_old) of the SplitMix64
+// sequence started at seed ^ (stream * golden), Box-Muller on (u1, u2).
+template <typename T>
+__global__ void k_rank_columns(int64_t n, int ld, int r_old, int r_new, double scale, uint64_t seed,
+                               uint64_t stream, T* X) {
+    const uint64_t golden = 0x9E3779B97F4A7C15ull;
+    const uint64_t base = seed ^ (stream * golden);
+    const int k = r_new - r_old;
+    const int64_t total = n * (int64_t)k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / k;
+        const int c = (int)(e - i * k);
+        const uint64_t x1 = splitmix_out(base + (uint64_t)(2 * e + 1) * golden);
+        const uint64_t x2 = splitmix_out(base + (uint64_t)(2 * e + 2) * golden);
+        const double u1 = (double)((x1 >> 11) + 1) * (1.0 / 9007199254740992.0);
+        const double u2 = (double)(x2 >> 11) * (1.0 / 9007199254740992.0);
+        const double g = sqrt(-2.0 * log(u1)) * cos(2.0 * 3.141592653589793 * u2);
+        X[i * ld + r_old + c] = T(scale * g);
+    }
+}
+
+// Row i of X gets rows of N(0,1) draws (same generator, stream = ~0), scaled
+// to unit norm when unit_rows (diagonal constraints) or by `scale` otherwise.
+template <typename T>
+__global__ void k_random_start(int64_t n, int ld, int r, uint64_t seed, int unit_rows, double scale, T* X) {
+    const uint64_t golden = 0x9E3779B97F4A7C15ull;
+    const uint64_t base = seed ^ (~0ull * golden);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double nrm = 0.0;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int c = 0; c < r; ++c) {
+                const int64_t e = i * r + c;
+                const uint64_t x1 = splitmix_out(base + (uint64_t)(2 * e + 1) * golden);
+                const uint64_t x2 = splitmix_out(base + (uint64_t)(2 * e + 2) * golden);
+                const double u1 = (double)((x1 >> 11) + 1) * (1.0 / 9007199254740992.0);
+                const double u2 = (double)(x2 >> 11) * (1.0 / 9007199254740992.0);
+                const double g = sqrt(-2.0 * log(u1)) * cos(2.0 * 3.141592653589793 * u2);
+                if (pass == 0) nrm += g * g;
+                else X[i * ld + c] = T(unit_rows ? g / sqrt(nrm) : scale * g);
+            }
+        }
+    }
+}
+
+template <typename TI, typename TO>
+__global__ void k_convert(int64_t n, int ld_in, int ld_out, int r, const TI* in, TO* out) {
+    const int64_t total = n * (int64_t)ld_out;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / ld_out;
+        const int c = (int)(e - i * ld_out);
+        out[e] = (c < r) ? TO(in[i * ld_in + c]) : TO(0.0);
+    }
+}
+
+// ---------------------------------------------------------------- host launchers
+void ctrl_root(cudaStream_t s, Ctrl* c, const double* pd, int nbd, const double* pl, int nbl, const double* pc, int nbc) {
+    k_ctrl_root<<<1, 256, 0, s>>>(c, pd, nbd, pl, nbl, pc, nbc);
+}
+void ls_finish(cudaStream_t s, const double* pl, int nbl, const double* pc, int nbc, double rho, double* out) {
+    k_ls_finish<<<1, 256, 0, s>>>(pl, nbl, pc, nbc, rho, out);
+}
+void ctrl_hist(cudaStream_t s, Ctrl* c, int mode, const double* pu, int nbu, const double* py, int nby) {
+    k_ctrl_hist<<<1, 256, 0, s>>>(c, mode, pu, nbu, py, nby);
+}
+void ctrl_outer(cudaStream_t s, Ctrl* c, const double* pc, int nbc, const double* po, int nbo) {
+    k_ctrl_outer<<<1, 256, 0, s>>>(c, pc, nbc, po, nbo);
+}
+void ctrl_init(cudaStream_t s, Ctrl* c, const double* pc, int nbc, const double* po, int nbo) {
+    k_ctrl_init<<<1, 256, 0, s>>>(c, pc, nbc, po, nbo);
+}
+void ctrl_resume(cudaStream_t s, Ctrl* c) { k_ctrl_resume<<<1, 1, 0, s>>>(c); }
+void quartic_step_dev(cudaStream_t s, const double* a, double* tau) { k_quartic_step<<<1, 1, 0, s>>>(a, tau); }
+void fold_to(cudaStream_t s, const double* part, int nb, int NQ, double* out) {
+    k_fold_to<<<1, 256, 0, s>>>(part, nb, NQ, out);
+}
+
+template <typename T>
+void sumsq(cudaStream_t s, int64_t n, int ld, int r, const void* X, double* part, int blocks) {
+    k_sumsq<T><<<blocks, kThreads, 0, s>>>(n, ld, r, static_cast<const T*>(X), part);
+}
+template void sumsq<double>(cudaStream_t, int64_t, int, int, const void*, double*, int);
+template void sumsq<float>(cudaStream_t, int64_t, int, int, const void*, double*, int);
+template void sumsq<dfloat>(cudaStream_t, int64_t, int, int, const void*, double*, int);
+
+template <typename T>
+void rank_columns(cudaStream_t s, int64_t n, int ld, int r_old, int r_new, double scale, uint64_t seed,
+                  uint64_t stream, void* X, int blocks) {
+    k_rank_columns<T><<<blocks, kThreads, 0, s>>>(n, ld, r_old, r_new, scale, seed, stream, static_cast<T*>(X));
+}
+template void rank_columns<double>(cudaStream_t, int64_t, int, int, int, double, uint64_t, uint64_t, void*, int);
+template void rank_columns<float>(cudaStream_t, int64_t, int, int, int, double, uint64_t, uint64_t, void*, int);
+template void rank_columns<dfloat>(cudaStream_t, int64_t, int, int, int, double, uint64_t, uint64_t, void*, int);
+
+template <typename T>
+void random_start(cudaStream_t s, int64_t n, int ld, int r, uint64_t seed, int unit_rows, double scale, void* X,
+                  int blocks) {
+    k_random_start<T><<<blocks, kThreads, 0, s>>>(n, ld, r, seed, unit_rows, scale, static_cast<T*>(X));
+}
+template void random_start<double>(cudaStream_t, int64_t, int, int, uint64_t, int, double, void*, int);
+template void random_start<float>(cudaStream_t, int64_t, int, int, uint64_t, int, double, void*, int);
+template void random_start<dfloat>(cudaStream_t, int64_t, int, int, uint64_t, int, double, void*, int);
+
+template <typename TI, typename TO>
+void convert(cudaStream_t s, int64_t n, int ld_in, int ld_out, int r, const void* in, void* out, int blocks) {
+    k_convert<TI, TO><<<blocks, kThreads, 0, s>>>(n, ld_in, ld_out, r, static_cast<const TI*>(in),
+                                                   static_cast<TO*>(out));
+}
+template void convert<double, double>(cudaStream_t, int64_t, int, int, int, const void*, void*, int);
+template void convert<double, float>(cudaStream_t, int64_t, int, int, int, const void*, void*, int);
+template void convert<float, double>(cudaStream_t, int64_t, int, int, int, const void*, void*, int);
+template void convert<float, float>(cudaStream_t, int64_t, int, int, int, const void*, void*, int);
+template void convert<double, dfloat>(cudaStream_t, int64_t, int, int, int, const void*, void*, int);
+template void convert<dfloat, double>(cudaStream_t, int64_t, int, int, int, const void*, void*, int);
+template void convert<dfloat, dfloat>(cudaStream_t, int64_t, int, int, int, const void*, void*, int);
+
+}  // namespace lorads

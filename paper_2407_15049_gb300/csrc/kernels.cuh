@@ -1,0 +1,698 @@
+// Streaming kernels of the LoRADS hot path (templates; instantiated per
+// precision in kern_*.cu).  Every kernel is memory-bound by design: rows of the
+// n x ld factors are read with 16-byte vector loads by groups of L lanes,
+// sparse rows are gathered through L2, and all reductions end in per-block FP64
+// partial sums that a single-block control kernel folds in a fixed order.
+#pragma once
+
+#include <type_traits>
+#include "common.cuh"
+
+namespace lorads {
+
+// ------------------------------------------------------------------ problem arrays
+struct ProbDev {
+    int64_t n, m;
+    // C: full symmetric CSR
+    const int64_t* c_rowptr;
+    const int32_t* c_col;
+    const double* c_val;
+    const float* c_val32;
+    const dfloat* c_valdf;
+    // diagonal constraints by row: constraint index (-1: none) and coefficient
+    const int32_t* dk;
+    const double* da;
+    // off-diagonal constraints as a symmetric pattern: slot -> (column, constraint, coef)
+    const int64_t* a_rowptr;
+    const int32_t* a_col;
+    const int32_t* a_k;
+    const double* a_a;
+    // constraint list, diagonal constraints first: (row <= col, coef, original index)
+    const int32_t* k_row;
+    const int32_t* k_col;
+    const double* k_a;
+    const int32_t* k_id;
+    int64_t m_diag, m_off;
+    const double* b;
+};
+
+// ------------------------------------------------------------------ gating
+// Kernels of the captured iteration graph check the control block first and
+// return at once when the current phase does not need them.
+enum { PH_ALWAYS = 0, PH_INNER = 1, PH_STEP = 2, PH_OUTER = 3 };
+enum { PHASE_INNER = 0, PHASE_OUTER = 1 };
+
+__device__ __forceinline__ bool gated_off(const Ctrl* g, int ph) {
+    if (g == nullptr || ph == PH_ALWAYS) return false;
+    if (g->solve_done | g->pause) return true;
+    if (ph == PH_OUTER) return g->phase != PHASE_OUTER;
+    if (g->phase != PHASE_INNER) return true;
+    if (ph == PH_STEP) return g->step_ok == 0;
+    return false;
+}
+
+template <typename T>
+using arith_t = typename Arith<T>::type;
+
+// precision rank of an arithmetic type: float < double-float < double
+template <typename T> struct PrecRank;
+template <> struct PrecRank<float> { static constexpr int v = 0; };
+template <> struct PrecRank<dfloat> { static constexpr int v = 1; };
+template <> struct PrecRank<double> { static constexpr int v = 2; };
+
+template <int R> struct RankType;
+template <> struct RankType<0> { using type = float; };
+template <> struct RankType<1> { using type = dfloat; };
+template <> struct RankType<2> { using type = double; };
+
+// wider of the arithmetic types of two storage types
+template <typename A, typename B>
+using wide_t = typename RankType<(PrecRank<arith_t<A>>::v > PrecRank<arith_t<B>>::v ? PrecRank<arith_t<A>>::v
+                                                                                   : PrecRank<arith_t<B>>::v)>::type;
+
+// partial-sum type: double on the all-FP64 path, double-float otherwise (no FP64 pipe)
+template <typename A, typename B>
+using part_t = std::conditional_t<std::is_same_v<arith_t<A>, double> && std::is_same_v<arith_t<B>, double>,
+                                  double, dfloat>;
+
+// value type of C entries multiplied against rows of type TX
+template <typename TX>
+using cval_t = arith_t<TX>;
+
+template <typename TV> __device__ __forceinline__ const TV* cvals(const ProbDev& p);
+template <> __device__ __forceinline__ const double* cvals<double>(const ProbDev& p) { return p.c_val; }
+template <> __device__ __forceinline__ const float* cvals<float>(const ProbDev& p) { return p.c_val32; }
+template <> __device__ __forceinline__ const dfloat* cvals<dfloat>(const ProbDev& p) { return p.c_valdf; }
+
+// read-only scalar loads
+__device__ __forceinline__ double ldv(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ldv(const float* p) { return __ldg(p); }
+__device__ __forceinline__ dfloat ldv(const dfloat* p) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return dfloat(v.x, v.y);
+}
+
+// Warp-uniform row loop: each warp owns 32/L consecutive rows per trip, so the
+// group shuffles below always see the full warp.
+struct RowLoop {
+    int L, lig, gw, rows_per_warp;
+    int64_t first, stride;
+    __device__ __forceinline__ explicit RowLoop(int L_) : L(L_) {
+        lig = threadIdx.x & (L - 1);
+        gw = (threadIdx.x & 31) / L;
+        rows_per_warp = 32 / L;
+        const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+        const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        first = warp * rows_per_warp;
+        stride = nwarps * rows_per_warp;
+    }
+};
+
+// Row helpers: lane `lig` of a group of L handles units c*L + lig < Q.
+// Units past Q are zero on load and skipped on store.
+template <typename T, int CPL>
+__device__ __forceinline__ void load_row(Unit<T> (&u)[CPL], const T* base, int64_t row, int ld, int L, int Q, int lig) {
+    const T* p = base + row * (int64_t)ld + lig * 4;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+        if (c * L + lig < Q) u[c].load(p + c * L * 4);
+        else
+#pragma unroll
+            for (int e = 0; e < 4; ++e) u[c].v[e] = 0;
+    }
+}
+
+template <typename T, int CPL>
+__device__ __forceinline__ void load_row_stream(Unit<T> (&u)[CPL], const T* base, int64_t row, int ld, int L, int Q,
+                                                int lig) {
+    const T* p = base + row * (int64_t)ld + lig * 4;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+        if (c * L + lig < Q) u[c].load_stream(p + c * L * 4);
+        else
+#pragma unroll
+            for (int e = 0; e < 4; ++e) u[c].v[e] = 0;
+    }
+}
+
+template <typename T, int CPL>
+__device__ __forceinline__ void store_row(const Unit<T> (&u)[CPL], T* base, int64_t row, int ld, int L, int Q, int lig) {
+    T* p = base + row * (int64_t)ld + lig * 4;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c)
+        if (c * L + lig < Q) u[c].store_stream(p + c * L * 4);
+}
+
+template <typename A, typename T1, typename T2, int CPL>
+__device__ __forceinline__ A dot_units(const Unit<T1> (&x)[CPL], const Unit<T2> (&y)[CPL]) {
+    A s = A(0);
+#pragma unroll
+    for (int c = 0; c < CPL; ++c)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) s = fma(A(x[c].v[e]), A(y[c].v[e]), s);
+    return s;
+}
+
+// ================================================================== SpMM over C
+// out = C X  (+ the diagonal-constraint part -A*(v) X when v != nullptr),
+// optional epilogues:
+//   EPI_LS : line-search partials at R (= argument R) along D (= X):
+//            p1 = 2<CD, R>, p2 = <CD, D>, and for diagonal constraints
+//            sum y~ q1, sum y~ q2, sum q1^2, sum q1 q2, sum q2^2
+//   EPI_OBJ: <C X, X> (objective with X = R)
+enum { EPI_NONE = 0, EPI_LS = 1, EPI_OBJ = 2 };
+
+template <typename TX, typename TO, typename TR, int CPL, int EPI>
+__global__ void __launch_bounds__(kThreads)
+k_spmm_c(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int L, int Q,
+         const double* __restrict__ v, int write_out,
+         const TR* __restrict__ R, const double* __restrict__ y, const double* __restrict__ zrow,
+         const Ctrl* ctrl, double rho_arg, double* __restrict__ part, const Ctrl* gate, int ph) {
+    if (gated_off(gate, ph)) return;
+    using A = arith_t<TO>;
+    using TV = cval_t<TX>;
+    using PA = part_t<TO, TR>;
+    constexpr int NQ = EPI == EPI_LS ? PL_N : (EPI == EPI_OBJ ? PO_N : 1);
+    PA accq[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) accq[q] = PA(0);
+    const double rho = ctrl ? ctrl->rho : rho_arg;
+    const TV* __restrict__ cv = cvals<TV>(p);
+    RowLoop rl(L);
+    for (int64_t base = rl.first; base < p.n; base += rl.stride) {
+        const int64_t i = base + rl.gw;
+        const bool act = i < p.n;
+        A acc[CPL][4];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[c][e] = A(0);
+        if (act) {
+            int64_t s = __ldg(p.c_rowptr + i);
+            const int64_t e_ = __ldg(p.c_rowptr + i + 1);
+            constexpr int UN = CPL == 1 ? 4 : 2;       // nonzeros in flight per lane
+            for (; s + UN <= e_; s += UN) {
+                int j[UN];
+                A w[UN];
+#pragma unroll
+                for (int u = 0; u < UN; ++u) {
+                    j[u] = __ldg(p.c_col + s + u);
+                    w[u] = A(ldv(cv + s + u));
+                }
+                Unit<TX> x[UN][CPL];
+#pragma unroll
+                for (int u = 0; u < UN; ++u) load_row<TX, CPL>(x[u], X, j[u], ld, L, Q, rl.lig);
+#pragma unroll
+                for (int u = 0; u < UN; ++u)
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) acc[c][e] = fma(w[u], A(x[u][c].v[e]), acc[c][e]);
+            }
+            for (; s < e_; ++s) {
+                const int j0 = __ldg(p.c_col + s);
+                const A w0 = A(ldv(cv + s));
+                Unit<TX> x0[CPL];
+                load_row<TX, CPL>(x0, X, j0, ld, L, Q, rl.lig);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[c][e] = fma(w0, A(x0[c].v[e]), acc[c][e]);
+            }
+            if (v != nullptr && p.dk != nullptr) {
+                const int k = __ldg(p.dk + i);
+                if (k >= 0) {
+                    const A w = A(-__ldg(p.da + i) * __ldg(v + k));
+                    Unit<TX> xi[CPL];
+                    load_row<TX, CPL>(xi, X, i, ld, L, Q, rl.lig);
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) acc[c][e] = fma(w, A(xi[c].v[e]), acc[c][e]);
+                }
+            }
+            if (write_out) {
+                Unit<TO> o[CPL];
+#pragma unroll
+                for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) o[c].v[e] = acc[c][e];
+                store_row<TO, CPL>(o, out, i, ld, L, Q, rl.lig);
+            }
+        }
+        if constexpr (EPI == EPI_OBJ) {
+            if (act) {
+                Unit<TX> xi[CPL];
+                load_row<TX, CPL>(xi, X, i, ld, L, Q, rl.lig);
+                A t = A(0);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) t = fma(acc[c][e], A(xi[c].v[e]), t);
+                accq[PO_CRR] += PA(t);
+            }
+        }
+        if constexpr (EPI == EPI_LS) {
+            using AW = wide_t<TR, TX>;           // |r|^2 (when not cached) and <CD, R>
+            using AD = arith_t<TX>;              // products of D with D and with R
+            AW t_p1 = AW(0), t_rr = AW(0);
+            AD t_p2 = AD(0), t_rd = AD(0), t_dd = AD(0);
+            if (act) {
+                Unit<TX> di[CPL];
+                Unit<TR> ri[CPL];
+                load_row<TX, CPL>(di, X, i, ld, L, Q, rl.lig);
+                load_row_stream<TR, CPL>(ri, R, i, ld, L, Q, rl.lig);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const AD d = AD(di[c].v[e]);
+                        const AD rlow = AD(ri[c].v[e]);
+                        t_p2 = fma(AD(acc[c][e]), d, t_p2);
+                        t_rd = fma(rlow, d, t_rd);
+                        t_dd = fma(d, d, t_dd);
+                        if (zrow == nullptr) {
+                            const AW r = AW(ri[c].v[e]);
+                            t_p1 = fma(AW(acc[c][e]), r, t_p1);
+                            t_rr = fma(r, r, t_rr);
+                        }
+                    }
+            }
+            accq[PL_P2] += PA(t_p2);
+            if (zrow == nullptr) accq[PL_P1] += PA(AW(2) * t_p1);
+            if (p.dk != nullptr) {
+                if (zrow == nullptr) t_rr = group_sum(t_rr, L);
+                t_rd = group_sum(t_rd, L);
+                t_dd = group_sum(t_dd, L);
+                if (act && rl.lig == 0) {
+                    const int k = __ldg(p.dk + i);
+                    if (k >= 0) {
+                        const double a = __ldg(p.da + i);
+                        const double z = zrow ? __ldg(zrow + i) : a * double(t_rr) - __ldg(p.b + k);
+                        const double yt = __ldg(y + k) - rho * z;
+                        const double q1 = 2.0 * a * double(t_rd);
+                        const double q2 = a * double(t_dd);
+                        accq[PL_YQ1] += PA(yt * q1);
+                        accq[PL_YQ2] += PA(yt * q2);
+                        accq[PL_Q1Q1] += PA(q1 * q1);
+                        accq[PL_Q1Q2] += PA(q1 * q2);
+                        accq[PL_Q2Q2] += PA(q2 * q2);
+                    }
+                }
+            }
+        }
+    }
+    if constexpr (EPI != EPI_NONE) block_partials<NQ>(accq, part);
+}
+
+// ================================================================== SpMM over the
+// off-diagonal constraint pattern:  out = beta_acc * out + alpha * A*_off(v) X
+template <typename TX, typename TO, int CPL>
+__global__ void __launch_bounds__(kThreads)
+k_spmm_a(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int L, int Q,
+         const double* __restrict__ v, double alpha, int accumulate, const Ctrl* gate, int ph) {
+    if (gated_off(gate, ph)) return;
+    using A = arith_t<TO>;
+    RowLoop rl(L);
+    for (int64_t base = rl.first; base < p.n; base += rl.stride) {
+        const int64_t i = base + rl.gw;
+        if (i >= p.n) continue;
+        A acc[CPL][4];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[c][e] = A(0);
+        const int64_t s0 = __ldg(p.a_rowptr + i), s1 = __ldg(p.a_rowptr + i + 1);
+        for (int64_t s = s0; s < s1; ++s) {
+            const int j = __ldg(p.a_col + s);
+            const A w = A(alpha * __ldg(p.a_a + s) * __ldg(v + __ldg(p.a_k + s)));
+            Unit<TX> x[CPL];
+            load_row<TX, CPL>(x, X, j, ld, L, Q, rl.lig);
+#pragma unroll
+            for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[c][e] = fma(w, A(x[c].v[e]), acc[c][e]);
+        }
+        Unit<TO> o[CPL];
+        if (accumulate) {
+            load_row<TO, CPL>(o, out, i, ld, L, Q, rl.lig);
+#pragma unroll
+            for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) o[c].v[e] = arith_t<TO>(o[c].v[e]) + acc[c][e];
+        } else {
+#pragma unroll
+            for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) o[c].v[e] = acc[c][e];
+        }
+        store_row<TO, CPL>(o, out, i, ld, L, Q, rl.lig);
+    }
+}
+
+// ================================================================== constraint pass
+// One group of L lanes per constraint t in [k0, k1) of the ordered list
+// (diagonal constraints first).  With f = 1 (i == j) or 2 (i < j):
+//   CONS_EVAL: out[k] = a (u_i.v_j + [i!=j] u_j.v_i)                  = <A_k, U V^T>
+//   CONS_LS  : z = f a r_i.r_j - b, y~ = y - rho z, q1 = f a (r_i.d_j + d_i.r_j),
+//              q2 = f a d_i.d_j; partials of y~q1, y~q2, q1^2, q1q2, q2^2
+//   CONS_YTIL: out[k] = y~ ;  partial |z|^2
+//   CONS_YUPD: y[k] <- y~  ;  partials |z|^2, b^T y_new
+//   CONS_ZZ  : partial |z|^2
+enum { CONS_EVAL = 0, CONS_LS = 1, CONS_YTIL = 2, CONS_YUPD = 3, CONS_ZZ = 4 };
+
+template <typename TU, typename TV, int CPL, int MODE>
+__global__ void __launch_bounds__(kThreads)
+k_cons(ProbDev p, int64_t k0, int64_t k1, const TU* __restrict__ U, const TV* __restrict__ V, int ld, int L, int Q,
+       double* y, double* __restrict__ out, double* zk, const Ctrl* ctrl, double rho_arg,
+       double* __restrict__ part, const Ctrl* gate, int ph) {
+    if (gated_off(gate, ph)) return;
+    constexpr int NQ = MODE == CONS_LS ? PL_N : PC_N;
+    using PA = part_t<TU, TV>;
+    PA accq[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) accq[q] = PA(0);
+    const double rho = ctrl ? ctrl->rho : rho_arg;
+    const bool same = (const void*)U == (const void*)V;
+    using AU = wide_t<TU, TU>;
+    using AW = wide_t<TU, TV>;
+    using AV = wide_t<TV, TV>;
+    RowLoop rl(L);
+    const int64_t cnt = k1 - k0;
+    for (int64_t base = rl.first; base < cnt; base += rl.stride) {
+        const int64_t t = k0 + base + rl.gw;
+        const bool act = t < k1;
+        int i = 0, j = 0;
+        if (act) {
+            i = __ldg(p.k_row + t);
+            j = __ldg(p.k_col + t);
+        }
+        const bool diag = (i == j);
+        // dots of the gathered rows; partial per lane, then group sums
+        AU s_uu = AU(0);          // u_i.u_j (EVAL with U==V, and R-only modes)
+        AW s_uv = AW(0), s_vu = AW(0);   // u_i.v_j, u_j.v_i
+        AV s_vv = AV(0);          // v_i.v_j
+        if (act) {
+            Unit<TU> ui[CPL], uj[CPL];
+            load_row<TU, CPL>(ui, U, i, ld, L, Q, rl.lig);
+            if (!diag) load_row<TU, CPL>(uj, U, j, ld, L, Q, rl.lig);
+            if constexpr (MODE == CONS_EVAL) {
+                if (same || diag) {
+                    if (same) {
+                        s_uu = diag ? dot_units<AU>(ui, ui) : dot_units<AU>(ui, uj);
+                    } else {
+                        Unit<TV> vi[CPL];
+                        load_row<TV, CPL>(vi, V, i, ld, L, Q, rl.lig);
+                        s_uv = dot_units<AW>(ui, vi);
+                    }
+                } else {
+                    Unit<TV> vi[CPL], vj[CPL];
+                    load_row<TV, CPL>(vi, V, i, ld, L, Q, rl.lig);
+                    load_row<TV, CPL>(vj, V, j, ld, L, Q, rl.lig);
+                    s_uv = dot_units<AW>(ui, vj);
+                    s_vu = dot_units<AW>(uj, vi);
+                }
+            } else {
+                if (MODE != CONS_LS || zk == nullptr)
+                    s_uu = diag ? dot_units<AU>(ui, ui) : dot_units<AU>(ui, uj);
+                if constexpr (MODE == CONS_LS) {
+                    Unit<TV> di[CPL], dj[CPL];
+                    load_row<TV, CPL>(di, V, i, ld, L, Q, rl.lig);
+                    if (diag) {
+                        s_uv = dot_units<AW>(ui, di);
+                        s_vu = s_uv;
+                        s_vv = dot_units<AV>(di, di);
+                    } else {
+                        load_row<TV, CPL>(dj, V, j, ld, L, Q, rl.lig);
+                        s_uv = dot_units<AW>(ui, dj);
+                        s_vu = dot_units<AW>(di, uj);
+                        s_vv = dot_units<AV>(di, dj);
+                    }
+                }
+            }
+        }
+        s_uu = group_sum(s_uu, L);
+        if constexpr (MODE == CONS_EVAL || MODE == CONS_LS) {
+            s_uv = group_sum(s_uv, L);
+            s_vu = group_sum(s_vu, L);
+            s_vv = group_sum(s_vv, L);
+        }
+        if (act && rl.lig == 0) {
+            const double a = __ldg(p.k_a + t);
+            const int kid = __ldg(p.k_id + t);
+            const double f = diag ? 1.0 : 2.0;
+            if constexpr (MODE == CONS_EVAL) {
+                double val;
+                if (same) val = f * a * double(s_uu);
+                else if (diag) val = a * double(s_uv);
+                else val = a * (double(s_uv) + double(s_vu));
+                out[kid] = val;
+            } else {
+                const double z = (MODE == CONS_LS && zk != nullptr) ? zk[kid]
+                                                                    : f * a * double(s_uu) - __ldg(p.b + kid);
+                if constexpr (MODE == CONS_LS) {
+                    const double yt = y[kid] - rho * z;
+                    const double q1 = f * a * (double(s_uv) + double(s_vu));
+                    const double q2 = f * a * double(s_vv);
+                    accq[PL_YQ1] += PA(yt * q1);
+                    accq[PL_YQ2] += PA(yt * q2);
+                    accq[PL_Q1Q1] += PA(q1 * q1);
+                    accq[PL_Q1Q2] += PA(q1 * q2);
+                    accq[PL_Q2Q2] += PA(q2 * q2);
+                } else {
+                    accq[PC_ZZ] += PA(z * z);
+                    if constexpr (MODE == CONS_YTIL) {
+                        out[kid] = y[kid] - rho * z;
+                        if (zk != nullptr) zk[kid] = z;
+                    } else if constexpr (MODE == CONS_YUPD) {
+                        const double yn = y[kid] - rho * z;
+                        y[kid] = yn;
+                        accq[PC_BY] += PA(__ldg(p.b + kid) * yn);
+                    }
+                }
+            }
+        }
+    }
+    if constexpr (MODE != CONS_EVAL) block_partials<NQ>(accq, part);
+}
+
+// ================================================================== direction
+// D = cG G + sum_u (cS_u S_u + cY_u Y_u) over the stored pairs (the two-loop
+// recursion of Algorithm 1 carried out on coefficients); partials <G,D>, ||D||^2.
+template <typename TD>
+__global__ void __launch_bounds__(kThreads)
+k_dir(int64_t nunits, const TD* __restrict__ G, TD* __restrict__ D, const TD* __restrict__ hist,
+      int64_t slot_stride, const Ctrl* ctrl, double* __restrict__ part, const Ctrl* gate, int ph) {
+    if (gated_off(gate, ph)) return;
+    using A = arith_t<TD>;
+    using PA = part_t<TD, TD>;
+    PA accq[PD_N] = {PA(0), PA(0)};
+    const int mem = ctrl->mem_count;
+    const A cG = A(ctrl->cG);
+    A cS[kMaxMem], cY[kMaxMem];
+    const TD* Sp[kMaxMem];
+    const TD* Yp[kMaxMem];
+#pragma unroll
+    for (int t = 0; t < kMaxMem; ++t) {
+        const int s = ctrl->order[t];
+        cS[t] = A(ctrl->cS[s]);
+        cY[t] = A(ctrl->cY[s]);
+        Sp[t] = hist + (int64_t)(2 * s) * slot_stride;
+        Yp[t] = hist + (int64_t)(2 * s + 1) * slot_stride;
+    }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nunits; u += stride) {
+        Unit<TD> g, d;
+        g.load_stream(G + u * 4);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) d.v[e] = cG * A(g.v[e]);
+#pragma unroll
+        for (int t = 0; t < kMaxMem; ++t) {
+            if (t < mem) {
+                Unit<TD> s, y;
+                s.load_stream(Sp[t] + u * 4);
+                y.load_stream(Yp[t] + u * 4);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) d.v[e] = fma(cS[t], A(s.v[e]), fma(cY[t], A(y.v[e]), A(d.v[e])));
+            }
+        }
+        Unit<TD> dst;
+        A gd = A(0), dd = A(0);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            dst.v[e] = d.v[e];
+            const A dv = A(dst.v[e]);           // value as stored
+            gd += A(g.v[e]) * dv;
+            dd += dv * dv;
+        }
+        dst.store(D + u * 4);
+        accq[PD_GD] += PA(gd);
+        accq[PD_DD] += PA(dd);
+    }
+    block_partials<PD_N>(accq, part);
+}
+
+// ================================================================== step (flat)
+// R += tau D, CR += tau CD  (used when the gradient needs a separate pattern pass)
+template <typename TR, typename TD>
+__global__ void __launch_bounds__(kThreads)
+k_step(int64_t nunits, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restrict__ D,
+       const TD* __restrict__ CD, const Ctrl* ctrl, const Ctrl* gate, int ph) {
+    if (gated_off(gate, ph)) return;
+    using A = arith_t<TR>;
+    const A tau = A(ctrl->tau);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nunits; u += stride) {
+        Unit<TR> r, cr;
+        Unit<TD> d, cd;
+        r.load_stream(R + u * 4);
+        cr.load_stream(CR + u * 4);
+        d.load_stream(D + u * 4);
+        cd.load_stream(CD + u * 4);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            r.v[e] = fma(tau, A(d.v[e]), A(r.v[e]));
+            cr.v[e] = fma(tau, A(cd.v[e]), A(cr.v[e]));
+        }
+        r.store_stream(R + u * 4);
+        cr.store_stream(CR + u * 4);
+    }
+}
+
+// ================================================================== row update
+// Per row i (group of L lanes):
+//   STEP : r += tau d, cr += tau cd                         (Algorithm 1 step)
+//   grad : g' = 2 (cr - a_i y~_k r - w_i),  y~_k = y_k - rho (a_i |r|^2 - b_k)
+//          for the diagonal constraint k of row i, w = A*_off(y~) R (if given)
+//   HIST : s_new = tau d, y_new = g' - g   into the new slot, and the dot
+//          products that keep the Gram data of the stored pairs current
+// partials: ||g'||^2, sum z_k^2 (diagonal constraints), and the Gram dots.
+template <typename TR, typename TD, int CPL, bool STEP, bool HIST>
+__global__ void __launch_bounds__(kThreads)
+k_update(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restrict__ D,
+         const TD* __restrict__ CD, TD* __restrict__ G, const TD* __restrict__ W,
+         TD* __restrict__ hist, int64_t slot_stride, int ld, int L, int Q,
+         const double* __restrict__ y, double* __restrict__ zrow, const Ctrl* ctrl, double* __restrict__ part,
+         const Ctrl* gate, int ph) {
+    if (gated_off(gate, ph)) return;
+    using AR = arith_t<TR>;
+    using AD = arith_t<TD>;
+    using PA = part_t<TR, TD>;
+    PA accq[PU_N];
+#pragma unroll
+    for (int q = 0; q < PU_N; ++q) accq[q] = PA(0);
+    const double rho = ctrl->rho;
+    const double taud = ctrl->tau;
+    const AR tau = AR(taud);
+    int nold = 0;
+    TD* Snew = nullptr;
+    TD* Ynew = nullptr;
+    const TD* So[kMaxMem - 1];
+    const TD* Yo[kMaxMem - 1];
+    if constexpr (HIST) {
+        nold = ctrl->old_count;
+        const int ns = ctrl->new_slot;
+        Snew = hist + (int64_t)(2 * ns) * slot_stride;
+        Ynew = hist + (int64_t)(2 * ns + 1) * slot_stride;
+#pragma unroll
+        for (int t = 0; t < kMaxMem - 1; ++t) {
+            const int s = ctrl->old_slots[t < nold ? t : 0];
+            So[t] = hist + (int64_t)(2 * s) * slot_stride;
+            Yo[t] = hist + (int64_t)(2 * s + 1) * slot_stride;
+        }
+    }
+    RowLoop rl(L);
+    for (int64_t base = rl.first; base < p.n; base += rl.stride) {
+        const int64_t i = base + rl.gw;
+        const bool act = i < p.n;
+        Unit<TR> r[CPL], cr[CPL];
+        Unit<TD> d[CPL];
+        AR rr = AR(0);
+        if (act) {
+            load_row_stream<TR, CPL>(r, R, i, ld, L, Q, rl.lig);
+            load_row_stream<TR, CPL>(cr, CR, i, ld, L, Q, rl.lig);
+            if constexpr (STEP || HIST) load_row_stream<TD, CPL>(d, D, i, ld, L, Q, rl.lig);
+            if constexpr (STEP) {
+                Unit<TD> cd[CPL];
+                load_row_stream<TD, CPL>(cd, CD, i, ld, L, Q, rl.lig);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        r[c].v[e] = fma(tau, AR(d[c].v[e]), AR(r[c].v[e]));
+                        cr[c].v[e] = fma(tau, AR(cd[c].v[e]), AR(cr[c].v[e]));
+                    }
+                store_row<TR, CPL>(r, R, i, ld, L, Q, rl.lig);
+                store_row<TR, CPL>(cr, CR, i, ld, L, Q, rl.lig);
+            }
+            rr = dot_units<AR>(r, r);
+        }
+        // diagonal-constraint coefficient a_i y~_k of row i
+        AR coef = AR(0);
+        if (p.dk != nullptr) {
+            rr = group_sum(rr, L);
+            if (act) {
+                const int k = __ldg(p.dk + i);
+                if (k >= 0) {
+                    const double a = __ldg(p.da + i);
+                    const double z = a * double(rr) - __ldg(p.b + k);
+                    coef = AR(a * (__ldg(y + k) - rho * z));
+                    if (rl.lig == 0) {
+                        accq[PU_ZZ] += PA(z * z);
+                        if (zrow != nullptr) zrow[i] = z;
+                    }
+                }
+            }
+        }
+        if (act) {
+            Unit<TD> g[CPL];
+            Unit<TD> w[CPL];
+            if (W != nullptr) load_row_stream<TD, CPL>(w, W, i, ld, L, Q, rl.lig);
+#pragma unroll
+            for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    AR gv = AR(cr[c].v[e]) - coef * AR(r[c].v[e]);
+                    if (W != nullptr) gv -= AR(w[c].v[e]);
+                    g[c].v[e] = AD(AR(2) * gv);
+                }
+            if constexpr (HIST) {
+                Unit<TD> gold[CPL], sn[CPL], yn[CPL];
+                load_row_stream<TD, CPL>(gold, G, i, ld, L, Q, rl.lig);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        sn[c].v[e] = AD(taud) * AD(d[c].v[e]);
+                        yn[c].v[e] = AD(g[c].v[e]) - AD(gold[c].v[e]);
+                    }
+                store_row<TD, CPL>(sn, Snew, i, ld, L, Q, rl.lig);
+                store_row<TD, CPL>(yn, Ynew, i, ld, L, Q, rl.lig);
+                accq[PU_GSN] += PA(dot_units<AD>(g, sn));
+                accq[PU_GYN] += PA(dot_units<AD>(g, yn));
+                accq[PU_SYN] += PA(dot_units<AD>(sn, yn));
+                accq[PU_YYN] += PA(dot_units<AD>(yn, yn));
+                accq[PU_SSN] += PA(dot_units<AD>(sn, sn));
+#pragma unroll
+                for (int t = 0; t < kMaxMem - 1; ++t) {
+                    if (t < nold) {
+                        Unit<TD> so[CPL], yo[CPL];
+                        load_row_stream<TD, CPL>(so, So[t], i, ld, L, Q, rl.lig);
+                        load_row_stream<TD, CPL>(yo, Yo[t], i, ld, L, Q, rl.lig);
+                        PA* q = accq + PU_FIXED + PU_PER_OLD * t;
+                        q[0] += PA(dot_units<AD>(g, so));
+                        q[1] += PA(dot_units<AD>(g, yo));
+                        q[2] += PA(dot_units<AD>(sn, yo));
+                        q[3] += PA(dot_units<AD>(so, yn));
+                        q[4] += PA(dot_units<AD>(yn, yo));
+                    }
+                }
+            }
+            store_row<TD, CPL>(g, G, i, ld, L, Q, rl.lig);
+            accq[PU_GG] += PA(dot_units<AD>(g, g));
+        }
+    }
+    block_partials<PU_N>(accq, part);
+}
+
+}  // namespace lorads

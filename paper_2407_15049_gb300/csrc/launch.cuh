@@ -1,0 +1,123 @@
+// Host launchers of the streaming kernels.  Declared for every precision in
+// launch_decl.h and explicitly instantiated per precision in kern_*.cu, so the
+// template-heavy device code compiles in parallel translation units.
+#pragma once
+
+#include "kernels.cuh"
+#include "launch_decl.h"
+
+namespace lorads {
+
+#define LORADS_CPL_SWITCH(cpl, ...)                                   \
+    switch (cpl) {                                                      \
+        case 1: { constexpr int CPL = 1; __VA_ARGS__; } break;         \
+        case 2: { constexpr int CPL = 2; __VA_ARGS__; } break;         \
+        case 3: { constexpr int CPL = 3; __VA_ARGS__; } break;         \
+        case 4: { constexpr int CPL = 4; __VA_ARGS__; } break;         \
+        default: break;                                                 \
+    }
+
+template <typename TX, typename TO, typename TR>
+void launch_spmm_c(const SpmmCArgs& a) {
+    const TX* X = static_cast<const TX*>(a.X);
+    TO* out = static_cast<TO*>(a.out);
+    const TR* R = static_cast<const TR*>(a.R);
+    LORADS_CPL_SWITCH(a.sh.CPL, {
+        if (a.epi == EPI_LS)
+            k_spmm_c<TX, TO, TR, CPL, EPI_LS><<<a.blocks, kThreads, 0, a.stream>>>(
+                a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.write_out, R, a.y, a.zrow, a.ctrl, a.rho, a.part, a.gate, a.ph);
+        else if (a.epi == EPI_OBJ)
+            k_spmm_c<TX, TO, TR, CPL, EPI_OBJ><<<a.blocks, kThreads, 0, a.stream>>>(
+                a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.write_out, R, a.y, a.zrow, a.ctrl, a.rho, a.part, a.gate, a.ph);
+        else
+            k_spmm_c<TX, TO, TR, CPL, EPI_NONE><<<a.blocks, kThreads, 0, a.stream>>>(
+                a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.write_out, R, a.y, a.zrow, a.ctrl, a.rho, a.part, a.gate, a.ph);
+    })
+}
+
+template <typename TX, typename TO>
+void launch_spmm_a(const SpmmAArgs& a) {
+    const TX* X = static_cast<const TX*>(a.X);
+    TO* out = static_cast<TO*>(a.out);
+    LORADS_CPL_SWITCH(a.sh.CPL, {
+        k_spmm_a<TX, TO, CPL><<<a.blocks, kThreads, 0, a.stream>>>(
+            a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.alpha, a.accumulate, a.gate, a.ph);
+    })
+}
+
+template <typename TU, typename TV>
+void launch_cons(const ConsArgs& a) {
+    const TU* U = static_cast<const TU*>(a.U);
+    const TV* V = static_cast<const TV*>(a.V);
+    if (a.k1 <= a.k0) return;
+    LORADS_CPL_SWITCH(a.sh.CPL, {
+        switch (a.mode) {
+            case CONS_EVAL:
+                k_cons<TU, TV, CPL, CONS_EVAL><<<a.blocks, kThreads, 0, a.stream>>>(
+                    a.p, a.k0, a.k1, U, V, a.ld, a.sh.L, a.sh.Q, a.y, a.out, a.zk, a.ctrl, a.rho, a.part, a.gate, a.ph);
+                break;
+            case CONS_LS:
+                k_cons<TU, TV, CPL, CONS_LS><<<a.blocks, kThreads, 0, a.stream>>>(
+                    a.p, a.k0, a.k1, U, V, a.ld, a.sh.L, a.sh.Q, a.y, a.out, a.zk, a.ctrl, a.rho, a.part, a.gate, a.ph);
+                break;
+            case CONS_YTIL:
+                k_cons<TU, TV, CPL, CONS_YTIL><<<a.blocks, kThreads, 0, a.stream>>>(
+                    a.p, a.k0, a.k1, U, V, a.ld, a.sh.L, a.sh.Q, a.y, a.out, a.zk, a.ctrl, a.rho, a.part, a.gate, a.ph);
+                break;
+            case CONS_YUPD:
+                k_cons<TU, TV, CPL, CONS_YUPD><<<a.blocks, kThreads, 0, a.stream>>>(
+                    a.p, a.k0, a.k1, U, V, a.ld, a.sh.L, a.sh.Q, a.y, a.out, a.zk, a.ctrl, a.rho, a.part, a.gate, a.ph);
+                break;
+            case CONS_ZZ:
+                k_cons<TU, TV, CPL, CONS_ZZ><<<a.blocks, kThreads, 0, a.stream>>>(
+                    a.p, a.k0, a.k1, U, V, a.ld, a.sh.L, a.sh.Q, a.y, a.out, a.zk, a.ctrl, a.rho, a.part, a.gate, a.ph);
+                break;
+            default: break;
+        }
+    })
+}
+
+template <typename TD>
+void launch_dir(const DirArgs& a) {
+    k_dir<TD><<<a.blocks, kThreads, 0, a.stream>>>(
+        a.nunits, static_cast<const TD*>(a.G), static_cast<TD*>(a.D), static_cast<const TD*>(a.hist),
+        a.slot_stride, a.ctrl, a.part, a.gate, a.ph);
+}
+
+template <typename TR, typename TD>
+void launch_step(const StepArgs& a) {
+    k_step<TR, TD><<<a.blocks, kThreads, 0, a.stream>>>(
+        a.nunits, static_cast<TR*>(a.R), static_cast<TR*>(a.CR), static_cast<const TD*>(a.D),
+        static_cast<const TD*>(a.CD), a.ctrl, a.gate, a.ph);
+}
+
+template <typename TR, typename TD>
+void launch_update(const UpdateArgs& a) {
+    TR* R = static_cast<TR*>(a.R);
+    TR* CR = static_cast<TR*>(a.CR);
+    const TD* D = static_cast<const TD*>(a.D);
+    const TD* CD = static_cast<const TD*>(a.CD);
+    TD* G = static_cast<TD*>(a.G);
+    const TD* W = static_cast<const TD*>(a.W);
+    TD* H = static_cast<TD*>(a.hist);
+    LORADS_CPL_SWITCH(a.sh.CPL, {
+        if (a.step && a.hist_on)
+            k_update<TR, TD, CPL, true, true><<<a.blocks, kThreads, 0, a.stream>>>(
+                a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.zrow, a.ctrl, a.part, a.gate, a.ph);
+        else if (!a.step && a.hist_on)
+            k_update<TR, TD, CPL, false, true><<<a.blocks, kThreads, 0, a.stream>>>(
+                a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.zrow, a.ctrl, a.part, a.gate, a.ph);
+        else
+            k_update<TR, TD, CPL, false, false><<<a.blocks, kThreads, 0, a.stream>>>(
+                a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.zrow, a.ctrl, a.part, a.gate, a.ph);
+    })
+}
+
+#define LORADS_INSTANTIATE_SPMM_C(TX, TO, TR) template void launch_spmm_c<TX, TO, TR>(const SpmmCArgs&);
+#define LORADS_INSTANTIATE_SPMM_A(TX, TO) template void launch_spmm_a<TX, TO>(const SpmmAArgs&);
+#define LORADS_INSTANTIATE_CONS(TU, TV) template void launch_cons<TU, TV>(const ConsArgs&);
+#define LORADS_INSTANTIATE_DIR(TD) template void launch_dir<TD>(const DirArgs&);
+#define LORADS_INSTANTIATE_STEP(TR, TD) template void launch_step<TR, TD>(const StepArgs&);
+#define LORADS_INSTANTIATE_UPDATE(TR, TD) template void launch_update<TR, TD>(const UpdateArgs&);
+
+}  // namespace lorads

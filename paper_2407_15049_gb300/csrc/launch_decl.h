@@ -1,0 +1,95 @@
+// Argument blocks and declarations of the kernel launchers (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include "common.cuh"
+
+namespace lorads {
+
+struct ProbDev;
+
+struct SpmmCArgs {
+    const ProbDev& p;
+    const void* X; void* out; int ld; Shape sh;
+    const double* v; int write_out; int epi;
+    const void* R; const double* y; const double* zrow; const Ctrl* ctrl; double rho; double* part;
+    int blocks; const Ctrl* gate; int ph; cudaStream_t stream;
+};
+
+struct SpmmAArgs {
+    const ProbDev& p;
+    const void* X; void* out; int ld; Shape sh;
+    const double* v; double alpha; int accumulate;
+    int blocks; const Ctrl* gate; int ph; cudaStream_t stream;
+};
+
+struct ConsArgs {
+    const ProbDev& p;
+    int mode; int64_t k0, k1;
+    const void* U; const void* V; int ld; Shape sh;
+    double* y; double* out; double* zk; const Ctrl* ctrl; double rho; double* part;
+    int blocks; const Ctrl* gate; int ph; cudaStream_t stream;
+};
+
+struct DirArgs {
+    int64_t nunits; const void* G; void* D; const void* hist; int64_t slot_stride;
+    const Ctrl* ctrl; double* part; int blocks; const Ctrl* gate; int ph; cudaStream_t stream;
+};
+
+struct StepArgs {
+    int64_t nunits; void* R; void* CR; const void* D; const void* CD;
+    const Ctrl* ctrl; int blocks; const Ctrl* gate; int ph; cudaStream_t stream;
+};
+
+struct UpdateArgs {
+    const ProbDev& p;
+    bool step; bool hist_on;
+    void* R; void* CR; const void* D; const void* CD; void* G; const void* W; void* hist;
+    int64_t slot_stride; int ld; Shape sh; const double* y; double* zrow; const Ctrl* ctrl; double* part;
+    int blocks; const Ctrl* gate; int ph; cudaStream_t stream;
+};
+
+template <typename TX, typename TO, typename TR> void launch_spmm_c(const SpmmCArgs& a);
+template <typename TX, typename TO> void launch_spmm_a(const SpmmAArgs& a);
+template <typename TU, typename TV> void launch_cons(const ConsArgs& a);
+template <typename TD> void launch_dir(const DirArgs& a);
+template <typename TR, typename TD> void launch_step(const StepArgs& a);
+template <typename TR, typename TD> void launch_update(const UpdateArgs& a);
+
+using bf16 = __nv_bfloat16;
+
+// instantiated in kern_fp64.cu
+extern template void launch_spmm_c<double, double, double>(const SpmmCArgs&);
+extern template void launch_spmm_a<double, double>(const SpmmAArgs&);
+extern template void launch_cons<double, double>(const ConsArgs&);
+extern template void launch_dir<double>(const DirArgs&);
+extern template void launch_step<double, double>(const StepArgs&);
+extern template void launch_update<double, double>(const UpdateArgs&);
+// kern_mixed.cu: double-float master R / C R, FP32 direction, gradient and history
+extern template void launch_spmm_c<float, float, dfloat>(const SpmmCArgs&);
+extern template void launch_spmm_a<dfloat, float>(const SpmmAArgs&);
+extern template void launch_cons<dfloat, float>(const ConsArgs&);
+extern template void launch_step<dfloat, float>(const StepArgs&);
+extern template void launch_update<dfloat, float>(const UpdateArgs&);
+// kern_df.cu: double-float everywhere
+extern template void launch_spmm_c<dfloat, dfloat, dfloat>(const SpmmCArgs&);
+extern template void launch_spmm_a<dfloat, dfloat>(const SpmmAArgs&);
+extern template void launch_cons<dfloat, dfloat>(const ConsArgs&);
+extern template void launch_dir<dfloat>(const DirArgs&);
+extern template void launch_step<dfloat, dfloat>(const StepArgs&);
+extern template void launch_update<dfloat, dfloat>(const UpdateArgs&);
+// kern_fp32.cu
+extern template void launch_spmm_c<float, float, float>(const SpmmCArgs&);
+extern template void launch_spmm_a<float, float>(const SpmmAArgs&);
+extern template void launch_cons<float, float>(const ConsArgs&);
+extern template void launch_dir<float>(const DirArgs&);
+extern template void launch_step<float, float>(const StepArgs&);
+extern template void launch_update<float, float>(const UpdateArgs&);
+// kern_bf16.cu: bf16 storage, FP32 arithmetic (standalone entry points)
+extern template void launch_spmm_c<bf16, float, bf16>(const SpmmCArgs&);
+extern template void launch_spmm_a<bf16, float>(const SpmmAArgs&);
+extern template void launch_cons<bf16, bf16>(const ConsArgs&);
+
+}  // namespace lorads

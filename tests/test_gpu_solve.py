@@ -1,0 +1,169 @@
+"""GPU solver parity against the FP64 oracle.
+
+* Trajectory: with the same R0 and the same caps, the GPU iterate after a fixed
+  number of L-BFGS steps equals the oracle's (the algorithm is deterministic).
+* Convergence: both reach rel. KKT <= 1e-5 and their objectives agree to 1e-5.
+* Closed forms of the MaxCut SDP on the GPU.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import lorads_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_2407_15049_gb300 as L  # noqa: E402
+
+PREC = {"fp64": L.LORADS_FP64, "mixed": L.LORADS_MIXED, "fp32": L.LORADS_FP32}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    L.build()
+
+
+def _gpu_solve(inst, R0, prec="fp64", **kw):
+    ctx = L.lorads_create(inst, L.default_params(prec=PREC[prec], **kw))
+    try:
+        res = L.lorads_solve(ctx, R0)
+        R, y = L.lorads_get_solution(ctx, inst.n, inst.m)
+    finally:
+        L.lorads_destroy(ctx)
+    return res, R, y
+
+
+def _oracle_params(**kw):
+    return O.Params(**kw)
+
+
+@pytest.mark.parametrize("k", [1, 5, 30])
+def test_trajectory_matches_oracle_maxcut(k):
+    n = 1000
+    inst = W.maxcut_instance(n, W.er_graph(n, 4 * n, 0, "unit"))
+    R0 = W.initial_factor(inst, 10, 1)
+    caps = dict(max_outer=1, max_inner=k, tol=1e-300)
+    ref = O.solve(O.Problem(inst), R0, O.Params(**caps))
+    res, R, y = _gpu_solve(inst, R0, **caps)
+    assert res["inner_iters"] == ref["inner"]
+    scale = np.abs(ref["R"]).max()
+    assert np.max(np.abs(R - ref["R"])) <= 1e-9 * scale * max(1, k / 10)
+    assert np.max(np.abs(y - ref["y"])) <= 1e-8 * (1 + np.abs(ref["y"]).max())
+
+
+@pytest.mark.parametrize("k", [1, 5, 30])
+def test_trajectory_matches_oracle_matrix_completion(k):
+    inst = W.mc_instance(60, 80, 3, 2500, seed=2)
+    R0 = W.initial_factor(inst, 12, 4)
+    caps = dict(max_outer=1, max_inner=k, tol=1e-300)
+    ref = O.solve(O.Problem(inst), R0, O.Params(**caps))
+    res, R, y = _gpu_solve(inst, R0, **caps)
+    assert res["inner_iters"] == ref["inner"]
+    scale = np.abs(ref["R"]).max()
+    assert np.max(np.abs(R - ref["R"])) <= 1e-9 * scale * max(1, k / 10)
+
+
+def test_trajectory_with_rank_growth():
+    """Every outer step hits max_inner: the rank grows 4 -> 6 -> 9 as in App. A.1."""
+    n = 40
+    inst = W.maxcut_instance(n, W.er_graph(n, 120, 5, "pm1"))
+    R0 = W.initial_factor(inst, 4, 2)
+    caps = dict(max_outer=3, max_inner=3, tol=1e-300, rank_update_threshold=1, seed=11)
+    ref = O.solve(O.Problem(inst), R0, O.Params(**caps))
+    res, R, y = _gpu_solve(inst, R0, **caps)
+    assert R.shape[1] == ref["R"].shape[1] == 9
+    assert np.max(np.abs(R - ref["R"])) <= 1e-9 * np.abs(ref["R"]).max()
+
+
+def _converged_pair(inst, r, seed, prec="fp64", **kw):
+    R0 = W.initial_factor(inst, r, seed)
+    ref = O.solve(O.Problem(inst), R0, O.Params(**kw))
+    res, R, y = _gpu_solve(inst, R0, prec=prec, **kw)
+    return ref, res, R, y
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+def test_maxcut_er_1000_converges_to_oracle_objective(prec):
+    """The small workload: ER n = 1000, average degree 8, unit weights, r = 10."""
+    n = 1000
+    inst = W.maxcut_instance(n, W.er_graph(n, 4 * n, 0, "unit"))
+    ref, res, R, y = _converged_pair(inst, 10, 1, prec=prec)
+    assert ref["status"] == "ok"
+    assert res["status_name"] == "LORADS_OK", res
+    assert res["err1"] <= 1e-5 and abs(res["err3"]) <= 1e-5
+    assert res["primal_obj"] == pytest.approx(ref["primal_obj"], rel=1e-5)
+    z = np.sum(R * R, axis=1) - 1
+    assert np.linalg.norm(z) / 2 <= 1.0001e-5
+
+
+def test_maxcut_pm1_torus_converges():
+    side = 40
+    inst = W.maxcut_instance(side * side, W.torus_graph(side, 0, "pm1"))
+    ref, res, R, y = _converged_pair(inst, W.rank_log2(side * side), 3)
+    assert res["status_name"] == "LORADS_OK"
+    assert res["primal_obj"] == pytest.approx(ref["primal_obj"], rel=1e-5)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_matrix_completion_converges(prec):
+    n1 = n2 = 100
+    k = int(math.ceil(5 * n1 * math.log(n1)))
+    inst = W.mc_instance(n1, n2, 3, k, seed=6)
+    r = W.rank_log2(inst.m)
+    ref, res, R, y = _converged_pair(inst, r, 2, prec=prec, max_outer=400)
+    assert ref["status"] == "ok"
+    assert res["status_name"] == "LORADS_OK", res
+    assert res["primal_obj"] == pytest.approx(ref["primal_obj"], rel=1e-5)
+    M = inst.meta["U"] @ inst.meta["V"].T
+    nuc = np.linalg.svd(M, compute_uv=False).sum()
+    assert res["primal_obj"] == pytest.approx(2 * nuc, rel=1e-3)
+
+
+def test_closed_forms_on_gpu():
+    n = 10
+    inst = W.maxcut_instance(n, W.complete_graph(n))
+    res, _, _ = _gpu_solve(inst, W.initial_factor(inst, 4, 1))
+    assert -res["primal_obj"] == pytest.approx(n * n / 4, rel=1e-5)
+    for n in (5, 7):
+        inst = W.maxcut_instance(n, W.cycle_graph(n))
+        res, _, _ = _gpu_solve(inst, W.initial_factor(inst, 3, 1))
+        assert -res["primal_obj"] == pytest.approx(0.5 * n * (1 + math.cos(math.pi / n)), rel=1e-5)
+    side = 6
+    edges = W.bipartite_torus_graph(side)
+    inst = W.maxcut_instance(side * side, edges)
+    res, _, _ = _gpu_solve(inst, W.initial_factor(inst, 6, 1))
+    assert -res["primal_obj"] == pytest.approx(len(edges[0]), rel=1e-5)
+
+
+def test_device_resident_start_and_repeat():
+    """R0 given as a device tensor; two solves in a row give the same answer."""
+    n = 500
+    inst = W.maxcut_instance(n, W.er_graph(n, 2 * n, 4, "pm1"))
+    R0 = W.initial_factor(inst, 9, 2)
+    ctx = L.lorads_create(inst)
+    try:
+        a = L.lorads_solve(ctx, torch.as_tensor(R0, device="cuda"), on_device=True)
+        b = L.lorads_solve(ctx, R0)
+    finally:
+        L.lorads_destroy(ctx)
+    assert a["status_name"] == b["status_name"] == "LORADS_OK"
+    assert a["primal_obj"] == b["primal_obj"] and a["inner_iters"] == b["inner_iters"]
+
+
+def test_profiled_solve_matches_graph_solve():
+    n = 800
+    inst = W.maxcut_instance(n, W.er_graph(n, 3 * n, 5, "pm1"))
+    R0 = W.initial_factor(inst, 10, 2)
+    res_g, _, _ = _gpu_solve(inst, R0)
+    ctx = L.lorads_create(inst, L.default_params(verbose=2))
+    try:
+        res_p = L.lorads_solve(ctx, R0)
+        times = L.lorads_kernel_times(ctx)
+    finally:
+        L.lorads_destroy(ctx)
+    assert res_p["primal_obj"] == res_g["primal_obj"] and res_p["inner_iters"] == res_g["inner_iters"]
+    assert times["k_spmm_c(CD,ls)"][1] == res_g["inner_iters"]
+    assert all(ms > 0 for ms, _ in times.values())

@@ -1,0 +1,140 @@
+"""CPU tests of the C-ABI library: it builds, loads, exports every declared
+symbol, and rejects invalid inputs on the host (before any device call)."""
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import workloads as W
+import paper_2407_15049_gb300 as L
+from paper_2407_15049_gb300 import _native as N
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    L.build()
+    return N.load()
+
+
+def _declared_functions():
+    text = (ROOT / "include" / "lorads.h").read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lorads_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_abi():
+    names = _declared_functions()
+    for want in ["lorads_create", "lorads_spmm", "lorads_constraint_eval", "lorads_linesearch_coeffs",
+                 "lorads_solve", "lorads_destroy"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+    assert set(_declared_functions()) == set(N.SIGNATURES), "binding and header disagree"
+
+
+def test_default_params(lib):
+    p = N.default_params()
+    assert p.tol == 1e-5 and p.lbfgs_mem == 4 and p.max_inner == 500 and p.rho_growth == 2.0
+    assert p.lbfgs_scaling == 1 and p.rho_policy == 1 and p.inner_scale == 1 and p.rank_update_threshold == 3
+    assert p.inner_rel == 1.0 and p.infeas_decrease == 0.25 and p.time_limit == 1e4
+
+
+def _maxcut(n=12, seed=0):
+    return W.maxcut_instance(n, W.er_graph(n, 20, seed, "pm1"))
+
+
+def _expect(status_name, inst, **kw):
+    with pytest.raises(N.LoradsError) as ei:
+        N.lorads_create(inst, **kw)
+    assert N.STATUS_NAMES[ei.value.status] == status_name, str(ei.value)
+    return str(ei.value)
+
+
+def test_rejects_asymmetric_C(lib):
+    inst = _maxcut()
+    inst.val = inst.val.copy()
+    s = inst.rowptr[3]
+    if inst.colind[s] == 3:
+        s += 1
+    inst.val[s] += 0.5
+    _expect("LORADS_ERR_NOT_SYMMETRIC", inst)
+
+
+def test_rejects_out_of_range_index(lib):
+    inst = _maxcut()
+    inst.colind = inst.colind.copy()
+    inst.colind[-1] = inst.n
+    _expect("LORADS_ERR_INVALID_ARG", inst)
+
+
+def test_rejects_unsorted_row(lib):
+    inst = _maxcut()
+    inst.colind = inst.colind.copy()
+    r = next(i for i in range(inst.n) if inst.rowptr[i + 1] - inst.rowptr[i] >= 2)
+    s = inst.rowptr[r]
+    inst.colind[s], inst.colind[s + 1] = inst.colind[s + 1], inst.colind[s]
+    _expect("LORADS_ERR_INVALID_ARG", inst)
+
+
+def test_rejects_nan(lib):
+    inst = _maxcut()
+    inst.b = inst.b.copy()
+    inst.b[2] = np.nan
+    _expect("LORADS_ERR_INVALID_ARG", inst)
+    inst = _maxcut()
+    inst.val = inst.val.copy()
+    inst.val[0] = np.inf
+    _expect("LORADS_ERR_INVALID_ARG", inst)
+
+
+def test_rejects_lower_triangle_triplet(lib):
+    inst = W.mc_instance(4, 5, 2, 6, seed=1)
+    inst.row, inst.col = inst.col.copy(), inst.row.copy()
+    _expect("LORADS_ERR_INVALID_ARG", inst)
+
+
+def test_rejects_multi_entry_constraint(lib):
+    inst = _maxcut()
+    inst.con = inst.con.copy()
+    inst.con[1] = 0                    # constraint 0 gets two triplets, constraint 1 none
+    msg = _expect("LORADS_ERR_UNSUPPORTED", inst)
+    assert "triplet" in msg
+
+
+def test_rejects_duplicate_entry_constraints(lib):
+    inst = W.mc_instance(4, 5, 2, 6, seed=1)
+    inst.row = inst.row.copy()
+    inst.col = inst.col.copy()
+    inst.row[1], inst.col[1] = inst.row[0], inst.col[0]
+    _expect("LORADS_ERR_UNSUPPORTED", inst)
+
+
+def test_rejects_empty_problem(lib):
+    inst = _maxcut()
+    inst.m = 0
+    inst.con = inst.con[:0]
+    inst.row = inst.row[:0]
+    inst.col = inst.col[:0]
+    inst.aval = inst.aval[:0]
+    inst.b = inst.b[:0]
+    _expect("LORADS_ERR_INVALID_ARG", inst)
+
+
+def test_rejects_bad_lbfgs_memory(lib):
+    _expect("LORADS_ERR_INVALID_ARG", _maxcut(), params=N.default_params(lbfgs_mem=9))
+
+
+def test_workload_generators_shapes():
+    inst = W.maxcut_instance(50, W.er_graph(50, 100, 0, "pm1"))
+    assert inst.rowptr[-1] == 2 * 100 + 50 and inst.m == 50
+    i, j, w = W.torus_graph(10, 0)
+    assert len(i) == 200 and set(np.unique(w)) <= {-1.0, 1.0}
+    mc = W.mc_instance(30, 40, 3, 200, seed=2)
+    assert mc.n == 70 and mc.m == 200 and np.all(mc.col >= 30)
+    assert W.rank_log2(1000) == 10 and W.rank_log2(10**6) == 20 and W.rank_log2(10**7) == 24
