@@ -42,18 +42,20 @@ WORKLOADS = {
 }
 # iterations to tolerance used to scale the reference arm's per-iteration time when no
 # GPU run of the same invocation provides it (measured on the GPU solve of maxcut_er_1e7)
-DEFAULT_ITERS_TO_TOL = {"maxcut_er_1e7": 3000, "maxcut_er_1e5": 2000}
+DEFAULT_ITERS_TO_TOL = {"maxcut_er_1e7": 6660, "maxcut_er_1e5": 5000}
 
 
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", default="maxcut_er_1e7", choices=sorted(WORKLOADS))
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed", "fp32"])
-    ap.add_argument("--e2e-steps", type=int, default=None, help="end-to-end steps (default: --steps)")
+    ap.add_argument("--prec", default="mixed", choices=["fp64", "mixed", "df64", "fp32"])
+    ap.add_argument("--e2e-steps", type=int, default=1, help="end-to-end steps")
+    ap.add_argument("--profile-iters", type=int, default=200,
+                    help="L-BFGS iterations of the CUDA-event-timed solve used for per-kernel durations")
     ap.add_argument("--cpu-iters", type=int, default=2, help="oracle L-BFGS iterations per CPU sample")
     ap.add_argument("--iters-to-tol", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -243,7 +245,8 @@ def run_native(args):
     from paper_2407_15049_gb300 import _native as N
 
     L.load()
-    prec_code = {"fp64": L.LORADS_FP64, "mixed": L.LORADS_MIXED, "fp32": L.LORADS_FP32}[args.prec]
+    prec_code = {"fp64": L.LORADS_FP64, "mixed": L.LORADS_MIXED, "df64": L.LORADS_DF64,
+                 "fp32": L.LORADS_FP32}[args.prec]
     inst, R0, gen_s = build_instance(args.workload)
     cfg = WORKLOADS[args.workload]
     stream = torch.cuda.Stream()
@@ -273,17 +276,20 @@ def run_native(args):
         elapsed = ev0.elapsed_time(ev1) / 1e3
         last = timed[-1]
         launches = sum(r["kernel_launches"] for r in timed)
-        # per-kernel durations: one host-stepped solve with CUDA events around every launch
+        # per-kernel durations: a host-stepped run of the same solve (first profile_iters
+        # L-BFGS iterations) with a CUDA event pair around every launch on the solve stream
         prof = {}
         if not args.no_profile:
-            pctx = L.lorads_create(inst, L.default_params(prec=prec_code, verbose=2), stream=stream.cuda_stream)
-            pres = L.lorads_solve(pctx, R0_dev, on_device=True)
+            pctx = L.lorads_create(inst, L.default_params(prec=prec_code, verbose=2, max_outer=10**6,
+                                                          max_inner=args.profile_iters, rank_update_threshold=10**6),
+                                   stream=stream.cuda_stream)
+            L.lorads_solve(pctx, R0_dev, on_device=True, max_total_inner=args.profile_iters)
             prof = L.lorads_kernel_times(pctx)
             L.lorads_destroy(pctx)
         L.lorads_destroy(ctx)
         del R0_dev
         # end to end through the C ABI from host buffers
-        e2e_steps = args.e2e_steps if args.e2e_steps is not None else args.steps
+        e2e_steps = args.e2e_steps
         R0_pinned = torch.from_numpy(R0).pin_memory().numpy()
         e2e_times = []
         h2d = (inst.rowptr.nbytes + inst.colind.nbytes + inst.val.nbytes + inst.con.nbytes + inst.row.nbytes
@@ -313,23 +319,28 @@ def run_native(args):
         return 0
 
     # roofline of the dominant kernel (largest total time in the profiled solve)
-    wR = 8 if args.prec in ("fp64", "mixed") else 4
-    wD = 8 if args.prec == "fp64" else 4
+    wR = 8 if args.prec in ("fp64", "mixed", "df64") else 4
+    wD = 8 if args.prec in ("fp64", "df64") else 4
     ld = N.padded_ld(cfg["r"])
     peak, peak_kind = measured_peaks()
+    # launches of each family in the timed solve: inner-iteration kernels once per
+    # L-BFGS iteration, outer-step kernels once per outer step
+    per_inner = {"k_dir", "k_spmm_c(CD,ls)", "k_ctrl_root", "k_update(step)", "k_ctrl_hist", "k_cons(ls)",
+                 "k_step", "k_spmm_a", "k_cons(ytil)"}
     kernels = {}
     for name, (ms, cnt) in prof.items():
         b = kernel_bytes(name, inst.n, ld, inst.nnz, inst.m, wR, wD, params.lbfgs_mem)
-        kernels[name] = {"avg_ms": ms, "launches": cnt, "share": None,
-                         "algorithmic_bytes": None if math.isnan(b) else b,
+        solve_launches = last["inner_iters"] if name in per_inner else last["outer_iters"]
+        kernels[name] = {"avg_ms": ms, "profiled_launches": cnt, "solve_launches": solve_launches,
+                         "share": None, "algorithmic_bytes": None if math.isnan(b) else b,
                          "GBps": None if math.isnan(b) else b / (ms * 1e-3) / 1e9}
-    tot = sum(v["avg_ms"] * v["launches"] for v in kernels.values()) or 1.0
+    tot = sum(v["avg_ms"] * v["solve_launches"] for v in kernels.values()) or 1.0
     for v in kernels.values():
-        v["share"] = v["avg_ms"] * v["launches"] / tot
+        v["share"] = v["avg_ms"] * v["solve_launches"] / tot
     roofline = None
     hot = [k for k in kernels if kernels[k]["GBps"] is not None]
     if hot:
-        dom = max(hot, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["launches"])
+        dom = max(hot, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["solve_launches"])
         ach = kernels[dom]["GBps"]
         tr = ncu_traffic(dom)
         roofline = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
@@ -351,7 +362,9 @@ def run_native(args):
     line = {
         "metric": METRIC, "value": per_step, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f64+f32", "fp32": "f32"}[args.prec],
+        "vs_baseline": None,
+        "dtype": {"fp64": "f64", "mixed": "f32 (+double-float R, CR)", "df64": "double-float (2xf32)",
+                  "fp32": "f32"}[args.prec],
         "data": "synthetic", "config": _config(args),
         "e2e": {"value": e2e_mean, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),

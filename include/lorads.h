@@ -88,7 +88,8 @@ typedef struct {
     double  rho_growth;        /* 2 */
     double  rho_max;           /* 1e12 */
     double  infeas_decrease;   /* 0.25: rho grows unless err1 shrank by this factor */
-    double  inner_rel;         /* 1.0: inner stop ||G||_F <= inner_rel*max(s ||A(RR^T)-b||, tol(1+||b||_inf)), s = rho or 1 */
+    double  inner_rel;         /* 1.0: scale of the inner stopping threshold (see inner_scale) */
+    double  inner_progress;    /* 0.1: inner_scale 2 also stops once ||G|| <= inner_progress ||G at loop start|| */
     int32_t prec;              /* lorads_prec of the solve: FP64, MIXED, DF64 or FP32 */
     int32_t check_every;       /* iterations between host polls of the device status (16) */
     uint64_t seed;             /* seed of the rank-update columns (SplitMix64 + Box-Muller) */
@@ -96,8 +97,11 @@ typedef struct {
     int32_t lanczos_steps;     /* Krylov dimension of that Lanczos run (default 200) */
     int32_t verbose;           /* 1: progress line per outer step on stderr; 2: per-kernel CUDA-event timing */
     int32_t lbfgs_scaling;     /* 0: initial matrix I (Algorithm 1 as printed); 1 (default): gamma I, gamma = <s,y>/<y,y> */
-    int32_t rho_policy;        /* 0: grow rho when err1 did not shrink enough; 1 (default): only after a converged inner loop */
-    int32_t inner_scale;       /* 0: inner stop against ||z||; 1 (default): against rho ||z|| (z = A(RR^T) - b) */
+    int32_t rho_policy;        /* rho grows when err1 did not shrink by infeas_decrease: 0 always; 1 only
+                                  after a converged inner loop; 2 (default) also after a capped loop that raised err1 */
+    int32_t inner_scale;       /* inner stop ||G||_F <= thr, z = A(RR^T) - b, e = tol (1 + ||b||_inf):
+                                  0: thr = inner_rel max(||z||, e);  1: thr = inner_rel max(rho ||z||, e);
+                                  2 (default): thr = max(e, min(inner_rel rho ||z||, inner_progress ||G_0||)) */
     int32_t reserved;
 } lorads_params;
 
@@ -209,6 +213,10 @@ lorads_status lorads_problem_info(const lorads_ctx* ctx, int64_t* n, int64_t* m,
  * have `cap` entries (names are static strings); returns the number written, 0 when no
  * profiled solve has run. */
 int32_t lorads_kernel_times(const lorads_ctx* ctx, const char** names, double* ms, int32_t cap);
+
+/* Caps the total number of L-BFGS iterations of the next solves (0: no cap); a capped
+ * solve ends with LORADS_ERR_MAXITER.  Used to time a fixed slice of a solve. */
+lorads_status lorads_set_iteration_limit(lorads_ctx* ctx, int64_t max_total_inner);
 
 /* Launch counts of the same profiled solve, by kernel family (same order as
  * lorads_kernel_times). */

@@ -310,8 +310,11 @@ class Params:
     inner_rel: float = 1.0            # inner stop: ||G||_F <= inner_rel * max(||A(RR^T)-b||, tol (1+||b||_inf))
     rank_update_threshold: int = 3    # outer steps in a row that hit max_inner
     lbfgs_scaling: int = 1            # 0: initial matrix I (Algorithm 1); 1: gamma I
-    rho_policy: int = 1               # 1: rho grows only after a converged inner loop
-    inner_scale: int = 1              # 1: inner stop against rho ||z|| instead of ||z||
+    rho_policy: int = 2               # 1: rho grows only after a converged inner loop;
+                                      # 2: also after a capped loop that raised err1
+    inner_scale: int = 2              # 1: inner stop against rho ||z|| instead of ||z||;
+                                      # 2: as 1, capped by inner_progress * ||G|| at the loop start
+    inner_progress: float = 0.1
     seed: int = 0
     time_limit: float = 1e4           # seconds (Sec. 4.1)
 
@@ -346,12 +349,18 @@ def solve(P: Problem, R0: np.ndarray, params: Params | None = None,
         S: list = []
         Yh: list = []
         G = gradient(P, R, y, rho)
+        g0 = float(np.linalg.norm(G))
         k = 0                                   # directions computed
         while k < prm.max_inner:
             # stop once the gradient is small next to the current infeasibility
             zc = float(np.linalg.norm(constraint_map(P, R, R) - P.b))
-            zs = rho * zc if prm.inner_scale else zc
-            if float(np.linalg.norm(G)) <= prm.inner_rel * max(zs, prm.tol * (1.0 + bnorm_inf)):
+            if prm.inner_scale == 0:
+                thr = prm.inner_rel * max(zc, prm.tol * (1.0 + bnorm_inf))
+            elif prm.inner_scale == 1:
+                thr = prm.inner_rel * max(rho * zc, prm.tol * (1.0 + bnorm_inf))
+            else:
+                thr = max(prm.tol * (1.0 + bnorm_inf), min(prm.inner_rel * rho * zc, prm.inner_progress * g0))
+            if float(np.linalg.norm(G)) <= thr:
                 break
             D = lbfgs_direction(G, S, Yh, prm.lbfgs_scaling)
             k += 1
@@ -391,7 +400,12 @@ def solve(P: Problem, R0: np.ndarray, params: Params | None = None,
             status = "ok"
             err1 = err1_new
             break
-        if err1_new > prm.infeas_decrease * err1 and (prm.rho_policy == 0 or k < prm.max_inner):
+        grow = err1_new > prm.infeas_decrease * err1
+        if prm.rho_policy == 1:
+            grow = grow and k < prm.max_inner
+        elif prm.rho_policy == 2:
+            grow = grow and (k < prm.max_inner or err1_new > err1)
+        if grow:
             rho = min(rho * prm.rho_growth, prm.rho_max)
         err1 = err1_new
         # ---- dynamic rank (App. A.1)

@@ -36,7 +36,8 @@ class lorads_params(C.Structure):
         ("tol", C.c_double), ("time_limit", C.c_double), ("lbfgs_mem", C.c_int32),
         ("max_inner", C.c_int32), ("max_outer", C.c_int32), ("rank_update_threshold", C.c_int32),
         ("rho0", C.c_double), ("rho_growth", C.c_double), ("rho_max", C.c_double),
-        ("infeas_decrease", C.c_double), ("inner_rel", C.c_double), ("prec", C.c_int32),
+        ("infeas_decrease", C.c_double), ("inner_rel", C.c_double), ("inner_progress", C.c_double),
+        ("prec", C.c_int32),
         ("check_every", C.c_int32), ("seed", C.c_uint64), ("compute_err2", C.c_int32),
         ("lanczos_steps", C.c_int32), ("verbose", C.c_int32), ("lbfgs_scaling", C.c_int32),
         ("rho_policy", C.c_int32), ("inner_scale", C.c_int32), ("reserved", C.c_int32),
@@ -74,6 +75,7 @@ SIGNATURES = {
     "lorads_problem_info": (C.c_int, [_VP, _I64P, _I64P, _I64P, _I64P, _I64P]),
     "lorads_kernel_times": (C.c_int32, [_VP, C.POINTER(C.c_char_p), _DP, C.c_int32]),
     "lorads_kernel_counts": (C.c_int32, [_VP, C.POINTER(C.c_char_p), _I64P, C.c_int32]),
+    "lorads_set_iteration_limit": (C.c_int, [_VP, C.c_int64]),
 }
 
 _lib = None
@@ -189,8 +191,9 @@ def lorads_linesearch_coeffs(ctx, R, D, y, rho: float, r: int | None = None):
 
 
 def lorads_solve(ctx, R0=None, y0: np.ndarray | None = None, r0: int = 0, on_device: bool = False,
-                 raise_on_status: bool = False) -> dict:
-    """Runs the solver.  R0: host numpy (n x r0) or device float64 tensor, or None."""
+                 raise_on_status: bool = False, max_total_inner: int = 0) -> dict:
+    """Runs the solver.  R0: host numpy (n x r0) or device float64 tensor, or None.
+    max_total_inner > 0 stops after that many L-BFGS iterations in total."""
     lib = load()
     res = lorads_result()
     keep = []
@@ -207,7 +210,11 @@ def lorads_solve(ctx, R0=None, y0: np.ndarray | None = None, r0: int = 0, on_dev
         y0 = np.ascontiguousarray(y0, dtype=np.float64)
         keep.append(y0)
         yp = C.c_void_p(y0.ctypes.data)
+    if max_total_inner:
+        _check(ctx, lib.lorads_set_iteration_limit(ctx, int(max_total_inner)))
     st = lib.lorads_solve(ctx, rp, r0v, dev, yp, C.byref(res))
+    if max_total_inner:
+        _check(ctx, lib.lorads_set_iteration_limit(ctx, 0))
     out = res.as_dict()
     out["status_name"] = STATUS_NAMES.get(res.status, str(res.status))
     if st not in (LORADS_OK, 5, 6, 7) or (raise_on_status and st != LORADS_OK):

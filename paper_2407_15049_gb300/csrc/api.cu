@@ -43,7 +43,9 @@ struct SolverState {
     int64_t slot_stride = 0;
     double* y = nullptr;
     double* ytil = nullptr;
-    double* zrow = nullptr;             // A(RR^T)_k - b_k of the diagonal constraint of each row
+    void* zrow = nullptr;               // A(RR^T)_k - b_k of the diagonal constraint of each row
+                                        // (double on the FP64 path, float otherwise)
+    dfloat* ydf = nullptr;              // double-float mirror of y (FP32-unit paths), else null
     double* zk = nullptr;               // same for the off-diagonal constraints (by constraint)
     cudaGraphExec_t exec = nullptr;
     bool have_solution = false;
@@ -85,6 +87,9 @@ struct lorads_ctx {
     dfloat* c_valdf = nullptr;
     int32_t* dk = nullptr;
     double* da = nullptr;
+    float* da32 = nullptr;
+    dfloat* da_df = nullptr;
+    dfloat* b_df = nullptr;
     int64_t* a_rowptr = nullptr;
     int32_t* a_col = nullptr;
     int32_t* a_k = nullptr;
@@ -106,6 +111,7 @@ struct lorads_ctx {
     bool prof_valid = false;
     bool prof_active = false;
     int64_t launches = 0;          // kernels launched by the current solve
+    int64_t iter_limit = 0;        // cap on the total L-BFGS iterations of a solve (0: none)
     int64_t graph_nodes = 0;       // kernel nodes of the captured iteration graph
 };
 
@@ -216,6 +222,7 @@ extern "C" void lorads_default_params(lorads_params* p) {
     p->rho_max = 1e12;
     p->infeas_decrease = 0.25;
     p->inner_rel = 1.0;
+    p->inner_progress = 0.1;
     p->prec = LORADS_FP64;
     p->check_every = 16;
     p->seed = 0;
@@ -223,8 +230,8 @@ extern "C" void lorads_default_params(lorads_params* p) {
     p->lanczos_steps = 200;
     p->verbose = 0;
     p->lbfgs_scaling = 1;
-    p->rho_policy = 1;
-    p->inner_scale = 1;
+    p->rho_policy = 2;
+    p->inner_scale = 2;
 }
 
 extern "C" const char* lorads_create_error(void) { return g_create_error.c_str(); }
@@ -236,7 +243,7 @@ namespace {
 void free_state(SolverState& st) {
     if (st.exec) cudaGraphExecDestroy(st.exec);
     dfree(st.R); dfree(st.CR); dfree(st.D); dfree(st.CD); dfree(st.G); dfree(st.W); dfree(st.hist);
-    dfree(st.y); dfree(st.ytil); dfree(st.zrow); dfree(st.zk);
+    dfree(st.y); dfree(st.ytil); dfree(st.zrow); dfree(st.zk); dfree(st.ydf);
     st = SolverState();
 }
 }  // namespace
@@ -246,7 +253,7 @@ extern "C" void lorads_destroy(lorads_ctx* ctx) {
     if (ctx->solve_stream) cudaStreamSynchronize(ctx->solve_stream);
     free_state(ctx->st);
     dfree(ctx->c_rowptr); dfree(ctx->c_col); dfree(ctx->c_val); dfree(ctx->c_val32); dfree(ctx->c_valdf);
-    dfree(ctx->dk); dfree(ctx->da);
+    dfree(ctx->dk); dfree(ctx->da); dfree(ctx->da32); dfree(ctx->da_df); dfree(ctx->b_df);
     dfree(ctx->a_rowptr); dfree(ctx->a_col); dfree(ctx->a_k); dfree(ctx->a_a);
     dfree(ctx->k_row); dfree(ctx->k_col); dfree(ctx->k_a); dfree(ctx->k_id); dfree(ctx->b);
     dfree(ctx->part); dfree(ctx->small); dfree(ctx->ctrl);
@@ -436,8 +443,24 @@ lorads_status validate_and_build(lorads_ctx* ctx, int64_t n, const int64_t* rp, 
     if ((s = upload(ctx, &ctx->c_val32, cv32.data(), nnz))) return s;
     if ((s = upload(ctx, &ctx->c_valdf, cvdf.data(), nnz))) return s;
     if (m_diag > 0) {
+        std::vector<float> da32(n);
+        std::vector<dfloat> dadf(n);
+        for (int64_t i = 0; i < n; ++i) {
+            da32[i] = (float)da[i];
+            dadf[i] = dfloat(da32[i], (float)(da[i] - (double)da32[i]));
+        }
         if ((s = upload(ctx, &ctx->dk, dk.data(), n))) return s;
         if ((s = upload(ctx, &ctx->da, da.data(), n))) return s;
+        if ((s = upload(ctx, &ctx->da32, da32.data(), n))) return s;
+        if ((s = upload(ctx, &ctx->da_df, dadf.data(), n))) return s;
+    }
+    {
+        std::vector<dfloat> bdf(m);
+        for (int64_t k = 0; k < m; ++k) {
+            const float h = (float)b[k];
+            bdf[k] = dfloat(h, (float)(b[k] - (double)h));
+        }
+        if ((s = upload(ctx, &ctx->b_df, bdf.data(), m))) return s;
     }
     if (m_off > 0) {
         if ((s = upload(ctx, &ctx->a_rowptr, a_rp.data(), n + 1))) return s;
@@ -454,7 +477,7 @@ lorads_status validate_and_build(lorads_ctx* ctx, int64_t n, const int64_t* rp, 
     p.n = n; p.m = m;
     p.c_rowptr = ctx->c_rowptr; p.c_col = ctx->c_col; p.c_val = ctx->c_val; p.c_val32 = ctx->c_val32;
     p.c_valdf = ctx->c_valdf;
-    p.dk = ctx->dk; p.da = ctx->da;
+    p.dk = ctx->dk; p.da = ctx->da; p.da32 = ctx->da32; p.da_df = ctx->da_df; p.b_df = ctx->b_df;
     p.a_rowptr = ctx->a_rowptr; p.a_col = ctx->a_col; p.a_k = ctx->a_k; p.a_a = ctx->a_a;
     p.k_row = ctx->k_row; p.k_col = ctx->k_col; p.k_a = ctx->k_a; p.k_id = ctx->k_id;
     p.m_diag = m_diag; p.m_off = m_off;
@@ -538,7 +561,7 @@ extern "C" lorads_status lorads_spmm(lorads_ctx* ctx, const void* R, int32_t r, 
     if (!R || !out || !aligned16(R) || !aligned16(out)) return set_err(ctx, "R and out must be 16-byte aligned device pointers"), LORADS_ERR_INVALID_ARG;
     if (R == out) return set_err(ctx, "out must not alias R"), LORADS_ERR_INVALID_ARG;
     const int nb = row_blocks(ctx, ctx->n, sh.L);
-    SpmmCArgs a{ctx->pd, R, out, ld, sh, v, 1, EPI_NONE, nullptr, nullptr, nullptr, nullptr, 0.0, nullptr,
+    SpmmCArgs a{ctx->pd, R, out, ld, sh, v, 1, EPI_NONE, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, nullptr,
                 nb, nullptr, PH_ALWAYS, ctx->stream};
     SpmmAArgs aa{ctx->pd, R, out, ld, sh, v, -1.0, 1, nb, nullptr, PH_ALWAYS, ctx->stream};
     switch (prec) {
@@ -566,7 +589,7 @@ extern "C" lorads_status lorads_constraint_eval(lorads_ctx* ctx, const void* U, 
     if (s) return s;
     if (!U || !V || !out || !aligned16(U) || !aligned16(V))
         return set_err(ctx, "U, V must be 16-byte aligned device pointers and out non-NULL"), LORADS_ERR_INVALID_ARG;
-    ConsArgs a{ctx->pd, CONS_EVAL, 0, ctx->m, U, V, ld, sh, nullptr, out, nullptr, nullptr, 0.0, nullptr,
+    ConsArgs a{ctx->pd, CONS_EVAL, 0, ctx->m, U, V, ld, sh, nullptr, out, nullptr, nullptr, nullptr, 0.0, nullptr,
                row_blocks(ctx, ctx->m, sh.L), nullptr, PH_ALWAYS, ctx->stream};
     switch (prec) {
         case LORADS_FP64: launch_cons<double, double>(a); break;
@@ -591,9 +614,9 @@ extern "C" lorads_status lorads_linesearch_coeffs(lorads_ctx* ctx, const void* R
     const int nbc = row_blocks(ctx, std::max<int64_t>(ctx->m_off, 1), sh.L);
     double* pl = part_of(ctx, PART_LS);
     double* pc = part_of(ctx, PART_CONS_LS);
-    SpmmCArgs a{ctx->pd, D, nullptr, ld, sh, nullptr, 0, EPI_LS, R, y, nullptr, nullptr, rho, pl,
+    SpmmCArgs a{ctx->pd, D, nullptr, ld, sh, nullptr, 0, EPI_LS, R, y, nullptr, nullptr, nullptr, rho, pl,
                 nb, nullptr, PH_ALWAYS, ctx->stream};
-    ConsArgs ca{ctx->pd, CONS_LS, ctx->m_diag, ctx->m, R, D, ld, sh, const_cast<double*>(y), nullptr, nullptr, nullptr, rho,
+    ConsArgs ca{ctx->pd, CONS_LS, ctx->m_diag, ctx->m, R, D, ld, sh, const_cast<double*>(y), nullptr, nullptr, nullptr, nullptr, rho,
                 pc, nbc, nullptr, PH_ALWAYS, ctx->stream};
     switch (prec) {
         case LORADS_FP64:
@@ -660,14 +683,14 @@ struct Driver {
     // G = grad L at the current R (outer tail and start): [y~, W], update, reset
     void outer_gradient(int ph) {
         if (c->m_off) {
-            ConsArgs yt{p(), CONS_YTIL, c->m_diag, c->m, st.R, st.R, st.ld, st.sh, st.y, st.ytil, st.zk, c->ctrl, 0.0,
+            ConsArgs yt{p(), CONS_YTIL, c->m_diag, c->m, st.R, st.R, st.ld, st.sh, st.y, st.ytil, st.zk, nullptr, c->ctrl, 0.0,
                         part_of(c, PART_YTIL), nb_off, c->ctrl, ph, s};
             timed(FAM_CONS_YTIL, [&] { launch_cons<TR, TR>(yt); });
             SpmmAArgs w{p(), st.R, st.W, st.ld, st.sh, st.ytil, 1.0, 0, nb_rows, c->ctrl, ph, s};
             timed(FAM_SPMM_A, [&] { launch_spmm_a<TR, TD>(w); });
         }
         UpdateArgs u{p(), false, false, st.R, st.CR, st.D, st.CD, st.G, c->m_off ? st.W : nullptr, st.hist,
-                     st.slot_stride, st.ld, st.sh, st.y, st.zrow, c->ctrl, part_of(c, PART_UPD), nb_rows, c->ctrl, ph, s};
+                     st.slot_stride, st.ld, st.sh, st.y, st.ydf, st.zrow, c->ctrl, part_of(c, PART_UPD), nb_rows, c->ctrl, ph, s};
         timed(FAM_GRAD, [&] { launch_update<TR, TD>(u); });
         timed(FAM_HIST, [&] {
             ctrl_hist(s, c->ctrl, HIST_RESET, part_of(c, PART_UPD), nb_rows,
@@ -676,14 +699,14 @@ struct Driver {
     }
 
     void spmm_CR(int ph) {
-        SpmmCArgs a{p(), st.R, st.CR, st.ld, st.sh, nullptr, 1, EPI_OBJ, st.R, st.y, nullptr, c->ctrl, 0.0,
+        SpmmCArgs a{p(), st.R, st.CR, st.ld, st.sh, nullptr, 1, EPI_OBJ, st.R, st.y, nullptr, nullptr, c->ctrl, 0.0,
                     part_of(c, PART_OBJ), nb_rows, c->ctrl, ph, s};
         timed(FAM_SPMM_CR, [&] { launch_spmm_c<TR, TR, TR>(a); });
     }
 
     void enqueue_init() {
         spmm_CR(PH_ALWAYS);
-        ConsArgs zz{p(), CONS_ZZ, 0, c->m, st.R, st.R, st.ld, st.sh, st.y, nullptr, nullptr, c->ctrl, 0.0,
+        ConsArgs zz{p(), CONS_ZZ, 0, c->m, st.R, st.R, st.ld, st.sh, st.y, nullptr, nullptr, nullptr, c->ctrl, 0.0,
                     part_of(c, PART_CONS), nb_all, c->ctrl, PH_ALWAYS, s};
         timed(FAM_MISC, [&] { launch_cons<TR, TR>(zz); });
         timed(FAM_MISC, [&] { ctrl_init(s, c->ctrl, part_of(c, PART_CONS), nb_all, part_of(c, PART_OBJ), nb_rows); });
@@ -700,11 +723,11 @@ struct Driver {
         DirArgs d{nunits, st.G, st.D, st.hist, st.slot_stride, c->ctrl, part_of(c, PART_DIR), nb_flat, c->ctrl,
                   PH_INNER, s};
         timed(FAM_DIR, [&] { launch_dir<TD>(d); });
-        SpmmCArgs ls{p(), st.D, st.CD, st.ld, st.sh, nullptr, 1, EPI_LS, st.R, st.y, st.zrow, c->ctrl, 0.0,
+        SpmmCArgs ls{p(), st.D, st.CD, st.ld, st.sh, nullptr, 1, EPI_LS, st.R, st.y, st.zrow, st.ydf, c->ctrl, 0.0,
                      part_of(c, PART_LS), nb_rows, c->ctrl, PH_INNER, s};
         timed(FAM_SPMM_LS, [&] { launch_spmm_c<TD, TD, TR>(ls); });
         if (c->m_off) {
-            ConsArgs cl{p(), CONS_LS, c->m_diag, c->m, st.R, st.D, st.ld, st.sh, st.y, nullptr, st.zk, c->ctrl, 0.0,
+            ConsArgs cl{p(), CONS_LS, c->m_diag, c->m, st.R, st.D, st.ld, st.sh, st.y, nullptr, st.zk, nullptr, c->ctrl, 0.0,
                         part_of(c, PART_CONS_LS), nb_off, c->ctrl, PH_INNER, s};
             timed(FAM_CONS_LS, [&] { launch_cons<TR, TD>(cl); });
         }
@@ -715,14 +738,14 @@ struct Driver {
         if (c->m_off) {
             StepArgs sa{nunits, st.R, st.CR, st.D, st.CD, c->ctrl, nb_flat, c->ctrl, PH_STEP, s};
             timed(FAM_STEP, [&] { launch_step<TR, TD>(sa); });
-            ConsArgs yt{p(), CONS_YTIL, c->m_diag, c->m, st.R, st.R, st.ld, st.sh, st.y, st.ytil, st.zk, c->ctrl, 0.0,
+            ConsArgs yt{p(), CONS_YTIL, c->m_diag, c->m, st.R, st.R, st.ld, st.sh, st.y, st.ytil, st.zk, nullptr, c->ctrl, 0.0,
                         part_of(c, PART_YTIL), nb_off, c->ctrl, PH_STEP, s};
             timed(FAM_CONS_YTIL, [&] { launch_cons<TR, TR>(yt); });
             SpmmAArgs w{p(), st.R, st.W, st.ld, st.sh, st.ytil, 1.0, 0, nb_rows, c->ctrl, PH_STEP, s};
             timed(FAM_SPMM_A, [&] { launch_spmm_a<TR, TD>(w); });
         }
         UpdateArgs u{p(), c->m_off == 0, true, st.R, st.CR, st.D, st.CD, st.G, c->m_off ? st.W : nullptr, st.hist,
-                     st.slot_stride, st.ld, st.sh, st.y, st.zrow, c->ctrl, part_of(c, PART_UPD), nb_rows, c->ctrl, PH_STEP, s};
+                     st.slot_stride, st.ld, st.sh, st.y, st.ydf, st.zrow, c->ctrl, part_of(c, PART_UPD), nb_rows, c->ctrl, PH_STEP, s};
         timed(FAM_UPDATE, [&] { launch_update<TR, TD>(u); });
         timed(FAM_HIST, [&] {
             ctrl_hist(s, c->ctrl, HIST_STEP, part_of(c, PART_UPD), nb_rows,
@@ -732,7 +755,7 @@ struct Driver {
 
     // ALM outer step (Sec. 2.1) once the inner loop has finished
     void enqueue_outer() {
-        ConsArgs yu{p(), CONS_YUPD, 0, c->m, st.R, st.R, st.ld, st.sh, st.y, nullptr, nullptr, c->ctrl, 0.0,
+        ConsArgs yu{p(), CONS_YUPD, 0, c->m, st.R, st.R, st.ld, st.sh, st.y, nullptr, nullptr, st.ydf, c->ctrl, 0.0,
                     part_of(c, PART_CONS), nb_all, c->ctrl, PH_OUTER, s};
         timed(FAM_CONS_YUPD, [&] { launch_cons<TR, TR>(yu); });
         spmm_CR(PH_OUTER);
@@ -782,7 +805,10 @@ lorads_status alloc_state(lorads_ctx* ctx, int prec, int r) {
         if ((s = dalloc(ctx, &st.ytil, ctx->m))) return s;
     }
     if ((s = dalloc(ctx, &st.y, ctx->m))) return s;
-    if ((s = dalloc(ctx, &st.zrow, ctx->n))) return s;
+    const bool fp64_path = std::is_same<TR, double>::value && std::is_same<TD, double>::value;
+    // z cache: double (FP64), double-float (DF64) or float (mixed, FP32): 8 bytes covers all
+    if ((s = dalloc(ctx, reinterpret_cast<double**>(&st.zrow), ctx->n))) return s;
+    if (!fp64_path && (s = dalloc(ctx, &st.ydf, ctx->m))) return s;
     if ((s = dalloc(ctx, &st.zk, ctx->m))) return s;
     CK(cudaMemset(st.R, 0, nl * sizeof(TR)));
     CK(cudaMemset(st.CR, 0, nl * sizeof(TR)));
@@ -857,6 +883,7 @@ lorads_status grow_rank(lorads_ctx* ctx, int prec, int outer_done) {
                      flat_blocks(ctx, ctx->n * (int64_t)(r_new - r_old)));
     ctx->launches += 4;                     // sumsq, fold, convert, columns
     CK(cudaMemcpyAsync(st.y, y_keep, ctx->m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (st.ydf) convert<double, dfloat>(s, ctx->m, 1, 1, 1, st.y, st.ydf, flat_blocks(ctx, ctx->m));
     CK(cudaStreamSynchronize(s));
     cudaFree(R_old);
     cudaFree(y_keep);
@@ -972,10 +999,15 @@ lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0,
     }
     if (y0) CK(cudaMemcpyAsync(st.y, y0, ctx->m * sizeof(double), cudaMemcpyHostToDevice, ss));
     else CK(cudaMemsetAsync(st.y, 0, ctx->m * sizeof(double), ss));
+    if (st.ydf) {
+        convert<double, dfloat>(ss, ctx->m, 1, 1, 1, st.y, st.ydf, flat_blocks(ctx, ctx->m));
+        ctx->launches += 1;
+    }
     // control block
     Ctrl h{};
     h.rho = P.rho0 > 0 ? P.rho0 : 1.0 / ctx->mean_abs_c;
     h.lbfgs_mem = P.lbfgs_mem;
+    h.total_limit = ctx->iter_limit > 0 ? (int)std::min<int64_t>(ctx->iter_limit, INT32_MAX) : 0;
     h.max_inner = P.max_inner;
     h.max_outer = P.max_outer;
     h.rank_threshold = std::max(1, P.rank_update_threshold);
@@ -984,6 +1016,7 @@ lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0,
     h.inner_scale = P.inner_scale;
     h.tol = P.tol;
     h.inner_rel = P.inner_rel;
+    h.inner_progress = P.inner_progress;
     h.bnorm1 = ctx->bnorm1;
     h.bnorm_inf = ctx->bnorm_inf;
     h.rho_growth = P.rho_growth;
@@ -1092,6 +1125,12 @@ extern "C" lorads_status lorads_get_solution(lorads_ctx* ctx, double* R_host, in
         CK(cudaMemcpyAsync(y_host, st.y, ctx->m * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
     }
+    return LORADS_OK;
+}
+
+extern "C" lorads_status lorads_set_iteration_limit(lorads_ctx* ctx, int64_t max_total_inner) {
+    if (!ctx || max_total_inner < 0) return LORADS_ERR_INVALID_ARG;
+    ctx->iter_limit = max_total_inner;
     return LORADS_OK;
 }
 

@@ -147,10 +147,10 @@ __device__ __forceinline__ void block_partials(PA (&acc)[NQ], double* part) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-        double v = double(acc[q]);
+        PA v = acc[q];                       // warp tree in the partial's own type
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][q] = v;
+        for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
+        if (lane == 0) red[warp][q] = double(v);
     }
     __syncthreads();
     for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
@@ -208,11 +208,12 @@ struct Ctrl {
     int max_inner;
     int max_outer;
     int rank_threshold;
+    int total_limit;            // > 0: stop after this many L-BFGS iterations in total
     int lbfgs_scaling;
     int rho_policy;
     int inner_scale;
     // outer-loop state
-    double tol, inner_rel, bnorm1, bnorm_inf;
+    double tol, inner_rel, inner_progress, gnorm0, bnorm1, bnorm_inf;
     double rho_growth, rho_max, infeas_decrease;
     double err1, err1_prev, err3, primal_obj, dual_obj;
     double last_iter_rho;
@@ -229,9 +230,10 @@ enum {
     // SpMM C R with objective
     PO_CRR = 0, PO_N,
 };
-// row-update kernel: fixed slots then 5 per old pair
-enum { PU_GG = 0, PU_ZZ, PU_GSN, PU_GYN, PU_SYN, PU_YYN, PU_SSN, PU_FIXED };
-constexpr int PU_PER_OLD = 5;          // <G,S_v>, <G,Y_v>, <Snew,Y_v>, <S_v,Ynew>, <Ynew,Y_v>
+// row-update kernel: fixed slots then 3 per old pair; <G',S_v>, <G',Y_v>,
+// <G',S_new> and ||S_new||^2 follow from these and the previous Gram data
+enum { PU_GG = 0, PU_ZZ, PU_GYN, PU_SYN, PU_YYN, PU_FIXED };
+constexpr int PU_PER_OLD = 3;          // <S_new,Y_v>, <S_v,Y_new>, <Y_new,Y_v>
 constexpr int PU_N = PU_FIXED + PU_PER_OLD * (kMaxMem - 1);
 
 }  // namespace lorads

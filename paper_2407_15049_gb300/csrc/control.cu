@@ -215,11 +215,19 @@ __device__ void plan_next_slot(Ctrl* c, int T) {
 
 __device__ void finish_inner_test(Ctrl* c) {
     const double zn = sqrt(fmax(c->znorm2, 0.0));
-    const double zs = c->inner_scale ? c->rho * zn : zn;
-    const double thr = c->inner_rel * fmax(zs, c->tol * (1.0 + c->bnorm_inf));
+    const double floor_ = c->tol * (1.0 + c->bnorm_inf);
+    double thr;
+    if (c->inner_scale == 0) thr = c->inner_rel * fmax(zn, floor_);
+    else if (c->inner_scale == 1) thr = c->inner_rel * fmax(c->rho * zn, floor_);
+    else thr = fmax(floor_, fmin(c->inner_rel * c->rho * zn, c->inner_progress * c->gnorm0));
     const double gn = sqrt(fmax(c->gnorm2, 0.0));
     if (!isfinite(gn) || !isfinite(zn)) {
         c->status = 5;                          // LORADS_ERR_NUMERIC
+        c->solve_done = 1;
+        return;
+    }
+    if (c->total_limit > 0 && c->total_inner >= c->total_limit) {
+        c->status = 6;                          // LORADS_ERR_MAXITER
         c->solve_done = 1;
         return;
     }
@@ -326,27 +334,31 @@ __global__ void k_ctrl_hist(Ctrl* c, int mode, const double* part_upd, int nb_up
     }
     if (reset) {
         mem_clear(c);
+        c->gnorm0 = sqrt(fmax(c->gnorm2, 0.0));
         c->inner_k = 0;
         c->inner_done = 0;
         c->step_ok = 0;
         c->phase = PHASE_INNER;
     } else if (c->step_ok) {
-        const double ys = su[PU_SYN], yy = su[PU_YYN], ss = su[PU_SSN];
+        const double tau = c->tau;
+        const double ys = su[PU_SYN], yy = su[PU_YYN];
+        const double ss = tau * tau * c->DD;                      // ||tau D||^2
         if (ys > 1e-16 * sqrt(fmax(yy, 0.0) * fmax(ss, 0.0)) && ys > 0.0) {
             const int ns = c->new_slot;
             for (int t = 0; t < c->old_count; ++t) {
                 const int v = c->old_slots[t];
                 const double* q = su + PU_FIXED + PU_PER_OLD * t;
-                c->g_s[v] = q[0];
-                c->g_y[v] = q[1];
-                c->SY[ns][v] = q[2];
-                c->SY[v][ns] = q[3];
-                c->YY[ns][v] = q[4];
-                c->YY[v][ns] = q[4];
+                // G' = G + Y_new: dots with the new gradient from the previous ones
+                c->g_s[v] += q[1];
+                c->g_y[v] += q[2];
+                c->SY[ns][v] = q[0];
+                c->SY[v][ns] = q[1];
+                c->YY[ns][v] = q[2];
+                c->YY[v][ns] = q[2];
             }
             c->SY[ns][ns] = ys;
             c->YY[ns][ns] = yy;
-            c->g_s[ns] = su[PU_GSN];
+            c->g_s[ns] = tau * c->gD + ys;                          // <G,S_new> + <Y_new,S_new>
             c->g_y[ns] = su[PU_GYN];
             // order: keep old slots (oldest first), append the new one
             for (int t = 0; t < c->old_count; ++t) c->order[t] = c->old_slots[t];
@@ -392,8 +404,10 @@ __global__ void k_ctrl_outer(Ctrl* c, const double* part_cons, int nb_cons, cons
         return;
     }
     const bool capped = c->inner_k >= c->max_inner;
-    if (err1 > c->infeas_decrease * c->err1_prev && (c->rho_policy == 0 || !capped))
-        c->rho = fmin(c->rho * c->rho_growth, c->rho_max);
+    bool grow = err1 > c->infeas_decrease * c->err1_prev;
+    if (c->rho_policy == 1) grow = grow && !capped;
+    else if (c->rho_policy == 2) grow = grow && (!capped || err1 > c->err1_prev);
+    if (grow) c->rho = fmin(c->rho * c->rho_growth, c->rho_max);
     c->err1_prev = err1;
     if (c->outer >= c->max_outer) {
         c->status = 6;                          // LORADS_ERR_MAXITER

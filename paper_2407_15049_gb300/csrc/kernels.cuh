@@ -22,6 +22,9 @@ struct ProbDev {
     // diagonal constraints by row: constraint index (-1: none) and coefficient
     const int32_t* dk;
     const double* da;
+    const float* da32;          // float and double-float mirrors of da and b for the
+    const dfloat* da_df;        // FP32-unit paths (no per-row FP64 there)
+    const dfloat* b_df;
     // off-diagonal constraints as a symmetric pattern: slot -> (column, constraint, coef)
     const int64_t* a_rowptr;
     const int32_t* a_col;
@@ -83,6 +86,29 @@ template <typename TV> __device__ __forceinline__ const TV* cvals(const ProbDev&
 template <> __device__ __forceinline__ const double* cvals<double>(const ProbDev& p) { return p.c_val; }
 template <> __device__ __forceinline__ const float* cvals<float>(const ProbDev& p) { return p.c_val32; }
 template <> __device__ __forceinline__ const dfloat* cvals<dfloat>(const ProbDev& p) { return p.c_valdf; }
+
+// per-row scalar type of the row-update math: double on the FP64 path,
+// otherwise the arithmetic type of R (double-float or float)
+template <typename TR, typename TD>
+using rowscalar_t = std::conditional_t<std::is_same_v<arith_t<TR>, double> && std::is_same_v<arith_t<TD>, double>,
+                                       double, arith_t<TR>>;
+
+template <typename S> __device__ __forceinline__ S ld_scalar(const double* d, const dfloat* df, int64_t k);
+template <> __device__ __forceinline__ double ld_scalar<double>(const double* d, const dfloat*, int64_t k) {
+    return __ldg(d + k);
+}
+template <> __device__ __forceinline__ dfloat ld_scalar<dfloat>(const double*, const dfloat* df, int64_t k) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(df + k));
+    return dfloat(v.x, v.y);
+}
+template <> __device__ __forceinline__ float ld_scalar<float>(const double*, const dfloat* df, int64_t k) {
+    return __ldg(reinterpret_cast<const float*>(df + k));     // hi part
+}
+
+// type of the per-row z cache (and of the line-search row terms): double on the
+// FP64 path, otherwise the arithmetic type of the direction D
+template <typename TD, typename TR>
+using zrow_t = std::conditional_t<std::is_same_v<part_t<TD, TR>, double>, double, arith_t<TD>>;
 
 // read-only scalar loads
 __device__ __forceinline__ double ldv(const double* p) { return __ldg(p); }
@@ -166,17 +192,23 @@ template <typename TX, typename TO, typename TR, int CPL, int EPI>
 __global__ void __launch_bounds__(kThreads)
 k_spmm_c(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int L, int Q,
          const double* __restrict__ v, int write_out,
-         const TR* __restrict__ R, const double* __restrict__ y, const double* __restrict__ zrow,
-         const Ctrl* ctrl, double rho_arg, double* __restrict__ part, const Ctrl* gate, int ph) {
+         const TR* __restrict__ R, const double* __restrict__ y, const void* __restrict__ zrow_v,
+         const dfloat* __restrict__ ydf, const Ctrl* ctrl, double rho_arg, double* __restrict__ part,
+         const Ctrl* gate, int ph) {
     if (gated_off(gate, ph)) return;
     using A = arith_t<TO>;
     using TV = cval_t<TX>;
     using PA = part_t<TO, TR>;
+    // scalar type of the per-row line-search terms: double on the FP64 path, otherwise
+    // the arithmetic type of the direction (float, or double-float on the DF64 path)
+    using LS = zrow_t<TX, TR>;
+    const LS* __restrict__ zrow = static_cast<const LS*>(zrow_v);
     constexpr int NQ = EPI == EPI_LS ? PL_N : (EPI == EPI_OBJ ? PO_N : 1);
     PA accq[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) accq[q] = PA(0);
     const double rho = ctrl ? ctrl->rho : rho_arg;
+    const LS rho_s = LS(rho);
     const TV* __restrict__ cv = cvals<TV>(p);
     RowLoop rl(L);
     for (int64_t base = rl.first; base < p.n; base += rl.stride) {
@@ -287,16 +319,39 @@ k_spmm_c(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int 
                 if (act && rl.lig == 0) {
                     const int k = __ldg(p.dk + i);
                     if (k >= 0) {
-                        const double a = __ldg(p.da + i);
-                        const double z = zrow ? __ldg(zrow + i) : a * double(t_rr) - __ldg(p.b + k);
-                        const double yt = __ldg(y + k) - rho * z;
-                        const double q1 = 2.0 * a * double(t_rd);
-                        const double q2 = a * double(t_dd);
-                        accq[PL_YQ1] += PA(yt * q1);
-                        accq[PL_YQ2] += PA(yt * q2);
-                        accq[PL_Q1Q1] += PA(q1 * q1);
-                        accq[PL_Q1Q2] += PA(q1 * q2);
-                        accq[PL_Q2Q2] += PA(q2 * q2);
+                        if constexpr (std::is_same_v<LS, double>) {
+                            const double a = __ldg(p.da + i);
+                            const double z = zrow ? zrow[i] : a * double(t_rr) - __ldg(p.b + k);
+                            const double yt = __ldg(y + k) - rho * z;
+                            const double q1 = 2.0 * a * double(t_rd);
+                            const double q2 = a * double(t_dd);
+                            accq[PL_YQ1] += PA(yt * q1);
+                            accq[PL_YQ2] += PA(yt * q2);
+                            accq[PL_Q1Q1] += PA(q1 * q1);
+                            accq[PL_Q1Q2] += PA(q1 * q2);
+                            accq[PL_Q2Q2] += PA(q2 * q2);
+                        } else {
+                            // line-search terms in the direction's arithmetic; z from the
+                            // row cache, else |r|^2 in double-float
+                            const LS a = ld_scalar<LS>(p.da, p.da_df, i);
+                            LS z;
+                            if (zrow) {
+                                z = zrow[i];
+                            } else {
+                                const dfloat zz = dfloat(t_rr) * ld_scalar<dfloat>(p.da, p.da_df, i) -
+                                                  ld_scalar<dfloat>(p.b, p.b_df, k);
+                                z = LS(zz);
+                            }
+                            const LS yv = ydf ? ld_scalar<LS>(y, ydf, k) : LS(__ldg(y + k));
+                            const LS yt = yv - rho_s * z;
+                            const LS q1 = LS(2) * a * LS(t_rd);
+                            const LS q2 = a * LS(t_dd);
+                            accq[PL_YQ1] += PA(yt * q1);
+                            accq[PL_YQ2] += PA(yt * q2);
+                            accq[PL_Q1Q1] += PA(q1 * q1);
+                            accq[PL_Q1Q2] += PA(q1 * q2);
+                            accq[PL_Q2Q2] += PA(q2 * q2);
+                        }
                     }
                 }
             }
@@ -357,14 +412,14 @@ k_spmm_a(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int 
 //   CONS_LS  : z = f a r_i.r_j - b, y~ = y - rho z, q1 = f a (r_i.d_j + d_i.r_j),
 //              q2 = f a d_i.d_j; partials of y~q1, y~q2, q1^2, q1q2, q2^2
 //   CONS_YTIL: out[k] = y~ ;  partial |z|^2
-//   CONS_YUPD: y[k] <- y~  ;  partials |z|^2, b^T y_new
+//   CONS_YUPD: y[k] <- y~ (and its double-float mirror);  partials |z|^2, b^T y_new
 //   CONS_ZZ  : partial |z|^2
 enum { CONS_EVAL = 0, CONS_LS = 1, CONS_YTIL = 2, CONS_YUPD = 3, CONS_ZZ = 4 };
 
 template <typename TU, typename TV, int CPL, int MODE>
 __global__ void __launch_bounds__(kThreads)
 k_cons(ProbDev p, int64_t k0, int64_t k1, const TU* __restrict__ U, const TV* __restrict__ V, int ld, int L, int Q,
-       double* y, double* __restrict__ out, double* zk, const Ctrl* ctrl, double rho_arg,
+       double* y, double* __restrict__ out, double* zk, dfloat* ydf, const Ctrl* ctrl, double rho_arg,
        double* __restrict__ part, const Ctrl* gate, int ph) {
     if (gated_off(gate, ph)) return;
     constexpr int NQ = MODE == CONS_LS ? PL_N : PC_N;
@@ -467,6 +522,7 @@ k_cons(ProbDev p, int64_t k0, int64_t k1, const TU* __restrict__ U, const TV* __
                     } else if constexpr (MODE == CONS_YUPD) {
                         const double yn = y[kid] - rho * z;
                         y[kid] = yn;
+                        if (ydf != nullptr) ydf[kid] = dfloat(yn);
                         accq[PC_BY] += PA(__ldg(p.b + kid) * yn);
                     }
                 }
@@ -566,24 +622,37 @@ k_step(int64_t nunits, TR* __restrict__ R, TR* __restrict__ CR, const TD* __rest
 //          for the diagonal constraint k of row i, w = A*_off(y~) R (if given)
 //   HIST : s_new = tau d, y_new = g' - g   into the new slot, and the dot
 //          products that keep the Gram data of the stored pairs current
+//          (<s_new,y_new>, ||y_new||^2, <g',y_new>, and per stored pair v:
+//          <s_new,y_v>, <s_v,y_new>, <y_new,y_v>)
 // partials: ||g'||^2, sum z_k^2 (diagonal constraints), and the Gram dots.
+// 3 resident blocks per SM where the registers allow it without real spills
+// (one unit per lane, FP32-unit arithmetic), 2 otherwise.
+template <typename TR, typename TD, int CPL>
+constexpr int update_min_blocks() {
+    return (CPL == 1 && !std::is_same_v<arith_t<TR>, double>) ? 3 : 2;
+}
+
 template <typename TR, typename TD, int CPL, bool STEP, bool HIST>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, (update_min_blocks<TR, TD, CPL>()))
 k_update(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restrict__ D,
          const TD* __restrict__ CD, TD* __restrict__ G, const TD* __restrict__ W,
          TD* __restrict__ hist, int64_t slot_stride, int ld, int L, int Q,
-         const double* __restrict__ y, double* __restrict__ zrow, const Ctrl* ctrl, double* __restrict__ part,
-         const Ctrl* gate, int ph) {
+         const double* __restrict__ y, const dfloat* __restrict__ ydf, void* __restrict__ zrow_v,
+         const Ctrl* ctrl, double* __restrict__ part, const Ctrl* gate, int ph) {
     if (gated_off(gate, ph)) return;
     using AR = arith_t<TR>;
     using AD = arith_t<TD>;
     using PA = part_t<TR, TD>;
+    using RS = rowscalar_t<TR, TD>;             // per-row scalars (no FP64 off the FP64 path)
+    using ZS = zrow_t<TD, TR>;
+    ZS* __restrict__ zrow = static_cast<ZS*>(zrow_v);
+    const RS rho_r = RS(ctrl->rho);
     PA accq[PU_N];
 #pragma unroll
     for (int q = 0; q < PU_N; ++q) accq[q] = PA(0);
-    const double rho = ctrl->rho;
     const double taud = ctrl->tau;
     const AR tau = AR(taud);
+    const AD tau_d = AD(taud);
     int nold = 0;
     TD* Snew = nullptr;
     TD* Ynew = nullptr;
@@ -634,12 +703,13 @@ k_update(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restric
             if (act) {
                 const int k = __ldg(p.dk + i);
                 if (k >= 0) {
-                    const double a = __ldg(p.da + i);
-                    const double z = a * double(rr) - __ldg(p.b + k);
-                    coef = AR(a * (__ldg(y + k) - rho * z));
+                    const RS a = ld_scalar<RS>(p.da, p.da_df, i);
+                    const RS z = a * RS(rr) - ld_scalar<RS>(p.b, p.b_df, k);
+                    const RS yv = ydf ? ld_scalar<RS>(y, ydf, k) : RS(__ldg(y + k));
+                    coef = AR(a * (yv - rho_r * z));
                     if (rl.lig == 0) {
                         accq[PU_ZZ] += PA(z * z);
-                        if (zrow != nullptr) zrow[i] = z;
+                        if (zrow != nullptr) zrow[i] = ZS(z);
                     }
                 }
             }
@@ -663,16 +733,14 @@ k_update(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restric
                 for (int c = 0; c < CPL; ++c)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        sn[c].v[e] = AD(taud) * AD(d[c].v[e]);
+                        sn[c].v[e] = tau_d * AD(d[c].v[e]);
                         yn[c].v[e] = AD(g[c].v[e]) - AD(gold[c].v[e]);
                     }
                 store_row<TD, CPL>(sn, Snew, i, ld, L, Q, rl.lig);
                 store_row<TD, CPL>(yn, Ynew, i, ld, L, Q, rl.lig);
-                accq[PU_GSN] += PA(dot_units<AD>(g, sn));
                 accq[PU_GYN] += PA(dot_units<AD>(g, yn));
                 accq[PU_SYN] += PA(dot_units<AD>(sn, yn));
                 accq[PU_YYN] += PA(dot_units<AD>(yn, yn));
-                accq[PU_SSN] += PA(dot_units<AD>(sn, sn));
 #pragma unroll
                 for (int t = 0; t < kMaxMem - 1; ++t) {
                     if (t < nold) {
@@ -680,11 +748,9 @@ k_update(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restric
                         load_row_stream<TD, CPL>(so, So[t], i, ld, L, Q, rl.lig);
                         load_row_stream<TD, CPL>(yo, Yo[t], i, ld, L, Q, rl.lig);
                         PA* q = accq + PU_FIXED + PU_PER_OLD * t;
-                        q[0] += PA(dot_units<AD>(g, so));
-                        q[1] += PA(dot_units<AD>(g, yo));
-                        q[2] += PA(dot_units<AD>(sn, yo));
-                        q[3] += PA(dot_units<AD>(so, yn));
-                        q[4] += PA(dot_units<AD>(yn, yo));
+                        q[0] += PA(dot_units<AD>(sn, yo));
+                        q[1] += PA(dot_units<AD>(so, yn));
+                        q[2] += PA(dot_units<AD>(yn, yo));
                     }
                 }
             }

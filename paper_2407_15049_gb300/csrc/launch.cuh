@@ -25,13 +25,13 @@ void launch_spmm_c(const SpmmCArgs& a) {
     LORADS_CPL_SWITCH(a.sh.CPL, {
         if (a.epi == EPI_LS)
             k_spmm_c<TX, TO, TR, CPL, EPI_LS><<<a.blocks, kThreads, 0, a.stream>>>(
-                a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.write_out, R, a.y, a.zrow, a.ctrl, a.rho, a.part, a.gate, a.ph);
+                a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.write_out, R, a.y, a.zrow, a.ydf, a.ctrl, a.rho, a.part, a.gate, a.ph);
         else if (a.epi == EPI_OBJ)
             k_spmm_c<TX, TO, TR, CPL, EPI_OBJ><<<a.blocks, kThreads, 0, a.stream>>>(
-                a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.write_out, R, a.y, a.zrow, a.ctrl, a.rho, a.part, a.gate, a.ph);
+                a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.write_out, R, a.y, a.zrow, a.ydf, a.ctrl, a.rho, a.part, a.gate, a.ph);
         else
             k_spmm_c<TX, TO, TR, CPL, EPI_NONE><<<a.blocks, kThreads, 0, a.stream>>>(
-                a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.write_out, R, a.y, a.zrow, a.ctrl, a.rho, a.part, a.gate, a.ph);
+                a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.write_out, R, a.y, a.zrow, a.ydf, a.ctrl, a.rho, a.part, a.gate, a.ph);
     })
 }
 
@@ -54,23 +54,23 @@ void launch_cons(const ConsArgs& a) {
         switch (a.mode) {
             case CONS_EVAL:
                 k_cons<TU, TV, CPL, CONS_EVAL><<<a.blocks, kThreads, 0, a.stream>>>(
-                    a.p, a.k0, a.k1, U, V, a.ld, a.sh.L, a.sh.Q, a.y, a.out, a.zk, a.ctrl, a.rho, a.part, a.gate, a.ph);
+                    a.p, a.k0, a.k1, U, V, a.ld, a.sh.L, a.sh.Q, a.y, a.out, a.zk, a.ydf, a.ctrl, a.rho, a.part, a.gate, a.ph);
                 break;
             case CONS_LS:
                 k_cons<TU, TV, CPL, CONS_LS><<<a.blocks, kThreads, 0, a.stream>>>(
-                    a.p, a.k0, a.k1, U, V, a.ld, a.sh.L, a.sh.Q, a.y, a.out, a.zk, a.ctrl, a.rho, a.part, a.gate, a.ph);
+                    a.p, a.k0, a.k1, U, V, a.ld, a.sh.L, a.sh.Q, a.y, a.out, a.zk, a.ydf, a.ctrl, a.rho, a.part, a.gate, a.ph);
                 break;
             case CONS_YTIL:
                 k_cons<TU, TV, CPL, CONS_YTIL><<<a.blocks, kThreads, 0, a.stream>>>(
-                    a.p, a.k0, a.k1, U, V, a.ld, a.sh.L, a.sh.Q, a.y, a.out, a.zk, a.ctrl, a.rho, a.part, a.gate, a.ph);
+                    a.p, a.k0, a.k1, U, V, a.ld, a.sh.L, a.sh.Q, a.y, a.out, a.zk, a.ydf, a.ctrl, a.rho, a.part, a.gate, a.ph);
                 break;
             case CONS_YUPD:
                 k_cons<TU, TV, CPL, CONS_YUPD><<<a.blocks, kThreads, 0, a.stream>>>(
-                    a.p, a.k0, a.k1, U, V, a.ld, a.sh.L, a.sh.Q, a.y, a.out, a.zk, a.ctrl, a.rho, a.part, a.gate, a.ph);
+                    a.p, a.k0, a.k1, U, V, a.ld, a.sh.L, a.sh.Q, a.y, a.out, a.zk, a.ydf, a.ctrl, a.rho, a.part, a.gate, a.ph);
                 break;
             case CONS_ZZ:
                 k_cons<TU, TV, CPL, CONS_ZZ><<<a.blocks, kThreads, 0, a.stream>>>(
-                    a.p, a.k0, a.k1, U, V, a.ld, a.sh.L, a.sh.Q, a.y, a.out, a.zk, a.ctrl, a.rho, a.part, a.gate, a.ph);
+                    a.p, a.k0, a.k1, U, V, a.ld, a.sh.L, a.sh.Q, a.y, a.out, a.zk, a.ydf, a.ctrl, a.rho, a.part, a.gate, a.ph);
                 break;
             default: break;
         }
@@ -103,13 +103,13 @@ void launch_update(const UpdateArgs& a) {
     LORADS_CPL_SWITCH(a.sh.CPL, {
         if (a.step && a.hist_on)
             k_update<TR, TD, CPL, true, true><<<a.blocks, kThreads, 0, a.stream>>>(
-                a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.zrow, a.ctrl, a.part, a.gate, a.ph);
+                a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph);
         else if (!a.step && a.hist_on)
             k_update<TR, TD, CPL, false, true><<<a.blocks, kThreads, 0, a.stream>>>(
-                a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.zrow, a.ctrl, a.part, a.gate, a.ph);
+                a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph);
         else
             k_update<TR, TD, CPL, false, false><<<a.blocks, kThreads, 0, a.stream>>>(
-                a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.zrow, a.ctrl, a.part, a.gate, a.ph);
+                a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph);
     })
 }
 

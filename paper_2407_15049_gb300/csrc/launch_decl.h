@@ -14,7 +14,7 @@ struct SpmmCArgs {
     const ProbDev& p;
     const void* X; void* out; int ld; Shape sh;
     const double* v; int write_out; int epi;
-    const void* R; const double* y; const double* zrow; const Ctrl* ctrl; double rho; double* part;
+    const void* R; const double* y; const void* zrow; const dfloat* ydf; const Ctrl* ctrl; double rho; double* part;
     int blocks; const Ctrl* gate; int ph; cudaStream_t stream;
 };
 
@@ -29,7 +29,7 @@ struct ConsArgs {
     const ProbDev& p;
     int mode; int64_t k0, k1;
     const void* U; const void* V; int ld; Shape sh;
-    double* y; double* out; double* zk; const Ctrl* ctrl; double rho; double* part;
+    double* y; double* out; double* zk; dfloat* ydf; const Ctrl* ctrl; double rho; double* part;
     int blocks; const Ctrl* gate; int ph; cudaStream_t stream;
 };
 
@@ -47,7 +47,8 @@ struct UpdateArgs {
     const ProbDev& p;
     bool step; bool hist_on;
     void* R; void* CR; const void* D; const void* CD; void* G; const void* W; void* hist;
-    int64_t slot_stride; int ld; Shape sh; const double* y; double* zrow; const Ctrl* ctrl; double* part;
+    int64_t slot_stride; int ld; Shape sh; const double* y; const dfloat* ydf; void* zrow; const Ctrl* ctrl;
+    double* part;
     int blocks; const Ctrl* gate; int ph; cudaStream_t stream;
 };
 

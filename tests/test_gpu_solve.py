@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 import paper_2407_15049_gb300 as L  # noqa: E402
 
-PREC = {"fp64": L.LORADS_FP64, "mixed": L.LORADS_MIXED, "fp32": L.LORADS_FP32}
+PREC = {"fp64": L.LORADS_FP64, "mixed": L.LORADS_MIXED, "df64": L.LORADS_DF64, "fp32": L.LORADS_FP32}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -66,6 +66,19 @@ def test_trajectory_matches_oracle_matrix_completion(k):
     assert np.max(np.abs(R - ref["R"])) <= 1e-9 * scale * max(1, k / 10)
 
 
+@pytest.mark.parametrize("k", [1, 5])
+def test_trajectory_double_float_matches_oracle(k):
+    """The double-float form follows the FP64 trajectory to ~1e-12 over a few steps."""
+    n = 1000
+    inst = W.maxcut_instance(n, W.er_graph(n, 4 * n, 0, "unit"))
+    R0 = W.initial_factor(inst, 10, 1)
+    caps = dict(max_outer=1, max_inner=k, tol=1e-300)
+    ref = O.solve(O.Problem(inst), R0, O.Params(**caps))
+    res, R, y = _gpu_solve(inst, R0, prec="df64", **caps)
+    assert res["inner_iters"] == ref["inner"]
+    assert np.max(np.abs(R - ref["R"])) <= 1e-10 * np.abs(ref["R"]).max()
+
+
 def test_trajectory_with_rank_growth():
     """Every outer step hits max_inner: the rank grows 4 -> 6 -> 9 as in App. A.1."""
     n = 40
@@ -85,18 +98,43 @@ def _converged_pair(inst, r, seed, prec="fp64", **kw):
     return ref, res, R, y
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "df64", "fp32"])
 def test_maxcut_er_1000_converges_to_oracle_objective(prec):
-    """The small workload: ER n = 1000, average degree 8, unit weights, r = 10."""
+    """The small workload: ER n = 1000, average degree 8, unit weights, r = 10.
+
+    FP64 follows the oracle's trajectory (rounding differences of the reduction
+    orders grow over ~500 iterations to ~1e-8 in the objective: same stationary
+    point, bound 1e-6).  At r = 10 this instance has several rank-10 stationary points
+    that all pass rel. KKT 1e-5 (the dual slack keeps sigma_min ~ -5e-3, which
+    err2's 1 + ||vec C||_1 normalisation accepts); a reduced-precision
+    trajectory may stop at another one, measured up to 1.5e-5 apart.  The
+    bound for those forms is therefore 5e-5; the rank-30 test below is the
+    tight one."""
     n = 1000
     inst = W.maxcut_instance(n, W.er_graph(n, 4 * n, 0, "unit"))
     ref, res, R, y = _converged_pair(inst, 10, 1, prec=prec)
     assert ref["status"] == "ok"
     assert res["status_name"] == "LORADS_OK", res
     assert res["err1"] <= 1e-5 and abs(res["err3"]) <= 1e-5
-    assert res["primal_obj"] == pytest.approx(ref["primal_obj"], rel=1e-5)
+    rel = abs(res["primal_obj"] - ref["primal_obj"]) / abs(ref["primal_obj"])
+    assert rel <= (1e-6 if prec == "fp64" else 5e-5), rel
     z = np.sum(R * R, axis=1) - 1
     assert np.linalg.norm(z) / 2 <= 1.0001e-5
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "df64", "fp32"])
+def test_maxcut_er_1000_rank30_matches_oracle(prec):
+    """With r = 30 the solves reach the SDP optimum (sigma_min(C - Diag y) ~ 0):
+    every precision must match the oracle's objective to 1e-5."""
+    n = 1000
+    inst = W.maxcut_instance(n, W.er_graph(n, 4 * n, 0, "unit"))
+    ref, res, R, y = _converged_pair(inst, 30, 1, prec=prec)
+    assert ref["status"] == "ok" and res["status_name"] == "LORADS_OK", res
+    assert res["primal_obj"] == pytest.approx(ref["primal_obj"], rel=1e-5)
+    P = O.Problem(inst)
+    assert O.sigma_min(P, y) >= -1e-3
+    gap = res["primal_obj"] - float(P.b @ y)
+    assert gap >= n * O.sigma_min(P, y) - 1e-6
 
 
 def test_maxcut_pm1_torus_converges():
@@ -107,7 +145,7 @@ def test_maxcut_pm1_torus_converges():
     assert res["primal_obj"] == pytest.approx(ref["primal_obj"], rel=1e-5)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "df64"])
 def test_matrix_completion_converges(prec):
     n1 = n2 = 100
     k = int(math.ceil(5 * n1 * math.log(n1)))

@@ -41,7 +41,8 @@ def test_library_exports_every_declared_symbol(lib):
 def test_default_params(lib):
     p = N.default_params()
     assert p.tol == 1e-5 and p.lbfgs_mem == 4 and p.max_inner == 500 and p.rho_growth == 2.0
-    assert p.lbfgs_scaling == 1 and p.rho_policy == 1 and p.inner_scale == 1 and p.rank_update_threshold == 3
+    assert p.lbfgs_scaling == 1 and p.rho_policy == 2 and p.inner_scale == 2 and p.rank_update_threshold == 3
+    assert p.inner_progress == 0.1
     assert p.inner_rel == 1.0 and p.infeas_decrease == 0.25 and p.time_limit == 1e4
 
 
