@@ -222,6 +222,38 @@ lorads_status lorads_set_iteration_limit(lorads_ctx* ctx, int64_t max_total_inne
  * lorads_kernel_times). */
 int32_t lorads_kernel_counts(const lorads_ctx* ctx, const char** names, int64_t* counts, int32_t cap);
 
+/* Exact line-search coefficients for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a deployment variant of
+ * lorads_linesearch_coeffs (FP64) that needs no context.  It is meant for code that
+ * must not call cudaMalloc where it needs the step -- work recorded while a stream is
+ * captured into a CUDA graph, frameworks whose allocator owns all device memory, or
+ * latency-critical loops that cannot take cudaMalloc's implicit synchronisation.
+ *   n, c_rowptr[n+1] (int64), c_colind, c_val   C as full symmetric CSR, device.
+ *   m, a_con, a_row, a_col, a_val (m triplets, one per constraint, row <= col), b[m]:
+ *                     device; a_con is the constraint index of each triplet.
+ *   R, D              device FP64, n x ld (ld a multiple of 4, at most 512), 16-byte aligned.
+ *   y                 device double[m].   rho >= 0.
+ *   out               device double[5]: a1, a2, a3, a4, tau (as lorads_linesearch_coeffs).
+ *   cuda_stream       stream to run on (NULL = legacy default stream).  Asynchronous.
+ * Inputs are not validated beyond sizes and pointers: pass what lorads_create accepts.
+ * Scratch: one fixed device array inside the library (2 x 1024 x 7 doubles, 114,688
+ * bytes) that every GPU loading the library keeps until exit.  It is shared by all
+ * calls on a device, so calls that overlap on the GPU race and must be ordered by the
+ * caller; nothing needs clearing between calls.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before starting any stream capture.  Sizes beyond the limits
+ * above return LORADS_ERR_INVALID_ARG; the message is in lorads_noalloc_error().
+ * Calls no allocation routine. */
+lorads_status lorads_linesearch_coeffs_noalloc(int64_t n, const int64_t* c_rowptr, const int32_t* c_colind,
+                                               const double* c_val, int64_t m, const int32_t* a_con,
+                                               const int32_t* a_row, const int32_t* a_col, const double* a_val,
+                                               const double* b, const double* R, const double* D, int32_t r,
+                                               int32_t ld, const double* y, double rho, double* out,
+                                               void* cuda_stream);
+
+/* Message of the last lorads_linesearch_coeffs_noalloc failure in this thread. */
+const char* lorads_noalloc_error(void);
+
 #ifdef __cplusplus
 }
 #endif

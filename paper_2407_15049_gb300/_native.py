@@ -76,6 +76,9 @@ SIGNATURES = {
     "lorads_kernel_times": (C.c_int32, [_VP, C.POINTER(C.c_char_p), _DP, C.c_int32]),
     "lorads_kernel_counts": (C.c_int32, [_VP, C.POINTER(C.c_char_p), _I64P, C.c_int32]),
     "lorads_set_iteration_limit": (C.c_int, [_VP, C.c_int64]),
+    "lorads_linesearch_coeffs_noalloc": (C.c_int, [C.c_int64, _VP, _VP, _VP, C.c_int64, _VP, _VP, _VP, _VP, _VP,
+                                                   _VP, _VP, C.c_int32, C.c_int32, _VP, C.c_double, _VP, _VP]),
+    "lorads_noalloc_error": (C.c_char_p, []),
 }
 
 _lib = None
