@@ -96,13 +96,15 @@ typedef struct {
     int32_t compute_err2;      /* 1: evaluate err2 (Lanczos on C - A*(y)) at the end */
     int32_t lanczos_steps;     /* Krylov dimension of that Lanczos run (default 200) */
     int32_t verbose;           /* 1: progress line per outer step on stderr; 2: per-kernel CUDA-event timing */
+    int32_t reserved;
     int32_t lbfgs_scaling;     /* 0: initial matrix I (Algorithm 1 as printed); 1 (default): gamma I, gamma = <s,y>/<y,y> */
     int32_t rho_policy;        /* rho grows when err1 did not shrink by infeas_decrease: 0 always; 1 only
                                   after a converged inner loop; 2 (default) also after a capped loop that raised err1 */
+    int32_t kernel_variant;    /* row update: 0 (default) register-staged; 1 TMA-staged (bulk copies into
+                                  shared memory, one block per SM) where it applies */
     int32_t inner_scale;       /* inner stop ||G||_F <= thr, z = A(RR^T) - b, e = tol (1 + ||b||_inf):
                                   0: thr = inner_rel max(||z||, e);  1: thr = inner_rel max(rho ||z||, e);
                                   2 (default): thr = max(e, min(inner_rel rho ||z||, inner_progress ||G_0||)) */
-    int32_t reserved;
 } lorads_params;
 
 typedef struct {

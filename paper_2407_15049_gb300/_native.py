@@ -39,8 +39,9 @@ class lorads_params(C.Structure):
         ("infeas_decrease", C.c_double), ("inner_rel", C.c_double), ("inner_progress", C.c_double),
         ("prec", C.c_int32),
         ("check_every", C.c_int32), ("seed", C.c_uint64), ("compute_err2", C.c_int32),
-        ("lanczos_steps", C.c_int32), ("verbose", C.c_int32), ("lbfgs_scaling", C.c_int32),
-        ("rho_policy", C.c_int32), ("inner_scale", C.c_int32), ("reserved", C.c_int32),
+        ("lanczos_steps", C.c_int32), ("verbose", C.c_int32), ("reserved", C.c_int32),
+        ("lbfgs_scaling", C.c_int32), ("rho_policy", C.c_int32), ("kernel_variant", C.c_int32),
+        ("inner_scale", C.c_int32),
     ]
 
 

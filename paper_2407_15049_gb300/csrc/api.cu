@@ -232,6 +232,7 @@ extern "C" void lorads_default_params(lorads_params* p) {
     p->lbfgs_scaling = 1;
     p->rho_policy = 2;
     p->inner_scale = 2;
+    p->kernel_variant = 0;
 }
 
 extern "C" const char* lorads_create_error(void) { return g_create_error.c_str(); }
@@ -652,10 +653,17 @@ struct Driver {
     int nb_rows, nb_flat, nb_off, nb_all;
     int64_t nunits;
 
+    int nb_upd;                 // grid of the row update (TMA path or register path)
+    bool tma;
+
     Driver(lorads_ctx* ctx) : c(ctx), st(ctx->st), s(ctx->solve_stream) { refresh(); }
 
     void refresh() {
         nb_rows = row_blocks(c, c->n, st.sh.L);
+        const int tb = (c->m_off == 0 && c->prm.kernel_variant == 1)
+                           ? tma_update_blocks<TR, TD>(c->n, st.ld, c->num_sms) : 0;
+        tma = tb > 0;
+        nb_upd = tma ? tb : nb_rows;
         nunits = c->n * (int64_t)st.ld / 4;
         nb_flat = flat_blocks(c, nunits);
         nb_off = row_blocks(c, std::max<int64_t>(c->m_off, 1), st.sh.L);
@@ -745,10 +753,11 @@ struct Driver {
             timed(FAM_SPMM_A, [&] { launch_spmm_a<TR, TD>(w); });
         }
         UpdateArgs u{p(), c->m_off == 0, true, st.R, st.CR, st.D, st.CD, st.G, c->m_off ? st.W : nullptr, st.hist,
-                     st.slot_stride, st.ld, st.sh, st.y, st.ydf, st.zrow, c->ctrl, part_of(c, PART_UPD), nb_rows, c->ctrl, PH_STEP, s};
-        timed(FAM_UPDATE, [&] { launch_update<TR, TD>(u); });
+                     st.slot_stride, st.ld, st.sh, st.y, st.ydf, st.zrow, c->ctrl, part_of(c, PART_UPD), nb_upd, c->ctrl, PH_STEP, s};
+        if (tma) timed(FAM_UPDATE, [&] { launch_update_tma<TR, TD>(u, c->ctrl); });
+        else timed(FAM_UPDATE, [&] { launch_update<TR, TD>(u); });
         timed(FAM_HIST, [&] {
-            ctrl_hist(s, c->ctrl, HIST_STEP, part_of(c, PART_UPD), nb_rows,
+            ctrl_hist(s, c->ctrl, HIST_STEP, part_of(c, PART_UPD), nb_upd,
                       c->m_off ? part_of(c, PART_YTIL) : nullptr, nb_off);
         });
     }
@@ -1030,6 +1039,10 @@ lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0,
         drv.enqueue_init();
     }
     if ((s = check_launch(ctx, "solve init"))) return s;
+    if (!prepare_update_tma<TR, TD>(st.ld)) {
+        cudaGetLastError();
+        ctx->prm.kernel_variant = 0;            // fall back to the register-staged row update
+    }
     if (P.verbose >= 2) return run_profiled<TR, TD>(ctx, prec, t0, res);
     if ((s = capture<TR, TD>(ctx))) return s;
     // ---- iterate: launch the graph in batches, poll the status of the previous batch

@@ -200,6 +200,7 @@ struct Ctrl {
     int solve_done;
     int pause;                  // host action needed (rank update)
     int status;                 // lorads_status of the solve
+    int dev_error;              // set by a kernel whose bounded wait expired
     int inner_k;                // directions computed in this outer step
     int outer;
     int total_inner;

@@ -214,6 +214,11 @@ __device__ void plan_next_slot(Ctrl* c, int T) {
 }
 
 __device__ void finish_inner_test(Ctrl* c) {
+    if (c->dev_error) {
+        c->status = 7;                          // LORADS_ERR_TIMEOUT: a device wait expired
+        c->solve_done = 1;
+        return;
+    }
     const double zn = sqrt(fmax(c->znorm2, 0.0));
     const double floor_ = c->tol * (1.0 + c->bnorm_inf);
     double thr;

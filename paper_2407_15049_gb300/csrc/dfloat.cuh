@@ -87,12 +87,48 @@ __device__ __forceinline__ dfloat add_fp(dfloat x, float y) {             // DWP
     return dfloat(zh, zl);
 }
 __device__ __forceinline__ dfloat& operator+=(dfloat& x, dfloat y) { return x = x + y; }
+__device__ __forceinline__ dfloat& operator+=(dfloat& x, float y) { return x = add_fp(x, y); }
 __device__ __forceinline__ dfloat& operator-=(dfloat& x, dfloat y) { return x = x - y; }
 // fma for every arithmetic type of the kernels (a lorads::fma would otherwise hide
 // the float and double ones inside this namespace)
 __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) { return a * b + c; }
+
+// ----------------------------------------------------------------- fused row-update helpers
+// Generic forms (double, float, double-float with a double-float operand) and
+// cheaper forms for a double-float master with float work arrays.
+
+// r + tau*d: the float product tau*d is the step actually taken (and stored as s)
+template <typename AR, typename AD>
+__device__ __forceinline__ AR step_add(AR r, AR tau, AD tau_d, AD d) { return fma(tau, AR(d), r); }
+template <>
+__device__ __forceinline__ dfloat step_add<dfloat, float>(dfloat r, dfloat, float tau_d, float d) {
+    return add_fp(r, __fmul_rn(tau_d, d));
+}
+
+// acc + r*r
+template <typename AR>
+__device__ __forceinline__ AR sq_add(AR acc, AR r) { return fma(r, r, acc); }
+template <>
+__device__ __forceinline__ dfloat sq_add<dfloat>(dfloat acc, dfloat r) {
+    float ph, pl;
+    two_prod(r.hi, r.hi, ph, pl);                       // exact hi^2
+    pl = __fmaf_rn(2.f * r.hi, r.lo, pl);               // + 2 hi lo (lo^2 below the precision)
+    return add_fp(add_fp(acc, ph), pl);
+}
+
+// 2 (cr - coef r), rounded to the work type
+template <typename AR, typename AD>
+__device__ __forceinline__ AD grad_elem(AR cr, AR coef, AR r) { return AD(AR(2) * (cr - coef * r)); }
+template <>
+__device__ __forceinline__ float grad_elem<dfloat, float>(dfloat cr, dfloat coef, dfloat r) {
+    float ph, pl, sh, sl;
+    two_prod(coef.hi, r.hi, ph, pl);                    // exact coef_hi r_hi
+    two_sum(cr.hi, -ph, sh, sl);                        // exact cr_hi - coef_hi r_hi
+    const float low = sl - pl + cr.lo - __fmaf_rn(coef.hi, r.lo, coef.lo * r.hi);
+    return 2.f * (sh + low);
+}
 
 // full-warp butterfly exchange for every arithmetic type used in reductions
 __device__ __forceinline__ float shfl_xor(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }

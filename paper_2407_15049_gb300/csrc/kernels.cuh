@@ -310,7 +310,7 @@ k_spmm_c(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int 
                         }
                     }
             }
-            accq[PL_P2] += PA(t_p2);
+            accq[PL_P2] += t_p2;
             if (zrow == nullptr) accq[PL_P1] += PA(AW(2) * t_p1);
             if (p.dk != nullptr) {
                 if (zrow == nullptr) t_rr = group_sum(t_rr, L);
@@ -582,8 +582,8 @@ k_dir(int64_t nunits, const TD* __restrict__ G, TD* __restrict__ D, const TD* __
             dd += dv * dv;
         }
         dst.store(D + u * 4);
-        accq[PD_GD] += PA(gd);
-        accq[PD_DD] += PA(dd);
+        accq[PD_GD] += gd;
+        accq[PD_DD] += dd;
     }
     block_partials<PD_N>(accq, part);
 }
@@ -688,13 +688,16 @@ k_update(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restric
                 for (int c = 0; c < CPL; ++c)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        r[c].v[e] = fma(tau, AR(d[c].v[e]), AR(r[c].v[e]));
-                        cr[c].v[e] = fma(tau, AR(cd[c].v[e]), AR(cr[c].v[e]));
+                        r[c].v[e] = step_add<AR, AD>(AR(r[c].v[e]), tau, tau_d, AD(d[c].v[e]));
+                        cr[c].v[e] = step_add<AR, AD>(AR(cr[c].v[e]), tau, tau_d, AD(cd[c].v[e]));
                     }
                 store_row<TR, CPL>(r, R, i, ld, L, Q, rl.lig);
                 store_row<TR, CPL>(cr, CR, i, ld, L, Q, rl.lig);
             }
-            rr = dot_units<AR>(r, r);
+#pragma unroll
+            for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) rr = sq_add<AR>(rr, AR(r[c].v[e]));
         }
         // diagonal-constraint coefficient a_i y~_k of row i
         AR coef = AR(0);
@@ -722,9 +725,12 @@ k_update(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restric
             for (int c = 0; c < CPL; ++c)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    AR gv = AR(cr[c].v[e]) - coef * AR(r[c].v[e]);
-                    if (W != nullptr) gv -= AR(w[c].v[e]);
-                    g[c].v[e] = AD(AR(2) * gv);
+                    if (W != nullptr) {
+                        const AR gv = AR(cr[c].v[e]) - coef * AR(r[c].v[e]) - AR(w[c].v[e]);
+                        g[c].v[e] = AD(AR(2) * gv);
+                    } else {
+                        g[c].v[e] = grad_elem<AR, AD>(AR(cr[c].v[e]), coef, AR(r[c].v[e]));
+                    }
                 }
             if constexpr (HIST) {
                 Unit<TD> gold[CPL], sn[CPL], yn[CPL];
@@ -738,9 +744,9 @@ k_update(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restric
                     }
                 store_row<TD, CPL>(sn, Snew, i, ld, L, Q, rl.lig);
                 store_row<TD, CPL>(yn, Ynew, i, ld, L, Q, rl.lig);
-                accq[PU_GYN] += PA(dot_units<AD>(g, yn));
-                accq[PU_SYN] += PA(dot_units<AD>(sn, yn));
-                accq[PU_YYN] += PA(dot_units<AD>(yn, yn));
+                accq[PU_GYN] += dot_units<AD>(g, yn);
+                accq[PU_SYN] += dot_units<AD>(sn, yn);
+                accq[PU_YYN] += dot_units<AD>(yn, yn);
 #pragma unroll
                 for (int t = 0; t < kMaxMem - 1; ++t) {
                     if (t < nold) {
@@ -748,14 +754,14 @@ k_update(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restric
                         load_row_stream<TD, CPL>(so, So[t], i, ld, L, Q, rl.lig);
                         load_row_stream<TD, CPL>(yo, Yo[t], i, ld, L, Q, rl.lig);
                         PA* q = accq + PU_FIXED + PU_PER_OLD * t;
-                        q[0] += PA(dot_units<AD>(sn, yo));
-                        q[1] += PA(dot_units<AD>(so, yn));
-                        q[2] += PA(dot_units<AD>(yn, yo));
+                        q[0] += dot_units<AD>(sn, yo);
+                        q[1] += dot_units<AD>(so, yn);
+                        q[2] += dot_units<AD>(yn, yo);
                     }
                 }
             }
             store_row<TD, CPL>(g, G, i, ld, L, Q, rl.lig);
-            accq[PU_GG] += PA(dot_units<AD>(g, g));
+            accq[PU_GG] += dot_units<AD>(g, g);
         }
     }
     block_partials<PU_N>(accq, part);
