@@ -408,6 +408,8 @@ def solve(P: Problem, R0: np.ndarray, params: Params | None = None,
         if grow:
             rho = min(rho * prm.rho_growth, prm.rho_max)
         err1 = err1_new
+        if outer == prm.max_outer - 1:
+            break                               # out of outer steps: no rank update after the last one
         # ---- dynamic rank (App. A.1)
         hit_cap_streak = hit_cap_streak + 1 if k >= prm.max_inner else 0
         if hit_cap_streak >= prm.rank_update_threshold:
