@@ -189,6 +189,15 @@ lorads_status lorads_linesearch_coeffs(lorads_ctx* ctx, const void* R, const voi
 lorads_status lorads_solve(lorads_ctx* ctx, const double* R0, int32_t r0, int32_t r0_on_device,
                            const double* y0, lorads_result* res);
 
+/* sigma_min(C - A*(y)), the dual-slack eigenvalue behind err2 of Sec. 4.1 (which the
+ * paper evaluates on the CPU), by a `steps`-step Lanczos run on the GPU with the
+ * library's FP64 SpMM; the start vector is drawn from SplitMix64(seed).  The smallest
+ * Ritz value is returned (an upper bound that converges to sigma_min).
+ *   y          device double[m], or NULL for the multipliers of the last solve.
+ *   sigma_out  host.   Synchronous. */
+lorads_status lorads_dual_min_eig(lorads_ctx* ctx, const double* y, int32_t steps, uint64_t seed,
+                                  double* sigma_out);
+
 /* Copies the last solution to the host.  R_host (n x rank, leading dimension rank) and
  * y_host (m) may be NULL; R_capacity is the number of doubles R_host can hold.
  * *rank_out (may be NULL) receives the rank.  Synchronous. */
@@ -255,6 +264,155 @@ lorads_status lorads_linesearch_coeffs_noalloc(int64_t n, const int64_t* c_rowpt
 
 /* Message of the last lorads_linesearch_coeffs_noalloc failure in this thread. */
 const char* lorads_noalloc_error(void);
+
+/* ------------------------------------------------------------------ batched solve
+ * Many independent instances of Eq. (1.1) solved by ONE persistent kernel launch
+ * (captured in a CUDA graph).  The paper solves one instance at a time; this is the
+ * serving form of the same method: every block of the launch takes the next instance
+ * from a device work queue and runs the whole solve of lorads_solve on it (ALM of
+ * Sec. 2.1, Algorithm 1, App. A.1/A.2) with block-wide reductions, taking the same
+ * decisions from the same sums.  Instances are independent units: no communication.
+ * Every instance keeps its problem arrays and iterate in device memory owned by the
+ * batch; the iterate of each instance is allocated for up to two rank updates
+ * (r0 -> ceil(1.5 r0) -> ceil(1.5 ceil(1.5 r0)), at most ceil(sqrt(2m)) and 128); a rank
+ * request beyond that is dropped and the solve continues at the current rank. */
+typedef struct lorads_batch lorads_batch;
+
+/* Launch shape of the persistent kernel (lorads_batch_tune picks one). */
+typedef struct {
+    int32_t ctas_per_sm;    /* resident solver blocks per SM; grid = SMs x this (1..4) */
+    int32_t rows_per_warp;  /* rows a warp works on at once: 1, 2, 4 or 8; lanes per row =
+                               max(32 / rows_per_warp, smallest power of two >= ld/4) */
+    int32_t order;          /* queue order: 0 input order, 1 largest estimated work first */
+    int32_t reserved;
+} lorads_batch_shape;
+
+typedef struct {
+    double  seconds;          /* device time of the launch (CUDA events around the graph) */
+    double  instances_per_s;  /* count / seconds */
+    double  latency_p50_ms;   /* per-instance completion time after the first block started */
+    double  latency_p99_ms;
+    double  latency_max_ms;
+    int64_t inner_iters;      /* L-BFGS iterations over all instances */
+    int32_t solved;           /* instances that ended with LORADS_OK */
+    int32_t grid;             /* blocks launched */
+    lorads_batch_shape shape; /* shape of the launch */
+} lorads_batch_stats;
+
+/* Uploads `count` instances, each in the format of lorads_create, concatenated:
+ *   n[count], m[count]        order of X and number of constraints of each instance.
+ *   c_rowptr                  the n_i + 1 row pointers of each instance one after the other
+ *                             (each list starts at 0); c_colind / c_val: the nnz_i = rowptr_i[n_i]
+ *                             entries of each instance one after the other.
+ *   a_con, a_row, a_col, a_val, b:  the m_i triplets / right-hand sides of each instance in
+ *                             turn (one triplet per constraint; indices local to the instance).
+ *   r0[count]                 starting rank of each instance, or NULL: ceil(log2 m_i) (>= 1).
+ *   R0                        NULL (rows drawn on the device as in lorads_solve) or the
+ *                             n_i x r0_i row-major FP64 starting factors one after the other.
+ *   p                         parameters (NULL = defaults); prec must be LORADS_FP64,
+ *                             LORADS_MIXED or LORADS_FP32; compute_err2, check_every and
+ *                             kernel_variant do not apply.
+ * All inputs are host memory and are copied.  Each instance is validated as by
+ * lorads_create; the first failure names the instance (lorads_batch_create_error). */
+lorads_status lorads_batch_create(lorads_batch** out, int32_t count, const int64_t* n, const int64_t* m,
+                                  const int64_t* c_rowptr, const int32_t* c_colind, const double* c_val,
+                                  const int32_t* a_con, const int32_t* a_row, const int32_t* a_col,
+                                  const double* a_val, const double* b, const int32_t* r0, const double* R0,
+                                  const lorads_params* p, void* cuda_stream);
+
+/* Solves every instance in one launch of the persistent kernel (shape: the last one set
+ * or tuned; default 2 blocks per SM, 8 rows per warp, largest first).  Each instance
+ * starts again from its starting point.  results[count] (host, may be NULL) receive one
+ * lorads_result per instance in input order (seconds = that instance's own solve time,
+ * err2 = -1); stats (host, may be NULL) the launch figures.  Returns LORADS_OK when the
+ * launch completed, whatever the instances' statuses.  Synchronous. */
+lorads_status lorads_batch_solve(lorads_batch* b, lorads_result* results, lorads_batch_stats* stats);
+
+/* Times the persistent launch for each candidate shape (blocks per SM allowed by the
+ * kernel's occupancy x rows per warp x queue order) with every instance capped at
+ * probe_iters L-BFGS iterations, keeps the fastest as the batch's shape and writes it
+ * to *best (may be NULL).  Synchronous. */
+lorads_status lorads_batch_tune(lorads_batch* b, int32_t probe_iters, lorads_batch_shape* best);
+
+/* Sets the launch shape used by the next lorads_batch_solve. */
+lorads_status lorads_batch_set_shape(lorads_batch* b, const lorads_batch_shape* shape);
+
+/* Caps every instance's total L-BFGS iterations in the next solves (0: no cap). */
+lorads_status lorads_batch_set_iteration_limit(lorads_batch* b, int64_t max_total_inner);
+
+/* Copies instance i's last solution to the host (as lorads_get_solution). */
+lorads_status lorads_batch_get_solution(lorads_batch* b, int32_t i, double* R_host, int64_t R_capacity,
+                                        int32_t* rank_out, double* y_host);
+
+/* Message of the last lorads_batch_create failure in this thread. */
+const char* lorads_batch_create_error(void);
+
+/* Message of the last failure on this batch ("" if none). */
+const char* lorads_batch_last_error(const lorads_batch* b);
+
+/* Frees the batch and everything it owns.  NULL-safe. */
+void lorads_batch_destroy(lorads_batch* b);
+
+/* ------------------------------------------------------------------ learned warm start
+ * A small message-passing network that predicts a starting factor R0 (unit rows, the
+ * feasible set of the MaxCut constraints X_ii = 1 of Sec. 4.2) from the pattern of C, to
+ * replace the random start of the solve.  The paper has no such network; it is trained
+ * on the factors R* that lorads_solve / lorads_batch_solve return.  Definition (F = 16,
+ * H = 32, w_ij = C_ij for i != j, s_i = sum_j |w_ij|, deg_i = #{j != i: C_ij stored}):
+ *   x_i   = [1, log(1 + deg_i)/4, sum_j w_ij / s_i, C_ii / s_i, g_i1..g_i12]  (ratios 0 if s_i = 0),
+ *           g_ik = standard normal number e = 12 i + k - 1 of the SplitMix64 / Box-Muller stream
+ *           of lorads_solve's start draws with base seed ^ (0x474E4E * 0x9E3779B97F4A7C15);
+ *   layer l = 1..3:  m_i = sum_{j != i} (w_ij / s_i) h_j,  h_i <- relu(W_s h_i + W_n m_i + b);
+ *   o_i = W_o h_i + b_o (r_out values),  r_hat_i = o_i / ||o_i||;
+ *   loss = (1/|E|) sum over stored pairs i < j of (r_hat_i . r_hat_j - X*_ij)^2,
+ *           X*_ij = r*_i . r*_j  (invariant to rotations of R*).
+ * Parameters: one float vector, for l = 1..3: W_s (H x F_in row-major, F_in = 16 then 32),
+ * W_n (H x F_in), b (H); then W_o (r_out x H), b_o (r_out).
+ * Graph arguments are C as a symmetric CSR matrix in DEVICE memory (n, rowptr int64,
+ * colind int32, val double: the arrays lorads_create accepts, uploaded by the caller).
+ * Activations are stored in bf16 (act_prec LORADS_BF16; weights rounded to bf16 for the
+ * forward pass) or float (LORADS_FP32); arithmetic and gradients are float; Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8) updates float master weights.  All calls run on the
+ * network's stream and are asynchronous unless stated. */
+typedef struct lorads_gnn lorads_gnn;
+
+/* Number of parameters for r_out outputs (1..32), or -1. */
+int64_t lorads_gnn_param_count(int32_t r_out);
+
+/* New network with parameters theta0 (host, lorads_gnn_param_count(r_out) floats). */
+lorads_status lorads_gnn_create(lorads_gnn** out, int32_t r_out, int32_t act_prec, const float* theta0,
+                                void* cuda_stream);
+
+/* Copies the parameters to / from the host (count >= the parameter count); set also resets
+ * the Adam moments.  Synchronous. */
+lorads_status lorads_gnn_get_params(lorads_gnn* g, float* theta_host, int64_t count);
+lorads_status lorads_gnn_set_params(lorads_gnn* g, const float* theta_host, int64_t count);
+
+/* Forward pass on the graph of C: R_out (device, n x ld FP64, ld >= r_out) receives
+ * r_hat in columns 0..r_out-1 and zeros after. */
+lorads_status lorads_gnn_predict(lorads_gnn* g, int64_t n, const int64_t* c_rowptr, const int32_t* c_colind,
+                                 const double* c_val, uint64_t feature_seed, int32_t ld, double* R_out);
+
+/* Training targets: targets[e] = r_i . r_j for every stored entry e = (i, j) of C
+ * (0 on the diagonal).  R: device n x ld FP64 (columns 0..r-1 used); targets: device
+ * float[nnz(C)].  Runs on cuda_stream. */
+lorads_status lorads_gnn_edge_targets(int64_t n, const int64_t* c_rowptr, const int32_t* c_colind, const double* R,
+                                      int32_t r, int32_t ld, float* targets, void* cuda_stream);
+
+/* One training step on one graph: forward, loss, hand-written backward, then an Adam
+ * step with learning rate lr (lr = 0: no update).  n_edges = number of pairs i < j with
+ * C_ij stored.  loss_out (host, may be NULL; synchronises when given) receives the loss
+ * before the update; grad_out (device, may be NULL) the gradient. */
+lorads_status lorads_gnn_train_step(lorads_gnn* g, int64_t n, const int64_t* c_rowptr, const int32_t* c_colind,
+                                    const double* c_val, uint64_t feature_seed, const float* targets,
+                                    int64_t n_edges, float lr, double* loss_out, float* grad_out);
+
+/* Message of the last failure on this network / of the last lorads_gnn_create. */
+const char* lorads_gnn_last_error(const lorads_gnn* g);
+const char* lorads_gnn_create_error(void);
+
+/* Frees the network.  NULL-safe. */
+void lorads_gnn_destroy(lorads_gnn* g);
 
 #ifdef __cplusplus
 }

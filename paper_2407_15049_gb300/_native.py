@@ -57,6 +57,27 @@ class lorads_result(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class lorads_batch_shape(C.Structure):
+    _fields_ = [("ctas_per_sm", C.c_int32), ("rows_per_warp", C.c_int32), ("order", C.c_int32),
+                ("reserved", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
+class lorads_batch_stats(C.Structure):
+    _fields_ = [
+        ("seconds", C.c_double), ("instances_per_s", C.c_double), ("latency_p50_ms", C.c_double),
+        ("latency_p99_ms", C.c_double), ("latency_max_ms", C.c_double), ("inner_iters", C.c_int64),
+        ("solved", C.c_int32), ("grid", C.c_int32), ("shape", lorads_batch_shape),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {name: getattr(self, name) for name, _ in self._fields_ if name != "shape"}
+        d["shape"] = self.shape.as_dict()
+        return d
+
+
 _VP, _DP, _I64P, _I32P = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int32)
 
 # exported symbol -> (restype, argtypes)
@@ -80,6 +101,28 @@ SIGNATURES = {
     "lorads_linesearch_coeffs_noalloc": (C.c_int, [C.c_int64, _VP, _VP, _VP, C.c_int64, _VP, _VP, _VP, _VP, _VP,
                                                    _VP, _VP, C.c_int32, C.c_int32, _VP, C.c_double, _VP, _VP]),
     "lorads_noalloc_error": (C.c_char_p, []),
+    "lorads_dual_min_eig": (C.c_int, [_VP, _VP, C.c_int32, C.c_uint64, _DP]),
+    "lorads_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, _I64P, _I64P, _I64P, _I32P, _DP, _I32P,
+                                      _I32P, _I32P, _DP, _DP, _I32P, _DP, C.POINTER(lorads_params), C.c_void_p]),
+    "lorads_batch_solve": (C.c_int, [_VP, C.POINTER(lorads_result), C.POINTER(lorads_batch_stats)]),
+    "lorads_batch_tune": (C.c_int, [_VP, C.c_int32, C.POINTER(lorads_batch_shape)]),
+    "lorads_batch_set_shape": (C.c_int, [_VP, C.POINTER(lorads_batch_shape)]),
+    "lorads_batch_set_iteration_limit": (C.c_int, [_VP, C.c_int64]),
+    "lorads_batch_get_solution": (C.c_int, [_VP, C.c_int32, _DP, C.c_int64, _I32P, _DP]),
+    "lorads_batch_create_error": (C.c_char_p, []),
+    "lorads_batch_last_error": (C.c_char_p, [_VP]),
+    "lorads_batch_destroy": (None, [_VP]),
+    "lorads_gnn_param_count": (C.c_int64, [C.c_int32]),
+    "lorads_gnn_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.POINTER(C.c_float), C.c_void_p]),
+    "lorads_gnn_get_params": (C.c_int, [_VP, C.POINTER(C.c_float), C.c_int64]),
+    "lorads_gnn_set_params": (C.c_int, [_VP, C.POINTER(C.c_float), C.c_int64]),
+    "lorads_gnn_predict": (C.c_int, [_VP, C.c_int64, _VP, _VP, _VP, C.c_uint64, C.c_int32, _VP]),
+    "lorads_gnn_edge_targets": (C.c_int, [C.c_int64, _VP, _VP, _VP, C.c_int32, C.c_int32, _VP, _VP]),
+    "lorads_gnn_train_step": (C.c_int, [_VP, C.c_int64, _VP, _VP, _VP, C.c_uint64, _VP, C.c_int64, C.c_float, _DP,
+                                        _VP]),
+    "lorads_gnn_last_error": (C.c_char_p, [_VP]),
+    "lorads_gnn_create_error": (C.c_char_p, []),
+    "lorads_gnn_destroy": (None, [_VP]),
 }
 
 _lib = None
@@ -237,6 +280,13 @@ def lorads_get_solution(ctx, n: int, m: int):
     return R, y
 
 
+def lorads_dual_min_eig(ctx, y=None, steps: int = 200, seed: int = 1) -> float:
+    """sigma_min(C - A*(y)) by Lanczos on the GPU (y: device float64[m] or None)."""
+    out = C.c_double()
+    _check(ctx, load().lorads_dual_min_eig(ctx, _dptr(y), int(steps), int(seed), C.byref(out)))
+    return out.value
+
+
 def lorads_problem_info(ctx) -> dict:
     vals = [C.c_int64() for _ in range(5)]
     _check(ctx, load().lorads_problem_info(ctx, *[C.byref(v) for v in vals]))
@@ -257,3 +307,149 @@ def lorads_kernel_times(ctx) -> dict:
 def padded_ld(r: int) -> int:
     """Row width the kernels use for rank r (r rounded up to a multiple of 4)."""
     return (int(r) + 3) // 4 * 4
+
+
+# ------------------------------------------------------------------ batched solve
+def _bcheck(batch, status: int):
+    if status != LORADS_OK:
+        raise LoradsError(status, load().lorads_batch_last_error(batch).decode() if batch else "")
+
+
+def lorads_batch_create(instances, params: lorads_params | None = None, r0=None, R0=None,
+                        stream: int | None = None) -> C.c_void_p:
+    """Uploads a list of SDP instances (objects as for lorads_create) as one batch.
+    r0: per-instance starting ranks or None; R0: list of n_i x r0_i float64 arrays or None."""
+    lib = load()
+    cat = lambda key, dt: np.ascontiguousarray(  # noqa: E731
+        np.concatenate([np.asarray(getattr(t, key), dtype=dt) for t in instances]), dtype=dt)
+    n = np.array([t.n for t in instances], dtype=np.int64)
+    m = np.array([t.m for t in instances], dtype=np.int64)
+    rowptr, colind, val = cat("rowptr", np.int64), cat("colind", np.int32), cat("val", np.float64)
+    con, row, col = cat("con", np.int32), cat("row", np.int32), cat("col", np.int32)
+    aval, b = cat("aval", np.float64), cat("b", np.float64)
+    r0a = None if r0 is None else np.ascontiguousarray(r0, dtype=np.int32)
+    R0a = None
+    if R0 is not None:
+        R0a = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64).ravel() for x in R0]))
+        if r0a is None:
+            r0a = np.array([np.asarray(x).shape[1] for x in R0], dtype=np.int32)
+    out = C.c_void_p()
+    st = lib.lorads_batch_create(
+        C.byref(out), len(instances), _ptr(n, C.c_int64), _ptr(m, C.c_int64), _ptr(rowptr, C.c_int64),
+        _ptr(colind, C.c_int32), _ptr(val, C.c_double), _ptr(con, C.c_int32), _ptr(row, C.c_int32),
+        _ptr(col, C.c_int32), _ptr(aval, C.c_double), _ptr(b, C.c_double),
+        _ptr(r0a, C.c_int32) if r0a is not None else None, _ptr(R0a, C.c_double) if R0a is not None else None,
+        C.byref(params) if params is not None else None, C.c_void_p(stream) if stream else None)
+    if st != LORADS_OK:
+        raise LoradsError(st, lib.lorads_batch_create_error().decode())
+    return out
+
+
+def lorads_batch_solve(batch, count: int, max_total_inner: int = 0):
+    """Solves every instance in one persistent launch.  Returns (list of result dicts, stats dict)."""
+    lib = load()
+    if max_total_inner:
+        _bcheck(batch, lib.lorads_batch_set_iteration_limit(batch, int(max_total_inner)))
+    res = (lorads_result * count)()
+    stats = lorads_batch_stats()
+    st = lib.lorads_batch_solve(batch, res, C.byref(stats))
+    if max_total_inner:
+        _bcheck(batch, lib.lorads_batch_set_iteration_limit(batch, 0))
+    _bcheck(batch, st)
+    out = []
+    for r in res:
+        d = r.as_dict()
+        d["status_name"] = STATUS_NAMES.get(r.status, str(r.status))
+        out.append(d)
+    return out, stats.as_dict()
+
+
+def lorads_batch_tune(batch, probe_iters: int = 30) -> dict:
+    shape = lorads_batch_shape()
+    _bcheck(batch, load().lorads_batch_tune(batch, int(probe_iters), C.byref(shape)))
+    return shape.as_dict()
+
+
+def lorads_batch_set_shape(batch, ctas_per_sm: int, rows_per_warp: int, order: int) -> None:
+    shape = lorads_batch_shape(int(ctas_per_sm), int(rows_per_warp), int(order), 0)
+    _bcheck(batch, load().lorads_batch_set_shape(batch, C.byref(shape)))
+
+
+def lorads_batch_get_solution(batch, i: int, n: int, m: int):
+    """Returns (R as numpy n x rank, y as numpy m) of instance i."""
+    lib = load()
+    rank = C.c_int32()
+    _bcheck(batch, lib.lorads_batch_get_solution(batch, int(i), None, 0, C.byref(rank), None))
+    R = np.zeros((n, rank.value))
+    y = np.zeros(m)
+    _bcheck(batch, lib.lorads_batch_get_solution(batch, int(i), _ptr(R, C.c_double), R.size, C.byref(rank),
+                                                 _ptr(y, C.c_double)))
+    return R, y
+
+
+def lorads_batch_destroy(batch) -> None:
+    if batch:
+        load().lorads_batch_destroy(batch)
+
+
+# ------------------------------------------------------------------ learned warm start
+def _gcheck(net, status: int):
+    if status != LORADS_OK:
+        raise LoradsError(status, load().lorads_gnn_last_error(net).decode() if net else "")
+
+
+def lorads_gnn_param_count(r_out: int) -> int:
+    return int(load().lorads_gnn_param_count(int(r_out)))
+
+
+def lorads_gnn_create(r_out: int, theta0: np.ndarray, act_prec: int = LORADS_BF16,
+                      stream: int | None = None) -> C.c_void_p:
+    lib = load()
+    th = np.ascontiguousarray(theta0, dtype=np.float32)
+    if th.size != lorads_gnn_param_count(r_out):
+        raise ValueError("theta0 has the wrong size")
+    out = C.c_void_p()
+    st = lib.lorads_gnn_create(C.byref(out), int(r_out), int(act_prec), _ptr(th, C.c_float),
+                               C.c_void_p(stream) if stream else None)
+    if st != LORADS_OK:
+        raise LoradsError(st, lib.lorads_gnn_create_error().decode())
+    return out
+
+
+def lorads_gnn_get_params(net, r_out: int) -> np.ndarray:
+    th = np.zeros(lorads_gnn_param_count(r_out), dtype=np.float32)
+    _gcheck(net, load().lorads_gnn_get_params(net, _ptr(th, C.c_float), th.size))
+    return th
+
+
+def lorads_gnn_set_params(net, theta: np.ndarray) -> None:
+    th = np.ascontiguousarray(theta, dtype=np.float32)
+    _gcheck(net, load().lorads_gnn_set_params(net, _ptr(th, C.c_float), th.size))
+
+
+def lorads_gnn_predict(net, graph: dict, feature_seed: int, R_out, ld: int) -> None:
+    """graph: dict with n and device tensors rowptr (int64), colind (int32), val (float64)."""
+    _gcheck(net, load().lorads_gnn_predict(net, int(graph["n"]), _dptr(graph["rowptr"]), _dptr(graph["colind"]),
+                                           _dptr(graph["val"]), int(feature_seed), int(ld), _dptr(R_out)))
+
+
+def lorads_gnn_edge_targets(graph: dict, R, r: int, ld: int, targets, stream: int | None = None) -> None:
+    st = load().lorads_gnn_edge_targets(int(graph["n"]), _dptr(graph["rowptr"]), _dptr(graph["colind"]), _dptr(R),
+                                        int(r), int(ld), _dptr(targets), C.c_void_p(stream) if stream else None)
+    if st != LORADS_OK:
+        raise LoradsError(st, "lorads_gnn_edge_targets")
+
+
+def lorads_gnn_train_step(net, graph: dict, feature_seed: int, targets, lr: float, grad_out=None,
+                          want_loss: bool = True):
+    loss = C.c_double()
+    _gcheck(net, load().lorads_gnn_train_step(net, int(graph["n"]), _dptr(graph["rowptr"]), _dptr(graph["colind"]),
+                                              _dptr(graph["val"]), int(feature_seed), _dptr(targets),
+                                              int(graph["n_edges"]), float(lr),
+                                              C.byref(loss) if want_loss else None, _dptr(grad_out)))
+    return loss.value if want_loss else None
+
+
+def lorads_gnn_destroy(net) -> None:
+    if net:
+        load().lorads_gnn_destroy(net)

@@ -17,6 +17,7 @@
 #include "control.h"
 #include "kernels.cuh"
 #include "launch_decl.h"
+#include "prob_host.h"
 
 using namespace lorads;
 
@@ -279,148 +280,16 @@ lorads_status validate_and_build(lorads_ctx* ctx, int64_t n, const int64_t* rp, 
                                  const double* cv, int64_t m, int64_t nnz_a, const int32_t* acon,
                                  const int32_t* arow, const int32_t* acol, const double* aval,
                                  const double* b) {
-    if (n < 1 || n > INT32_MAX) return set_err(ctx, "n must be in [1, 2^31)"), LORADS_ERR_INVALID_ARG;
-    if (m < 1 || m > INT32_MAX) return set_err(ctx, "m must be in [1, 2^31)"), LORADS_ERR_INVALID_ARG;
-    if (!rp || !ci || !cv || !acon || !arow || !acol || !aval || !b)
-        return set_err(ctx, "null input pointer"), LORADS_ERR_INVALID_ARG;
-    if (rp[0] != 0) return set_err(ctx, "c_rowptr[0] must be 0"), LORADS_ERR_INVALID_ARG;
-    for (int64_t i = 0; i < n; ++i)
-        if (rp[i + 1] < rp[i]) return set_err(ctx, "c_rowptr must be nondecreasing"), LORADS_ERR_INVALID_ARG;
-    const int64_t nnz = rp[n];
-    double sum_abs = 0.0;
-    int64_t cnt_nz = 0;
-    for (int64_t i = 0; i < n; ++i) {
-        for (int64_t s = rp[i]; s < rp[i + 1]; ++s) {
-            const int32_t j = ci[s];
-            if (j < 0 || j >= n) return set_err(ctx, "C column index out of range at row " + std::to_string(i)), LORADS_ERR_INVALID_ARG;
-            if (s > rp[i] && ci[s - 1] >= j)
-                return set_err(ctx, "C column indices must be sorted and distinct within row " + std::to_string(i)),
-                       LORADS_ERR_INVALID_ARG;
-            if (!std::isfinite(cv[s])) return set_err(ctx, "non-finite value in C"), LORADS_ERR_INVALID_ARG;
-            if (cv[s] != 0.0) { sum_abs += std::fabs(cv[s]); ++cnt_nz; }
-        }
-    }
-    // symmetry: (i, j, v) needs (j, i, v)
-    for (int64_t i = 0; i < n; ++i) {
-        for (int64_t s = rp[i]; s < rp[i + 1]; ++s) {
-            const int32_t j = ci[s];
-            const int32_t* lo = ci + rp[j];
-            const int32_t* hi = ci + rp[j + 1];
-            const int32_t* f = std::lower_bound(lo, hi, (int32_t)i);
-            if (f == hi || *f != i || cv[f - ci] != cv[s])
-                return set_err(ctx, "C is not symmetric at (" + std::to_string(i) + "," + std::to_string(j) + ")"),
-                       LORADS_ERR_NOT_SYMMETRIC;
-        }
-    }
-    ctx->cnorm1 = sum_abs;
-    ctx->mean_abs_c = cnt_nz ? sum_abs / (double)cnt_nz : 1.0;
-    // constraints
-    if (nnz_a != m)
-        return set_err(ctx, "every constraint must be a single triplet (nnz_a == m); constraints with several "
-                            "entries are not supported"),
-               LORADS_ERR_UNSUPPORTED;
-    std::vector<int32_t> seen(m, 0);
-    std::vector<int32_t> trip_of(m, -1);
-    for (int64_t t = 0; t < nnz_a; ++t) {
-        const int32_t k = acon[t], i = arow[t], j = acol[t];
-        if (k < 0 || k >= m) return set_err(ctx, "a_con out of range"), LORADS_ERR_INVALID_ARG;
-        if (i < 0 || j < 0 || i >= n || j >= n || i > j)
-            return set_err(ctx, "constraint triplet needs 0 <= a_row <= a_col < n"), LORADS_ERR_INVALID_ARG;
-        if (!std::isfinite(aval[t]) || aval[t] == 0.0)
-            return set_err(ctx, "constraint coefficient must be finite and nonzero"), LORADS_ERR_INVALID_ARG;
-        if (seen[k]++) return set_err(ctx, "constraint with several triplets"), LORADS_ERR_UNSUPPORTED;
-        trip_of[k] = (int32_t)t;
-    }
-    double bmax = 0.0, b1 = 0.0;
-    for (int64_t k = 0; k < m; ++k) {
-        if (!std::isfinite(b[k])) return set_err(ctx, "non-finite b"), LORADS_ERR_INVALID_ARG;
-        bmax = std::max(bmax, std::fabs(b[k]));
-        b1 += std::fabs(b[k]);
-    }
-    ctx->bnorm_inf = bmax;
-    ctx->bnorm1 = b1;
-    // diagonal constraints by row
-    std::vector<int32_t> dk(n, -1);
-    std::vector<double> da(n, 0.0);
-    int64_t m_diag = 0;
-    std::vector<int64_t> offkeys;
-    for (int64_t k = 0; k < m; ++k) {
-        const int32_t t = trip_of[k];
-        const int32_t i = arow[t], j = acol[t];
-        if (i == j) {
-            if (dk[i] >= 0) return set_err(ctx, "two constraints on the same diagonal entry"), LORADS_ERR_UNSUPPORTED;
-            dk[i] = (int32_t)k;
-            da[i] = aval[t];
-            ++m_diag;
-        }
-    }
-    const int64_t m_off = m - m_diag;
-    // ordered constraint list: diagonal constraints by row, then off-diagonal by (row, col)
-    std::vector<int32_t> order;
-    order.reserve(m);
-    for (int64_t i = 0; i < n; ++i)
-        if (dk[i] >= 0) order.push_back(dk[i]);
-    {
-        std::vector<std::pair<int64_t, int32_t>> off;
-        off.reserve(m_off);
-        for (int64_t k = 0; k < m; ++k) {
-            const int32_t t = trip_of[k];
-            if (arow[t] != acol[t]) off.emplace_back((int64_t)arow[t] * n + acol[t], (int32_t)k);
-        }
-        std::sort(off.begin(), off.end());
-        for (size_t q = 1; q < off.size(); ++q)
-            if (off[q].first == off[q - 1].first)
-                return set_err(ctx, "two constraints on the same off-diagonal entry"), LORADS_ERR_UNSUPPORTED;
-        for (auto& pr : off) order.push_back(pr.second);
-    }
-    std::vector<int32_t> k_row(m), k_col(m), k_id(m);
-    std::vector<double> k_a(m);
-    for (int64_t q = 0; q < m; ++q) {
-        const int32_t k = order[q];
-        const int32_t t = trip_of[k];
-        k_row[q] = arow[t];
-        k_col[q] = acol[t];
-        k_a[q] = aval[t];
-        k_id[q] = k;
-    }
-    // off-diagonal constraint pattern (symmetric, sorted by column within a row)
-    std::vector<int64_t> a_rp(n + 1, 0);
-    std::vector<int32_t> a_col, a_k;
-    std::vector<double> a_a;
-    if (m_off > 0) {
-        for (int64_t q = m_diag; q < m; ++q) {
-            a_rp[k_row[q] + 1]++;
-            a_rp[k_col[q] + 1]++;
-        }
-        for (int64_t i = 0; i < n; ++i) a_rp[i + 1] += a_rp[i];
-        const int64_t nz = a_rp[n];
-        a_col.resize(nz);
-        a_k.resize(nz);
-        a_a.resize(nz);
-        std::vector<int64_t> fill(a_rp.begin(), a_rp.end() - 1);
-        for (int64_t q = m_diag; q < m; ++q) {
-            const int32_t i = k_row[q], j = k_col[q];
-            int64_t s = fill[i]++;
-            a_col[s] = j; a_k[s] = k_id[q]; a_a[s] = k_a[q];
-            s = fill[j]++;
-            a_col[s] = i; a_k[s] = k_id[q]; a_a[s] = k_a[q];
-        }
-        // sort each row by column
-        std::vector<int64_t> idx;
-        for (int64_t i = 0; i < n; ++i) {
-            const int64_t s0 = a_rp[i], s1 = a_rp[i + 1];
-            if (s1 - s0 < 2) continue;
-            idx.resize(s1 - s0);
-            for (int64_t q = 0; q < s1 - s0; ++q) idx[q] = s0 + q;
-            std::sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return a_col[x] < a_col[y]; });
-            std::vector<int32_t> tc(s1 - s0), tk(s1 - s0);
-            std::vector<double> ta(s1 - s0);
-            for (int64_t q = 0; q < s1 - s0; ++q) { tc[q] = a_col[idx[q]]; tk[q] = a_k[idx[q]]; ta[q] = a_a[idx[q]]; }
-            for (int64_t q = 0; q < s1 - s0; ++q) { a_col[s0 + q] = tc[q]; a_k[s0 + q] = tk[q]; a_a[s0 + q] = ta[q]; }
-        }
-        ctx->nnz_aoff = nz;
-    }
-    ctx->n = n; ctx->m = m; ctx->nnz_c = nnz; ctx->m_diag = m_diag; ctx->m_off = m_off;
+    HostProb hp;
+    const lorads_status hs = build_host_prob(&hp, &ctx->err, n, rp, ci, cv, m, nnz_a, acon, arow, acol, aval, b);
+    if (hs != LORADS_OK) return hs;
+    ctx->cnorm1 = hp.cnorm1;
+    ctx->mean_abs_c = hp.mean_abs_c;
+    ctx->bnorm_inf = hp.bnorm_inf;
+    ctx->bnorm1 = hp.bnorm1;
+    ctx->nnz_aoff = hp.nnz_aoff;
+    ctx->n = n; ctx->m = m; ctx->nnz_c = hp.nnz_c; ctx->m_diag = hp.m_diag; ctx->m_off = hp.m_off;
+    const int64_t nnz = hp.nnz_c, m_diag = hp.m_diag, m_off = hp.m_off;
     // device (queried only once the host-side checks have passed)
     cudaError_t ce = cudaGetDevice(&ctx->device);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -432,47 +301,28 @@ lorads_status validate_and_build(lorads_ctx* ctx, int64_t n, const int64_t* rp, 
     ctx->max_blocks = ctx->num_sms * 8;
     // upload
     lorads_status s;
-    std::vector<float> cv32(cv, cv + nnz);
-    std::vector<dfloat> cvdf(nnz);
-    for (int64_t q = 0; q < nnz; ++q) {
-        const float h = (float)cv[q];
-        cvdf[q] = dfloat(h, (float)(cv[q] - (double)h));
-    }
     if ((s = upload(ctx, &ctx->c_rowptr, rp, n + 1))) return s;
     if ((s = upload(ctx, &ctx->c_col, ci, nnz))) return s;
     if ((s = upload(ctx, &ctx->c_val, cv, nnz))) return s;
-    if ((s = upload(ctx, &ctx->c_val32, cv32.data(), nnz))) return s;
-    if ((s = upload(ctx, &ctx->c_valdf, cvdf.data(), nnz))) return s;
+    if ((s = upload(ctx, &ctx->c_val32, hp.cv32.data(), nnz))) return s;
+    if ((s = upload(ctx, &ctx->c_valdf, hp.cvdf.data(), nnz))) return s;
     if (m_diag > 0) {
-        std::vector<float> da32(n);
-        std::vector<dfloat> dadf(n);
-        for (int64_t i = 0; i < n; ++i) {
-            da32[i] = (float)da[i];
-            dadf[i] = dfloat(da32[i], (float)(da[i] - (double)da32[i]));
-        }
-        if ((s = upload(ctx, &ctx->dk, dk.data(), n))) return s;
-        if ((s = upload(ctx, &ctx->da, da.data(), n))) return s;
-        if ((s = upload(ctx, &ctx->da32, da32.data(), n))) return s;
-        if ((s = upload(ctx, &ctx->da_df, dadf.data(), n))) return s;
+        if ((s = upload(ctx, &ctx->dk, hp.dk.data(), n))) return s;
+        if ((s = upload(ctx, &ctx->da, hp.da.data(), n))) return s;
+        if ((s = upload(ctx, &ctx->da32, hp.da32.data(), n))) return s;
+        if ((s = upload(ctx, &ctx->da_df, hp.dadf.data(), n))) return s;
     }
-    {
-        std::vector<dfloat> bdf(m);
-        for (int64_t k = 0; k < m; ++k) {
-            const float h = (float)b[k];
-            bdf[k] = dfloat(h, (float)(b[k] - (double)h));
-        }
-        if ((s = upload(ctx, &ctx->b_df, bdf.data(), m))) return s;
-    }
+    if ((s = upload(ctx, &ctx->b_df, hp.bdf.data(), m))) return s;
     if (m_off > 0) {
-        if ((s = upload(ctx, &ctx->a_rowptr, a_rp.data(), n + 1))) return s;
-        if ((s = upload(ctx, &ctx->a_col, a_col.data(), a_col.size()))) return s;
-        if ((s = upload(ctx, &ctx->a_k, a_k.data(), a_k.size()))) return s;
-        if ((s = upload(ctx, &ctx->a_a, a_a.data(), a_a.size()))) return s;
+        if ((s = upload(ctx, &ctx->a_rowptr, hp.a_rp.data(), n + 1))) return s;
+        if ((s = upload(ctx, &ctx->a_col, hp.a_col.data(), hp.a_col.size()))) return s;
+        if ((s = upload(ctx, &ctx->a_k, hp.a_k.data(), hp.a_k.size()))) return s;
+        if ((s = upload(ctx, &ctx->a_a, hp.a_a.data(), hp.a_a.size()))) return s;
     }
-    if ((s = upload(ctx, &ctx->k_row, k_row.data(), m))) return s;
-    if ((s = upload(ctx, &ctx->k_col, k_col.data(), m))) return s;
-    if ((s = upload(ctx, &ctx->k_a, k_a.data(), m))) return s;
-    if ((s = upload(ctx, &ctx->k_id, k_id.data(), m))) return s;
+    if ((s = upload(ctx, &ctx->k_row, hp.k_row.data(), m))) return s;
+    if ((s = upload(ctx, &ctx->k_col, hp.k_col.data(), m))) return s;
+    if ((s = upload(ctx, &ctx->k_a, hp.k_a.data(), m))) return s;
+    if ((s = upload(ctx, &ctx->k_id, hp.k_id.data(), m))) return s;
     if ((s = upload(ctx, &ctx->b, b, m))) return s;
     ProbDev& p = ctx->pd;
     p.n = n; p.m = m;
@@ -1094,6 +944,10 @@ lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0,
 
 }  // namespace
 
+namespace {
+lorads_status run_lanczos(lorads_ctx* ctx, const double* ydev, int k, uint64_t seed, double* sigma_out);
+}  // namespace
+
 extern "C" lorads_status lorads_solve(lorads_ctx* ctx, const double* R0, int32_t r0, int32_t r0_on_device,
                                       const double* y0, lorads_result* res) {
     if (!ctx) return LORADS_ERR_INVALID_ARG;
@@ -1111,6 +965,16 @@ extern "C" lorads_status lorads_solve(lorads_ctx* ctx, const double* R0, int32_t
                    LORADS_ERR_INVALID_ARG;
     }
     if (res && res->status == 0 && s != LORADS_OK) res->status = s;
+    // err2 of Sec. 4.1 at the returned multiplier: sigma_min(C - A*(y)) by Lanczos
+    if (ctx->prm.compute_err2 && ctx->st.have_solution && (s == LORADS_OK || s == LORADS_ERR_MAXITER)) {
+        double sig = 0.0;
+        const lorads_status ls = run_lanczos(ctx, ctx->st.y, ctx->prm.lanczos_steps, ctx->prm.seed, &sig);
+        if (ls != LORADS_OK) return ls;
+        if (res) {
+            res->sigma_min = sig;
+            res->err2 = std::max(0.0, -sig) / (1.0 + ctx->cnorm1);
+        }
+    }
     return s;
 }
 
@@ -1139,6 +1003,82 @@ extern "C" lorads_status lorads_get_solution(lorads_ctx* ctx, double* R_host, in
         CK(cudaStreamSynchronize(s));
     }
     return LORADS_OK;
+}
+
+// ============================================================== dual slack eigenvalue
+namespace {
+
+// sigma_min(C - A*(y)) by a k-step Lanczos run (no reorthogonalisation: the
+// smallest Ritz value converges first and bounds sigma_min from above).
+lorads_status run_lanczos(lorads_ctx* ctx, const double* ydev, int k, uint64_t seed, double* sigma_out) {
+    const int64_t n = ctx->n;
+    k = (int)std::max<int64_t>(1, std::min<int64_t>(k, n));
+    cudaStream_t s = ctx->solve_stream;
+    double *buf = nullptr, *lz = nullptr;
+    lorads_status rs;
+    if ((rs = dalloc(ctx, &buf, (size_t)3 * n * 4))) return rs;
+    if ((rs = dalloc(ctx, &lz, (size_t)2 * k + 8))) { cudaFree(buf); return rs; }
+    double* v = buf;
+    double* vp = buf + (size_t)n * 4;
+    double* w = buf + (size_t)2 * n * 4;
+    CK(cudaMemsetAsync(buf, 0, (size_t)3 * n * 4 * sizeof(double), s));
+    CK(cudaMemsetAsync(lz, 0, ((size_t)2 * k + 8) * sizeof(double), s));
+    const int beta_off = k, sc = 2 * k + 2;
+    Shape sh;
+    shape_for_ld(4, &sh);
+    const int nbf = flat_blocks(ctx, n), nbr = row_blocks(ctx, n, sh.L);
+    double* part = part_of(ctx, PART_MISC);
+    lz_random(s, n, seed, v, part, nbf);
+    lz_scalar(s, part, nbf, lz, sc, 1);
+    lz_scale(s, n, v, lz, sc, nbf);
+    for (int j = 0; j < k; ++j) {
+        SpmmCArgs a{ctx->pd, v, w, 4, sh, ydev, 1, EPI_NONE, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0,
+                    nullptr, nbr, nullptr, PH_ALWAYS, s};
+        launch_spmm_c<double, double, double>(a);
+        if (ctx->m_off) {
+            SpmmAArgs aa{ctx->pd, v, w, 4, sh, ydev, -1.0, 1, nbr, nullptr, PH_ALWAYS, s};
+            launch_spmm_a<double, double>(aa);
+        }
+        lz_dot(s, n, w, v, part, nbf);
+        lz_scalar(s, part, nbf, lz, j, 0);                                  // alpha_j
+        lz_orth(s, n, w, v, vp, lz, j, j > 0 ? beta_off + j : -1, part, nbf);
+        lz_scalar(s, part, nbf, lz, beta_off + j + 1, 1);                   // beta_{j+1}
+        if (j + 1 < k) {
+            lz_scale(s, n, w, lz, beta_off + j + 1, nbf);
+            double* t = vp;
+            vp = v;
+            v = w;
+            w = t;
+        }
+    }
+    lz_tridiag_min(s, lz, k, beta_off, lz + sc + 1);
+    lorads_status cs = check_launch(ctx, "lanczos");
+    if (cs == LORADS_OK) {
+        cudaError_t e = cudaMemcpyAsync(sigma_out, lz + sc + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            ctx->err = std::string("lanczos: ") + cudaGetErrorString(e);
+            cs = LORADS_ERR_CUDA;
+        }
+    }
+    cudaFree(buf);
+    cudaFree(lz);
+    return cs;
+}
+
+}  // namespace
+
+extern "C" lorads_status lorads_dual_min_eig(lorads_ctx* ctx, const double* y, int32_t steps, uint64_t seed,
+                                             double* sigma_out) {
+    if (!ctx || !sigma_out || steps < 1) return LORADS_ERR_INVALID_ARG;
+    const double* ydev = y;
+    if (!ydev) {
+        if (!ctx->st.have_solution) return set_err(ctx, "y is NULL and no solution is stored"), LORADS_ERR_INVALID_ARG;
+        ydev = ctx->st.y;
+    }
+    CK(cudaEventRecord(ctx->ev_sync, ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->solve_stream, ctx->ev_sync, 0));
+    return run_lanczos(ctx, ydev, steps, seed, sigma_out);
 }
 
 extern "C" lorads_status lorads_set_iteration_limit(lorads_ctx* ctx, int64_t max_total_inner) {

@@ -139,10 +139,18 @@ template <> struct Arith<__nv_bfloat16> { using type = float; };
 
 // ------------------------------------------------------------------ reductions
 // Sums NQ per-thread partials (double or double-float) over the block and
-// writes them as doubles to part[blockIdx.x * NQ + q].  Fixed order:
+// writes them as doubles to part[bid * NQ + q].  Fixed order:
 // deterministic for a fixed grid.
+// Block index and count a kernel body runs with: the hardware grid for a
+// launch of its own, or one block standing for the whole grid when a
+// persistent kernel runs the body for one instance.
+struct VGrid {
+    int bid, nblk;
+};
+__device__ __forceinline__ VGrid hw_grid() { return VGrid{(int)blockIdx.x, (int)gridDim.x}; }
+
 template <int NQ, typename PA>
-__device__ __forceinline__ void block_partials(PA (&acc)[NQ], double* part) {
+__device__ __forceinline__ void block_partials(PA (&acc)[NQ], double* part, int bid) {
     __shared__ double red[kWarps][NQ > 0 ? NQ : 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -157,8 +165,12 @@ __device__ __forceinline__ void block_partials(PA (&acc)[NQ], double* part) {
         double s = 0.0;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) s += red[w][q];
-        part[(size_t)blockIdx.x * NQ + q] = s;
+        part[(size_t)bid * NQ + q] = s;
     }
+}
+template <int NQ, typename PA>
+__device__ __forceinline__ void block_partials(PA (&acc)[NQ], double* part) {
+    block_partials<NQ, PA>(acc, part, (int)blockIdx.x);
 }
 
 // Reduces a group-of-L-lanes value; every lane of the group gets the sum.
@@ -169,6 +181,8 @@ __device__ __forceinline__ V group_sum(V v, int L) {
 }
 
 // ------------------------------------------------------------------ control block
+enum { PHASE_INNER = 0, PHASE_OUTER = 1 };
+
 // Device-resident state of one solve.  Written by the single-block control
 // kernels, read by every streaming kernel (which skip their work when the
 // phase flags say so).

@@ -21,6 +21,14 @@ void ctrl_resume(cudaStream_t s, Ctrl* c);
 void quartic_step_dev(cudaStream_t s, const double* a, double* tau);
 void fold_to(cudaStream_t s, const double* part, int nb, int NQ, double* out);
 
+void lz_random(cudaStream_t s, int64_t n, uint64_t seed, double* v, double* part, int blocks);
+void lz_scalar(cudaStream_t s, const double* part, int nb, double* lz, int slot, int mode);
+void lz_scale(cudaStream_t s, int64_t n, double* v, const double* lz, int slot, int blocks);
+void lz_dot(cudaStream_t s, int64_t n, const double* w, const double* v, double* part, int blocks);
+void lz_orth(cudaStream_t s, int64_t n, double* w, const double* v, const double* vp, const double* lz, int a_slot,
+             int b_slot, double* part, int blocks);
+void lz_tridiag_min(cudaStream_t s, const double* lz, int k, int beta_off, double* out);
+
 template <typename T> void sumsq(cudaStream_t s, int64_t n, int ld, int r, const void* X, double* part, int blocks);
 template <typename T>
 void rank_columns(cudaStream_t s, int64_t n, int ld, int r_old, int r_new, double scale, uint64_t seed,

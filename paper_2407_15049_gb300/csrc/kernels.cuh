@@ -43,7 +43,6 @@ struct ProbDev {
 // Kernels of the captured iteration graph check the control block first and
 // return at once when the current phase does not need them.
 enum { PH_ALWAYS = 0, PH_INNER = 1, PH_STEP = 2, PH_OUTER = 3 };
-enum { PHASE_INNER = 0, PHASE_OUTER = 1 };
 
 __device__ __forceinline__ bool gated_off(const Ctrl* g, int ph) {
     if (g == nullptr || ph == PH_ALWAYS) return false;
@@ -123,12 +122,12 @@ __device__ __forceinline__ dfloat ldv(const dfloat* p) {
 struct RowLoop {
     int L, lig, gw, rows_per_warp;
     int64_t first, stride;
-    __device__ __forceinline__ explicit RowLoop(int L_) : L(L_) {
+    __device__ __forceinline__ RowLoop(int L_, VGrid vg) : L(L_) {
         lig = threadIdx.x & (L - 1);
         gw = (threadIdx.x & 31) / L;
         rows_per_warp = 32 / L;
-        const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-        const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        const int64_t warp = (vg.bid * (int64_t)blockDim.x + threadIdx.x) >> 5;
+        const int64_t nwarps = ((int64_t)vg.nblk * blockDim.x) >> 5;
         first = warp * rows_per_warp;
         stride = nwarps * rows_per_warp;
     }
@@ -189,13 +188,11 @@ __device__ __forceinline__ A dot_units(const Unit<T1> (&x)[CPL], const Unit<T2> 
 enum { EPI_NONE = 0, EPI_LS = 1, EPI_OBJ = 2 };
 
 template <typename TX, typename TO, typename TR, int CPL, int EPI>
-__global__ void __launch_bounds__(kThreads)
-k_spmm_c(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int L, int Q,
+__device__ __forceinline__ void
+k_spmm_c_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int L, int Q,
          const double* __restrict__ v, int write_out,
          const TR* __restrict__ R, const double* __restrict__ y, const void* __restrict__ zrow_v,
-         const dfloat* __restrict__ ydf, const Ctrl* ctrl, double rho_arg, double* __restrict__ part,
-         const Ctrl* gate, int ph) {
-    if (gated_off(gate, ph)) return;
+         const dfloat* __restrict__ ydf, const Ctrl* ctrl, double rho_arg, double* __restrict__ part, VGrid vg) {
     using A = arith_t<TO>;
     using TV = cval_t<TX>;
     using PA = part_t<TO, TR>;
@@ -210,7 +207,7 @@ k_spmm_c(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int 
     const double rho = ctrl ? ctrl->rho : rho_arg;
     const LS rho_s = LS(rho);
     const TV* __restrict__ cv = cvals<TV>(p);
-    RowLoop rl(L);
+    RowLoop rl(L, vg);
     for (int64_t base = rl.first; base < p.n; base += rl.stride) {
         const int64_t i = base + rl.gw;
         const bool act = i < p.n;
@@ -357,18 +354,17 @@ k_spmm_c(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int 
             }
         }
     }
-    if constexpr (EPI != EPI_NONE) block_partials<NQ>(accq, part);
+    if constexpr (EPI != EPI_NONE) block_partials<NQ>(accq, part, vg.bid);
 }
 
 // ================================================================== SpMM over the
 // off-diagonal constraint pattern:  out = beta_acc * out + alpha * A*_off(v) X
 template <typename TX, typename TO, int CPL>
-__global__ void __launch_bounds__(kThreads)
-k_spmm_a(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int L, int Q,
-         const double* __restrict__ v, double alpha, int accumulate, const Ctrl* gate, int ph) {
-    if (gated_off(gate, ph)) return;
+__device__ __forceinline__ void
+k_spmm_a_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int L, int Q,
+         const double* __restrict__ v, double alpha, int accumulate, VGrid vg) {
     using A = arith_t<TO>;
-    RowLoop rl(L);
+    RowLoop rl(L, vg);
     for (int64_t base = rl.first; base < p.n; base += rl.stride) {
         const int64_t i = base + rl.gw;
         if (i >= p.n) continue;
@@ -417,11 +413,10 @@ k_spmm_a(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int 
 enum { CONS_EVAL = 0, CONS_LS = 1, CONS_YTIL = 2, CONS_YUPD = 3, CONS_ZZ = 4 };
 
 template <typename TU, typename TV, int CPL, int MODE>
-__global__ void __launch_bounds__(kThreads)
-k_cons(ProbDev p, int64_t k0, int64_t k1, const TU* __restrict__ U, const TV* __restrict__ V, int ld, int L, int Q,
+__device__ __forceinline__ void
+k_cons_body(ProbDev p, int64_t k0, int64_t k1, const TU* __restrict__ U, const TV* __restrict__ V, int ld, int L, int Q,
        double* y, double* __restrict__ out, double* zk, dfloat* ydf, const Ctrl* ctrl, double rho_arg,
-       double* __restrict__ part, const Ctrl* gate, int ph) {
-    if (gated_off(gate, ph)) return;
+       double* __restrict__ part, VGrid vg) {
     constexpr int NQ = MODE == CONS_LS ? PL_N : PC_N;
     using PA = part_t<TU, TV>;
     PA accq[NQ];
@@ -432,7 +427,7 @@ k_cons(ProbDev p, int64_t k0, int64_t k1, const TU* __restrict__ U, const TV* __
     using AU = wide_t<TU, TU>;
     using AW = wide_t<TU, TV>;
     using AV = wide_t<TV, TV>;
-    RowLoop rl(L);
+    RowLoop rl(L, vg);
     const int64_t cnt = k1 - k0;
     for (int64_t base = rl.first; base < cnt; base += rl.stride) {
         const int64_t t = k0 + base + rl.gw;
@@ -529,17 +524,16 @@ k_cons(ProbDev p, int64_t k0, int64_t k1, const TU* __restrict__ U, const TV* __
             }
         }
     }
-    if constexpr (MODE != CONS_EVAL) block_partials<NQ>(accq, part);
+    if constexpr (MODE != CONS_EVAL) block_partials<NQ>(accq, part, vg.bid);
 }
 
 // ================================================================== direction
 // D = cG G + sum_u (cS_u S_u + cY_u Y_u) over the stored pairs (the two-loop
 // recursion of Algorithm 1 carried out on coefficients); partials <G,D>, ||D||^2.
 template <typename TD>
-__global__ void __launch_bounds__(kThreads)
-k_dir(int64_t nunits, const TD* __restrict__ G, TD* __restrict__ D, const TD* __restrict__ hist,
-      int64_t slot_stride, const Ctrl* ctrl, double* __restrict__ part, const Ctrl* gate, int ph) {
-    if (gated_off(gate, ph)) return;
+__device__ __forceinline__ void
+k_dir_body(int64_t nunits, const TD* __restrict__ G, TD* __restrict__ D, const TD* __restrict__ hist,
+      int64_t slot_stride, const Ctrl* ctrl, double* __restrict__ part, VGrid vg) {
     using A = arith_t<TD>;
     using PA = part_t<TD, TD>;
     PA accq[PD_N] = {PA(0), PA(0)};
@@ -556,8 +550,8 @@ k_dir(int64_t nunits, const TD* __restrict__ G, TD* __restrict__ D, const TD* __
         Sp[t] = hist + (int64_t)(2 * s) * slot_stride;
         Yp[t] = hist + (int64_t)(2 * s + 1) * slot_stride;
     }
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nunits; u += stride) {
+    const int64_t stride = (int64_t)vg.nblk * blockDim.x;
+    for (int64_t u = vg.bid * (int64_t)blockDim.x + threadIdx.x; u < nunits; u += stride) {
         Unit<TD> g, d;
         g.load_stream(G + u * 4);
 #pragma unroll
@@ -585,20 +579,19 @@ k_dir(int64_t nunits, const TD* __restrict__ G, TD* __restrict__ D, const TD* __
         accq[PD_GD] += gd;
         accq[PD_DD] += dd;
     }
-    block_partials<PD_N>(accq, part);
+    block_partials<PD_N>(accq, part, vg.bid);
 }
 
 // ================================================================== step (flat)
 // R += tau D, CR += tau CD  (used when the gradient needs a separate pattern pass)
 template <typename TR, typename TD>
-__global__ void __launch_bounds__(kThreads)
-k_step(int64_t nunits, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restrict__ D,
-       const TD* __restrict__ CD, const Ctrl* ctrl, const Ctrl* gate, int ph) {
-    if (gated_off(gate, ph)) return;
+__device__ __forceinline__ void
+k_step_body(int64_t nunits, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restrict__ D,
+       const TD* __restrict__ CD, const Ctrl* ctrl, VGrid vg) {
     using A = arith_t<TR>;
     const A tau = A(ctrl->tau);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nunits; u += stride) {
+    const int64_t stride = (int64_t)vg.nblk * blockDim.x;
+    for (int64_t u = vg.bid * (int64_t)blockDim.x + threadIdx.x; u < nunits; u += stride) {
         Unit<TR> r, cr;
         Unit<TD> d, cd;
         r.load_stream(R + u * 4);
@@ -633,13 +626,12 @@ constexpr int update_min_blocks() {
 }
 
 template <typename TR, typename TD, int CPL, bool STEP, bool HIST>
-__global__ void __launch_bounds__(kThreads, (update_min_blocks<TR, TD, CPL>()))
-k_update(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restrict__ D,
+__device__ __forceinline__ void
+k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restrict__ D,
          const TD* __restrict__ CD, TD* __restrict__ G, const TD* __restrict__ W,
          TD* __restrict__ hist, int64_t slot_stride, int ld, int L, int Q,
          const double* __restrict__ y, const dfloat* __restrict__ ydf, void* __restrict__ zrow_v,
-         const Ctrl* ctrl, double* __restrict__ part, const Ctrl* gate, int ph) {
-    if (gated_off(gate, ph)) return;
+         const Ctrl* ctrl, double* __restrict__ part, VGrid vg) {
     using AR = arith_t<TR>;
     using AD = arith_t<TD>;
     using PA = part_t<TR, TD>;
@@ -670,7 +662,7 @@ k_update(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restric
             Yo[t] = hist + (int64_t)(2 * s + 1) * slot_stride;
         }
     }
-    RowLoop rl(L);
+    RowLoop rl(L, vg);
     for (int64_t base = rl.first; base < p.n; base += rl.stride) {
         const int64_t i = base + rl.gw;
         const bool act = i < p.n;
@@ -764,7 +756,66 @@ k_update(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restric
             accq[PU_GG] += dot_units<AD>(g, g);
         }
     }
-    block_partials<PU_N>(accq, part);
+    block_partials<PU_N>(accq, part, vg.bid);
+}
+
+// ================================================================== kernels
+// One launch per body over the hardware grid; a kernel of the captured
+// iteration graph first checks the phase flags of the control block.
+
+template <typename TX, typename TO, typename TR, int CPL, int EPI>
+__global__ void __launch_bounds__(kThreads)
+k_spmm_c(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int L, int Q,
+         const double* __restrict__ v, int write_out,
+         const TR* __restrict__ R, const double* __restrict__ y, const void* __restrict__ zrow_v,
+         const dfloat* __restrict__ ydf, const Ctrl* ctrl, double rho_arg, double* __restrict__ part,
+         const Ctrl* gate, int ph) {
+    if (gated_off(gate, ph)) return;
+    k_spmm_c_body<TX, TO, TR, CPL, EPI>(p, X, out, ld, L, Q, v, write_out, R, y, zrow_v, ydf, ctrl, rho_arg, part, hw_grid());
+}
+
+template <typename TX, typename TO, int CPL>
+__global__ void __launch_bounds__(kThreads)
+k_spmm_a(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int L, int Q,
+         const double* __restrict__ v, double alpha, int accumulate, const Ctrl* gate, int ph) {
+    if (gated_off(gate, ph)) return;
+    k_spmm_a_body<TX, TO, CPL>(p, X, out, ld, L, Q, v, alpha, accumulate, hw_grid());
+}
+
+template <typename TU, typename TV, int CPL, int MODE>
+__global__ void __launch_bounds__(kThreads)
+k_cons(ProbDev p, int64_t k0, int64_t k1, const TU* __restrict__ U, const TV* __restrict__ V, int ld, int L, int Q,
+       double* y, double* __restrict__ out, double* zk, dfloat* ydf, const Ctrl* ctrl, double rho_arg,
+       double* __restrict__ part, const Ctrl* gate, int ph) {
+    if (gated_off(gate, ph)) return;
+    k_cons_body<TU, TV, CPL, MODE>(p, k0, k1, U, V, ld, L, Q, y, out, zk, ydf, ctrl, rho_arg, part, hw_grid());
+}
+
+template <typename TD>
+__global__ void __launch_bounds__(kThreads)
+k_dir(int64_t nunits, const TD* __restrict__ G, TD* __restrict__ D, const TD* __restrict__ hist,
+      int64_t slot_stride, const Ctrl* ctrl, double* __restrict__ part, const Ctrl* gate, int ph) {
+    if (gated_off(gate, ph)) return;
+    k_dir_body<TD>(nunits, G, D, hist, slot_stride, ctrl, part, hw_grid());
+}
+
+template <typename TR, typename TD>
+__global__ void __launch_bounds__(kThreads)
+k_step(int64_t nunits, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restrict__ D,
+       const TD* __restrict__ CD, const Ctrl* ctrl, const Ctrl* gate, int ph) {
+    if (gated_off(gate, ph)) return;
+    k_step_body<TR, TD>(nunits, R, CR, D, CD, ctrl, hw_grid());
+}
+
+template <typename TR, typename TD, int CPL, bool STEP, bool HIST>
+__global__ void __launch_bounds__(kThreads, (update_min_blocks<TR, TD, CPL>()))
+k_update(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restrict__ D,
+         const TD* __restrict__ CD, TD* __restrict__ G, const TD* __restrict__ W,
+         TD* __restrict__ hist, int64_t slot_stride, int ld, int L, int Q,
+         const double* __restrict__ y, const dfloat* __restrict__ ydf, void* __restrict__ zrow_v,
+         const Ctrl* ctrl, double* __restrict__ part, const Ctrl* gate, int ph) {
+    if (gated_off(gate, ph)) return;
+    k_update_body<TR, TD, CPL, STEP, HIST>(p, R, CR, D, CD, G, W, hist, slot_stride, ld, L, Q, y, ydf, zrow_v, ctrl, part, hw_grid());
 }
 
 }  // namespace lorads

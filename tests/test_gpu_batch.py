@@ -1,0 +1,174 @@
+"""Batched persistent solve (one launch, one block per instance) against the FP64 oracle.
+
+* Trajectory: with the same R0 and caps, every instance of a batch follows the
+  oracle's iterates, including rank updates inside the launch.
+* Convergence: each instance reaches rel. KKT <= 1e-5 at the oracle's objective.
+* Launch shapes change reduction order only; repeated launches are bit-identical.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import lorads_oracle as O
+from tests._util import mixed_instance
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_2407_15049_gb300 as L  # noqa: E402
+
+PREC = {"fp64": L.LORADS_FP64, "mixed": L.LORADS_MIXED, "fp32": L.LORADS_FP32}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    L.build()
+
+
+def _small_batch():
+    """Uneven instances: MaxCut on ER graphs and a torus, matrix completion, and a
+    generic mix of diagonal and off-diagonal constraints with empty rows."""
+    insts = [
+        W.maxcut_instance(300, W.er_graph(300, 1200, 3, "unit")),
+        W.maxcut_instance(64, W.torus_graph(8, 1, "pm1")),
+        W.mc_instance(30, 40, 2, 500, seed=5),
+        W.maxcut_instance(777, W.er_graph(777, 3000, 4, "pm1")),
+        mixed_instance(203, seed=3),
+        W.maxcut_instance(17, W.er_graph(17, 40, 6, "unit")),
+    ]
+    ranks = [9, 6, 10, 10, 8, 5]
+    R0 = [W.initial_factor(t, r, 10 + i) for i, (t, r) in enumerate(zip(insts, ranks))]
+    return insts, R0
+
+
+def _batch_run(insts, R0, prec="fp64", shape=None, max_total_inner=0, **kw):
+    b = L.lorads_batch_create(insts, L.default_params(prec=PREC[prec], **kw), R0=R0)
+    try:
+        if shape is not None:
+            L.lorads_batch_set_shape(b, *shape)
+        res, stats = L.lorads_batch_solve(b, len(insts), max_total_inner=max_total_inner)
+        sols = [L.lorads_batch_get_solution(b, i, t.n, t.m) for i, t in enumerate(insts)]
+    finally:
+        L.lorads_batch_destroy(b)
+    return res, stats, sols
+
+
+@pytest.mark.parametrize("k", [1, 5, 30])
+def test_batch_trajectories_match_oracle(k):
+    insts, R0 = _small_batch()
+    caps = dict(max_outer=1, max_inner=k, tol=1e-300)
+    res, stats, sols = _batch_run(insts, R0, **caps)
+    for i, t in enumerate(insts):
+        ref = O.solve(O.Problem(t), R0[i], O.Params(**caps))
+        R, y = sols[i]
+        assert res[i]["inner_iters"] == ref["inner"], (i, res[i])
+        scale = np.abs(ref["R"]).max()
+        assert np.max(np.abs(R - ref["R"])) <= 1e-9 * scale * max(1, k / 10), i
+        assert np.max(np.abs(y - ref["y"])) <= 1e-8 * (1 + np.abs(ref["y"]).max()), i
+    assert stats["grid"] >= 1 and stats["inner_iters"] == sum(r["inner_iters"] for r in res)
+
+
+def test_batch_rank_growth_matches_oracle():
+    """Outer steps that hit max_inner grow the rank inside the launch (4 -> 6 -> 9 for
+    the first instance), exactly as the oracle does."""
+    insts = [W.maxcut_instance(40, W.er_graph(40, 120, 5, "pm1")),
+             W.maxcut_instance(50, W.er_graph(50, 150, 7, "unit"))]
+    R0 = [W.initial_factor(t, 4, 2 + i) for i, t in enumerate(insts)]
+    caps = dict(max_outer=3, max_inner=3, tol=1e-300, rank_update_threshold=1, seed=11)
+    res, _, sols = _batch_run(insts, R0, **caps)
+    ranks = []
+    for i, t in enumerate(insts):
+        ref = O.solve(O.Problem(t), R0[i], O.Params(**caps))
+        R, _ = sols[i]
+        assert R.shape[1] == ref["R"].shape[1] == res[i]["rank"], i
+        ranks.append(R.shape[1])
+        assert np.max(np.abs(R - ref["R"])) <= 1e-9 * np.abs(ref["R"]).max(), i
+    assert ranks[0] == 9                 # two updates inside the launch
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_converges_to_oracle_objectives(prec):
+    insts = [W.maxcut_instance(n, W.er_graph(n, d * n // 2, s, "pm1"))
+             for n, d, s in [(200, 6, 1), (500, 4, 2), (350, 12, 3)]]
+    insts.append(W.mc_instance(40, 50, 2, 900, seed=8))
+    ranks = [W.rank_log2(t.m) for t in insts]
+    R0 = [W.initial_factor(t, r, 20 + i) for i, (t, r) in enumerate(zip(insts, ranks))]
+    res, stats, _ = _batch_run(insts, R0, prec=prec)
+    assert stats["solved"] == len(insts), res
+    for i, t in enumerate(insts):
+        ref = O.solve(O.Problem(t), R0[i], O.Params())
+        assert ref["status"] == "ok"
+        assert res[i]["err1"] <= 1e-5 and abs(res[i]["err3"]) <= 1e-5
+        rel = abs(res[i]["primal_obj"] - ref["primal_obj"]) / max(1.0, abs(ref["primal_obj"]))
+        assert rel <= (1e-6 if prec == "fp64" else 5e-5), (i, rel, res[i]["primal_obj"], ref["primal_obj"])
+
+
+def test_batch_random_start_matches_single_solve():
+    """R0 = NULL draws the same rows as lorads_solve: one step from each agrees."""
+    insts = [W.maxcut_instance(300, W.er_graph(300, 900, 1, "pm1")), W.mc_instance(20, 30, 2, 300, seed=4)]
+    caps = dict(max_outer=1, max_inner=1, tol=1e-300, seed=7)
+    b = L.lorads_batch_create(insts, L.default_params(**caps))
+    try:
+        L.lorads_batch_solve(b, len(insts))
+        got = [L.lorads_batch_get_solution(b, i, t.n, t.m) for i, t in enumerate(insts)]
+    finally:
+        L.lorads_batch_destroy(b)
+    for i, t in enumerate(insts):
+        ctx = L.lorads_create(t, L.default_params(**caps))
+        try:
+            L.lorads_solve(ctx, None, r0=W.rank_log2(t.m))
+            R, y = L.lorads_get_solution(ctx, t.n, t.m)
+        finally:
+            L.lorads_destroy(ctx)
+        assert got[i][0].shape == R.shape
+        assert np.max(np.abs(got[i][0] - R)) <= 1e-10 * np.abs(R).max()
+
+
+def test_batch_shapes_and_repeats():
+    """A repeated launch is bit-identical; other shapes only reorder reductions."""
+    insts, R0 = _small_batch()
+    caps = dict(max_outer=2, max_inner=20, tol=1e-300)
+    b = L.lorads_batch_create(insts, L.default_params(**caps), R0=R0)
+    try:
+        L.lorads_batch_set_shape(b, 1, 8, 1)
+        r1, _ = L.lorads_batch_solve(b, len(insts))
+        s1 = [L.lorads_batch_get_solution(b, i, t.n, t.m)[0] for i, t in enumerate(insts)]
+        r2, _ = L.lorads_batch_solve(b, len(insts))
+        s2 = [L.lorads_batch_get_solution(b, i, t.n, t.m)[0] for i, t in enumerate(insts)]
+        L.lorads_batch_set_shape(b, 2, 2, 0)
+        r3, st3 = L.lorads_batch_solve(b, len(insts))
+        s3 = [L.lorads_batch_get_solution(b, i, t.n, t.m)[0] for i, t in enumerate(insts)]
+    finally:
+        L.lorads_batch_destroy(b)
+    assert st3["shape"] == {"ctas_per_sm": 2, "rows_per_warp": 2, "order": 0}
+    for i in range(len(insts)):
+        assert np.array_equal(s1[i], s2[i])
+        assert r1[i]["primal_obj"] == r2[i]["primal_obj"]
+        assert np.max(np.abs(s3[i] - s1[i])) <= 1e-9 * np.abs(s1[i]).max()
+
+
+def test_batch_tune_then_solve():
+    insts = [W.maxcut_instance(n, W.er_graph(n, 3 * n, n, "pm1")) for n in (150, 400, 90, 1200, 260)]
+    b = L.lorads_batch_create(insts, L.default_params(prec=L.LORADS_MIXED))
+    try:
+        shape = L.lorads_batch_tune(b, 10)
+        assert shape["rows_per_warp"] in (1, 2, 4, 8) and shape["order"] in (0, 1)
+        assert 1 <= shape["ctas_per_sm"] <= 4
+        res, stats = L.lorads_batch_solve(b, len(insts))
+    finally:
+        L.lorads_batch_destroy(b)
+    assert stats["shape"] == shape
+    assert stats["solved"] == len(insts), res
+    assert stats["latency_p50_ms"] <= stats["latency_p99_ms"] <= stats["latency_max_ms"]
+
+
+def test_batch_iteration_cap_reports_maxiter():
+    insts = [W.maxcut_instance(500, W.er_graph(500, 2000, 9, "pm1"))]
+    b = L.lorads_batch_create(insts, L.default_params())
+    try:
+        res, _ = L.lorads_batch_solve(b, 1, max_total_inner=7)
+        res2, _ = L.lorads_batch_solve(b, 1)
+    finally:
+        L.lorads_batch_destroy(b)
+    assert res[0]["status_name"] == "LORADS_ERR_MAXITER" and res[0]["inner_iters"] == 7
+    assert res2[0]["status_name"] == "LORADS_OK"

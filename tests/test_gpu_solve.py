@@ -205,3 +205,33 @@ def test_profiled_solve_matches_graph_solve():
     assert res_p["primal_obj"] == res_g["primal_obj"] and res_p["inner_iters"] == res_g["inner_iters"]
     assert times["k_spmm_c(CD,ls)"][1] == res_g["inner_iters"]
     assert all(ms > 0 for ms, _ in times.values())
+
+
+@pytest.mark.parametrize("case", ["maxcut_solution", "mc_random_y"])
+def test_dual_min_eig_matches_dense_eigenvalue(case):
+    """sigma_min(C - A*(y)) by the GPU Lanczos run against numpy's dense eigvalsh."""
+    if case == "maxcut_solution":
+        n = 1000
+        inst = W.maxcut_instance(n, W.er_graph(n, 4 * n, 0, "unit"))
+        ctx = L.lorads_create(inst, L.default_params(compute_err2=1, lanczos_steps=300))
+        try:
+            res = L.lorads_solve(ctx, W.initial_factor(inst, 10, 1))
+            _, y = L.lorads_get_solution(ctx, inst.n, inst.m)
+            sig = L.lorads_dual_min_eig(ctx, None, steps=300)
+        finally:
+            L.lorads_destroy(ctx)
+        P = O.Problem(inst)
+        ref = O.sigma_min(P, y)
+        assert res["sigma_min"] == pytest.approx(sig, abs=1e-9)
+        assert res["err2"] == pytest.approx(abs(min(0.0, ref)) / (1 + np.abs(P.C.data).sum()), rel=1e-6, abs=1e-12)
+    else:
+        inst = W.mc_instance(300, 400, 3, 20000, seed=3)
+        y = np.random.default_rng(0).standard_normal(inst.m)
+        ctx = L.lorads_create(inst)
+        try:
+            sig = L.lorads_dual_min_eig(ctx, torch.as_tensor(y, device="cuda"), steps=400)
+        finally:
+            L.lorads_destroy(ctx)
+        ref = O.sigma_min(O.Problem(inst), y)
+    scale = 1.0 + abs(ref)
+    assert sig == pytest.approx(ref, abs=1e-7 * scale)

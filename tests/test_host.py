@@ -131,6 +131,35 @@ def test_rejects_bad_lbfgs_memory(lib):
     _expect("LORADS_ERR_INVALID_ARG", _maxcut(), params=N.default_params(lbfgs_mem=9))
 
 
+def _expect_batch(status_name, insts, **kw):
+    with pytest.raises(N.LoradsError) as ei:
+        N.lorads_batch_create(insts, **kw)
+    assert N.STATUS_NAMES[ei.value.status] == status_name, str(ei.value)
+    return str(ei.value)
+
+
+def test_batch_rejects_a_bad_instance_and_names_it(lib):
+    good = _maxcut()
+    bad = _maxcut(seed=1)
+    bad.colind = bad.colind.copy()
+    bad.colind[-1] = bad.n
+    msg = _expect_batch("LORADS_ERR_INVALID_ARG", [good, good, bad])
+    assert "instance 2" in msg
+    asym = _maxcut(seed=2)
+    asym.val = asym.val.copy()
+    asym.val[asym.rowptr[5] + 1] += 1.0
+    msg = _expect_batch("LORADS_ERR_NOT_SYMMETRIC", [asym, good])
+    assert "instance 0" in msg
+
+
+def test_batch_rejects_bad_precision_and_rank(lib):
+    good = _maxcut()
+    _expect_batch("LORADS_ERR_INVALID_ARG", [good], params=N.default_params(prec=N.LORADS_DF64))
+    _expect_batch("LORADS_ERR_INVALID_ARG", [good], params=N.default_params(lbfgs_mem=0))
+    msg = _expect_batch("LORADS_ERR_INVALID_ARG", [good, good], r0=[4, 200])
+    assert "instance 1" in msg and "r0" in msg
+
+
 def test_workload_generators_shapes():
     inst = W.maxcut_instance(50, W.er_graph(50, 100, 0, "pm1"))
     assert inst.rowptr[-1] == 2 * 100 + 50 and inst.m == 50

@@ -249,6 +249,29 @@ def initial_factor(inst: SDPInstance, r: int, seed: int) -> np.ndarray:
     return np.ascontiguousarray(R)
 
 
+def serving_batch(count: int = 512, seed: int = 0, n_range=(200, 20000), side_range=(100, 5000)):
+    """Uneven instances for batched solving: about 3/4 MaxCut SDPs on ER graphs
+    (n log-uniform in n_range, average degree uniform in {3..20}, weights in
+    {-1,+1}) and 1/4 matrix-completion SDPs (M side x side, side uniform in
+    side_range, rank uniform in {2..5}, |Omega| = ceil(5 side ln side)).
+    Instance k is generated from seed * 1_000_003 + k.  Returns a list."""
+    rng = np.random.default_rng(seed)
+    kinds = rng.random(count) < 0.75
+    out = []
+    for k in range(count):
+        s = seed * 1_000_003 + k
+        if kinds[k]:
+            n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+            deg = int(rng.integers(3, 21))
+            out.append(maxcut_instance(n, er_graph(n, max(1, deg * n // 2), s, "pm1")))
+        else:
+            side = int(rng.integers(side_range[0], side_range[1] + 1))
+            rank = int(rng.integers(2, 6))
+            n_samples = min(side * side, int(math.ceil(5 * side * math.log(side))))
+            out.append(mc_instance(side, side, rank, n_samples, s))
+    return out
+
+
 def config_instance(name: str, seed: int = 0):
     """The named synthetic workloads (shapes and distributions of the paper's workloads).
 
