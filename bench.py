@@ -40,6 +40,13 @@ WORKLOADS = {
     "maxcut_er_1e5": dict(n=100_000, edges=200_000, weights="pm1", r=17, seed=0,
                           desc="MaxCut SDP, Erdos-Renyi n=1e5, M=2e5 edges (avg degree 4), w in {-1,+1}, r=17"),
 }
+BATCH_WORKLOADS = {
+    "serving_batch_512": dict(count=512, seed=0,
+                              desc="512 uneven SDPs: ~3/4 MaxCut on ER graphs (n log-uniform in [200, 20000], "
+                                   "average degree 3-20, w in {-1,+1}), ~1/4 matrix completion (side 100-5000, "
+                                   "rank 2-5, |Omega| = 5 side ln side); r0 = ceil(log2 m)"),
+}
+BATCH_METRIC = "instances/s to rel. KKT 1e-5, one persistent launch (512 mixed MaxCut / matrix-completion SDPs)"
 # iterations to tolerance used to scale the reference arm's per-iteration time when no
 # GPU run of the same invocation provides it (measured on the GPU solve of maxcut_er_1e7)
 DEFAULT_ITERS_TO_TOL = {"maxcut_er_1e7": 6660, "maxcut_er_1e5": 5000}
@@ -51,7 +58,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", default="maxcut_er_1e7", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="maxcut_er_1e7", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS))
     ap.add_argument("--prec", default="mixed", choices=["fp64", "mixed", "df64", "fp32"])
     ap.add_argument("--e2e-steps", type=int, default=1, help="end-to-end steps")
     ap.add_argument("--profile-iters", type=int, default=200,
@@ -60,6 +67,9 @@ def _args():
     ap.add_argument("--iters-to-tol", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--instance-time-limit", type=float, default=60.0,
+                    help="batched solve: per-instance time limit (s); instances past it count as unsolved")
+    ap.add_argument("--tune-iters", type=int, default=20, help="batched solve: iterations per autotuner probe")
     return ap.parse_args()
 
 
@@ -380,8 +390,182 @@ def run_native(args):
     return 0
 
 
+def batch_bytes(inst, ld: int, wR: int, wD: int, T: int, inner: int, outer: int) -> float:
+    """Algorithmic bytes of one instance's batched solve: per L-BFGS iteration the
+    direction, line-search SpMM / constraint pass and row update (each operand once),
+    per outer step the multiplier pass and C R."""
+    n, m, nnz = inst.n, inst.m, inst.nnz
+    fam = lambda f: kernel_bytes(f, n, ld, nnz, m, wR, wD, T)  # noqa: E731
+    per_inner = fam("k_dir") + fam("k_spmm_c(CD,ls)") + fam("k_update(step)")
+    m_off = m - (n if inst.kind == "maxcut" else 0)
+    if m_off > 0:                       # constraint line-search pass, y~ pass, A*(y~) R
+        per_inner += m_off * (4 * 4 + 8 * 3) + 2 * m_off * ld * (wR + wD) + 2 * m_off * ld * wR + n * ld * wD
+    per_outer = fam("k_cons(yupd)") + fam("k_spmm_c(CR,obj)") + fam("k_update(grad)")
+    return per_inner * inner + per_outer * outer
+
+
+def _oracle_instance_seconds(inst, r0):
+    from oracle import lorads_oracle as O
+    import workloads as W
+    R0 = W.initial_factor(inst, r0, 1)
+    t = time.perf_counter()
+    ref = O.solve(O.Problem(inst), R0, O.Params())
+    return time.perf_counter() - t, ref
+
+
+def _batch_cpu_sample(B, budget_s: float = 20.0):
+    """The oracle on a seeded sample of the batch's instances, smallest first until
+    about budget_s of CPU time: instances per second on that sample."""
+    import numpy as np
+    import workloads as W
+    rng = np.random.default_rng(5)
+    idx = sorted(rng.choice(len(B), size=min(16, len(B)), replace=False), key=lambda i: B[i].n)
+    done, spent, names = 0, 0.0, []
+    for i in idx:
+        if spent > budget_s:
+            break
+        s, _ = _oracle_instance_seconds(B[i], W.rank_log2(B[i].m))
+        spent += s
+        done += 1
+        names.append(f"{B[i].kind} n={B[i].n}")
+    return done / spent if spent > 0 else None, spent, names
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+    import workloads as W
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cfg = BATCH_WORKLOADS[args.workload]
+    t = time.perf_counter()
+    B = W.serving_batch(cfg["count"], cfg["seed"])
+    gen_s = time.perf_counter() - t
+    count = len(B)
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        per = []
+        for _ in range(args.steps):
+            v, spent, names = _batch_cpu_sample(B, budget_s=20.0)
+            per.append((v, spent, names))
+        v, spent, names = per[-1]
+        line = {"impl": "reference", "metric": BATCH_METRIC, "value": v, "unit": "instances/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": spent * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "description": cfg["desc"]},
+                "cpu_baseline": {"value": v, "unit": "instances/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"{len(names)} seeded instances of the batch, smallest first, solved to "
+                                           f"tolerance by the oracle ({spent:.1f} s): " + ", ".join(names)},
+                "e2e": {"value": v, "unit": "instances/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_2407_15049_gb300 as L
+    L.load()
+    prec_code = {"fp64": L.LORADS_FP64, "mixed": L.LORADS_MIXED, "fp32": L.LORADS_FP32}[args.prec]
+    params = L.default_params(prec=prec_code, time_limit=args.instance_time_limit)
+    t = time.perf_counter()
+    b = L.lorads_batch_create(B, params)
+    create_s = time.perf_counter() - t
+    t = time.perf_counter()
+    shape = L.lorads_batch_tune(b, args.tune_iters)
+    tune_s = time.perf_counter() - t
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        L.lorads_batch_solve(b, count)
+    barrier()
+    secs, stats = [], None
+    with ClockSampler(local) as clk:
+        barrier()
+        for _ in range(args.steps):
+            res, stats = L.lorads_batch_solve(b, count)
+            secs.append(stats["seconds"])
+        barrier()
+    per_step = max(secs)
+    L.lorads_batch_destroy(b)
+    # end to end: host arrays -> create -> solve -> every solution back to the host
+    barrier()
+    t = time.perf_counter()
+    b2 = L.lorads_batch_create(B, params)
+    L.lorads_batch_set_shape(b2, shape["ctas_per_sm"], shape["rows_per_warp"], shape["order"], shape["threads"])
+    res2, st2 = L.lorads_batch_solve(b2, count)
+    d2h = 0
+    for i, inst in enumerate(B):
+        Rh, yh = L.lorads_batch_get_solution(b2, i, inst.n, inst.m)
+        d2h += Rh.nbytes + yh.nbytes
+    L.lorads_batch_destroy(b2)
+    barrier()
+    e2e_s = time.perf_counter() - t
+    h2d = sum(x.rowptr.nbytes + x.colind.nbytes + x.val.nbytes + x.con.nbytes + x.row.nbytes + x.col.nbytes
+              + x.aval.nbytes + x.b.nbytes for x in B)
+    if world > 1:
+        tt = torch.tensor([per_step, e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        per_step, e2e_s = tt.tolist()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    wR = 8 if args.prec in ("fp64", "mixed") else 4
+    wD = 8 if args.prec == "fp64" else 4
+    alg = 0.0
+    for inst, r in zip(B, res):
+        alg += batch_bytes(inst, L.padded_ld(max(r["rank"], 1)), wR, wD, params.lbfgs_mem, r["inner_iters"],
+                           r["outer_iters"])
+    peak, peak_kind = measured_peaks()
+    ach = alg / per_step / 1e9
+    kinds = np.array([x.kind for x in B])
+    stat = np.array([r["status"] for r in res])
+    solved = {k: int(np.sum((kinds == k) & (stat == 0))) for k in ("maxcut", "mc")}
+    totals = {k: int(np.sum(kinds == k)) for k in ("maxcut", "mc")}
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, spent, names = _batch_cpu_sample(B, budget_s=20.0)
+        cpu = {"value": v, "unit": "instances/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(names)} seeded instances of the batch, smallest first, solved to tolerance by "
+                         f"the oracle ({spent:.1f} s, numpy single thread): " + ", ".join(names)}
+    line = {
+        "metric": BATCH_METRIC, "value": count * world / per_step, "unit": "instances/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "mixed": "f32 (+double-float R, CR)", "fp32": "f32"}[args.prec],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": cfg["desc"], "count": count,
+                   "solver_precision": args.prec, "instance_time_limit_s": args.instance_time_limit,
+                   "tolerance": 1e-5, "shape": shape, "l2_policy": "state of all instances 1.1x L2 and up; "
+                   "each launch restarts every instance from its start", "parallelism": f"replicas x{world}"},
+        "e2e": {"value": count / e2e_s, "unit": "instances/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": args.steps,
+        "latency_ms": {"p50": stats["latency_p50_ms"], "p99": stats["latency_p99_ms"],
+                       "max": stats["latency_max_ms"]},
+        "solved": solved, "instances": totals, "inner_iters": stats["inner_iters"],
+        "roofline": {"kernel": "k_batch_solve", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                     "frac": ach / peak, "peak_kind": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_launch": alg, "avg_launch_ms": per_step * 1e3},
+        "cpu_baseline": cpu, "clocks": clk.summary(),
+        "setup_s": {"generate": gen_s, "create": create_s, "tune": tune_s},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = _args()
+    if args.workload in BATCH_WORKLOADS:
+        return run_batch(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_native(args)

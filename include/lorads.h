@@ -284,7 +284,12 @@ typedef struct {
     int32_t rows_per_warp;  /* rows a warp works on at once: 1, 2, 4 or 8; lanes per row =
                                max(32 / rows_per_warp, smallest power of two >= ld/4) */
     int32_t order;          /* queue order: 0 input order, 1 largest estimated work first */
-    int32_t reserved;
+    int32_t threads;        /* threads per block: 256 or 512 (0 = 256) */
+    int32_t cluster;        /* 1 (or 0): one block per instance; 2, 4 or 8: thread-block clusters of that
+                               size solve the first team_count instances of the queue together (their
+                               blocks split rows and constraints and reduce through distributed shared
+                               memory), then their blocks take the remaining instances one each */
+    int32_t team_count;     /* instances solved by a whole cluster (cluster > 1) */
 } lorads_batch_shape;
 
 typedef struct {
@@ -321,17 +326,18 @@ lorads_status lorads_batch_create(lorads_batch** out, int32_t count, const int64
                                   const lorads_params* p, void* cuda_stream);
 
 /* Solves every instance in one launch of the persistent kernel (shape: the last one set
- * or tuned; default 2 blocks per SM, 8 rows per warp, largest first).  Each instance
+ * or tuned; default 256 threads, 2 blocks per SM, 8 rows per warp, largest first).  Each instance
  * starts again from its starting point.  results[count] (host, may be NULL) receive one
  * lorads_result per instance in input order (seconds = that instance's own solve time,
  * err2 = -1); stats (host, may be NULL) the launch figures.  Returns LORADS_OK when the
  * launch completed, whatever the instances' statuses.  Synchronous. */
 lorads_status lorads_batch_solve(lorads_batch* b, lorads_result* results, lorads_batch_stats* stats);
 
-/* Times the persistent launch for each candidate shape (blocks per SM allowed by the
- * kernel's occupancy x rows per warp x queue order) with every instance capped at
- * probe_iters L-BFGS iterations, keeps the fastest as the batch's shape and writes it
- * to *best (may be NULL).  Synchronous. */
+/* Times the persistent launch for each candidate shape (threads per block x blocks per SM
+ * allowed by the kernel's occupancy x rows per warp x queue order, then clusters of 2, 4
+ * and 8 blocks for the 1, 2 or 4 x (clusters resident) largest instances) with every
+ * instance capped at probe_iters L-BFGS iterations, keeps the fastest as the batch's
+ * shape and writes it to *best (may be NULL).  Synchronous. */
 lorads_status lorads_batch_tune(lorads_batch* b, int32_t probe_iters, lorads_batch_shape* best);
 
 /* Sets the launch shape used by the next lorads_batch_solve. */
@@ -343,6 +349,13 @@ lorads_status lorads_batch_set_iteration_limit(lorads_batch* b, int64_t max_tota
 /* Copies instance i's last solution to the host (as lorads_get_solution). */
 lorads_status lorads_batch_get_solution(lorads_batch* b, int32_t i, double* R_host, int64_t R_capacity,
                                         int32_t* rank_out, double* y_host);
+
+/* Device time (ms, %globaltimer at the block's barriers) that the last lorads_batch_solve
+ * spent in each phase of instance i's solve (i = -1: summed over all instances): init,
+ * direction, spmm_ls, cons_ls, root, step, ytil, spmm_a, update, hist, outer,
+ * outer_gradient, rank_update.  names (static strings) and ms have cap entries (either may
+ * be NULL); returns the number written (0 before a solve). */
+int32_t lorads_batch_phase_times(const lorads_batch* b, int32_t i, const char** names, double* ms, int32_t cap);
 
 /* Message of the last lorads_batch_create failure in this thread. */
 const char* lorads_batch_create_error(void);

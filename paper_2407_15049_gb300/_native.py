@@ -59,10 +59,10 @@ class lorads_result(C.Structure):
 
 class lorads_batch_shape(C.Structure):
     _fields_ = [("ctas_per_sm", C.c_int32), ("rows_per_warp", C.c_int32), ("order", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("threads", C.c_int32), ("cluster", C.c_int32), ("team_count", C.c_int32)]
 
     def as_dict(self) -> dict:
-        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class lorads_batch_stats(C.Structure):
@@ -110,6 +110,7 @@ SIGNATURES = {
     "lorads_batch_set_iteration_limit": (C.c_int, [_VP, C.c_int64]),
     "lorads_batch_get_solution": (C.c_int, [_VP, C.c_int32, _DP, C.c_int64, _I32P, _DP]),
     "lorads_batch_create_error": (C.c_char_p, []),
+    "lorads_batch_phase_times": (C.c_int32, [_VP, C.c_int32, C.POINTER(C.c_char_p), _DP, C.c_int32]),
     "lorads_batch_last_error": (C.c_char_p, [_VP]),
     "lorads_batch_destroy": (None, [_VP]),
     "lorads_gnn_param_count": (C.c_int64, [C.c_int32]),
@@ -370,8 +371,10 @@ def lorads_batch_tune(batch, probe_iters: int = 30) -> dict:
     return shape.as_dict()
 
 
-def lorads_batch_set_shape(batch, ctas_per_sm: int, rows_per_warp: int, order: int) -> None:
-    shape = lorads_batch_shape(int(ctas_per_sm), int(rows_per_warp), int(order), 0)
+def lorads_batch_set_shape(batch, ctas_per_sm: int, rows_per_warp: int, order: int, threads: int = 256,
+                           cluster: int = 1, team_count: int = 0) -> None:
+    shape = lorads_batch_shape(int(ctas_per_sm), int(rows_per_warp), int(order), int(threads), int(cluster),
+                               int(team_count))
     _bcheck(batch, load().lorads_batch_set_shape(batch, C.byref(shape)))
 
 
@@ -385,6 +388,14 @@ def lorads_batch_get_solution(batch, i: int, n: int, m: int):
     _bcheck(batch, lib.lorads_batch_get_solution(batch, int(i), _ptr(R, C.c_double), R.size, C.byref(rank),
                                                  _ptr(y, C.c_double)))
     return R, y
+
+
+def lorads_batch_phase_times(batch, i: int = -1) -> dict:
+    """{phase: ms} of instance i's solve in the last launch (i = -1: all instances)."""
+    names = (C.c_char_p * 16)()
+    ms = (C.c_double * 16)()
+    k = load().lorads_batch_phase_times(batch, int(i), names, ms, 16)
+    return {names[q].decode(): ms[q] for q in range(k)}
 
 
 def lorads_batch_destroy(batch) -> None:

@@ -100,6 +100,8 @@ struct lorads_ctx {
     double* k_a = nullptr;
     int32_t* k_id = nullptr;
     double* b = nullptr;
+    dfloat* k_adf = nullptr;
+    dfloat* a_adf = nullptr;
     ProbDev pd{};
     // scratch
     double* part = nullptr;
@@ -258,6 +260,7 @@ extern "C" void lorads_destroy(lorads_ctx* ctx) {
     dfree(ctx->dk); dfree(ctx->da); dfree(ctx->da32); dfree(ctx->da_df); dfree(ctx->b_df);
     dfree(ctx->a_rowptr); dfree(ctx->a_col); dfree(ctx->a_k); dfree(ctx->a_a);
     dfree(ctx->k_row); dfree(ctx->k_col); dfree(ctx->k_a); dfree(ctx->k_id); dfree(ctx->b);
+    dfree(ctx->k_adf); dfree(ctx->a_adf);
     dfree(ctx->part); dfree(ctx->small); dfree(ctx->ctrl);
     if (ctx->h_small) cudaFreeHost(ctx->h_small);
     if (ctx->h_ctrl) cudaFreeHost(ctx->h_ctrl);
@@ -324,6 +327,8 @@ lorads_status validate_and_build(lorads_ctx* ctx, int64_t n, const int64_t* rp, 
     if ((s = upload(ctx, &ctx->k_a, hp.k_a.data(), m))) return s;
     if ((s = upload(ctx, &ctx->k_id, hp.k_id.data(), m))) return s;
     if ((s = upload(ctx, &ctx->b, b, m))) return s;
+    if ((s = upload(ctx, &ctx->k_adf, hp.k_adf.data(), m))) return s;
+    if (m_off > 0 && (s = upload(ctx, &ctx->a_adf, hp.a_adf.data(), hp.a_adf.size()))) return s;
     ProbDev& p = ctx->pd;
     p.n = n; p.m = m;
     p.c_rowptr = ctx->c_rowptr; p.c_col = ctx->c_col; p.c_val = ctx->c_val; p.c_val32 = ctx->c_val32;
@@ -333,6 +338,8 @@ lorads_status validate_and_build(lorads_ctx* ctx, int64_t n, const int64_t* rp, 
     p.k_row = ctx->k_row; p.k_col = ctx->k_col; p.k_a = ctx->k_a; p.k_id = ctx->k_id;
     p.m_diag = m_diag; p.m_off = m_off;
     p.b = ctx->b;
+    p.k_adf = ctx->k_adf;
+    p.a_adf = ctx->a_adf;
     return LORADS_OK;
 }
 
@@ -497,6 +504,8 @@ namespace {
 
 template <typename TR, typename TD>
 struct Driver {
+    // y~ of the off-diagonal constraints is double-float on every path but FP64
+    static constexpr int kYtilDf = std::is_same<TR, double>::value ? 0 : 1;
     lorads_ctx* c;
     SolverState& st;
     cudaStream_t s;
@@ -541,10 +550,10 @@ struct Driver {
     // G = grad L at the current R (outer tail and start): [y~, W], update, reset
     void outer_gradient(int ph) {
         if (c->m_off) {
-            ConsArgs yt{p(), CONS_YTIL, c->m_diag, c->m, st.R, st.R, st.ld, st.sh, st.y, st.ytil, st.zk, nullptr, c->ctrl, 0.0,
+            ConsArgs yt{p(), CONS_YTIL, c->m_diag, c->m, st.R, st.R, st.ld, st.sh, st.y, st.ytil, st.zk, st.ydf, c->ctrl, 0.0,
                         part_of(c, PART_YTIL), nb_off, c->ctrl, ph, s};
             timed(FAM_CONS_YTIL, [&] { launch_cons<TR, TR>(yt); });
-            SpmmAArgs w{p(), st.R, st.W, st.ld, st.sh, st.ytil, 1.0, 0, nb_rows, c->ctrl, ph, s};
+            SpmmAArgs w{p(), st.R, st.W, st.ld, st.sh, st.ytil, 1.0, 0, nb_rows, c->ctrl, ph, s, kYtilDf};
             timed(FAM_SPMM_A, [&] { launch_spmm_a<TR, TD>(w); });
         }
         UpdateArgs u{p(), false, false, st.R, st.CR, st.D, st.CD, st.G, c->m_off ? st.W : nullptr, st.hist,
@@ -585,7 +594,7 @@ struct Driver {
                      part_of(c, PART_LS), nb_rows, c->ctrl, PH_INNER, s};
         timed(FAM_SPMM_LS, [&] { launch_spmm_c<TD, TD, TR>(ls); });
         if (c->m_off) {
-            ConsArgs cl{p(), CONS_LS, c->m_diag, c->m, st.R, st.D, st.ld, st.sh, st.y, nullptr, st.zk, nullptr, c->ctrl, 0.0,
+            ConsArgs cl{p(), CONS_LS, c->m_diag, c->m, st.R, st.D, st.ld, st.sh, st.y, nullptr, st.zk, st.ydf, c->ctrl, 0.0,
                         part_of(c, PART_CONS_LS), nb_off, c->ctrl, PH_INNER, s};
             timed(FAM_CONS_LS, [&] { launch_cons<TR, TD>(cl); });
         }
@@ -596,10 +605,10 @@ struct Driver {
         if (c->m_off) {
             StepArgs sa{nunits, st.R, st.CR, st.D, st.CD, c->ctrl, nb_flat, c->ctrl, PH_STEP, s};
             timed(FAM_STEP, [&] { launch_step<TR, TD>(sa); });
-            ConsArgs yt{p(), CONS_YTIL, c->m_diag, c->m, st.R, st.R, st.ld, st.sh, st.y, st.ytil, st.zk, nullptr, c->ctrl, 0.0,
+            ConsArgs yt{p(), CONS_YTIL, c->m_diag, c->m, st.R, st.R, st.ld, st.sh, st.y, st.ytil, st.zk, st.ydf, c->ctrl, 0.0,
                         part_of(c, PART_YTIL), nb_off, c->ctrl, PH_STEP, s};
             timed(FAM_CONS_YTIL, [&] { launch_cons<TR, TR>(yt); });
-            SpmmAArgs w{p(), st.R, st.W, st.ld, st.sh, st.ytil, 1.0, 0, nb_rows, c->ctrl, PH_STEP, s};
+            SpmmAArgs w{p(), st.R, st.W, st.ld, st.sh, st.ytil, 1.0, 0, nb_rows, c->ctrl, PH_STEP, s, kYtilDf};
             timed(FAM_SPMM_A, [&] { launch_spmm_a<TR, TD>(w); });
         }
         UpdateArgs u{p(), c->m_off == 0, true, st.R, st.CR, st.D, st.CD, st.G, c->m_off ? st.W : nullptr, st.hist,

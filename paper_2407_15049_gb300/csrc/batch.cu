@@ -20,6 +20,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "../../include/lorads.h"
 #include "common.cuh"
 #include "control_dev.cuh"
@@ -27,6 +29,7 @@
 #include "prob_host.h"
 
 using namespace lorads;
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -53,21 +56,28 @@ struct BInst {
 };
 
 // Per-instance result written by the kernel.
+// phases of the per-instance solve timed by the persistent kernel
+enum { BP_INIT = 0, BP_DIR, BP_LS, BP_CONS_LS, BP_ROOT, BP_STEP, BP_YTIL, BP_SPMM_A, BP_UPDATE, BP_HIST, BP_OUTER,
+       BP_GRAD, BP_RANK, BP_N };
+
 struct BOut {
     Ctrl ctrl;
     int r, ld;
     long long t_begin, t_end;     // %globaltimer (ns)
+    long long phase_ns[BP_N];     // time of each phase (thread 0 of the block, after its barrier)
 };
 
 // shared-memory slots of the reduced sums (one block: the partial is the sum)
-enum { SP_DIR = 0, SP_LS = 2, SP_CLS = 9, SP_UPD = 16, SP_CONS = 30, SP_OBJ = 32, SP_YT = 34, SP_ZERO = 40,
-       SP_MISC = 48, SP_N = 56 };
+// (SP_CONS, SP_OBJ, SP_TIME are adjacent: the outer step reduces them together)
+enum { SP_DIR = 0, SP_LS = 2, SP_CLS = 9, SP_UPD = 16, SP_CONS = 30, SP_OBJ = 32, SP_TIME = 33, SP_YT = 34,
+       SP_ZERO = 40, SP_MISC = 48, SP_N = 56 };
 static_assert(SP_LS - SP_DIR >= PD_N && SP_CLS - SP_LS >= PL_N && SP_UPD - SP_CLS >= PL_N &&
-                  SP_CONS - SP_UPD >= PU_N && SP_OBJ - SP_CONS >= PC_N && SP_YT - SP_OBJ >= PO_N &&
-                  SP_ZERO - SP_YT >= PC_N && SP_MISC - SP_ZERO >= PL_N,
+                  SP_CONS - SP_UPD >= PU_N && SP_OBJ - SP_CONS == PC_N && SP_TIME - SP_OBJ == PO_N &&
+                  SP_YT - SP_TIME >= 1 && SP_ZERO - SP_YT >= PC_N && SP_MISC - SP_ZERO >= PL_N,
               "partial-sum slots overlap");
 
 constexpr int kBatchLdMax = 128;          // one 16-byte unit per lane (CPL = 1)
+constexpr int kBatchMaxThreads = 512;     // threads per block: 256 or 512 (register budget 128 each)
 
 __device__ __forceinline__ long long globaltimer_ns() {
     long long t;
@@ -89,11 +99,27 @@ __device__ __forceinline__ double as_double(T v) {
 
 // Starting factor: the given R0, else rows of SplitMix64 normals as the
 // single-instance solve draws them (unit rows for diagonal constraints).
+// The blocks that solve one instance: one block (size 1), or the blocks of a
+// thread-block cluster that split the rows and constraints of one large
+// instance, reduce their partial sums through distributed shared memory and
+// each keep an identical copy of the control block.
+struct Team {
+    int rank, size;
+    __device__ __forceinline__ void sync() const {
+        if (size > 1) cg::this_cluster().sync();
+        else __syncthreads();
+    }
+    __device__ __forceinline__ int64_t tid() const { return (int64_t)rank * blockDim.x + threadIdx.x; }
+    __device__ __forceinline__ int64_t nthreads() const { return (int64_t)size * blockDim.x; }
+};
+
+// Starting factor: the given R0, else rows of SplitMix64 normals as the
+// single-instance solve draws them (unit rows for diagonal constraints).
 template <typename TR>
-__device__ void batch_start(const BInst& I, TR* R, int r, int ld) {
+__device__ void batch_start(const BInst& I, TR* R, int r, int ld, const Team& tm) {
     const int64_t n = I.p.n;
     if (I.R0 != nullptr) {
-        for (int64_t e = threadIdx.x; e < n * ld; e += blockDim.x) {
+        for (int64_t e = tm.tid(); e < n * ld; e += tm.nthreads()) {
             const int64_t i = e / ld;
             const int c = (int)(e - i * ld);
             R[e] = c < r ? TR(I.R0[i * r + c]) : TR(0.0);
@@ -102,7 +128,7 @@ __device__ void batch_start(const BInst& I, TR* R, int r, int ld) {
     }
     const uint64_t golden = 0x9E3779B97F4A7C15ull;
     const uint64_t base = I.seed ^ (~0ull * golden);
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int64_t i = tm.tid(); i < n; i += tm.nthreads()) {
         double nrm = 0.0;
         for (int c = 0; c < r; ++c) {
             const double g = normal_at(base, i * r + c);
@@ -119,18 +145,48 @@ __device__ void batch_start(const BInst& I, TR* R, int r, int ld) {
     }
 }
 
+// sp: this block's partial sums; tot: the team's sums (== sp for one block)
 template <typename TR, typename TD>
-__device__ void batch_solve_one(const BInst& I, const Ctrl& c0, BOut& o, Ctrl* c, double* sp, int rows_per_warp,
-                                long long time_limit_ns) {
+__device__ void batch_solve_one(const BInst& I, const Ctrl& c0, BOut& o, Ctrl* c, double* sp, double* tot,
+                                int rows_per_warp, long long time_limit_ns, long long* ph, const Team tm) {
     using ZS = zrow_t<TD, TR>;
-    const VGrid vg{0, 1};
+    // y~ and the cached z of the off-diagonal constraints: double-float unless FP64
+    constexpr bool kYtilDf = !std::is_same<TR, double>::value;
+    const VGrid vg{tm.rank, tm.size, 0};
     const int tid = threadIdx.x;
     const long long t_begin = globaltimer_ns();
+    long long t_last = t_begin;
+    if (tid < BP_N) ph[tid] = 0;
+    // time since the previous tick goes to phase q (thread 0, right after a barrier)
+    auto tick = [&](int q) {
+        if (tid == 0) {
+            const long long now = globaltimer_ns();
+            ph[q] += now - t_last;
+            t_last = now;
+        }
+    };
+    // after a body that wrote its partials to sp[off, off+nq): the team's sums in
+    // tot (fixed rank order: every block gets bit-identical sums)
+    auto reduce = [&](int off, int nq) {
+        tm.sync();
+        if (tm.size > 1) {
+            cg::cluster_group cl = cg::this_cluster();
+            for (int q = tid; q < nq; q += blockDim.x) {
+                double acc = 0.0;
+                for (int rk = 0; rk < tm.size; ++rk) acc += cl.map_shared_rank(sp, rk)[off + q];
+                tot[off + q] = acc;
+            }
+            __syncthreads();
+        }
+    };
     {
         const int* src = reinterpret_cast<const int*>(&c0);
         int* dst = reinterpret_cast<int*>(c);
         for (int w = tid; w < (int)(sizeof(Ctrl) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
-        if (tid < SP_N - SP_ZERO) sp[SP_ZERO + tid] = 0.0;
+        if (tid < SP_N - SP_ZERO) {
+            sp[SP_ZERO + tid] = 0.0;
+            tot[SP_ZERO + tid] = 0.0;
+        }
     }
     const ProbDev p = I.p;
     TR* R = static_cast<TR*>(I.R);
@@ -152,41 +208,44 @@ __device__ void batch_solve_one(const BInst& I, const Ctrl& c0, BOut& o, Ctrl* c
     int L = batch_lanes(Q, rows_per_warp);
     int64_t nunits = p.n * (int64_t)ld / 4;
 
-    batch_start<TR>(I, R, r, ld);
-    for (int64_t k = tid; k < p.m; k += blockDim.x) {
+    batch_start<TR>(I, R, r, ld, tm);
+    for (int64_t k = tm.tid(); k < p.m; k += tm.nthreads()) {
         y[k] = 0.0;
         if (ydf) ydf[k] = dfloat(0.0f, 0.0f);
     }
-    __syncthreads();
+    tm.sync();
 
     auto spmm_cr = [&]() {
         k_spmm_c_body<TR, TR, TR, 1, EPI_OBJ>(p, R, CR, ld, L, Q, nullptr, 1, R, y, nullptr, nullptr, c, 0.0,
                                                sp + SP_OBJ, vg);
-        __syncthreads();
     };
     // G = grad L at the current R, then a fresh inner loop (memory empty)
     auto outer_gradient = [&]() {
         if (p.m_off) {
-            k_cons_body<TR, TR, 1, CONS_YTIL>(p, p.m_diag, p.m, R, R, ld, L, Q, y, ytil, zk, nullptr, c, 0.0,
+            k_cons_body<TR, TR, 1, CONS_YTIL>(p, p.m_diag, p.m, R, R, ld, L, Q, y, ytil, zk, ydf, c, 0.0,
                                               sp + SP_YT, vg);
-            __syncthreads();
-            k_spmm_a_body<TR, TD, 1>(p, R, W, ld, L, Q, ytil, 1.0, 0, vg);
-            __syncthreads();
+            tm.sync();
+            k_spmm_a_body<TR, TD, 1, kYtilDf>(p, R, W, ld, L, Q, ytil, 1.0, 0, vg);
+            tm.sync();
         }
         k_update_body<TR, TD, 1, false, false>(p, R, CR, D, CD, G, p.m_off ? W : nullptr, hist, sstride, ld, L, Q,
                                                y, ydf, zrow, c, sp + SP_UPD, vg);
-        __syncthreads();
-        if (tid == 0) ctrl_hist_apply(c, true, true, sp + SP_UPD, p.m_off ? sp + SP_YT : sp + SP_ZERO);
-        __syncthreads();
+        reduce(SP_UPD, PU_N);
+        if (p.m_off) reduce(SP_YT, PC_N);
+        if (tid == 0) ctrl_hist_apply(c, true, true, tot + SP_UPD, p.m_off ? tot + SP_YT : tot + SP_ZERO);
+        tm.sync();
+        tick(BP_GRAD);
     };
 
     // ---- start: err1 at R0, objective, first gradient
     spmm_cr();
+    tm.sync();
     k_cons_body<TR, TR, 1, CONS_ZZ>(p, 0, p.m, R, R, ld, L, Q, y, nullptr, nullptr, nullptr, c, 0.0, sp + SP_CONS,
                                     vg);
-    __syncthreads();
-    if (tid == 0) ctrl_init_apply(c, sp + SP_CONS, sp + SP_OBJ);
-    __syncthreads();
+    reduce(SP_CONS, PC_N + PO_N);
+    if (tid == 0) ctrl_init_apply(c, tot + SP_CONS, tot + SP_OBJ);
+    tm.sync();
+    tick(BP_INIT);
     outer_gradient();
 
     while (!c->solve_done) {
@@ -197,20 +256,20 @@ __device__ void batch_solve_one(const BInst& I, const Ctrl& c0, BOut& o, Ctrl* c
             r_new = min(r_new, min(I.r_cap, I.ld_cap));
             if (r_new > r_old) {
                 double acc[1] = {0.0};
-                for (int64_t e = tid; e < p.n * ld; e += blockDim.x) {
+                for (int64_t e = tm.tid(); e < p.n * ld; e += tm.nthreads()) {
                     const double v = as_double(R[e]);
                     acc[0] += v * v;
                 }
                 block_partials<1>(acc, sp + SP_MISC, 0);
-                __syncthreads();
-                const double scale = 1e-3 * sqrt(sp[SP_MISC]) / sqrt((double)p.n * r_old);
-                for (int64_t e = tid; e < p.n * ld; e += blockDim.x) CR[e] = R[e];     // old rows
-                __syncthreads();
+                reduce(SP_MISC, 1);
+                const double scale = 1e-3 * sqrt(tot[SP_MISC]) / sqrt((double)p.n * r_old);
+                for (int64_t e = tm.tid(); e < p.n * ld; e += tm.nthreads()) CR[e] = R[e];     // old rows
+                tm.sync();
                 const int ld_new = (r_new + 3) / 4 * 4;
                 const int k = r_new - r_old;
                 const uint64_t golden = 0x9E3779B97F4A7C15ull;
                 const uint64_t base = I.seed ^ ((uint64_t)(c->outer - 1) * golden);
-                for (int64_t e = tid; e < p.n * ld_new; e += blockDim.x) {
+                for (int64_t e = tm.tid(); e < p.n * ld_new; e += tm.nthreads()) {
                     const int64_t i = e / ld_new;
                     const int cc = (int)(e - i * ld_new);
                     TR v = TR(0.0);
@@ -218,7 +277,7 @@ __device__ void batch_solve_one(const BInst& I, const Ctrl& c0, BOut& o, Ctrl* c
                     else if (cc < r_new) v = TR(scale * normal_at(base, i * k + (cc - r_old)));
                     R[e] = v;
                 }
-                __syncthreads();
+                tm.sync();
                 r = r_new;
                 ld = ld_new;
                 Q = ld / 4;
@@ -229,94 +288,139 @@ __device__ void batch_solve_one(const BInst& I, const Ctrl& c0, BOut& o, Ctrl* c
                 c->pause = 0;
                 c->phase = PHASE_OUTER;
             }
-            __syncthreads();
             spmm_cr();
+            tm.sync();
+            tick(BP_RANK);
             outer_gradient();
             continue;
         }
         if (c->phase == PHASE_INNER) {
             // ---- one iteration of Algorithm 1: direction, exact line search, step
             k_dir_body<TD>(nunits, G, D, hist, sstride, c, sp + SP_DIR, vg);
-            __syncthreads();
+            tm.sync();
+            tick(BP_DIR);
             k_spmm_c_body<TD, TD, TR, 1, EPI_LS>(p, D, CD, ld, L, Q, nullptr, 1, R, y, zrow, ydf, c, 0.0,
                                                  sp + SP_LS, vg);
-            __syncthreads();
+            tm.sync();
+            tick(BP_LS);
             if (p.m_off) {
-                k_cons_body<TR, TD, 1, CONS_LS>(p, p.m_diag, p.m, R, D, ld, L, Q, y, nullptr, zk, nullptr, c, 0.0,
+                k_cons_body<TR, TD, 1, CONS_LS>(p, p.m_diag, p.m, R, D, ld, L, Q, y, nullptr, zk, ydf, c, 0.0,
                                                 sp + SP_CLS, vg);
-                __syncthreads();
+                tm.sync();
+                tick(BP_CONS_LS);
             }
-            if (tid == 0) ctrl_root_apply(c, sp + SP_DIR, sp + SP_LS, p.m_off ? sp + SP_CLS : sp + SP_ZERO);
-            __syncthreads();
+            reduce(SP_DIR, SP_UPD - SP_DIR);          // direction, C pass and constraint pass sums
+            if (tid == 0) ctrl_root_apply(c, tot + SP_DIR, tot + SP_LS, p.m_off ? tot + SP_CLS : tot + SP_ZERO);
+            tm.sync();
+            tick(BP_ROOT);
             if (c->solve_done) break;
             if (c->step_ok) {
                 if (p.m_off) {
                     k_step_body<TR, TD>(nunits, R, CR, D, CD, c, vg);
-                    __syncthreads();
-                    k_cons_body<TR, TR, 1, CONS_YTIL>(p, p.m_diag, p.m, R, R, ld, L, Q, y, ytil, zk, nullptr, c, 0.0,
+                    tm.sync();
+                    tick(BP_STEP);
+                    k_cons_body<TR, TR, 1, CONS_YTIL>(p, p.m_diag, p.m, R, R, ld, L, Q, y, ytil, zk, ydf, c, 0.0,
                                                       sp + SP_YT, vg);
-                    __syncthreads();
-                    k_spmm_a_body<TR, TD, 1>(p, R, W, ld, L, Q, ytil, 1.0, 0, vg);
-                    __syncthreads();
+                    tm.sync();
+                    tick(BP_YTIL);
+                    k_spmm_a_body<TR, TD, 1, kYtilDf>(p, R, W, ld, L, Q, ytil, 1.0, 0, vg);
+                    tm.sync();
+                    tick(BP_SPMM_A);
                     k_update_body<TR, TD, 1, false, true>(p, R, CR, D, CD, G, W, hist, sstride, ld, L, Q, y, ydf,
                                                           zrow, c, sp + SP_UPD, vg);
+                    reduce(SP_UPD, PU_N);
+                    reduce(SP_YT, PC_N);
                 } else {
                     k_update_body<TR, TD, 1, true, true>(p, R, CR, D, CD, G, nullptr, hist, sstride, ld, L, Q, y,
                                                          ydf, zrow, c, sp + SP_UPD, vg);
+                    reduce(SP_UPD, PU_N);
                 }
-                __syncthreads();
+                tick(BP_UPDATE);
             }
             if (tid == 0 && !c->solve_done && !c->pause && c->phase == PHASE_INNER)
-                ctrl_hist_apply(c, false, c->step_ok != 0, sp + SP_UPD, p.m_off ? sp + SP_YT : sp + SP_ZERO);
-            __syncthreads();
+                ctrl_hist_apply(c, false, c->step_ok != 0, tot + SP_UPD, p.m_off ? tot + SP_YT : tot + SP_ZERO);
+            tm.sync();
+            tick(BP_HIST);
         }
         if (!c->solve_done && !c->pause && c->phase == PHASE_OUTER) {
             // ---- multiplier step of Sec. 2.1 and the outer tests
             k_cons_body<TR, TR, 1, CONS_YUPD>(p, 0, p.m, R, R, ld, L, Q, y, nullptr, nullptr, ydf, c, 0.0,
                                               sp + SP_CONS, vg);
-            __syncthreads();
+            tm.sync();
             spmm_cr();
+            // the time limit: rank 0's clock, summed with the partials so that
+            // every block of a team takes the same decision
+            if (tid == 0) sp[SP_TIME] = tm.rank == 0 ? (double)(globaltimer_ns() - t_begin) : 0.0;
+            reduce(SP_CONS, PC_N + PO_N + 1);
             if (tid == 0) {
-                ctrl_outer_apply(c, sp + SP_CONS, sp + SP_OBJ);
-                if (!c->solve_done && time_limit_ns > 0 && globaltimer_ns() - t_begin > time_limit_ns) {
+                ctrl_outer_apply(c, tot + SP_CONS, tot + SP_OBJ);
+                if (!c->solve_done && time_limit_ns > 0 && tot[SP_TIME] > (double)time_limit_ns) {
                     c->status = LORADS_ERR_TIMEOUT;
                     c->solve_done = 1;
                 }
             }
-            __syncthreads();
+            tm.sync();
+            tick(BP_OUTER);
             if (!c->solve_done && !c->pause) outer_gradient();
         }
     }
-    __syncthreads();
-    {
+    tm.sync();
+    if (tm.rank == 0) {
         const int* src = reinterpret_cast<const int*>(c);
         int* dst = reinterpret_cast<int*>(&o.ctrl);
         for (int w = tid; w < (int)(sizeof(Ctrl) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
-    }
-    if (tid == 0) {
-        o.r = r;
-        o.ld = ld;
-        o.t_begin = t_begin;
-        o.t_end = globaltimer_ns();
+        if (tid == 0) {
+            o.r = r;
+            o.ld = ld;
+            o.t_begin = t_begin;
+            o.t_end = globaltimer_ns();
+            for (int q = 0; q < BP_N; ++q) o.phase_ns[q] = ph[q];
+        }
     }
 }
 
-// The persistent kernel: blocks take instances from the queue until it is empty.
+// The persistent kernel.  With clusters of size > 1, each cluster first takes
+// the large instances (order[0, n_team)) from one queue and solves each with
+// all its blocks; once that queue is empty its blocks take the remaining
+// instances one block each from a second queue.  Without clusters every block
+// takes instances from the second queue starting at order[0].
 template <typename TR, typename TD>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kBatchMaxThreads, 1)
 k_batch_solve(const BInst* __restrict__ insts, const Ctrl* __restrict__ ctrl0, BOut* out,
-              const int* __restrict__ order, int count, int* queue, int rows_per_warp, long long time_limit_ns) {
+              const int* __restrict__ order, int count, int n_team, int* queues, int rows_per_warp,
+              long long time_limit_ns) {
     __shared__ Ctrl c;
     __shared__ double sp[SP_N];
+    __shared__ double tot[SP_N];
+    __shared__ long long s_ph[BP_N];
     __shared__ int s_item;
+    __shared__ int s_team_item;
+    cg::cluster_group cl = cg::this_cluster();
+    const int csize = (int)cl.num_blocks();
+    bool team_phase = csize > 1;
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
-        __syncthreads();
-        const int it = s_item;
-        if (it >= count) return;
+        int it;
+        Team tm{0, 1};
+        if (team_phase) {
+            if (cl.block_rank() == 0 && threadIdx.x == 0) s_team_item = atomicAdd(queues, 1);
+            cl.sync();
+            it = *cl.map_shared_rank(&s_team_item, 0);
+            cl.sync();                      // every block has read rank 0's slot
+            if (it >= n_team) {
+                team_phase = false;         // the same decision in every block of the cluster
+                continue;
+            }
+            tm = Team{(int)cl.block_rank(), csize};
+        } else {
+            __syncthreads();
+            if (threadIdx.x == 0) s_item = (csize > 1 ? n_team : 0) + atomicAdd(queues + 1, 1);
+            __syncthreads();
+            it = s_item;
+            if (it >= count) return;
+        }
         const int k = order[it];
-        batch_solve_one<TR, TD>(insts[k], ctrl0[k], out[k], &c, sp, rows_per_warp, time_limit_ns);
+        batch_solve_one<TR, TD>(insts[k], ctrl0[k], out[k], &c, sp, tm.size > 1 ? tot : sp, rows_per_warp,
+                                time_limit_ns, s_ph, tm);
     }
 }
 
@@ -357,7 +461,7 @@ struct lorads_batch {
     std::vector<BOut> h_out;
     std::vector<int64_t> n, m;
     std::vector<double> cnorm1;
-    lorads_batch_shape shape{2, 8, 1, 0};
+    lorads_batch_shape shape{2, 8, 1, 256, 1, 0};
     int64_t iter_limit = 0;
     cudaGraphExec_t exec = nullptr;
     lorads_batch_shape exec_shape{0, 0, 0, 0};
@@ -408,6 +512,45 @@ void fill_ctrl0(const lorads_params& P, const HostProb& hp, int64_t iter_limit, 
     for (int q = 0; q < kMaxMem; ++q) h->order[q] = q;
 }
 
+int threads_of(const lorads_batch_shape& s) { return s.threads == 512 ? 512 : 256; }
+int cluster_of(const lorads_batch_shape& s) { return s.cluster > 1 ? s.cluster : 1; }
+
+// Grid of the launch: SMs x blocks per SM without clusters; with clusters, as
+// many whole clusters as can be resident at once (a persistent kernel needs all
+// its blocks resident: blocks of a cluster wait for one another).
+lorads_status launch_grid(lorads_batch* b, const lorads_batch_shape& sh, int* grid, int* n_team) {
+    const int cs = cluster_of(sh);
+    if (cs == 1) {
+        *grid = std::max(1, std::min(b->count, b->num_sms * sh.ctas_per_sm));
+        *n_team = 0;
+        return LORADS_OK;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs * 64);
+    cfg.blockDim = dim3(threads_of(sh));
+    cfg.dynamicSmemBytes = 0;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, kernel_for(b->prec), &cfg);
+    if (e != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();
+        b->err = std::string("cluster size ") + std::to_string(cs) + " cannot be resident: " +
+                 (e != cudaSuccess ? cudaGetErrorString(e) : "no cluster fits");
+        return LORADS_ERR_UNSUPPORTED;
+    }
+    // ctas_per_sm bounds the clusters as it bounds plain blocks
+    nclusters = std::min(nclusters, std::max(1, b->num_sms * sh.ctas_per_sm / cs));
+    *grid = nclusters * cs;
+    *n_team = std::min(b->count, std::max(0, sh.team_count));
+    return LORADS_OK;
+}
+
 lorads_status capture_batch(lorads_batch* b) {
     if (b->exec && std::memcmp(&b->exec_shape, &b->shape, sizeof(lorads_batch_shape)) == 0 &&
         b->exec_limit == b->iter_limit)
@@ -416,21 +559,38 @@ lorads_status capture_batch(lorads_batch* b) {
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
     }
-    const int grid = std::max(1, std::min(b->count, b->num_sms * b->shape.ctas_per_sm));
+    int grid = 0, n_team = 0;
+    lorads_status gs = launch_grid(b, b->shape, &grid, &n_team);
+    if (gs != LORADS_OK) return gs;
     const int* order = b->d_order + (b->shape.order ? b->count : 0);
     const long long tl = b->prm.time_limit > 0 ? (long long)std::min(b->prm.time_limit * 1e9, 9.0e18) : 0;
     const BInst* insts = b->d_inst;
     const Ctrl* ctrl0 = b->d_ctrl0;
     BOut* out = b->d_out;
     int count = b->count;
-    int* queue = b->d_queue;
+    int* queues = b->d_queue;
     int rpw = b->shape.rows_per_warp;
-    void* args[] = {(void*)&insts, (void*)&ctrl0, (void*)&out, (void*)&order, (void*)&count, (void*)&queue,
-                    (void*)&rpw, (void*)const_cast<long long*>(&tl)};
+    void* args[] = {(void*)&insts, (void*)&ctrl0, (void*)&out, (void*)&order, (void*)&count, (void*)&n_team,
+                    (void*)&queues, (void*)&rpw, (void*)const_cast<long long*>(&tl)};
     cudaGraph_t g = nullptr;
     BCK(cudaStreamBeginCapture(b->solve_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e1 = cudaMemsetAsync(b->d_queue, 0, sizeof(int), b->solve_stream);
-    cudaError_t e2 = cudaLaunchKernel(kernel_for(b->prec), dim3(grid), dim3(kThreads), args, 0, b->solve_stream);
+    cudaError_t e1 = cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(int), b->solve_stream);
+    cudaError_t e2;
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(threads_of(b->shape));
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = b->solve_stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cluster_of(b->shape);
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e2 = cudaLaunchKernelExC(&cfg, kernel_for(b->prec), args);
+    }
     cudaError_t e3 = cudaStreamEndCapture(b->solve_stream, &g);
     if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -451,9 +611,9 @@ lorads_status capture_batch(lorads_batch* b) {
     return LORADS_OK;
 }
 
-int max_ctas_per_sm(int prec) {
+int max_ctas_per_sm(int prec, int threads) {
     int nb = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for(prec), kThreads, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for(prec), threads, 0) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
@@ -525,7 +685,9 @@ lorads_status run_batch(lorads_batch* b, lorads_result* results, lorads_batch_st
         stats->latency_max_ms = lat.back();
         stats->inner_iters = inner;
         stats->solved = solved;
-        stats->grid = std::max(1, std::min(b->count, b->num_sms * b->shape.ctas_per_sm));
+        int grid = 0, n_team = 0;
+        launch_grid(b, b->shape, &grid, &n_team);
+        stats->grid = grid;
         stats->shape = b->shape;
     }
     return LORADS_OK;
@@ -533,8 +695,10 @@ lorads_status run_batch(lorads_batch* b, lorads_result* results, lorads_batch_st
 
 bool valid_shape(const lorads_batch_shape& s) {
     const int r = s.rows_per_warp;
+    const int c = s.cluster;
     return s.ctas_per_sm >= 1 && s.ctas_per_sm <= 4 && (r == 1 || r == 2 || r == 4 || r == 8) &&
-           (s.order == 0 || s.order == 1);
+           (s.order == 0 || s.order == 1) && (s.threads == 0 || s.threads == 256 || s.threads == 512) &&
+           (c == 0 || c == 1 || c == 2 || c == 4 || c == 8) && s.team_count >= 0;
 }
 
 void free_batch(lorads_batch* b) {
@@ -627,6 +791,8 @@ extern "C" lorads_status lorads_batch_create(lorads_batch** out, int32_t count, 
         ps += align_up(m * 8);                                             // b_df
         if (h.m_off) ps += align_up((n + 1) * 8) + 2 * align_up(h.a_col.size() * 4) + align_up(h.a_a.size() * 8);
         ps += 3 * align_up(m * 4) + align_up(m * 8) + align_up(m * 8);    // k_row/col/id, k_a, b
+        ps += align_up(m * 8);                                             // k_a double-float mirror
+        if (h.m_off) ps += align_up(h.a_a.size() * 8);                     // a_a double-float mirror
         if (R0) ps += align_up(n * r0[i] * 8);
         prob_off[i + 1] = prob_off[i] + ps;
         // state pool
@@ -712,6 +878,8 @@ extern "C" lorads_status lorads_batch_create(lorads_batch** out, int32_t count, 
         pd.k_id = static_cast<const int32_t*>(put(h.k_id.data(), m * 4));
         pd.k_a = static_cast<const double*>(put(h.k_a.data(), m * 8));
         pd.b = static_cast<const double*>(put(h.b, m * 8));
+        pd.k_adf = static_cast<const dfloat*>(put(h.k_adf.data(), m * 8));
+        if (h.m_off) pd.a_adf = static_cast<const dfloat*>(put(h.a_adf.data(), h.a_adf.size() * 8));
         pd.m_diag = h.m_diag;
         pd.m_off = h.m_off;
         BInst& I = b->h_inst[i];
@@ -767,8 +935,8 @@ extern "C" lorads_status lorads_batch_create(lorads_batch** out, int32_t count, 
     std::stable_sort(ord.begin() + count, ord.end(), [&](int x, int y) { return work[x] > work[y]; });
     BCREATE(cudaMalloc(&b->d_order, sizeof(int) * 2 * count));
     BCREATE(cudaMemcpy(b->d_order, ord.data(), sizeof(int) * 2 * count, cudaMemcpyHostToDevice));
-    BCREATE(cudaMalloc(&b->d_queue, sizeof(int)));
-    b->shape.ctas_per_sm = std::min(2, max_ctas_per_sm(b->prec));
+    BCREATE(cudaMalloc(&b->d_queue, 2 * sizeof(int)));
+    b->shape.ctas_per_sm = std::min(2, max_ctas_per_sm(b->prec, 256));
 #undef BCREATE
     *out = b;
     return LORADS_OK;
@@ -790,15 +958,22 @@ extern "C" lorads_status lorads_batch_solve(lorads_batch* b, lorads_result* resu
 extern "C" lorads_status lorads_batch_set_shape(lorads_batch* b, const lorads_batch_shape* shape) {
     if (!b || !shape) return LORADS_ERR_INVALID_ARG;
     if (!valid_shape(*shape)) {
-        b->err = "shape: ctas_per_sm in [1,4], rows_per_warp in {1,2,4,8}, order 0 or 1";
+        b->err = "shape: ctas_per_sm in [1,4], rows_per_warp in {1,2,4,8}, order 0 or 1, threads 256 or 512, "
+                 "cluster 1, 2, 4 or 8, team_count >= 0";
         return LORADS_ERR_INVALID_ARG;
     }
-    if (shape->ctas_per_sm > max_ctas_per_sm(b->prec)) {
+    lorads_batch_shape sh = *shape;
+    sh.threads = threads_of(sh);
+    sh.cluster = cluster_of(sh);
+    if (sh.cluster == 1) sh.team_count = 0;
+    if (sh.ctas_per_sm > max_ctas_per_sm(b->prec, sh.threads)) {
         b->err = "shape: more blocks per SM than the kernel's occupancy allows";
         return LORADS_ERR_INVALID_ARG;
     }
-    b->shape = *shape;
-    b->shape.reserved = 0;
+    int grid = 0, n_team = 0;
+    lorads_status gs = launch_grid(b, sh, &grid, &n_team);
+    if (gs != LORADS_OK) return gs;
+    b->shape = sh;
     return LORADS_OK;
 }
 
@@ -813,24 +988,48 @@ extern "C" lorads_status lorads_batch_tune(lorads_batch* b, int32_t probe_iters,
     const lorads_batch_shape keep = b->shape;
     lorads_status s = set_iter_limit(b, probe_iters);
     if (s != LORADS_OK) return s;
-    const int occ = max_ctas_per_sm(b->prec);
     double best_t = 1e300;
     lorads_batch_shape best_s = keep;
-    for (int order = 1; order >= 0; --order)
-        for (int ctas = 1; ctas <= occ; ++ctas)
-            for (int rpw : {8, 4, 2, 1}) {
-                b->shape = lorads_batch_shape{ctas, rpw, order, 0};
-                lorads_batch_stats st{};
-                if ((s = run_batch(b, nullptr, &st)) != LORADS_OK) {
-                    b->shape = keep;
-                    set_iter_limit(b, keep_limit);
-                    return s;
-                }
-                if (st.seconds < best_t) {
-                    best_t = st.seconds;
-                    best_s = b->shape;
-                }
-            }
+    auto probe = [&](const lorads_batch_shape& sh) -> lorads_status {
+        int grid = 0, n_team = 0;
+        if (launch_grid(b, sh, &grid, &n_team) != LORADS_OK) {
+            cudaGetLastError();
+            return LORADS_OK;                    // shape not launchable here: skip it
+        }
+        b->shape = sh;
+        lorads_batch_stats st{};
+        lorads_status rs = run_batch(b, nullptr, &st);
+        if (rs != LORADS_OK) return rs;
+        if (st.seconds < 0.97 * best_t) {        // a later candidate must win by 3% (timing noise)
+            best_t = st.seconds;
+            best_s = sh;
+        }
+        return LORADS_OK;
+    };
+    // one block per instance: threads x blocks per SM x rows per warp x order
+    for (int threads : {256, 512})
+        for (int order = 1; order >= 0; --order)
+            for (int ctas = 1; ctas <= max_ctas_per_sm(b->prec, threads); ++ctas)
+                for (int rpw : {8, 4, 2, 1})
+                    if ((s = probe(lorads_batch_shape{ctas, rpw, order, threads, 1, 0})) != LORADS_OK) break;
+    // clusters for the largest instances (largest first), on top of the best plain shape
+    const lorads_batch_shape base = best_s;
+    for (int cs : {2, 4, 8}) {
+        if (s != LORADS_OK) break;
+        const int nclusters = std::max(1, b->num_sms * base.ctas_per_sm / cs);
+        for (int mult : {1, 2, 4}) {
+            lorads_batch_shape sh = base;
+            sh.order = 1;
+            sh.cluster = cs;
+            sh.team_count = std::min(b->count, nclusters * mult);
+            if ((s = probe(sh)) != LORADS_OK) break;
+        }
+    }
+    if (s != LORADS_OK) {
+        b->shape = keep;
+        set_iter_limit(b, keep_limit);
+        return s;
+    }
     b->shape = best_s;
     if (best) *best = best_s;
     b->have_solution = false;           // the probes' iterates are not solutions
@@ -878,3 +1077,18 @@ extern "C" lorads_status lorads_batch_get_solution(lorads_batch* b, int32_t i, d
 }
 
 extern "C" const char* lorads_batch_create_error(void) { return g_batch_create_error.c_str(); }
+
+extern "C" int32_t lorads_batch_phase_times(const lorads_batch* b, int32_t i, const char** names, double* ms,
+                                            int32_t cap) {
+    static const char* const kNames[BP_N] = {"init", "direction", "spmm_ls", "cons_ls", "root", "step", "ytil",
+                                             "spmm_a", "update", "hist", "outer", "outer_gradient", "rank_update"};
+    if (!b || !b->have_solution || i < -1 || i >= b->count || cap < 1) return 0;
+    const int k = std::min<int>(cap, BP_N);
+    for (int q = 0; q < k; ++q) {
+        double t = 0.0;
+        for (int j = (i < 0 ? 0 : i); j < (i < 0 ? b->count : i + 1); ++j) t += (double)b->h_out[j].phase_ns[q];
+        if (names) names[q] = kNames[q];
+        if (ms) ms[q] = t * 1e-6;
+    }
+    return k;
+}

@@ -138,21 +138,23 @@ template <typename T> struct Arith { using type = T; };
 template <> struct Arith<__nv_bfloat16> { using type = float; };
 
 // ------------------------------------------------------------------ reductions
-// Sums NQ per-thread partials (double or double-float) over the block and
+// Sums NQ per-thread partials (double or double-float) over the block (up to
+// 1024 threads) and
 // writes them as doubles to part[bid * NQ + q].  Fixed order:
 // deterministic for a fixed grid.
 // Block index and count a kernel body runs with: the hardware grid for a
 // launch of its own, or one block standing for the whole grid when a
 // persistent kernel runs the body for one instance.
+// `pslot` is the partial-sum slot the block writes (its index in its own grid).
 struct VGrid {
-    int bid, nblk;
+    int bid, nblk, pslot;
 };
-__device__ __forceinline__ VGrid hw_grid() { return VGrid{(int)blockIdx.x, (int)gridDim.x}; }
+__device__ __forceinline__ VGrid hw_grid() { return VGrid{(int)blockIdx.x, (int)gridDim.x, (int)blockIdx.x}; }
 
 template <int NQ, typename PA>
 __device__ __forceinline__ void block_partials(PA (&acc)[NQ], double* part, int bid) {
-    __shared__ double red[kWarps][NQ > 0 ? NQ : 1];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ double red[32][NQ > 0 ? NQ : 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         PA v = acc[q];                       // warp tree in the partial's own type
@@ -163,8 +165,7 @@ __device__ __forceinline__ void block_partials(PA (&acc)[NQ], double* part, int 
     __syncthreads();
     for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
         double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) s += red[w][q];
+        for (int w = 0; w < nw; ++w) s += red[w][q];
         part[(size_t)bid * NQ + q] = s;
     }
 }

@@ -37,6 +37,10 @@ struct ProbDev {
     const int32_t* k_id;
     int64_t m_diag, m_off;
     const double* b;
+    // double-float mirrors of the constraint coefficients (list order and pattern
+    // order) for the FP32-unit paths; may be null for FP64 callers
+    const dfloat* k_adf;
+    const dfloat* a_adf;
 };
 
 // ------------------------------------------------------------------ gating
@@ -55,6 +59,8 @@ __device__ __forceinline__ bool gated_off(const Ctrl* g, int ph) {
 
 template <typename T>
 using arith_t = typename Arith<T>::type;
+template <typename T>
+using A_of_t = arith_t<T>;
 
 // precision rank of an arithmetic type: float < double-float < double
 template <typename T> struct PrecRank;
@@ -354,16 +360,32 @@ k_spmm_c_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld,
             }
         }
     }
-    if constexpr (EPI != EPI_NONE) block_partials<NQ>(accq, part, vg.bid);
+    if constexpr (EPI != EPI_NONE) block_partials<NQ>(accq, part, vg.pslot);
 }
 
 // ================================================================== SpMM over the
 // off-diagonal constraint pattern:  out = beta_acc * out + alpha * A*_off(v) X
-template <typename TX, typename TO, int CPL>
+// VDF: v holds double-float values and each weight alpha a v_k is formed in the
+// output's arithmetic from the double-float coefficient mirror (no FP64
+// operation); otherwise v is double and the weight is formed in FP64.
+template <typename TX, typename TO, int CPL, bool VDF>
+__device__ __forceinline__ A_of_t<TO> spmm_a_weight(const ProbDev& p, const void* v, double alpha, A_of_t<TO> alpha_a,
+                                                   int64_t s) {
+    using A = A_of_t<TO>;
+    const int k = __ldg(p.a_k + s);
+    if constexpr (VDF) {
+        return alpha_a * ld_scalar<A>(nullptr, p.a_adf, s) * ld_scalar<A>(nullptr, static_cast<const dfloat*>(v), k);
+    } else {
+        return A(alpha * __ldg(p.a_a + s) * __ldg(static_cast<const double*>(v) + k));
+    }
+}
+
+template <typename TX, typename TO, int CPL, bool VDF>
 __device__ __forceinline__ void
 k_spmm_a_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int L, int Q,
-         const double* __restrict__ v, double alpha, int accumulate, VGrid vg) {
+         const void* __restrict__ v, double alpha, int accumulate, VGrid vg) {
     using A = arith_t<TO>;
+    const A alpha_a = A(alpha);
     RowLoop rl(L, vg);
     for (int64_t base = rl.first; base < p.n; base += rl.stride) {
         const int64_t i = base + rl.gw;
@@ -374,9 +396,29 @@ k_spmm_a_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld,
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[c][e] = A(0);
         const int64_t s0 = __ldg(p.a_rowptr + i), s1 = __ldg(p.a_rowptr + i + 1);
-        for (int64_t s = s0; s < s1; ++s) {
+        int64_t s = s0;
+        constexpr int UN = CPL == 1 ? 4 : 2;           // entries in flight per lane
+        for (; s + UN <= s1; s += UN) {
+            int j[UN];
+            A w[UN];
+#pragma unroll
+            for (int u = 0; u < UN; ++u) {
+                j[u] = __ldg(p.a_col + s + u);
+                w[u] = spmm_a_weight<TX, TO, CPL, VDF>(p, v, alpha, alpha_a, s + u);
+            }
+            Unit<TX> x[UN][CPL];
+#pragma unroll
+            for (int u = 0; u < UN; ++u) load_row<TX, CPL>(x[u], X, j[u], ld, L, Q, rl.lig);
+#pragma unroll
+            for (int u = 0; u < UN; ++u)
+#pragma unroll
+                for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[c][e] = fma(w[u], A(x[u][c].v[e]), acc[c][e]);
+        }
+        for (; s < s1; ++s) {
             const int j = __ldg(p.a_col + s);
-            const A w = A(alpha * __ldg(p.a_a + s) * __ldg(v + __ldg(p.a_k + s)));
+            const A w = spmm_a_weight<TX, TO, CPL, VDF>(p, v, alpha, alpha_a, s);
             Unit<TX> x[CPL];
             load_row<TX, CPL>(x, X, j, ld, L, Q, rl.lig);
 #pragma unroll
@@ -415,7 +457,7 @@ enum { CONS_EVAL = 0, CONS_LS = 1, CONS_YTIL = 2, CONS_YUPD = 3, CONS_ZZ = 4 };
 template <typename TU, typename TV, int CPL, int MODE>
 __device__ __forceinline__ void
 k_cons_body(ProbDev p, int64_t k0, int64_t k1, const TU* __restrict__ U, const TV* __restrict__ V, int ld, int L, int Q,
-       double* y, double* __restrict__ out, double* zk, dfloat* ydf, const Ctrl* ctrl, double rho_arg,
+       double* y, void* __restrict__ out, void* zk, dfloat* ydf, const Ctrl* ctrl, double rho_arg,
        double* __restrict__ part, VGrid vg) {
     constexpr int NQ = MODE == CONS_LS ? PL_N : PC_N;
     using PA = part_t<TU, TV>;
@@ -427,104 +469,145 @@ k_cons_body(ProbDev p, int64_t k0, int64_t k1, const TU* __restrict__ U, const T
     using AU = wide_t<TU, TU>;
     using AW = wide_t<TU, TV>;
     using AV = wide_t<TV, TV>;
+    // per-constraint scalars: double on the all-FP64 path, double-float otherwise
+    // (GB300's FP64 rate is ~1/64 of FP32; conversions run on the FP64 pipe too).
+    // z = A(RR^T)_k - b_k, y~ and the cached z use the same type (zk, out: CS arrays).
+    using CS = std::conditional_t<std::is_same_v<PA, double>, double, dfloat>;
+    const CS rho_c = CS(rho);
+    CS* zkc = static_cast<CS*>(zk);
+    // what each mode gathers besides u_i, u_j
+    constexpr bool NEED_V = MODE == CONS_EVAL || MODE == CONS_LS;
+    // constraints in flight per lane group: the index, coefficient and multiplier
+    // loads and all row gathers of UC constraints are issued before any dot product
+    constexpr int UC = CPL == 1 ? (MODE == CONS_LS || MODE == CONS_EVAL ? 2 : 3) : 1;
     RowLoop rl(L, vg);
     const int64_t cnt = k1 - k0;
-    for (int64_t base = rl.first; base < cnt; base += rl.stride) {
-        const int64_t t = k0 + base + rl.gw;
-        const bool act = t < k1;
-        int i = 0, j = 0;
-        if (act) {
-            i = __ldg(p.k_row + t);
-            j = __ldg(p.k_col + t);
+    const int64_t step = (int64_t)rl.rows_per_warp;
+    for (int64_t base = rl.first * UC; base < cnt; base += rl.stride * UC) {
+        int64_t t[UC];
+        bool act[UC], diag[UC];
+        int i[UC], j[UC], kid[UC];
+        CS ak[UC], yk[UC], zb[UC];          // coefficient, y_k, and z_k (cached) or b_k
+        Unit<TU> ui[UC][CPL], uj[UC][CPL];
+        Unit<TV> vi[UC][CPL], vj[UC][CPL];
+#pragma unroll
+        for (int u = 0; u < UC; ++u) {
+            t[u] = k0 + base + u * step + rl.gw;
+            act[u] = t[u] < k1;
+            i[u] = act[u] ? __ldg(p.k_row + t[u]) : 0;
+            j[u] = act[u] ? __ldg(p.k_col + t[u]) : 0;
+            if constexpr (MODE == CONS_EVAL || std::is_same_v<CS, double>)
+                ak[u] = act[u] ? CS(__ldg(p.k_a + t[u])) : CS(0.0);
+            else
+                ak[u] = act[u] ? (p.k_adf ? ld_scalar<CS>(p.k_a, p.k_adf, t[u]) : CS(__ldg(p.k_a + t[u]))) : CS(0.0);
+            kid[u] = act[u] ? __ldg(p.k_id + t[u]) : 0;
+            diag[u] = i[u] == j[u];
         }
-        const bool diag = (i == j);
-        // dots of the gathered rows; partial per lane, then group sums
-        AU s_uu = AU(0);          // u_i.u_j (EVAL with U==V, and R-only modes)
-        AW s_uv = AW(0), s_vu = AW(0);   // u_i.v_j, u_j.v_i
-        AV s_vv = AV(0);          // v_i.v_j
-        if (act) {
-            Unit<TU> ui[CPL], uj[CPL];
-            load_row<TU, CPL>(ui, U, i, ld, L, Q, rl.lig);
-            if (!diag) load_row<TU, CPL>(uj, U, j, ld, L, Q, rl.lig);
-            if constexpr (MODE == CONS_EVAL) {
-                if (same || diag) {
-                    if (same) {
-                        s_uu = diag ? dot_units<AU>(ui, ui) : dot_units<AU>(ui, uj);
-                    } else {
-                        Unit<TV> vi[CPL];
-                        load_row<TV, CPL>(vi, V, i, ld, L, Q, rl.lig);
-                        s_uv = dot_units<AW>(ui, vi);
-                    }
-                } else {
-                    Unit<TV> vi[CPL], vj[CPL];
-                    load_row<TV, CPL>(vi, V, i, ld, L, Q, rl.lig);
-                    load_row<TV, CPL>(vj, V, j, ld, L, Q, rl.lig);
-                    s_uv = dot_units<AW>(ui, vj);
-                    s_vu = dot_units<AW>(uj, vi);
+#pragma unroll
+        for (int u = 0; u < UC; ++u) {
+            yk[u] = CS(0.0);
+            zb[u] = CS(0.0);
+            if (!act[u]) continue;
+            if constexpr (MODE != CONS_EVAL) {
+                if constexpr (MODE != CONS_ZZ) {
+                    if constexpr (std::is_same_v<CS, double>) yk[u] = y[kid[u]];
+                    else yk[u] = ydf ? ld_scalar<CS>(y, ydf, kid[u]) : CS(y[kid[u]]);
                 }
-            } else {
-                if (MODE != CONS_LS || zk == nullptr)
-                    s_uu = diag ? dot_units<AU>(ui, ui) : dot_units<AU>(ui, uj);
-                if constexpr (MODE == CONS_LS) {
-                    Unit<TV> di[CPL], dj[CPL];
-                    load_row<TV, CPL>(di, V, i, ld, L, Q, rl.lig);
-                    if (diag) {
-                        s_uv = dot_units<AW>(ui, di);
-                        s_vu = s_uv;
-                        s_vv = dot_units<AV>(di, di);
-                    } else {
-                        load_row<TV, CPL>(dj, V, j, ld, L, Q, rl.lig);
-                        s_uv = dot_units<AW>(ui, dj);
-                        s_vu = dot_units<AW>(di, uj);
-                        s_vv = dot_units<AV>(di, dj);
-                    }
+                if (MODE == CONS_LS && zk != nullptr) zb[u] = zkc[kid[u]];
+                else if constexpr (std::is_same_v<CS, double>) zb[u] = __ldg(p.b + kid[u]);
+                else zb[u] = p.b_df ? ld_scalar<CS>(p.b, p.b_df, kid[u]) : CS(__ldg(p.b + kid[u]));
+            }
+            load_row<TU, CPL>(ui[u], U, i[u], ld, L, Q, rl.lig);
+            if (!diag[u]) load_row<TU, CPL>(uj[u], U, j[u], ld, L, Q, rl.lig);
+            if constexpr (NEED_V) {
+                if (!(MODE == CONS_EVAL && same)) {
+                    load_row<TV, CPL>(vi[u], V, i[u], ld, L, Q, rl.lig);
+                    if (!diag[u]) load_row<TV, CPL>(vj[u], V, j[u], ld, L, Q, rl.lig);
                 }
             }
         }
-        s_uu = group_sum(s_uu, L);
-        if constexpr (MODE == CONS_EVAL || MODE == CONS_LS) {
-            s_uv = group_sum(s_uv, L);
-            s_vu = group_sum(s_vu, L);
-            s_vv = group_sum(s_vv, L);
-        }
-        if (act && rl.lig == 0) {
-            const double a = __ldg(p.k_a + t);
-            const int kid = __ldg(p.k_id + t);
-            const double f = diag ? 1.0 : 2.0;
-            if constexpr (MODE == CONS_EVAL) {
-                double val;
-                if (same) val = f * a * double(s_uu);
-                else if (diag) val = a * double(s_uv);
-                else val = a * (double(s_uv) + double(s_vu));
-                out[kid] = val;
-            } else {
-                const double z = (MODE == CONS_LS && zk != nullptr) ? zk[kid]
-                                                                    : f * a * double(s_uu) - __ldg(p.b + kid);
-                if constexpr (MODE == CONS_LS) {
-                    const double yt = y[kid] - rho * z;
-                    const double q1 = f * a * (double(s_uv) + double(s_vu));
-                    const double q2 = f * a * double(s_vv);
-                    accq[PL_YQ1] += PA(yt * q1);
-                    accq[PL_YQ2] += PA(yt * q2);
-                    accq[PL_Q1Q1] += PA(q1 * q1);
-                    accq[PL_Q1Q2] += PA(q1 * q2);
-                    accq[PL_Q2Q2] += PA(q2 * q2);
+#pragma unroll
+        for (int u = 0; u < UC; ++u) {
+            // dots of the gathered rows; partial per lane, then group sums
+            AU s_uu = AU(0);                  // u_i.u_j (EVAL with U==V, and R-only modes)
+            AW s_uv = AW(0), s_vu = AW(0);    // u_i.v_j, u_j.v_i
+            AV s_vv = AV(0);                  // v_i.v_j
+            if (act[u]) {
+                if constexpr (MODE == CONS_EVAL) {
+                    if (same) {
+                        s_uu = diag[u] ? dot_units<AU>(ui[u], ui[u]) : dot_units<AU>(ui[u], uj[u]);
+                    } else if (diag[u]) {
+                        s_uv = dot_units<AW>(ui[u], vi[u]);
+                    } else {
+                        s_uv = dot_units<AW>(ui[u], vj[u]);
+                        s_vu = dot_units<AW>(uj[u], vi[u]);
+                    }
                 } else {
-                    accq[PC_ZZ] += PA(z * z);
-                    if constexpr (MODE == CONS_YTIL) {
-                        out[kid] = y[kid] - rho * z;
-                        if (zk != nullptr) zk[kid] = z;
-                    } else if constexpr (MODE == CONS_YUPD) {
-                        const double yn = y[kid] - rho * z;
-                        y[kid] = yn;
-                        if (ydf != nullptr) ydf[kid] = dfloat(yn);
-                        accq[PC_BY] += PA(__ldg(p.b + kid) * yn);
+                    if (MODE != CONS_LS || zk == nullptr)
+                        s_uu = diag[u] ? dot_units<AU>(ui[u], ui[u]) : dot_units<AU>(ui[u], uj[u]);
+                    if constexpr (MODE == CONS_LS) {
+                        if (diag[u]) {
+                            s_uv = dot_units<AW>(ui[u], vi[u]);
+                            s_vu = s_uv;
+                            s_vv = dot_units<AV>(vi[u], vi[u]);
+                        } else {
+                            s_uv = dot_units<AW>(ui[u], vj[u]);
+                            s_vu = dot_units<AW>(vi[u], uj[u]);
+                            s_vv = dot_units<AV>(vi[u], vj[u]);
+                        }
+                    }
+                }
+            }
+            s_uu = group_sum(s_uu, L);
+            if constexpr (MODE == CONS_EVAL || MODE == CONS_LS) {
+                s_uv = group_sum(s_uv, L);
+                s_vu = group_sum(s_vu, L);
+                s_vv = group_sum(s_vv, L);
+            }
+            if (act[u] && rl.lig == 0) {
+                const int k = kid[u];
+                if constexpr (MODE == CONS_EVAL) {
+                    const double a = double(ak[u]);
+                    const double f = diag[u] ? 1.0 : 2.0;
+                    double val;
+                    if (same) val = f * a * double(s_uu);
+                    else if (diag[u]) val = a * double(s_uv);
+                    else val = a * (double(s_uv) + double(s_vu));
+                    static_cast<double*>(out)[k] = val;
+                } else {
+                    const CS fa = diag[u] ? ak[u] : CS(2.0f) * ak[u];
+                    const CS z = (MODE == CONS_LS && zk != nullptr) ? zb[u] : fa * CS(s_uu) - zb[u];
+                    if constexpr (MODE == CONS_LS) {
+                        const CS yt = yk[u] - rho_c * z;
+                        const CS q1 = fa * (CS(s_uv) + CS(s_vu));
+                        const CS q2 = fa * CS(s_vv);
+                        accq[PL_YQ1] += PA(yt * q1);
+                        accq[PL_YQ2] += PA(yt * q2);
+                        accq[PL_Q1Q1] += PA(q1 * q1);
+                        accq[PL_Q1Q2] += PA(q1 * q2);
+                        accq[PL_Q2Q2] += PA(q2 * q2);
+                    } else {
+                        accq[PC_ZZ] += PA(z * z);
+                        if constexpr (MODE == CONS_YTIL) {
+                            static_cast<CS*>(out)[k] = yk[u] - rho_c * z;
+                            if (zk != nullptr) zkc[k] = z;
+                        } else if constexpr (MODE == CONS_YUPD) {
+                            const CS yn = yk[u] - rho_c * z;
+                            y[k] = double(yn);
+                            if constexpr (std::is_same_v<CS, dfloat>) {
+                                if (ydf != nullptr) ydf[k] = yn;
+                            } else {
+                                if (ydf != nullptr) ydf[k] = dfloat(yn);
+                            }
+                            // b_k: zb holds it (z is recomputed in this mode)
+                            accq[PC_BY] += PA(zb[u] * yn);
+                        }
                     }
                 }
             }
         }
     }
-    if constexpr (MODE != CONS_EVAL) block_partials<NQ>(accq, part, vg.bid);
+    if constexpr (MODE != CONS_EVAL) block_partials<NQ>(accq, part, vg.pslot);
 }
 
 // ================================================================== direction
@@ -579,7 +662,7 @@ k_dir_body(int64_t nunits, const TD* __restrict__ G, TD* __restrict__ D, const T
         accq[PD_GD] += gd;
         accq[PD_DD] += dd;
     }
-    block_partials<PD_N>(accq, part, vg.bid);
+    block_partials<PD_N>(accq, part, vg.pslot);
 }
 
 // ================================================================== step (flat)
@@ -756,7 +839,7 @@ k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __re
             accq[PU_GG] += dot_units<AD>(g, g);
         }
     }
-    block_partials<PU_N>(accq, part, vg.bid);
+    block_partials<PU_N>(accq, part, vg.pslot);
 }
 
 // ================================================================== kernels
@@ -774,18 +857,18 @@ k_spmm_c(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int 
     k_spmm_c_body<TX, TO, TR, CPL, EPI>(p, X, out, ld, L, Q, v, write_out, R, y, zrow_v, ydf, ctrl, rho_arg, part, hw_grid());
 }
 
-template <typename TX, typename TO, int CPL>
+template <typename TX, typename TO, int CPL, bool VDF>
 __global__ void __launch_bounds__(kThreads)
 k_spmm_a(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int L, int Q,
-         const double* __restrict__ v, double alpha, int accumulate, const Ctrl* gate, int ph) {
+         const void* __restrict__ v, double alpha, int accumulate, const Ctrl* gate, int ph) {
     if (gated_off(gate, ph)) return;
-    k_spmm_a_body<TX, TO, CPL>(p, X, out, ld, L, Q, v, alpha, accumulate, hw_grid());
+    k_spmm_a_body<TX, TO, CPL, VDF>(p, X, out, ld, L, Q, v, alpha, accumulate, hw_grid());
 }
 
 template <typename TU, typename TV, int CPL, int MODE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 k_cons(ProbDev p, int64_t k0, int64_t k1, const TU* __restrict__ U, const TV* __restrict__ V, int ld, int L, int Q,
-       double* y, double* __restrict__ out, double* zk, dfloat* ydf, const Ctrl* ctrl, double rho_arg,
+       double* y, void* __restrict__ out, void* zk, dfloat* ydf, const Ctrl* ctrl, double rho_arg,
        double* __restrict__ part, const Ctrl* gate, int ph) {
     if (gated_off(gate, ph)) return;
     k_cons_body<TU, TV, CPL, MODE>(p, k0, k1, U, V, ld, L, Q, y, out, zk, ydf, ctrl, rho_arg, part, hw_grid());

@@ -40,8 +40,17 @@ template <typename TX, typename TO>
 void launch_spmm_a(const SpmmAArgs& a) {
     const TX* X = static_cast<const TX*>(a.X);
     TO* out = static_cast<TO*>(a.out);
+    if constexpr (!std::is_same_v<arith_t<TO>, double>) {
+        if (a.v_df) {
+            LORADS_CPL_SWITCH(a.sh.CPL, {
+                k_spmm_a<TX, TO, CPL, true><<<a.blocks, kThreads, 0, a.stream>>>(
+                    a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.alpha, a.accumulate, a.gate, a.ph);
+            })
+            return;
+        }
+    }
     LORADS_CPL_SWITCH(a.sh.CPL, {
-        k_spmm_a<TX, TO, CPL><<<a.blocks, kThreads, 0, a.stream>>>(
+        k_spmm_a<TX, TO, CPL, false><<<a.blocks, kThreads, 0, a.stream>>>(
             a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.alpha, a.accumulate, a.gate, a.ph);
     })
 }

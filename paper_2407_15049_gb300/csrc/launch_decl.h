@@ -18,18 +18,21 @@ struct SpmmCArgs {
     int blocks; const Ctrl* gate; int ph; cudaStream_t stream;
 };
 
+// v: double[m], or double-float[m] when v_df (weights then formed without FP64)
 struct SpmmAArgs {
     const ProbDev& p;
     const void* X; void* out; int ld; Shape sh;
-    const double* v; double alpha; int accumulate;
-    int blocks; const Ctrl* gate; int ph; cudaStream_t stream;
+    const void* v; double alpha; int accumulate;
+    int blocks; const Ctrl* gate; int ph; cudaStream_t stream; int v_df;
 };
 
+// out: double[m] (CONS_EVAL) or y~ in the pass's scalar type (CONS_YTIL: double on
+// the FP64 path, double-float otherwise); zk: cached z in that same type
 struct ConsArgs {
     const ProbDev& p;
     int mode; int64_t k0, k1;
     const void* U; const void* V; int ld; Shape sh;
-    double* y; double* out; double* zk; dfloat* ydf; const Ctrl* ctrl; double rho; double* part;
+    double* y; void* out; void* zk; dfloat* ydf; const Ctrl* ctrl; double rho; double* part;
     int blocks; const Ctrl* gate; int ph; cudaStream_t stream;
 };
 

@@ -185,6 +185,14 @@ lorads_status build_host_prob(HostProb* hp, std::string* err, int64_t n, const i
     hp->k_col = std::move(k_col);
     hp->k_a = std::move(k_a);
     hp->k_id = std::move(k_id);
+    auto split = [](double v) {
+        const float h = (float)v;
+        return dfloat(h, (float)(v - (double)h));
+    };
+    hp->k_adf.resize(hp->k_a.size());
+    for (size_t q = 0; q < hp->k_a.size(); ++q) hp->k_adf[q] = split(hp->k_a[q]);
+    hp->a_adf.resize(hp->a_a.size());
+    for (size_t q = 0; q < hp->a_a.size(); ++q) hp->a_adf[q] = split(hp->a_a[q]);
     return LORADS_OK;
 }
 

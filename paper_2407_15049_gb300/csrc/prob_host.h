@@ -35,6 +35,8 @@ struct HostProb {
     // constraint list: diagonal constraints by row, then off-diagonal by (row, col)
     std::vector<int32_t> k_row, k_col, k_id;
     std::vector<double> k_a;
+    // double-float mirrors of k_a and a_a
+    std::vector<dfloat> k_adf, a_adf;
 };
 
 // Validates the inputs of lorads_create and fills `hp`.  On failure returns the

@@ -138,13 +138,59 @@ def test_batch_shapes_and_repeats():
         L.lorads_batch_set_shape(b, 2, 2, 0)
         r3, st3 = L.lorads_batch_solve(b, len(insts))
         s3 = [L.lorads_batch_get_solution(b, i, t.n, t.m)[0] for i, t in enumerate(insts)]
+        L.lorads_batch_set_shape(b, 1, 4, 1, threads=512)
+        r4, st4 = L.lorads_batch_solve(b, len(insts))
+        s4 = [L.lorads_batch_get_solution(b, i, t.n, t.m)[0] for i, t in enumerate(insts)]
     finally:
         L.lorads_batch_destroy(b)
-    assert st3["shape"] == {"ctas_per_sm": 2, "rows_per_warp": 2, "order": 0}
+    assert st3["shape"] == {"ctas_per_sm": 2, "rows_per_warp": 2, "order": 0, "threads": 256, "cluster": 1,
+                            "team_count": 0}
+    assert st4["shape"] == {"ctas_per_sm": 1, "rows_per_warp": 4, "order": 1, "threads": 512, "cluster": 1,
+                            "team_count": 0}
     for i in range(len(insts)):
         assert np.array_equal(s1[i], s2[i])
         assert r1[i]["primal_obj"] == r2[i]["primal_obj"]
         assert np.max(np.abs(s3[i] - s1[i])) <= 1e-9 * np.abs(s1[i]).max()
+        assert np.max(np.abs(s4[i] - s1[i])) <= 1e-9 * np.abs(s1[i]).max()
+
+
+@pytest.mark.parametrize("cluster,team_count", [(2, 6), (4, 3), (8, 2)])
+def test_batch_clusters_match_one_block_per_instance(cluster, team_count):
+    """Instances solved by a thread-block cluster (rows split over its blocks, sums
+    reduced through distributed shared memory) follow the one-block trajectory."""
+    insts, R0 = _small_batch()
+    caps = dict(max_outer=2, max_inner=20, tol=1e-300)
+    b = L.lorads_batch_create(insts, L.default_params(**caps), R0=R0)
+    try:
+        L.lorads_batch_set_shape(b, 1, 8, 1)
+        r1, _ = L.lorads_batch_solve(b, len(insts))
+        s1 = [L.lorads_batch_get_solution(b, i, t.n, t.m) for i, t in enumerate(insts)]
+        L.lorads_batch_set_shape(b, 1, 8, 1, threads=256, cluster=cluster, team_count=team_count)
+        r2, st2 = L.lorads_batch_solve(b, len(insts))
+        s2 = [L.lorads_batch_get_solution(b, i, t.n, t.m) for i, t in enumerate(insts)]
+        r3, _ = L.lorads_batch_solve(b, len(insts))
+        s3 = [L.lorads_batch_get_solution(b, i, t.n, t.m) for i, t in enumerate(insts)]
+    finally:
+        L.lorads_batch_destroy(b)
+    assert st2["shape"]["cluster"] == cluster and st2["grid"] % cluster == 0
+    for i in range(len(insts)):
+        assert r2[i]["inner_iters"] == r1[i]["inner_iters"], i
+        assert np.max(np.abs(s2[i][0] - s1[i][0])) <= 1e-9 * np.abs(s1[i][0]).max(), i
+        assert np.max(np.abs(s2[i][1] - s1[i][1])) <= 1e-8 * (1 + np.abs(s1[i][1]).max()), i
+        assert np.array_equal(s3[i][0], s2[i][0])               # repeatable
+
+
+def test_batch_cluster_rank_growth_matches_oracle():
+    insts = [W.maxcut_instance(40, W.er_graph(40, 120, 5, "pm1")),
+             W.maxcut_instance(50, W.er_graph(50, 150, 7, "unit"))]
+    R0 = [W.initial_factor(t, 4, 2 + i) for i, t in enumerate(insts)]
+    caps = dict(max_outer=3, max_inner=3, tol=1e-300, rank_update_threshold=1, seed=11)
+    res, _, sols = _batch_run(insts, R0, shape=(1, 8, 1, 256, 4, 2), **caps)
+    for i, t in enumerate(insts):
+        ref = O.solve(O.Problem(t), R0[i], O.Params(**caps))
+        R, _ = sols[i]
+        assert R.shape[1] == ref["R"].shape[1]
+        assert np.max(np.abs(R - ref["R"])) <= 1e-9 * np.abs(ref["R"]).max(), i
 
 
 def test_batch_tune_then_solve():
@@ -153,6 +199,7 @@ def test_batch_tune_then_solve():
     try:
         shape = L.lorads_batch_tune(b, 10)
         assert shape["rows_per_warp"] in (1, 2, 4, 8) and shape["order"] in (0, 1)
+        assert shape["threads"] in (256, 512) and shape["cluster"] in (1, 2, 4, 8)
         assert 1 <= shape["ctas_per_sm"] <= 4
         res, stats = L.lorads_batch_solve(b, len(insts))
     finally:
