@@ -37,6 +37,8 @@ METRIC = "time to rel. KKT 1e-5 (MaxCut n=1e7); SpMM+A(RRᵀ) HBM GB/s vs 8 TB/s
 WORKLOADS = {
     "maxcut_er_1e7": dict(n=10_000_000, edges=20_000_000, weights="pm1", r=24, seed=0,
                           desc="MaxCut SDP, Erdos-Renyi n=1e7, M=2e7 edges (avg degree 4), w in {-1,+1}, r=24"),
+    "maxcut_er_1e6": dict(n=1_000_000, edges=2_000_000, weights="pm1", r=20, seed=0,
+                          desc="MaxCut SDP, Erdos-Renyi n=1e6, M=2e6 edges (avg degree 4), w in {-1,+1}, r=20"),
     "maxcut_er_1e5": dict(n=100_000, edges=200_000, weights="pm1", r=17, seed=0,
                           desc="MaxCut SDP, Erdos-Renyi n=1e5, M=2e5 edges (avg degree 4), w in {-1,+1}, r=17"),
 }
@@ -49,7 +51,7 @@ BATCH_WORKLOADS = {
 BATCH_METRIC = "instances/s to rel. KKT 1e-5, one persistent launch (512 mixed MaxCut / matrix-completion SDPs)"
 # iterations to tolerance used to scale the reference arm's per-iteration time when no
 # GPU run of the same invocation provides it (measured on the GPU solve of maxcut_er_1e7)
-DEFAULT_ITERS_TO_TOL = {"maxcut_er_1e7": 6660, "maxcut_er_1e5": 5000}
+DEFAULT_ITERS_TO_TOL = {"maxcut_er_1e7": 6660, "maxcut_er_1e6": 6900, "maxcut_er_1e5": 5000}
 
 
 def _args():
@@ -67,6 +69,13 @@ def _args():
     ap.add_argument("--iters-to-tol", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--warm-start", choices=["none", "gnn"], default="none",
+                    help="starting factor: seeded random rows, or the learned network (trained before timing "
+                         "on solved ER graphs; its prediction is inside the timed region)")
+    ap.add_argument("--train-graphs", type=int, default=96)
+    ap.add_argument("--train-epochs", type=int, default=40)
+    ap.add_argument("--compare-cold", action="store_true",
+                    help="with --warm-start gnn: also time one solve from the random start")
     ap.add_argument("--instance-time-limit", type=float, default=60.0,
                     help="batched solve: per-instance time limit (s); instances past it count as unsolved")
     ap.add_argument("--tune-iters", type=int, default=20, help="batched solve: iterations per autotuner probe")
@@ -233,7 +242,8 @@ def _config(args):
     cfg = WORKLOADS[args.workload]
     return {"workload": args.workload, "description": cfg["desc"], "n": cfg["n"], "m": cfg["n"],
             "nnz_C": cfg["n"] + 2 * cfg["edges"], "rank": cfg["r"], "solver_precision": args.prec,
-            "start": "cold (seeded unit-norm Gaussian rows)", "tolerance": 1e-5,
+            "start": ("learned warm start (network trained before timing; prediction timed)"
+                      if args.warm_start == "gnn" else "cold (seeded unit-norm Gaussian rows)"), "tolerance": 1e-5,
             "l2_policy": "inputs larger than L2 (R alone is 1.9 GB at FP64)",
             "parallelism": f"replicas x{args.gpus}"}
 
@@ -272,18 +282,47 @@ def run_native(args):
         ctx = L.lorads_create(inst, params, stream=stream.cuda_stream)
         create_s = time.perf_counter() - t
         R0_dev = torch.as_tensor(R0, device="cuda")
+        warm = None
+        if args.warm_start == "gnn":
+            import math as _m
+            import numpy as _np
+            import workloads as W
+            from paper_2407_15049_gb300 import warmstart as WS
+            rng = _np.random.default_rng(12345)
+            train = []
+            for k in range(args.train_graphs):
+                nk = int(round(_m.exp(rng.uniform(_m.log(1000), _m.log(30000)))))
+                train.append(W.maxcut_instance(nk, W.er_graph(nk, 2 * nk, 5000 + k, "pm1")))
+            net, warm = WS.train_on_solved(train, cfg["r"], epochs=args.train_epochs)
+            graph = WS.device_graph(inst)
+            ldw = N.padded_ld(cfg["r"])
+
+            def start():
+                return net.predict(graph, feature_seed=0, ld=ldw)[:, :cfg["r"]].contiguous()
+        else:
+            def start():
+                return R0_dev
         results = []
         for _ in range(args.warmup):
-            results.append(L.lorads_solve(ctx, R0_dev, on_device=True))
+            results.append(L.lorads_solve(ctx, start(), on_device=True))
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
             barrier()
             ev0.record(stream)
-            timed = [L.lorads_solve(ctx, R0_dev, on_device=True) for _ in range(args.steps)]
+            timed = [L.lorads_solve(ctx, start(), on_device=True) for _ in range(args.steps)]
             ev1.record(stream)
             barrier()
         elapsed = ev0.elapsed_time(ev1) / 1e3
+        cold = None
+        if warm is not None and args.compare_cold:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc = L.lorads_solve(ctx, R0_dev, on_device=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            cold = {"seconds": e0.elapsed_time(e1) / 1e3, "inner_iters": rc["inner_iters"],
+                    "outer_iters": rc["outer_iters"], "primal_obj": rc["primal_obj"], "status": rc["status_name"]}
         last = timed[-1]
         launches = sum(r["kernel_launches"] for r in timed)
         # per-kernel durations: a host-stepped run of the same solve (first profile_iters
@@ -309,7 +348,13 @@ def run_native(args):
             barrier()
             t = time.perf_counter()
             c2 = L.lorads_create(inst, params, stream=stream.cuda_stream)
-            rr = L.lorads_solve(c2, R0_pinned)
+            if warm is not None:
+                g2 = WS.device_graph(inst)
+                rr = L.lorads_solve(c2, net.predict(g2, feature_seed=0, ld=ldw)[:, :cfg["r"]].contiguous(),
+                                    on_device=True)
+                del g2
+            else:
+                rr = L.lorads_solve(c2, R0_pinned)
             Rh, yh = L.lorads_get_solution(c2, inst.n, inst.m)
             L.lorads_destroy(c2)
             barrier()
@@ -382,6 +427,9 @@ def run_native(args):
         "solve": {k: last[k] for k in ("status_name", "primal_obj", "dual_obj", "err1", "err3", "rho", "rank",
                                        "outer_iters", "inner_iters", "seconds")},
         "sdp_value": -last["primal_obj"],
+        "warm_start": None if warm is None else {
+            "kind": "learned (3-layer message passing, bf16 activations)", "training": {
+                k: v for k, v in warm.items() if k != "batch_stats"}, "cold_start_same_run": cold},
         "kernels": kernels, "setup_s": {"generate": gen_s, "create": create_s},
     }
     print(json.dumps(line), flush=True)

@@ -723,7 +723,8 @@ lorads_status grow_rank(lorads_ctx* ctx, int prec, int outer_done) {
     SolverState& st = ctx->st;
     const int r_old = st.r;
     const int r_cap = (int)std::ceil(std::sqrt(2.0 * (double)ctx->m));
-    const int r_new = std::min((int)std::ceil(1.5 * r_old), r_cap);
+    // App. A.1's rule, also bounded by the widest row the kernels support
+    const int r_new = std::min(std::min((int)std::ceil(1.5 * r_old), r_cap), kMaxLd);
     if (r_new <= r_old) return LORADS_OK;
     cudaStream_t s = ctx->solve_stream;
     // ||R||_F^2

@@ -108,3 +108,37 @@ class WarmStart:
                 tot += self.train_step(g, t, lr, feature_seed)
             hist.append(tot / len(samples))
         return hist
+
+
+def train_on_solved(instances, r: int, epochs: int = 40, lr: float = 3e-3, prec: int = N.LORADS_MIXED,
+                    seed: int = 0, time_limit: float = 60.0):
+    """Solves the training instances with the batched solver (one launch, rank r) and
+    fits a network to the factors it returns.  Returns (network, info dict)."""
+    import time
+    import torch
+    t0 = time.perf_counter()
+    b = N.lorads_batch_create(instances, N.default_params(prec=prec, time_limit=time_limit),
+                              r0=[r] * len(instances))
+    try:
+        res, stats = N.lorads_batch_solve(b, len(instances))
+        samples = []
+        for i, inst in enumerate(instances):
+            if res[i]["status"] != 0:
+                continue
+            R, _ = N.lorads_batch_get_solution(b, i, inst.n, inst.m)
+            dg = device_graph(inst)
+            Rd = torch.zeros((inst.n, N.padded_ld(R.shape[1])), dtype=torch.float64, device=dg["rowptr"].device)
+            Rd[:, :R.shape[1]] = torch.as_tensor(R, device=Rd.device)
+            samples.append((dg, edge_targets(dg, Rd, R.shape[1])))
+    finally:
+        N.lorads_batch_destroy(b)
+    t1 = time.perf_counter()
+    net = WarmStart(r, act="bf16", seed=seed, stream=torch.cuda.current_stream().cuda_stream)
+    hist = []
+    for ep in range(epochs):
+        hist += net.fit(samples, epochs=1, lr=lr if ep < 0.7 * epochs else lr / 3, seed=seed + ep)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return net, {"graphs": len(instances), "solved": len(samples), "solve_s": t1 - t0, "train_s": t2 - t1,
+                 "epochs": epochs, "loss_first": hist[0] if hist else None, "loss_last": hist[-1] if hist else None,
+                 "batch_stats": stats}
