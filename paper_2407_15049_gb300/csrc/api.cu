@@ -235,7 +235,7 @@ extern "C" void lorads_default_params(lorads_params* p) {
     p->lbfgs_scaling = 1;
     p->rho_policy = 2;
     p->inner_scale = 2;
-    p->kernel_variant = 0;
+    p->kernel_variant = 2;
 }
 
 extern "C" const char* lorads_create_error(void) { return g_create_error.c_str(); }
@@ -519,7 +519,7 @@ struct Driver {
 
     void refresh() {
         nb_rows = row_blocks(c, c->n, st.sh.L);
-        const int tb = (c->m_off == 0 && c->prm.kernel_variant == 1)
+        const int tb = (c->m_off == 0 && (c->prm.kernel_variant & 1))
                            ? tma_update_blocks<TR, TD>(c->n, st.ld, c->num_sms) : 0;
         tma = tb > 0;
         nb_upd = tma ? tb : nb_rows;
@@ -612,7 +612,8 @@ struct Driver {
             timed(FAM_SPMM_A, [&] { launch_spmm_a<TR, TD>(w); });
         }
         UpdateArgs u{p(), c->m_off == 0, true, st.R, st.CR, st.D, st.CD, st.G, c->m_off ? st.W : nullptr, st.hist,
-                     st.slot_stride, st.ld, st.sh, st.y, st.ydf, st.zrow, c->ctrl, part_of(c, PART_UPD), nb_upd, c->ctrl, PH_STEP, s};
+                     st.slot_stride, st.ld, st.sh, st.y, st.ydf, st.zrow, c->ctrl, part_of(c, PART_UPD), nb_upd, c->ctrl, PH_STEP, s,
+                     (c->prm.kernel_variant & 4) ? 2 : ((c->prm.kernel_variant & 2) ? 1 : 0)};
         if (tma) timed(FAM_UPDATE, [&] { launch_update_tma<TR, TD>(u, c->ctrl); });
         else timed(FAM_UPDATE, [&] { launch_update<TR, TD>(u); });
         timed(FAM_HIST, [&] {
@@ -901,7 +902,7 @@ lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0,
     if ((s = check_launch(ctx, "solve init"))) return s;
     if (!prepare_update_tma<TR, TD>(st.ld)) {
         cudaGetLastError();
-        ctx->prm.kernel_variant = 0;            // fall back to the register-staged row update
+        ctx->prm.kernel_variant &= ~1;          // fall back to the register-staged row update
     }
     if (P.verbose >= 2) return run_profiled<TR, TD>(ctx, prec, t0, res);
     if ((s = capture<TR, TD>(ctx))) return s;

@@ -901,4 +901,18 @@ k_update(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restric
     k_update_body<TR, TD, CPL, STEP, HIST>(p, R, CR, D, CD, G, W, hist, slot_stride, ld, L, Q, y, ydf, zrow_v, ctrl, part, hw_grid());
 }
 
+// The step update with EXTRA more resident blocks per SM (fewer registers per
+// thread, some spilled to L1): more rows in flight for the latency-bound pass.
+template <typename TR, typename TD, int CPL, int EXTRA>
+__global__ void __launch_bounds__(kThreads, (update_min_blocks<TR, TD, CPL>() + EXTRA))
+k_update_step_occ(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restrict__ D,
+                  const TD* __restrict__ CD, TD* __restrict__ G, const TD* __restrict__ W,
+                  TD* __restrict__ hist, int64_t slot_stride, int ld, int L, int Q,
+                  const double* __restrict__ y, const dfloat* __restrict__ ydf, void* __restrict__ zrow_v,
+                  const Ctrl* ctrl, double* __restrict__ part, const Ctrl* gate, int ph) {
+    if (gated_off(gate, ph)) return;
+    k_update_body<TR, TD, CPL, true, true>(p, R, CR, D, CD, G, W, hist, slot_stride, ld, L, Q, y, ydf, zrow_v, ctrl,
+                                           part, hw_grid());
+}
+
 }  // namespace lorads

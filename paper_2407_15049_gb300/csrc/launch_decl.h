@@ -53,6 +53,7 @@ struct UpdateArgs {
     int64_t slot_stride; int ld; Shape sh; const double* y; const dfloat* ydf; void* zrow; const Ctrl* ctrl;
     double* part;
     int blocks; const Ctrl* gate; int ph; cudaStream_t stream;
+    int extra_blocks;   // step update: 0, or the variant with 1 or 2 more resident blocks per SM
 };
 
 template <typename TX, typename TO, typename TR> void launch_spmm_c(const SpmmCArgs& a);
