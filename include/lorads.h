@@ -71,7 +71,10 @@ typedef enum {
     LORADS_FP32 = 1,
     LORADS_BF16 = 2,
     LORADS_MIXED = 3,  /* solve only: double-float R and C*R, FP32 direction/gradient/history */
-    LORADS_DF64 = 4    /* solve only: double-float (hi, lo float pairs, ~48-bit) everywhere */
+    LORADS_DF64 = 4,   /* solve only: double-float (hi, lo float pairs, ~48-bit) everywhere */
+    LORADS_MIXED_BF16 = 5  /* solve only: MIXED with the search direction D stored in bf16 (rounded once
+                              when formed; the C D product, line search, step and stored pair all use
+                              the rounded direction) */
 } lorads_prec;
 
 /* Solver constants.  The paper fixes tol (Sec. 4.1), the time limit (Sec. 4.1)
@@ -90,7 +93,7 @@ typedef struct {
     double  infeas_decrease;   /* 0.25: rho grows unless err1 shrank by this factor */
     double  inner_rel;         /* 1.0: scale of the inner stopping threshold (see inner_scale) */
     double  inner_progress;    /* 0.1: inner_scale 2 also stops once ||G|| <= inner_progress ||G at loop start|| */
-    int32_t prec;              /* lorads_prec of the solve: FP64, MIXED, DF64 or FP32 */
+    int32_t prec;              /* lorads_prec of the solve: FP64, MIXED, DF64, FP32 or MIXED_BF16 */
     int32_t check_every;       /* iterations between host polls of the device status (16) */
     uint64_t seed;             /* seed of the rank-update columns (SplitMix64 + Box-Muller) */
     int32_t compute_err2;      /* 1: evaluate err2 (Lanczos on C - A*(y)) at the end */

@@ -13,7 +13,7 @@ from ._native import (  # noqa: F401
     lorads_batch_get_solution, lorads_batch_destroy, lorads_batch_phase_times,
     lorads_gnn_param_count, lorads_gnn_create, lorads_gnn_get_params, lorads_gnn_set_params, lorads_gnn_predict,
     lorads_gnn_edge_targets, lorads_gnn_train_step, lorads_gnn_destroy,
-    LORADS_FP64, LORADS_FP32, LORADS_BF16, LORADS_MIXED, LORADS_DF64, load, SIGNATURES,
+    LORADS_FP64, LORADS_FP32, LORADS_BF16, LORADS_MIXED, LORADS_DF64, LORADS_MIXED_BF16, load, SIGNATURES,
 )
 
 __all__ = [

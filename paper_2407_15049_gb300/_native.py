@@ -22,7 +22,7 @@ STATUS_NAMES = {
     4: "LORADS_ERR_CUDA", 5: "LORADS_ERR_NUMERIC", 6: "LORADS_ERR_MAXITER", 7: "LORADS_ERR_TIMEOUT",
     8: "LORADS_ERR_UNSUPPORTED",
 }
-LORADS_FP64, LORADS_FP32, LORADS_BF16, LORADS_MIXED, LORADS_DF64 = 0, 1, 2, 3, 4
+LORADS_FP64, LORADS_FP32, LORADS_BF16, LORADS_MIXED, LORADS_DF64, LORADS_MIXED_BF16 = 0, 1, 2, 3, 4, 5
 
 
 class LoradsError(RuntimeError):

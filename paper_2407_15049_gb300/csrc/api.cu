@@ -502,7 +502,7 @@ extern "C" lorads_status lorads_linesearch_coeffs(lorads_ctx* ctx, const void* R
 // ============================================================== solver
 namespace {
 
-template <typename TR, typename TD>
+template <typename TR, typename TD, typename TDIR = TD>
 struct Driver {
     // y~ of the off-diagonal constraints is double-float on every path but FP64
     static constexpr int kYtilDf = std::is_same<TR, double>::value ? 0 : 1;
@@ -519,7 +519,7 @@ struct Driver {
 
     void refresh() {
         nb_rows = row_blocks(c, c->n, st.sh.L);
-        const int tb = (c->m_off == 0 && (c->prm.kernel_variant & 1))
+        const int tb = (c->m_off == 0 && (c->prm.kernel_variant & 1) && std::is_same<TD, TDIR>::value)
                            ? tma_update_blocks<TR, TD>(c->n, st.ld, c->num_sms) : 0;
         tma = tb > 0;
         nb_upd = tma ? tb : nb_rows;
@@ -558,7 +558,7 @@ struct Driver {
         }
         UpdateArgs u{p(), false, false, st.R, st.CR, st.D, st.CD, st.G, c->m_off ? st.W : nullptr, st.hist,
                      st.slot_stride, st.ld, st.sh, st.y, st.ydf, st.zrow, c->ctrl, part_of(c, PART_UPD), nb_rows, c->ctrl, ph, s};
-        timed(FAM_GRAD, [&] { launch_update<TR, TD>(u); });
+        timed(FAM_GRAD, [&] { launch_update<TR, TD, TDIR>(u); });
         timed(FAM_HIST, [&] {
             ctrl_hist(s, c->ctrl, HIST_RESET, part_of(c, PART_UPD), nb_rows,
                       c->m_off ? part_of(c, PART_YTIL) : nullptr, nb_off);
@@ -589,14 +589,14 @@ struct Driver {
     void enqueue_inner() {
         DirArgs d{nunits, st.G, st.D, st.hist, st.slot_stride, c->ctrl, part_of(c, PART_DIR), nb_flat, c->ctrl,
                   PH_INNER, s};
-        timed(FAM_DIR, [&] { launch_dir<TD>(d); });
+        timed(FAM_DIR, [&] { launch_dir<TD, TDIR>(d); });
         SpmmCArgs ls{p(), st.D, st.CD, st.ld, st.sh, nullptr, 1, EPI_LS, st.R, st.y, st.zrow, st.ydf, c->ctrl, 0.0,
                      part_of(c, PART_LS), nb_rows, c->ctrl, PH_INNER, s};
-        timed(FAM_SPMM_LS, [&] { launch_spmm_c<TD, TD, TR>(ls); });
+        timed(FAM_SPMM_LS, [&] { launch_spmm_c<TDIR, TD, TR>(ls); });
         if (c->m_off) {
             ConsArgs cl{p(), CONS_LS, c->m_diag, c->m, st.R, st.D, st.ld, st.sh, st.y, nullptr, st.zk, st.ydf, c->ctrl, 0.0,
                         part_of(c, PART_CONS_LS), nb_off, c->ctrl, PH_INNER, s};
-            timed(FAM_CONS_LS, [&] { launch_cons<TR, TD>(cl); });
+            timed(FAM_CONS_LS, [&] { launch_cons<TR, TDIR>(cl); });
         }
         timed(FAM_ROOT, [&] {
             ctrl_root(s, c->ctrl, part_of(c, PART_DIR), nb_flat, part_of(c, PART_LS), nb_rows,
@@ -604,7 +604,7 @@ struct Driver {
         });
         if (c->m_off) {
             StepArgs sa{nunits, st.R, st.CR, st.D, st.CD, c->ctrl, nb_flat, c->ctrl, PH_STEP, s};
-            timed(FAM_STEP, [&] { launch_step<TR, TD>(sa); });
+            timed(FAM_STEP, [&] { launch_step<TR, TD, TDIR>(sa); });
             ConsArgs yt{p(), CONS_YTIL, c->m_diag, c->m, st.R, st.R, st.ld, st.sh, st.y, st.ytil, st.zk, st.ydf, c->ctrl, 0.0,
                         part_of(c, PART_YTIL), nb_off, c->ctrl, PH_STEP, s};
             timed(FAM_CONS_YTIL, [&] { launch_cons<TR, TR>(yt); });
@@ -615,7 +615,7 @@ struct Driver {
                      st.slot_stride, st.ld, st.sh, st.y, st.ydf, st.zrow, c->ctrl, part_of(c, PART_UPD), nb_upd, c->ctrl, PH_STEP, s,
                      (c->prm.kernel_variant & 4) ? 2 : ((c->prm.kernel_variant & 2) ? 1 : 0)};
         if (tma) timed(FAM_UPDATE, [&] { launch_update_tma<TR, TD>(u, c->ctrl); });
-        else timed(FAM_UPDATE, [&] { launch_update<TR, TD>(u); });
+        else timed(FAM_UPDATE, [&] { launch_update<TR, TD, TDIR>(u); });
         timed(FAM_HIST, [&] {
             ctrl_hist(s, c->ctrl, HIST_STEP, part_of(c, PART_UPD), nb_upd,
                       c->m_off ? part_of(c, PART_YTIL) : nullptr, nb_off);
@@ -640,7 +640,7 @@ struct Driver {
     }
 };
 
-template <typename TR, typename TD>
+template <typename TR, typename TD, typename TDIR = TD>
 lorads_status alloc_state(lorads_ctx* ctx, int prec, int r) {
     SolverState& st = ctx->st;
     const int ld = padded_ld(r);
@@ -664,7 +664,7 @@ lorads_status alloc_state(lorads_ctx* ctx, int prec, int r) {
     const int T = ctx->prm.lbfgs_mem;
     if ((s = dalloc(ctx, reinterpret_cast<TR**>(&st.R), nl))) return s;
     if ((s = dalloc(ctx, reinterpret_cast<TR**>(&st.CR), nl))) return s;
-    if ((s = dalloc(ctx, reinterpret_cast<TD**>(&st.D), nl))) return s;
+    if ((s = dalloc(ctx, reinterpret_cast<TDIR**>(&st.D), nl))) return s;
     if ((s = dalloc(ctx, reinterpret_cast<TD**>(&st.CD), nl))) return s;
     if ((s = dalloc(ctx, reinterpret_cast<TD**>(&st.G), nl))) return s;
     if ((s = dalloc(ctx, reinterpret_cast<TD**>(&st.hist), nl * 2 * T))) return s;
@@ -681,7 +681,7 @@ lorads_status alloc_state(lorads_ctx* ctx, int prec, int r) {
     if ((s = dalloc(ctx, &st.zk, ctx->m))) return s;
     CK(cudaMemset(st.R, 0, nl * sizeof(TR)));
     CK(cudaMemset(st.CR, 0, nl * sizeof(TR)));
-    CK(cudaMemset(st.D, 0, nl * sizeof(TD)));
+    CK(cudaMemset(st.D, 0, nl * sizeof(TDIR)));
     CK(cudaMemset(st.CD, 0, nl * sizeof(TD)));
     CK(cudaMemset(st.G, 0, nl * sizeof(TD)));
     CK(cudaMemset(st.hist, 0, nl * 2 * T * sizeof(TD)));
@@ -689,14 +689,14 @@ lorads_status alloc_state(lorads_ctx* ctx, int prec, int r) {
     return LORADS_OK;
 }
 
-template <typename TR, typename TD>
+template <typename TR, typename TD, typename TDIR = TD>
 lorads_status capture(lorads_ctx* ctx) {
     SolverState& st = ctx->st;
     if (st.exec) {
         cudaGraphExecDestroy(st.exec);
         st.exec = nullptr;
     }
-    Driver<TR, TD> drv(ctx);
+    Driver<TR, TD, TDIR> drv(ctx);
     cudaGraph_t g = nullptr;
     const int64_t before = ctx->launches;
     CK(cudaStreamBeginCapture(ctx->solve_stream, cudaStreamCaptureModeThreadLocal));
@@ -719,7 +719,7 @@ lorads_status capture(lorads_ctx* ctx) {
 }
 
 // Grows the rank (App. A.1): new columns N(0, (1e-3 ||R||_F / sqrt(n r))^2).
-template <typename TR, typename TD>
+template <typename TR, typename TD, typename TDIR = TD>
 lorads_status grow_rank(lorads_ctx* ctx, int prec, int outer_done) {
     SolverState& st = ctx->st;
     const int r_old = st.r;
@@ -747,7 +747,7 @@ lorads_status grow_rank(lorads_ctx* ctx, int prec, int outer_done) {
     CK(cudaMemcpyAsync(y_keep, st.y, ctx->m * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(cudaStreamSynchronize(s));
     st.prec = -1;                                   // force reallocation
-    if ((rs = alloc_state<TR, TD>(ctx, prec, r_new))) return rs;
+    if ((rs = alloc_state<TR, TD, TDIR>(ctx, prec, r_new))) return rs;
     convert<TR, TR>(s, ctx->n, ld_old, st.ld, r_old, R_old, st.R, flat_blocks(ctx, ctx->n * (int64_t)st.ld));
     rank_columns<TR>(s, ctx->n, st.ld, r_old, r_new, scale, ctx->prm.seed, (uint64_t)(outer_done - 1), st.R,
                      flat_blocks(ctx, ctx->n * (int64_t)(r_new - r_old)));
@@ -788,7 +788,7 @@ lorads_status fill_result(lorads_ctx* ctx, std::chrono::steady_clock::time_point
 
 // Host-stepped solve with a CUDA-event pair around every launch (verbose >= 2):
 // same kernels and decisions as the graph path, one host sync per iteration.
-template <typename TR, typename TD>
+template <typename TR, typename TD, typename TDIR = TD>
 lorads_status run_profiled(lorads_ctx* ctx, int prec, std::chrono::steady_clock::time_point t0,
                            lorads_result* res) {
     lorads_status s;
@@ -808,10 +808,10 @@ lorads_status run_profiled(lorads_ctx* ctx, int prec, std::chrono::steady_clock:
         CK(cudaStreamSynchronize(ss));
         hc = ctx->h_ctrl[0];
         if (hc.solve_done) break;
-        Driver<TR, TD> drv(ctx);
+        Driver<TR, TD, TDIR> drv(ctx);
         if (hc.pause) {
-            if ((s = grow_rank<TR, TD>(ctx, prec, hc.outer))) return s;
-            Driver<TR, TD> d2(ctx);
+            if ((s = grow_rank<TR, TD, TDIR>(ctx, prec, hc.outer))) return s;
+            Driver<TR, TD, TDIR> d2(ctx);
             d2.enqueue_resume();
             continue;
         }
@@ -835,7 +835,7 @@ lorads_status run_profiled(lorads_ctx* ctx, int prec, std::chrono::steady_clock:
     return fill_result(ctx, t0, timed_out, res);
 }
 
-template <typename TR, typename TD>
+template <typename TR, typename TD, typename TDIR = TD>
 lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0, int32_t r0_on_device,
                         const double* y0, lorads_result* res) {
     const auto t0 = std::chrono::steady_clock::now();
@@ -844,7 +844,7 @@ lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0,
     lorads_status s;
     int r = r0;
     if (r <= 0) r = std::max(1, (int)std::ceil(std::log2((double)std::max<int64_t>(ctx->m, 2))));
-    if ((s = alloc_state<TR, TD>(ctx, prec, r))) return s;
+    if ((s = alloc_state<TR, TD, TDIR>(ctx, prec, r))) return s;
     SolverState& st = ctx->st;
     cudaStream_t ss = ctx->solve_stream;
     CK(cudaEventRecord(ctx->ev_sync, ctx->stream));
@@ -896,7 +896,7 @@ lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0,
     for (int q = 0; q < kMaxMem; ++q) h.order[q] = q;
     CK(cudaMemcpyAsync(ctx->ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, ss));
     {
-        Driver<TR, TD> drv(ctx);
+        Driver<TR, TD, TDIR> drv(ctx);
         drv.enqueue_init();
     }
     if ((s = check_launch(ctx, "solve init"))) return s;
@@ -904,8 +904,8 @@ lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0,
         cudaGetLastError();
         ctx->prm.kernel_variant &= ~1;          // fall back to the register-staged row update
     }
-    if (P.verbose >= 2) return run_profiled<TR, TD>(ctx, prec, t0, res);
-    if ((s = capture<TR, TD>(ctx))) return s;
+    if (P.verbose >= 2) return run_profiled<TR, TD, TDIR>(ctx, prec, t0, res);
+    if ((s = capture<TR, TD, TDIR>(ctx))) return s;
     // ---- iterate: launch the graph in batches, poll the status of the previous batch
     int slot = 0;
     bool pending = false;
@@ -931,11 +931,11 @@ lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0,
                 const Ctrl& now = ctx->h_ctrl[slot];
                 if (now.solve_done) break;
                 // pause: grow the rank, then continue with the outer tail
-                if ((s = grow_rank<TR, TD>(ctx, prec, now.outer))) return s;
-                Driver<TR, TD> drv(ctx);
+                if ((s = grow_rank<TR, TD, TDIR>(ctx, prec, now.outer))) return s;
+                Driver<TR, TD, TDIR> drv(ctx);
                 drv.enqueue_resume();
                 if ((s = check_launch(ctx, "resume"))) return s;
-                if ((s = capture<TR, TD>(ctx))) return s;
+                if ((s = capture<TR, TD, TDIR>(ctx))) return s;
                 pending = false;
                 slot = 0;
                 continue;
@@ -971,8 +971,11 @@ extern "C" lorads_status lorads_solve(lorads_ctx* ctx, const double* R0, int32_t
         case LORADS_MIXED: s = run_solve<dfloat, float>(ctx, prec, R0, r0, r0_on_device, y0, res); break;
         case LORADS_DF64: s = run_solve<dfloat, dfloat>(ctx, prec, R0, r0, r0_on_device, y0, res); break;
         case LORADS_FP32: s = run_solve<float, float>(ctx, prec, R0, r0, r0_on_device, y0, res); break;
+        case LORADS_MIXED_BF16:
+            s = run_solve<dfloat, float, __nv_bfloat16>(ctx, prec, R0, r0, r0_on_device, y0, res);
+            break;
         default:
-            return set_err(ctx, "params.prec must be FP64, MIXED, DF64 or FP32 for lorads_solve"),
+            return set_err(ctx, "params.prec must be FP64, MIXED, DF64, FP32 or MIXED_BF16 for lorads_solve"),
                    LORADS_ERR_INVALID_ARG;
     }
     if (res && res->status == 0 && s != LORADS_OK) res->status = s;

@@ -184,6 +184,13 @@ __device__ __forceinline__ A dot_units(const Unit<T1> (&x)[CPL], const Unit<T2> 
     return s;
 }
 
+// Value an element has once stored as T (bf16 rounds; every other type keeps it).
+template <typename T, typename A>
+__device__ __forceinline__ A as_stored(A v) {
+    if constexpr (std::is_same_v<T, __nv_bfloat16>) return A(__bfloat162float(__float2bfloat16_rn(float(v))));
+    else return v;
+}
+
 // ================================================================== SpMM over C
 // out = C X  (+ the diagonal-constraint part -A*(v) X when v != nullptr),
 // optional epilogues:
@@ -613,9 +620,11 @@ k_cons_body(ProbDev p, int64_t k0, int64_t k1, const TU* __restrict__ U, const T
 // ================================================================== direction
 // D = cG G + sum_u (cS_u S_u + cY_u Y_u) over the stored pairs (the two-loop
 // recursion of Algorithm 1 carried out on coefficients); partials <G,D>, ||D||^2.
-template <typename TD>
+// TDIR: storage of D (the direction may be stored narrower than G and the
+// history; <G,D> and ||D||^2 are then taken of the stored values).
+template <typename TD, typename TDIR = TD>
 __device__ __forceinline__ void
-k_dir_body(int64_t nunits, const TD* __restrict__ G, TD* __restrict__ D, const TD* __restrict__ hist,
+k_dir_body(int64_t nunits, const TD* __restrict__ G, TDIR* __restrict__ D, const TD* __restrict__ hist,
       int64_t slot_stride, const Ctrl* ctrl, double* __restrict__ part, VGrid vg) {
     using A = arith_t<TD>;
     using PA = part_t<TD, TD>;
@@ -649,11 +658,11 @@ k_dir_body(int64_t nunits, const TD* __restrict__ G, TD* __restrict__ D, const T
                 for (int e = 0; e < 4; ++e) d.v[e] = fma(cS[t], A(s.v[e]), fma(cY[t], A(y.v[e]), A(d.v[e])));
             }
         }
-        Unit<TD> dst;
+        Unit<TDIR> dst;
         A gd = A(0), dd = A(0);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            dst.v[e] = d.v[e];
+            dst.v[e] = as_stored<TDIR>(A(d.v[e]));
             const A dv = A(dst.v[e]);           // value as stored
             gd += A(g.v[e]) * dv;
             dd += dv * dv;
@@ -667,16 +676,17 @@ k_dir_body(int64_t nunits, const TD* __restrict__ G, TD* __restrict__ D, const T
 
 // ================================================================== step (flat)
 // R += tau D, CR += tau CD  (used when the gradient needs a separate pattern pass)
-template <typename TR, typename TD>
+template <typename TR, typename TD, typename TDIR = TD>
 __device__ __forceinline__ void
-k_step_body(int64_t nunits, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restrict__ D,
+k_step_body(int64_t nunits, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __restrict__ D,
        const TD* __restrict__ CD, const Ctrl* ctrl, VGrid vg) {
     using A = arith_t<TR>;
     const A tau = A(ctrl->tau);
     const int64_t stride = (int64_t)vg.nblk * blockDim.x;
     for (int64_t u = vg.bid * (int64_t)blockDim.x + threadIdx.x; u < nunits; u += stride) {
         Unit<TR> r, cr;
-        Unit<TD> d, cd;
+        Unit<TDIR> d;
+        Unit<TD> cd;
         r.load_stream(R + u * 4);
         cr.load_stream(CR + u * 4);
         d.load_stream(D + u * 4);
@@ -708,9 +718,9 @@ constexpr int update_min_blocks() {
     return (CPL == 1 && !std::is_same_v<arith_t<TR>, double>) ? 3 : 2;
 }
 
-template <typename TR, typename TD, int CPL, bool STEP, bool HIST>
+template <typename TR, typename TD, int CPL, bool STEP, bool HIST, typename TDIR = TD>
 __device__ __forceinline__ void
-k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restrict__ D,
+k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __restrict__ D,
          const TD* __restrict__ CD, TD* __restrict__ G, const TD* __restrict__ W,
          TD* __restrict__ hist, int64_t slot_stride, int ld, int L, int Q,
          const double* __restrict__ y, const dfloat* __restrict__ ydf, void* __restrict__ zrow_v,
@@ -750,12 +760,12 @@ k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __re
         const int64_t i = base + rl.gw;
         const bool act = i < p.n;
         Unit<TR> r[CPL], cr[CPL];
-        Unit<TD> d[CPL];
+        Unit<TDIR> d[CPL];
         AR rr = AR(0);
         if (act) {
             load_row_stream<TR, CPL>(r, R, i, ld, L, Q, rl.lig);
             load_row_stream<TR, CPL>(cr, CR, i, ld, L, Q, rl.lig);
-            if constexpr (STEP || HIST) load_row_stream<TD, CPL>(d, D, i, ld, L, Q, rl.lig);
+            if constexpr (STEP || HIST) load_row_stream<TDIR, CPL>(d, D, i, ld, L, Q, rl.lig);
             if constexpr (STEP) {
                 Unit<TD> cd[CPL];
                 load_row_stream<TD, CPL>(cd, CD, i, ld, L, Q, rl.lig);
@@ -874,44 +884,44 @@ k_cons(ProbDev p, int64_t k0, int64_t k1, const TU* __restrict__ U, const TV* __
     k_cons_body<TU, TV, CPL, MODE>(p, k0, k1, U, V, ld, L, Q, y, out, zk, ydf, ctrl, rho_arg, part, hw_grid());
 }
 
-template <typename TD>
+template <typename TD, typename TDIR = TD>
 __global__ void __launch_bounds__(kThreads)
-k_dir(int64_t nunits, const TD* __restrict__ G, TD* __restrict__ D, const TD* __restrict__ hist,
+k_dir(int64_t nunits, const TD* __restrict__ G, TDIR* __restrict__ D, const TD* __restrict__ hist,
       int64_t slot_stride, const Ctrl* ctrl, double* __restrict__ part, const Ctrl* gate, int ph) {
     if (gated_off(gate, ph)) return;
-    k_dir_body<TD>(nunits, G, D, hist, slot_stride, ctrl, part, hw_grid());
+    k_dir_body<TD, TDIR>(nunits, G, D, hist, slot_stride, ctrl, part, hw_grid());
 }
 
-template <typename TR, typename TD>
+template <typename TR, typename TD, typename TDIR = TD>
 __global__ void __launch_bounds__(kThreads)
-k_step(int64_t nunits, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restrict__ D,
+k_step(int64_t nunits, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __restrict__ D,
        const TD* __restrict__ CD, const Ctrl* ctrl, const Ctrl* gate, int ph) {
     if (gated_off(gate, ph)) return;
-    k_step_body<TR, TD>(nunits, R, CR, D, CD, ctrl, hw_grid());
+    k_step_body<TR, TD, TDIR>(nunits, R, CR, D, CD, ctrl, hw_grid());
 }
 
-template <typename TR, typename TD, int CPL, bool STEP, bool HIST>
+template <typename TR, typename TD, int CPL, bool STEP, bool HIST, typename TDIR = TD>
 __global__ void __launch_bounds__(kThreads, (update_min_blocks<TR, TD, CPL>()))
-k_update(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restrict__ D,
+k_update(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __restrict__ D,
          const TD* __restrict__ CD, TD* __restrict__ G, const TD* __restrict__ W,
          TD* __restrict__ hist, int64_t slot_stride, int ld, int L, int Q,
          const double* __restrict__ y, const dfloat* __restrict__ ydf, void* __restrict__ zrow_v,
          const Ctrl* ctrl, double* __restrict__ part, const Ctrl* gate, int ph) {
     if (gated_off(gate, ph)) return;
-    k_update_body<TR, TD, CPL, STEP, HIST>(p, R, CR, D, CD, G, W, hist, slot_stride, ld, L, Q, y, ydf, zrow_v, ctrl, part, hw_grid());
+    k_update_body<TR, TD, CPL, STEP, HIST, TDIR>(p, R, CR, D, CD, G, W, hist, slot_stride, ld, L, Q, y, ydf, zrow_v, ctrl, part, hw_grid());
 }
 
 // The step update with EXTRA more resident blocks per SM (fewer registers per
 // thread, some spilled to L1): more rows in flight for the latency-bound pass.
-template <typename TR, typename TD, int CPL, int EXTRA>
+template <typename TR, typename TD, int CPL, int EXTRA, typename TDIR = TD>
 __global__ void __launch_bounds__(kThreads, (update_min_blocks<TR, TD, CPL>() + EXTRA))
-k_update_step_occ(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TD* __restrict__ D,
+k_update_step_occ(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __restrict__ D,
                   const TD* __restrict__ CD, TD* __restrict__ G, const TD* __restrict__ W,
                   TD* __restrict__ hist, int64_t slot_stride, int ld, int L, int Q,
                   const double* __restrict__ y, const dfloat* __restrict__ ydf, void* __restrict__ zrow_v,
                   const Ctrl* ctrl, double* __restrict__ part, const Ctrl* gate, int ph) {
     if (gated_off(gate, ph)) return;
-    k_update_body<TR, TD, CPL, true, true>(p, R, CR, D, CD, G, W, hist, slot_stride, ld, L, Q, y, ydf, zrow_v, ctrl,
+    k_update_body<TR, TD, CPL, true, true, TDIR>(p, R, CR, D, CD, G, W, hist, slot_stride, ld, L, Q, y, ydf, zrow_v, ctrl,
                                            part, hw_grid());
 }
 

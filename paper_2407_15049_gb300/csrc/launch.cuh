@@ -87,44 +87,44 @@ void launch_cons(const ConsArgs& a) {
     })
 }
 
-template <typename TD>
+template <typename TD, typename TDIR>
 void launch_dir(const DirArgs& a) {
-    k_dir<TD><<<a.blocks, kThreads, 0, a.stream>>>(
-        a.nunits, static_cast<const TD*>(a.G), static_cast<TD*>(a.D), static_cast<const TD*>(a.hist),
+    k_dir<TD, TDIR><<<a.blocks, kThreads, 0, a.stream>>>(
+        a.nunits, static_cast<const TD*>(a.G), static_cast<TDIR*>(a.D), static_cast<const TD*>(a.hist),
         a.slot_stride, a.ctrl, a.part, a.gate, a.ph);
 }
 
-template <typename TR, typename TD>
+template <typename TR, typename TD, typename TDIR>
 void launch_step(const StepArgs& a) {
-    k_step<TR, TD><<<a.blocks, kThreads, 0, a.stream>>>(
-        a.nunits, static_cast<TR*>(a.R), static_cast<TR*>(a.CR), static_cast<const TD*>(a.D),
+    k_step<TR, TD, TDIR><<<a.blocks, kThreads, 0, a.stream>>>(
+        a.nunits, static_cast<TR*>(a.R), static_cast<TR*>(a.CR), static_cast<const TDIR*>(a.D),
         static_cast<const TD*>(a.CD), a.ctrl, a.gate, a.ph);
 }
 
-template <typename TR, typename TD>
+template <typename TR, typename TD, typename TDIR>
 void launch_update(const UpdateArgs& a) {
     TR* R = static_cast<TR*>(a.R);
     TR* CR = static_cast<TR*>(a.CR);
-    const TD* D = static_cast<const TD*>(a.D);
+    const TDIR* D = static_cast<const TDIR*>(a.D);
     const TD* CD = static_cast<const TD*>(a.CD);
     TD* G = static_cast<TD*>(a.G);
     const TD* W = static_cast<const TD*>(a.W);
     TD* H = static_cast<TD*>(a.hist);
     LORADS_CPL_SWITCH(a.sh.CPL, {
         if (a.step && a.hist_on && a.extra_blocks == 1)
-            k_update_step_occ<TR, TD, CPL, 1><<<a.blocks, kThreads, 0, a.stream>>>(
+            k_update_step_occ<TR, TD, CPL, 1, TDIR><<<a.blocks, kThreads, 0, a.stream>>>(
                 a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph);
         else if (a.step && a.hist_on && a.extra_blocks == 2)
-            k_update_step_occ<TR, TD, CPL, 2><<<a.blocks, kThreads, 0, a.stream>>>(
+            k_update_step_occ<TR, TD, CPL, 2, TDIR><<<a.blocks, kThreads, 0, a.stream>>>(
                 a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph);
         else if (a.step && a.hist_on)
-            k_update<TR, TD, CPL, true, true><<<a.blocks, kThreads, 0, a.stream>>>(
+            k_update<TR, TD, CPL, true, true, TDIR><<<a.blocks, kThreads, 0, a.stream>>>(
                 a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph);
         else if (!a.step && a.hist_on)
-            k_update<TR, TD, CPL, false, true><<<a.blocks, kThreads, 0, a.stream>>>(
+            k_update<TR, TD, CPL, false, true, TDIR><<<a.blocks, kThreads, 0, a.stream>>>(
                 a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph);
         else
-            k_update<TR, TD, CPL, false, false><<<a.blocks, kThreads, 0, a.stream>>>(
+            k_update<TR, TD, CPL, false, false, TDIR><<<a.blocks, kThreads, 0, a.stream>>>(
                 a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph);
     })
 }
@@ -181,8 +181,11 @@ void launch_update_tma(const UpdateArgs& a, Ctrl* ctrl) {
 #define LORADS_INSTANTIATE_SPMM_C(TX, TO, TR) template void launch_spmm_c<TX, TO, TR>(const SpmmCArgs&);
 #define LORADS_INSTANTIATE_SPMM_A(TX, TO) template void launch_spmm_a<TX, TO>(const SpmmAArgs&);
 #define LORADS_INSTANTIATE_CONS(TU, TV) template void launch_cons<TU, TV>(const ConsArgs&);
-#define LORADS_INSTANTIATE_DIR(TD) template void launch_dir<TD>(const DirArgs&);
-#define LORADS_INSTANTIATE_STEP(TR, TD) template void launch_step<TR, TD>(const StepArgs&);
-#define LORADS_INSTANTIATE_UPDATE(TR, TD) template void launch_update<TR, TD>(const UpdateArgs&);
+#define LORADS_INSTANTIATE_DIR(TD) template void launch_dir<TD, TD>(const DirArgs&);
+#define LORADS_INSTANTIATE_DIR2(TD, TDIR) template void launch_dir<TD, TDIR>(const DirArgs&);
+#define LORADS_INSTANTIATE_STEP(TR, TD) template void launch_step<TR, TD, TD>(const StepArgs&);
+#define LORADS_INSTANTIATE_STEP2(TR, TD, TDIR) template void launch_step<TR, TD, TDIR>(const StepArgs&);
+#define LORADS_INSTANTIATE_UPDATE(TR, TD) template void launch_update<TR, TD, TD>(const UpdateArgs&);
+#define LORADS_INSTANTIATE_UPDATE2(TR, TD, TDIR) template void launch_update<TR, TD, TDIR>(const UpdateArgs&);
 
 }  // namespace lorads

@@ -59,9 +59,10 @@ struct UpdateArgs {
 template <typename TX, typename TO, typename TR> void launch_spmm_c(const SpmmCArgs& a);
 template <typename TX, typename TO> void launch_spmm_a(const SpmmAArgs& a);
 template <typename TU, typename TV> void launch_cons(const ConsArgs& a);
-template <typename TD> void launch_dir(const DirArgs& a);
-template <typename TR, typename TD> void launch_step(const StepArgs& a);
-template <typename TR, typename TD> void launch_update(const UpdateArgs& a);
+// TDIR: storage type of the direction D (defaults to the work type TD)
+template <typename TD, typename TDIR = TD> void launch_dir(const DirArgs& a);
+template <typename TR, typename TD, typename TDIR = TD> void launch_step(const StepArgs& a);
+template <typename TR, typename TD, typename TDIR = TD> void launch_update(const UpdateArgs& a);
 // TMA-staged row update (step + pair, no W term); `ctrl` receives the device error flag.
 // tma_update_blocks: grid of that kernel (0 = not applicable for this row width).
 template <typename TR, typename TD> void launch_update_tma(const UpdateArgs& a, Ctrl* ctrl);
@@ -74,29 +75,35 @@ using bf16 = __nv_bfloat16;
 extern template void launch_spmm_c<double, double, double>(const SpmmCArgs&);
 extern template void launch_spmm_a<double, double>(const SpmmAArgs&);
 extern template void launch_cons<double, double>(const ConsArgs&);
-extern template void launch_dir<double>(const DirArgs&);
-extern template void launch_step<double, double>(const StepArgs&);
-extern template void launch_update<double, double>(const UpdateArgs&);
+extern template void launch_dir<double, double>(const DirArgs&);
+extern template void launch_step<double, double, double>(const StepArgs&);
+extern template void launch_update<double, double, double>(const UpdateArgs&);
 // kern_mixed.cu: double-float master R / C R, FP32 direction, gradient and history
 extern template void launch_spmm_c<float, float, dfloat>(const SpmmCArgs&);
 extern template void launch_spmm_a<dfloat, float>(const SpmmAArgs&);
 extern template void launch_cons<dfloat, float>(const ConsArgs&);
-extern template void launch_step<dfloat, float>(const StepArgs&);
-extern template void launch_update<dfloat, float>(const UpdateArgs&);
+extern template void launch_step<dfloat, float, float>(const StepArgs&);
+extern template void launch_update<dfloat, float, float>(const UpdateArgs&);
 // kern_df.cu: double-float everywhere
 extern template void launch_spmm_c<dfloat, dfloat, dfloat>(const SpmmCArgs&);
 extern template void launch_spmm_a<dfloat, dfloat>(const SpmmAArgs&);
 extern template void launch_cons<dfloat, dfloat>(const ConsArgs&);
-extern template void launch_dir<dfloat>(const DirArgs&);
-extern template void launch_step<dfloat, dfloat>(const StepArgs&);
-extern template void launch_update<dfloat, dfloat>(const UpdateArgs&);
+extern template void launch_dir<dfloat, dfloat>(const DirArgs&);
+extern template void launch_step<dfloat, dfloat, dfloat>(const StepArgs&);
+extern template void launch_update<dfloat, dfloat, dfloat>(const UpdateArgs&);
 // kern_fp32.cu
 extern template void launch_spmm_c<float, float, float>(const SpmmCArgs&);
 extern template void launch_spmm_a<float, float>(const SpmmAArgs&);
 extern template void launch_cons<float, float>(const ConsArgs&);
-extern template void launch_dir<float>(const DirArgs&);
-extern template void launch_step<float, float>(const StepArgs&);
-extern template void launch_update<float, float>(const UpdateArgs&);
+extern template void launch_dir<float, float>(const DirArgs&);
+extern template void launch_step<float, float, float>(const StepArgs&);
+extern template void launch_update<float, float, float>(const UpdateArgs&);
+// kern_mixed_bf16.cu: the mixed form with the direction D stored in bf16
+extern template void launch_dir<float, bf16>(const DirArgs&);
+extern template void launch_spmm_c<bf16, float, dfloat>(const SpmmCArgs&);
+extern template void launch_cons<dfloat, bf16>(const ConsArgs&);
+extern template void launch_step<dfloat, float, bf16>(const StepArgs&);
+extern template void launch_update<dfloat, float, bf16>(const UpdateArgs&);
 #define LORADS_DECLARE_TMA(TR, TD)                                                    \
     extern template void launch_update_tma<TR, TD>(const UpdateArgs&, Ctrl*);         \
     extern template int tma_update_blocks<TR, TD>(int64_t, int, int);                 \

@@ -18,7 +18,8 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 import paper_2407_15049_gb300 as L  # noqa: E402
 
-PREC = {"fp64": L.LORADS_FP64, "mixed": L.LORADS_MIXED, "df64": L.LORADS_DF64, "fp32": L.LORADS_FP32}
+PREC = {"fp64": L.LORADS_FP64, "mixed": L.LORADS_MIXED, "df64": L.LORADS_DF64, "fp32": L.LORADS_FP32,
+        "mixed_bf16": L.LORADS_MIXED_BF16}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -98,7 +99,7 @@ def _converged_pair(inst, r, seed, prec="fp64", **kw):
     return ref, res, R, y
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed", "df64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "df64", "fp32", "mixed_bf16"])
 def test_maxcut_er_1000_converges_to_oracle_objective(prec):
     """The small workload: ER n = 1000, average degree 8, unit weights, r = 10.
 
@@ -122,7 +123,7 @@ def test_maxcut_er_1000_converges_to_oracle_objective(prec):
     assert np.linalg.norm(z) / 2 <= 1.0001e-5
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed", "df64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "df64", "fp32", "mixed_bf16"])
 def test_maxcut_er_1000_rank30_matches_oracle(prec):
     """With r = 30 the solves reach the SDP optimum (sigma_min(C - Diag y) ~ 0):
     every precision must match the oracle's objective to 1e-5."""
@@ -145,7 +146,7 @@ def test_maxcut_pm1_torus_converges():
     assert res["primal_obj"] == pytest.approx(ref["primal_obj"], rel=1e-5)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed", "df64"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "df64", "mixed_bf16"])
 def test_matrix_completion_converges(prec):
     n1 = n2 = 100
     k = int(math.ceil(5 * n1 * math.log(n1)))
