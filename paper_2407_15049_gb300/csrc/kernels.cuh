@@ -232,24 +232,36 @@ k_spmm_c_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld,
         if (act) {
             int64_t s = __ldg(p.c_rowptr + i);
             const int64_t e_ = __ldg(p.c_rowptr + i + 1);
-            constexpr int UN = CPL == 1 ? 4 : 2;       // nonzeros in flight per lane
-            for (; s + UN <= e_; s += UN) {
+            // nonzeros in flight per lane: with one unit per lane, all the gathers of a
+            // row of up to 8 stored entries are issued together (masked slots load nothing)
+            constexpr int UN = CPL == 1 ? 8 : 2;
+            for (; s < e_; s += UN) {
+                if (CPL != 1 && s + UN > e_) break;
                 int j[UN];
                 A w[UN];
 #pragma unroll
                 for (int u = 0; u < UN; ++u) {
-                    j[u] = __ldg(p.c_col + s + u);
-                    w[u] = A(ldv(cv + s + u));
+                    const bool ok = s + u < e_;
+                    j[u] = ok ? __ldg(p.c_col + s + u) : -1;
+                    w[u] = ok ? A(ldv(cv + s + u)) : A(0);
                 }
                 Unit<TX> x[UN][CPL];
 #pragma unroll
-                for (int u = 0; u < UN; ++u) load_row<TX, CPL>(x[u], X, j[u], ld, L, Q, rl.lig);
+                for (int u = 0; u < UN; ++u) {
+                    if (j[u] >= 0) load_row<TX, CPL>(x[u], X, j[u], ld, L, Q, rl.lig);
+                    else
+#pragma unroll
+                        for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) x[u][c].v[e] = 0;
+                }
 #pragma unroll
                 for (int u = 0; u < UN; ++u)
+                    if (j[u] >= 0)
 #pragma unroll
-                    for (int c = 0; c < CPL; ++c)
+                        for (int c = 0; c < CPL; ++c)
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) acc[c][e] = fma(w[u], A(x[u][c].v[e]), acc[c][e]);
+                            for (int e = 0; e < 4; ++e) acc[c][e] = fma(w[u], A(x[u][c].v[e]), acc[c][e]);
             }
             for (; s < e_; ++s) {
                 const int j0 = __ldg(p.c_col + s);
