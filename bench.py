@@ -250,6 +250,18 @@ def _config(args):
 
 # ----------------------------------------------------------------------------- native
 
+def max_over_ranks(values, world: int, device: str = "cuda"):
+    """Element-wise maximum of per-rank timings over every rank (replicas: the job
+    takes as long as its slowest rank).  `None` entries count as 0."""
+    if world <= 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([0.0 if v is None else float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -270,7 +282,9 @@ def run_native(args):
     inst, R0, gen_s = build_instance(args.workload)
     cfg = WORKLOADS[args.workload]
     stream = torch.cuda.Stream()
-    params = L.default_params(prec=prec_code)
+    # rel. KKT = max(err1, err2, err3): err2 (Lanczos on C - A*(y)) is evaluated at the
+    # end of every timed solve
+    params = L.default_params(prec=prec_code, compute_err2=1)
 
     def barrier():
         torch.cuda.synchronize()
@@ -362,12 +376,9 @@ def run_native(args):
             d2h = Rh.nbytes + yh.nbytes
 
     per_step = elapsed / args.steps
+    e2e_mean = statistics.mean(e2e_times) if e2e_times else None
     if world > 1:
-        tt = torch.tensor([per_step, statistics.mean(e2e_times) if e2e_times else 0.0], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        per_step, e2e_mean = tt.tolist()
-    else:
-        e2e_mean = statistics.mean(e2e_times) if e2e_times else None
+        per_step, e2e_mean = max_over_ranks([per_step, e2e_mean], world)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -424,8 +435,8 @@ def run_native(args):
         "e2e": {"value": e2e_mean, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
-        "solve": {k: last[k] for k in ("status_name", "primal_obj", "dual_obj", "err1", "err3", "rho", "rank",
-                                       "outer_iters", "inner_iters", "seconds")},
+        "solve": {k: last[k] for k in ("status_name", "primal_obj", "dual_obj", "err1", "err2", "err3", "sigma_min",
+                                       "rho", "rank", "outer_iters", "inner_iters", "seconds")},
         "sdp_value": -last["primal_obj"],
         "warm_start": None if warm is None else {
             "kind": "learned (3-layer message passing, bf16 activations)", "training": {
@@ -557,9 +568,7 @@ def run_batch(args):
     h2d = sum(x.rowptr.nbytes + x.colind.nbytes + x.val.nbytes + x.con.nbytes + x.row.nbytes + x.col.nbytes
               + x.aval.nbytes + x.b.nbytes for x in B)
     if world > 1:
-        tt = torch.tensor([per_step, e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        per_step, e2e_s = tt.tolist()
+        per_step, e2e_s = max_over_ranks([per_step, e2e_s], world)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()

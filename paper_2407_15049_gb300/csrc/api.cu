@@ -987,6 +987,7 @@ extern "C" lorads_status lorads_solve(lorads_ctx* ctx, const double* R0, int32_t
         if (res) {
             res->sigma_min = sig;
             res->err2 = std::max(0.0, -sig) / (1.0 + ctx->cnorm1);
+            res->kernel_launches = ctx->launches;
         }
     }
     return s;
@@ -1066,6 +1067,7 @@ lorads_status run_lanczos(lorads_ctx* ctx, const double* ydev, int k, uint64_t s
         }
     }
     lz_tridiag_min(s, lz, k, beta_off, lz + sc + 1);
+    ctx->launches += 4 + (int64_t)k * (ctx->m_off ? 6 : 5) + (k - 1);
     lorads_status cs = check_launch(ctx, "lanczos");
     if (cs == LORADS_OK) {
         cudaError_t e = cudaMemcpyAsync(sigma_out, lz + sc + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
