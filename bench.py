@@ -179,10 +179,15 @@ def kernel_bytes(fam: str, n: int, ld: int, nnz: int, m: int, wR: int, wD: int, 
     return float("nan")
 
 
+# sources that define the single-instance streaming kernels (their device code)
+KERNEL_SOURCES = ("common.cuh", "dfloat.cuh", "kernels.cuh", "launch.cuh", "launch_decl.h", "update_tma.cuh",
+                  "kern_mixed.cu")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in sorted((ROOT / "paper_2407_15049_gb300" / "csrc").glob("*")):
-        h.update(f.read_bytes())
+    for name in KERNEL_SOURCES:
+        h.update((ROOT / "paper_2407_15049_gb300" / "csrc" / name).read_bytes())
     return h.hexdigest()[:16]
 
 
