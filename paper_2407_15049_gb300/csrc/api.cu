@@ -910,7 +910,6 @@ lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0,
     int slot = 0;
     bool pending = false;
     int last_outer_printed = -1;
-    lorads_status final_status = LORADS_OK;
     bool timed_out = false;
     for (;;) {
         for (int k = 0; k < P.check_every; ++k) CK(cudaGraphLaunch(st.exec, ss));
