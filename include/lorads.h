@@ -103,10 +103,15 @@ typedef struct {
     int32_t lbfgs_scaling;     /* 0: initial matrix I (Algorithm 1 as printed); 1 (default): gamma I, gamma = <s,y>/<y,y> */
     int32_t rho_policy;        /* rho grows when err1 did not shrink by infeas_decrease: 0 always; 1 only
                                   after a converged inner loop; 2 (default) also after a capped loop that raised err1 */
-    int32_t kernel_variant;    /* row update, bit flags: 0 register-staged; bit 0: TMA-staged (bulk copies into
+    int32_t kernel_variant;    /* kernel forms, bit flags: 0 register-staged row update; bit 0: TMA-staged (bulk copies into
                                   shared memory, one block per SM) where it applies; bits 1, 2: the
                                   register-staged step update with 1 or 2 more resident blocks per SM
-                                  (default 2: one more block, measured 16% faster at n = 1e7) */
+                                  (bit 1: one more block, measured 16% faster at n = 1e7); bit 3: the
+                                  line-search SpMM loads each row group's next row bounds one iteration
+                                  ahead and prefetches that row's entries, rows and scalars into L2
+                                  (measured 6% faster at n = 1e7); bit 4: the step update (with bit 1 or 2)
+                                  prefetches each group's next row into L2 (measured 1% slower).  Bits 3
+                                  and 4 change no arithmetic.  Default 10 = bits 1 and 3. */
     int32_t inner_scale;       /* inner stop ||G||_F <= thr, z = A(RR^T) - b, e = tol (1 + ||b||_inf):
                                   0: thr = inner_rel max(||z||, e);  1: thr = inner_rel max(rho ||z||, e);
                                   2 (default): thr = max(e, min(inner_rel rho ||z||, inner_progress ||G_0||)) */

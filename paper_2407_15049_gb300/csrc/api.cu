@@ -235,7 +235,7 @@ extern "C" void lorads_default_params(lorads_params* p) {
     p->lbfgs_scaling = 1;
     p->rho_policy = 2;
     p->inner_scale = 2;
-    p->kernel_variant = 2;
+    p->kernel_variant = 10;
 }
 
 extern "C" const char* lorads_create_error(void) { return g_create_error.c_str(); }
@@ -591,7 +591,7 @@ struct Driver {
                   PH_INNER, s};
         timed(FAM_DIR, [&] { launch_dir<TD, TDIR>(d); });
         SpmmCArgs ls{p(), st.D, st.CD, st.ld, st.sh, nullptr, 1, EPI_LS, st.R, st.y, st.zrow, st.ydf, c->ctrl, 0.0,
-                     part_of(c, PART_LS), nb_rows, c->ctrl, PH_INNER, s};
+                     part_of(c, PART_LS), nb_rows, c->ctrl, PH_INNER, s, (c->prm.kernel_variant & 8) ? 1 : 0};
         timed(FAM_SPMM_LS, [&] { launch_spmm_c<TDIR, TD, TR>(ls); });
         if (c->m_off) {
             ConsArgs cl{p(), CONS_LS, c->m_diag, c->m, st.R, st.D, st.ld, st.sh, st.y, nullptr, st.zk, st.ydf, c->ctrl, 0.0,
@@ -613,7 +613,8 @@ struct Driver {
         }
         UpdateArgs u{p(), c->m_off == 0, true, st.R, st.CR, st.D, st.CD, st.G, c->m_off ? st.W : nullptr, st.hist,
                      st.slot_stride, st.ld, st.sh, st.y, st.ydf, st.zrow, c->ctrl, part_of(c, PART_UPD), nb_upd, c->ctrl, PH_STEP, s,
-                     (c->prm.kernel_variant & 4) ? 2 : ((c->prm.kernel_variant & 2) ? 1 : 0)};
+                     (c->prm.kernel_variant & 4) ? 2 : ((c->prm.kernel_variant & 2) ? 1 : 0),
+                     (c->prm.kernel_variant & 16) ? 1 : 0};
         if (tma) timed(FAM_UPDATE, [&] { launch_update_tma<TR, TD>(u, c->ctrl); });
         else timed(FAM_UPDATE, [&] { launch_update<TR, TD, TDIR>(u); });
         timed(FAM_HIST, [&] {

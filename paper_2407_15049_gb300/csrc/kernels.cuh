@@ -166,6 +166,21 @@ __device__ __forceinline__ void load_row_stream(Unit<T> (&u)[CPL], const T* base
     }
 }
 
+// L2 prefetch (no register, no wait) of one address of global memory.
+__device__ __forceinline__ void prefetch_l2(const void* a) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
+// L2 prefetch of the units of `row` that lane `lig` loads: issued one row
+// iteration ahead, it turns the dependent loads of that iteration into L2 hits.
+template <typename T, int CPL>
+__device__ __forceinline__ void prefetch_row(const T* base, int64_t row, int ld, int L, int Q, int lig) {
+    const T* p = base + row * (int64_t)ld + lig * 4;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c)
+        if (c * L + lig < Q) prefetch_l2(p + c * L * 4);
+}
+
 template <typename T, int CPL>
 __device__ __forceinline__ void store_row(const Unit<T> (&u)[CPL], T* base, int64_t row, int ld, int L, int Q, int lig) {
     T* p = base + row * (int64_t)ld + lig * 4;
@@ -205,7 +220,8 @@ __device__ __forceinline__ void
 k_spmm_c_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int L, int Q,
          const double* __restrict__ v, int write_out,
          const TR* __restrict__ R, const double* __restrict__ y, const void* __restrict__ zrow_v,
-         const dfloat* __restrict__ ydf, const Ctrl* ctrl, double rho_arg, double* __restrict__ part, VGrid vg) {
+         const dfloat* __restrict__ ydf, const Ctrl* ctrl, double rho_arg, double* __restrict__ part, VGrid vg,
+         int pf = 0) {
     using A = arith_t<TO>;
     using TV = cval_t<TX>;
     using PA = part_t<TO, TR>;
@@ -221,17 +237,41 @@ k_spmm_c_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld,
     const LS rho_s = LS(rho);
     const TV* __restrict__ cv = cvals<TV>(p);
     RowLoop rl(L, vg);
+    // With pf: the bounds (and constraint index) of this group's next row are loaded one
+    // iteration ahead, and that row's entries, own-row streams and scalars are prefetched
+    // into L2, so of its dependent load phases only the neighbour gathers wait on HBM.
+    const bool own_row = EPI == EPI_LS || EPI == EPI_OBJ || (v != nullptr && p.dk != nullptr);
+    int64_t s_nx = -1, e_nx = -1;
     for (int64_t base = rl.first; base < p.n; base += rl.stride) {
         const int64_t i = base + rl.gw;
         const bool act = i < p.n;
+        const int64_t s_cur = s_nx, e_cur = e_nx;
+        s_nx = -1;
+        int k_nx = -1;
+        if (pf != 0) {
+            const int64_t nx = i + rl.stride;
+            if (nx < p.n) {
+                s_nx = __ldg(p.c_rowptr + nx);
+                e_nx = __ldg(p.c_rowptr + nx + 1);
+                if (own_row) prefetch_row<TX, CPL>(X, nx, ld, L, Q, rl.lig);
+                if constexpr (EPI == EPI_LS) prefetch_row<TR, CPL>(R, nx, ld, L, Q, rl.lig);
+                if (p.dk != nullptr && rl.lig == 0) {
+                    k_nx = __ldg(p.dk + nx);
+                    prefetch_l2(p.da + nx);
+                    if (p.da_df != nullptr) prefetch_l2(p.da_df + nx);
+                    if constexpr (EPI == EPI_LS)
+                        if (zrow != nullptr) prefetch_l2(zrow + nx);
+                }
+            }
+        }
         A acc[CPL][4];
 #pragma unroll
         for (int c = 0; c < CPL; ++c)
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[c][e] = A(0);
         if (act) {
-            int64_t s = __ldg(p.c_rowptr + i);
-            const int64_t e_ = __ldg(p.c_rowptr + i + 1);
+            int64_t s = s_cur >= 0 ? s_cur : __ldg(p.c_rowptr + i);
+            const int64_t e_ = s_cur >= 0 ? e_cur : __ldg(p.c_rowptr + i + 1);
             // nonzeros in flight per lane: with one unit per lane, all the gathers of a
             // row of up to 8 stored entries are issued together (masked slots load nothing)
             constexpr int UN = CPL == 1 ? 8 : 2;
@@ -272,6 +312,20 @@ k_spmm_c_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld,
                 for (int c = 0; c < CPL; ++c)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) acc[c][e] = fma(w0, A(x0[c].v[e]), acc[c][e]);
+            }
+            if (s_nx >= 0 && rl.lig < 2 && e_nx > s_nx) {
+                // the next row's stored entries (first and last sector) and multiplier terms
+                const int64_t q = rl.lig == 0 ? s_nx : e_nx - 1;
+                prefetch_l2(p.c_col + q);
+                prefetch_l2(cv + q);
+            }
+            if (k_nx >= 0) {
+                if (v != nullptr) prefetch_l2(v + k_nx);
+                if constexpr (EPI == EPI_LS) {
+                    prefetch_l2(ydf ? static_cast<const void*>(ydf + k_nx) : static_cast<const void*>(y + k_nx));
+                    if (zrow == nullptr) prefetch_l2(p.b_df ? static_cast<const void*>(p.b_df + k_nx)
+                                                            : static_cast<const void*>(p.b + k_nx));
+                }
             }
             if (v != nullptr && p.dk != nullptr) {
                 const int k = __ldg(p.dk + i);
@@ -736,7 +790,7 @@ k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __
          const TD* __restrict__ CD, TD* __restrict__ G, const TD* __restrict__ W,
          TD* __restrict__ hist, int64_t slot_stride, int ld, int L, int Q,
          const double* __restrict__ y, const dfloat* __restrict__ ydf, void* __restrict__ zrow_v,
-         const Ctrl* ctrl, double* __restrict__ part, VGrid vg) {
+         const Ctrl* ctrl, double* __restrict__ part, VGrid vg, int pf = 0) {
     using AR = arith_t<TR>;
     using AD = arith_t<TD>;
     using PA = part_t<TR, TD>;
@@ -771,6 +825,34 @@ k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __
     for (int64_t base = rl.first; base < p.n; base += rl.stride) {
         const int64_t i = base + rl.gw;
         const bool act = i < p.n;
+        int knx = -1;                            // constraint of the next row, loaded one iteration ahead
+        if (pf != 0) {
+            // Prefetch the next row of this group into L2: the several dependent load
+            // phases of that iteration (R..C D, the old G, each stored pair) then wait
+            // on L2 instead of HBM.
+            const int64_t nx = i + rl.stride;
+            if (nx < p.n) {
+                prefetch_row<TR, CPL>(R, nx, ld, L, Q, rl.lig);
+                prefetch_row<TR, CPL>(CR, nx, ld, L, Q, rl.lig);
+                if constexpr (STEP || HIST) prefetch_row<TDIR, CPL>(D, nx, ld, L, Q, rl.lig);
+                if constexpr (STEP) prefetch_row<TD, CPL>(CD, nx, ld, L, Q, rl.lig);
+                if (W != nullptr) prefetch_row<TD, CPL>(W, nx, ld, L, Q, rl.lig);
+                if constexpr (HIST) {
+                    prefetch_row<TD, CPL>(G, nx, ld, L, Q, rl.lig);
+#pragma unroll
+                    for (int t = 0; t < kMaxMem - 1; ++t)
+                        if (t < nold) {
+                            prefetch_row<TD, CPL>(So[t], nx, ld, L, Q, rl.lig);
+                            prefetch_row<TD, CPL>(Yo[t], nx, ld, L, Q, rl.lig);
+                        }
+                }
+                if (p.dk != nullptr && rl.lig == 0) {
+                    knx = __ldg(p.dk + nx);
+                    if constexpr (std::is_same_v<RS, double>) prefetch_l2(p.da + nx);
+                    else prefetch_l2(p.da_df + nx);
+                }
+            }
+        }
         Unit<TR> r[CPL], cr[CPL];
         Unit<TDIR> d[CPL];
         AR rr = AR(0);
@@ -860,6 +942,16 @@ k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __
             store_row<TD, CPL>(g, G, i, ld, L, Q, rl.lig);
             accq[PU_GG] += dot_units<AD>(g, g);
         }
+        if (knx >= 0) {
+            // the next row's multiplier and right-hand side
+            if constexpr (std::is_same_v<RS, double>) {
+                prefetch_l2(y + knx);
+                prefetch_l2(p.b + knx);
+            } else {
+                prefetch_l2(ydf ? static_cast<const void*>(ydf + knx) : static_cast<const void*>(y + knx));
+                prefetch_l2(p.b_df + knx);
+            }
+        }
     }
     block_partials<PU_N>(accq, part, vg.pslot);
 }
@@ -868,15 +960,24 @@ k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __
 // One launch per body over the hardware grid; a kernel of the captured
 // iteration graph first checks the phase flags of the control block.
 
+// Resident blocks per SM the SpMM over C is compiled for: 4 (64 registers,
+// no spills) for float rows with one unit per lane, where the pass is bound by
+// the latency of its dependent loads; otherwise left to the compiler.
+template <typename TX, typename TO, int CPL>
+constexpr int spmm_min_blocks() {
+    return (CPL == 1 && std::is_same_v<TX, float> && std::is_same_v<TO, float>) ? 4 : 1;
+}
+
 template <typename TX, typename TO, typename TR, int CPL, int EPI>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, (spmm_min_blocks<TX, TO, CPL>()))
 k_spmm_c(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int L, int Q,
          const double* __restrict__ v, int write_out,
          const TR* __restrict__ R, const double* __restrict__ y, const void* __restrict__ zrow_v,
          const dfloat* __restrict__ ydf, const Ctrl* ctrl, double rho_arg, double* __restrict__ part,
-         const Ctrl* gate, int ph) {
+         const Ctrl* gate, int ph, int pf) {
     if (gated_off(gate, ph)) return;
-    k_spmm_c_body<TX, TO, TR, CPL, EPI>(p, X, out, ld, L, Q, v, write_out, R, y, zrow_v, ydf, ctrl, rho_arg, part, hw_grid());
+    k_spmm_c_body<TX, TO, TR, CPL, EPI>(p, X, out, ld, L, Q, v, write_out, R, y, zrow_v, ydf, ctrl, rho_arg, part, hw_grid(),
+                                        pf);
 }
 
 template <typename TX, typename TO, int CPL, bool VDF>
@@ -931,10 +1032,10 @@ k_update_step_occ(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR
                   const TD* __restrict__ CD, TD* __restrict__ G, const TD* __restrict__ W,
                   TD* __restrict__ hist, int64_t slot_stride, int ld, int L, int Q,
                   const double* __restrict__ y, const dfloat* __restrict__ ydf, void* __restrict__ zrow_v,
-                  const Ctrl* ctrl, double* __restrict__ part, const Ctrl* gate, int ph) {
+                  const Ctrl* ctrl, double* __restrict__ part, const Ctrl* gate, int ph, int pf) {
     if (gated_off(gate, ph)) return;
     k_update_body<TR, TD, CPL, true, true, TDIR>(p, R, CR, D, CD, G, W, hist, slot_stride, ld, L, Q, y, ydf, zrow_v, ctrl,
-                                           part, hw_grid());
+                                           part, hw_grid(), pf);
 }
 
 }  // namespace lorads

@@ -26,13 +26,13 @@ void launch_spmm_c(const SpmmCArgs& a) {
     LORADS_CPL_SWITCH(a.sh.CPL, {
         if (a.epi == EPI_LS)
             k_spmm_c<TX, TO, TR, CPL, EPI_LS><<<a.blocks, kThreads, 0, a.stream>>>(
-                a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.write_out, R, a.y, a.zrow, a.ydf, a.ctrl, a.rho, a.part, a.gate, a.ph);
+                a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.write_out, R, a.y, a.zrow, a.ydf, a.ctrl, a.rho, a.part, a.gate, a.ph, a.prefetch);
         else if (a.epi == EPI_OBJ)
             k_spmm_c<TX, TO, TR, CPL, EPI_OBJ><<<a.blocks, kThreads, 0, a.stream>>>(
-                a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.write_out, R, a.y, a.zrow, a.ydf, a.ctrl, a.rho, a.part, a.gate, a.ph);
+                a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.write_out, R, a.y, a.zrow, a.ydf, a.ctrl, a.rho, a.part, a.gate, a.ph, a.prefetch);
         else
             k_spmm_c<TX, TO, TR, CPL, EPI_NONE><<<a.blocks, kThreads, 0, a.stream>>>(
-                a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.write_out, R, a.y, a.zrow, a.ydf, a.ctrl, a.rho, a.part, a.gate, a.ph);
+                a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.write_out, R, a.y, a.zrow, a.ydf, a.ctrl, a.rho, a.part, a.gate, a.ph, a.prefetch);
     })
 }
 
@@ -113,10 +113,10 @@ void launch_update(const UpdateArgs& a) {
     LORADS_CPL_SWITCH(a.sh.CPL, {
         if (a.step && a.hist_on && a.extra_blocks == 1)
             k_update_step_occ<TR, TD, CPL, 1, TDIR><<<a.blocks, kThreads, 0, a.stream>>>(
-                a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph);
+                a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph, a.prefetch);
         else if (a.step && a.hist_on && a.extra_blocks == 2)
             k_update_step_occ<TR, TD, CPL, 2, TDIR><<<a.blocks, kThreads, 0, a.stream>>>(
-                a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph);
+                a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph, a.prefetch);
         else if (a.step && a.hist_on)
             k_update<TR, TD, CPL, true, true, TDIR><<<a.blocks, kThreads, 0, a.stream>>>(
                 a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph);

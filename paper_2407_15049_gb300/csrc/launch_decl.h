@@ -16,6 +16,7 @@ struct SpmmCArgs {
     const double* v; int write_out; int epi;
     const void* R; const double* y; const void* zrow; const dfloat* ydf; const Ctrl* ctrl; double rho; double* part;
     int blocks; const Ctrl* gate; int ph; cudaStream_t stream;
+    int prefetch = 0;   // 1: carry the next row's bounds and prefetch its entries and row terms into L2
 };
 
 // v: double[m], or double-float[m] when v_df (weights then formed without FP64)
@@ -54,6 +55,7 @@ struct UpdateArgs {
     double* part;
     int blocks; const Ctrl* gate; int ph; cudaStream_t stream;
     int extra_blocks;   // step update: 0, or the variant with 1 or 2 more resident blocks per SM
+    int prefetch = 0;   // step update with extra blocks: 1 = L2 prefetch of each group's next row
 };
 
 template <typename TX, typename TO, typename TR> void launch_spmm_c(const SpmmCArgs& a);

@@ -236,3 +236,32 @@ def test_dual_min_eig_matches_dense_eigenvalue(case):
         ref = O.sigma_min(O.Problem(inst), y)
     scale = 1.0 + abs(ref)
     assert sig == pytest.approx(ref, abs=1e-7 * scale)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16"])
+def test_prefetch_variants_are_bit_identical(prec):
+    """The L2-prefetch forms of the line-search SpMM and of the step update
+    (kernel_variant bits 3 and 4) change no arithmetic: on a graph of more rows
+    than one pass of the grid covers, a capped solve gives bit-identical iterates
+    and multipliers with and without them."""
+    n = 60_000
+    inst = W.maxcut_instance(n, W.er_graph(n, 2 * n, 3, "pm1"))
+    R0 = W.initial_factor(inst, 12, 5)
+    caps = dict(max_outer=2, max_inner=15, tol=1e-300)
+    res0, Ra, ya = _gpu_solve(inst, R0, prec=prec, kernel_variant=2, **caps)
+    res1, Rb, yb = _gpu_solve(inst, R0, prec=prec, kernel_variant=2 | 8 | 16, **caps)
+    assert res0["inner_iters"] == res1["inner_iters"] > 15
+    assert np.array_equal(Ra, Rb) and np.array_equal(ya, yb)
+
+
+def test_prefetch_variant_follows_oracle_trajectory():
+    """FP64 with both prefetch forms, several grid passes per kernel: the iterate
+    after 5 L-BFGS steps equals the oracle's."""
+    n = 60_000
+    inst = W.maxcut_instance(n, W.er_graph(n, 2 * n, 3, "pm1"))
+    R0 = W.initial_factor(inst, 12, 5)
+    caps = dict(max_outer=1, max_inner=5, tol=1e-300)
+    ref = O.solve(O.Problem(inst), R0, O.Params(**caps))
+    res, R, y = _gpu_solve(inst, R0, prec="fp64", kernel_variant=2 | 8 | 16, **caps)
+    assert res["inner_iters"] == ref["inner"]
+    assert np.max(np.abs(R - ref["R"])) <= 1e-9 * np.abs(ref["R"]).max()
