@@ -51,7 +51,7 @@ BATCH_WORKLOADS = {
 BATCH_METRIC = "instances/s to rel. KKT 1e-5, one persistent launch (512 mixed MaxCut / matrix-completion SDPs)"
 # iterations to tolerance used to scale the reference arm's per-iteration time when no
 # GPU run of the same invocation provides it (measured on the GPU solve of maxcut_er_1e7)
-DEFAULT_ITERS_TO_TOL = {"maxcut_er_1e7": 6660, "maxcut_er_1e6": 6900, "maxcut_er_1e5": 5000}
+DEFAULT_ITERS_TO_TOL = {"maxcut_er_1e7": 8352, "maxcut_er_1e6": 6381, "maxcut_er_1e5": 5000}
 
 
 def _args():
