@@ -5,6 +5,7 @@ definitions, finite differences, polynomial interpolation, closed-form SDP
 values, exhaustive max cut and duality certificates.
 """
 import math
+from pathlib import Path
 
 import numpy as np
 import pytest
@@ -234,26 +235,32 @@ def _solve_maxcut(n, edges, seed=1, r=None, **kw):
     return P, res
 
 
-def test_complete_graph_value():
-    n = 10
-    P, res = _solve_maxcut(n, W.complete_graph(n))
+def _closed_forms():
+    """Rows of golden/maxcut_sdp_values.txt: (family, size, value)."""
+    path = Path(__file__).resolve().parent / "golden" / "maxcut_sdp_values.txt"
+    rows = []
+    for line in path.read_text().splitlines():
+        if line.strip() and not line.startswith("#"):
+            fam, size, value = line.split()[:3]
+            rows.append((fam, int(size), float(value)))
+    return rows
+
+
+@pytest.mark.parametrize("fam,size,value", _closed_forms())
+def test_closed_form_sdp_values(fam, size, value):
+    """Unit-weight MaxCut SDP optima with closed forms: K_n -> n^2/4, odd C_n ->
+    (n/2)(1 + cos(pi/n)), bipartite torus -> |E| (fixture values, derivations in
+    golden/make_golden.py)."""
+    if fam == "complete":
+        n, edges, r = size, W.complete_graph(size), None
+    elif fam == "odd_cycle":
+        n, edges, r = size, W.cycle_graph(size), 3
+    else:
+        n, edges, r = size * size, W.bipartite_torus_graph(size), None
+        assert len(edges[0]) == value
+    P, res = _solve_maxcut(n, edges, r=r)
     assert res["status"] == "ok"
-    assert -res["primal_obj"] == pytest.approx(n * n / 4, rel=1e-5)
-
-
-@pytest.mark.parametrize("n", [5, 7, 9])
-def test_odd_cycle_value(n):
-    P, res = _solve_maxcut(n, W.cycle_graph(n), r=3)
-    assert res["status"] == "ok"
-    assert -res["primal_obj"] == pytest.approx(0.5 * n * (1 + math.cos(math.pi / n)), rel=1e-5)
-
-
-def test_bipartite_torus_value():
-    side = 6
-    edges = W.bipartite_torus_graph(side)
-    P, res = _solve_maxcut(side * side, edges)
-    assert res["status"] == "ok"
-    assert -res["primal_obj"] == pytest.approx(len(edges[0]), rel=1e-5)
+    assert -res["primal_obj"] == pytest.approx(value, rel=1e-5)
 
 
 @pytest.mark.parametrize("weights,seed", [("unit", 0), ("unit", 1), ("pm1", 2), ("pm1", 3)])
