@@ -30,6 +30,11 @@ import threading
 import time
 from pathlib import Path
 
+# The oracle legs report single-thread CPU times: numpy's BLAS and OpenMP pools
+# are held at one thread (set before numpy is first imported).
+for _var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_var, "1")
+
 ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
@@ -204,6 +209,21 @@ def ncu_traffic(kernel: str):
 
 # ----------------------------------------------------------------------------- CPU oracle
 
+def host_cpu() -> str:
+    """Architecture, logical CPU count and model name of the host (for the CPU-baseline lines)."""
+    import platform
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return f"{platform.machine()}, {os.cpu_count()} logical CPUs" + (f", {model}" if model else "")
+
+
 def oracle_sample(inst, R0, iters: int):
     """Seconds per L-BFGS iteration of the FP64 oracle on the full instance."""
     from oracle import lorads_oracle as O
@@ -235,8 +255,9 @@ def run_reference(args):
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": _config(args),
         "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
-                         "sample": f"{args.cpu_iters} L-BFGS iterations of the n=1e7 solve per step "
-                                   f"({s_iter:.2f} s/iteration), scaled by {iters_to_tol} iterations to tolerance"},
+                         "sample": f"{args.cpu_iters} L-BFGS iterations of the n={WORKLOADS[args.workload]['n']:,} solve per step "
+                                   f"({s_iter:.2f} s/iteration, one thread on {host_cpu()}), scaled by "
+                                   f"{iters_to_tol} iterations to tolerance"},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -428,8 +449,8 @@ def run_native(args):
         s_iter = oracle_sample(inst, R0, args.cpu_iters)
         iters = last["inner_iters"]
         cpu = {"value": s_iter * iters, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_iters} L-BFGS iterations of the same n=1e7 solve ({s_iter:.2f} s/iteration, "
-                         f"numpy/scipy single thread), scaled by the {iters} iterations this solve needed"}
+               "sample": f"{args.cpu_iters} L-BFGS iterations of the same n={cfg['n']:,} solve ({s_iter:.2f} s/iteration, "
+                         f"one thread on {host_cpu()}), scaled by the {iters} iterations this solve needed"}
     line = {
         "metric": METRIC, "value": per_step, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
@@ -521,7 +542,7 @@ def run_batch(args):
                 "config": {"workload": args.workload, "description": cfg["desc"]},
                 "cpu_baseline": {"value": v, "unit": "instances/s", "cores": 1, "kind": "oracle",
                                  "sample": f"{len(names)} seeded instances of the batch, smallest first, solved to "
-                                           f"tolerance by the oracle ({spent:.1f} s): " + ", ".join(names)},
+                                           f"tolerance by the oracle ({spent:.1f} s, one thread on {host_cpu()}): " + ", ".join(names)},
                 "e2e": {"value": v, "unit": "instances/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return 0
@@ -595,7 +616,7 @@ def run_batch(args):
         v, spent, names = _batch_cpu_sample(B, budget_s=20.0)
         cpu = {"value": v, "unit": "instances/s", "cores": 1, "kind": "oracle",
                "sample": f"{len(names)} seeded instances of the batch, smallest first, solved to tolerance by "
-                         f"the oracle ({spent:.1f} s, numpy single thread): " + ", ".join(names)}
+                         f"the oracle ({spent:.1f} s, one thread on {host_cpu()}): " + ", ".join(names)}
     line = {
         "metric": BATCH_METRIC, "value": count * world / per_step, "unit": "instances/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
