@@ -263,6 +263,39 @@ def test_closed_form_sdp_values(fam, size, value):
     assert -res["primal_obj"] == pytest.approx(value, rel=1e-5)
 
 
+def test_bruteforce_cut_closed_forms():
+    """Exact max cuts with closed forms: K_n -> floor(n/2) ceil(n/2), odd C_n -> n - 1,
+    even C_n -> n, a bipartite torus -> |E|; a +-1 weighted triangle by hand."""
+    for n in (4, 5, 7):
+        assert O.maxcut_bruteforce(n, W.complete_graph(n)) == (n // 2) * ((n + 1) // 2)
+    for n in (5, 7, 6):
+        assert O.maxcut_bruteforce(n, W.cycle_graph(n)) == (n - 1 if n % 2 else n)
+    edges = W.bipartite_torus_graph(4)
+    assert O.maxcut_bruteforce(16, edges) == len(edges[0])
+    # triangle with weights +1 (0-1), -1 (1-2), +1 (0-2): the best cut isolates vertex 0
+    tri = (np.array([0, 1, 0]), np.array([1, 2, 2]), np.array([1.0, -1.0, 1.0]))
+    assert O.maxcut_bruteforce(3, tri) == 2.0
+
+
+def test_sigma_min_is_the_smallest_eigenvalue_of_the_dual_slack():
+    """sigma_min(C - A*(y)) on a tiny MaxCut instance: the dense matrix written out
+    entry by entry from C = -L/4 and A*(y) = Diag(y), against the spectrum's minimum
+    over a Rayleigh-quotient grid bound and numpy's eigvalsh."""
+    inst = W.maxcut_instance(5, W.cycle_graph(5))
+    P = O.Problem(inst)
+    y = np.array([0.3, -0.2, 0.1, 0.0, -0.4])
+    S = np.zeros((5, 5))
+    for i in range(5):
+        j = (i + 1) % 5
+        S[i, j] = S[j, i] = 0.25                 # -L/4 off the diagonal (unit weights)
+    np.fill_diagonal(S, -0.5 - y)                # -deg/4 - y_i
+    lam = np.linalg.eigvalsh(S)[0]
+    assert O.sigma_min(P, y) == pytest.approx(lam, abs=1e-12)
+    x = np.random.default_rng(0).standard_normal((5, 2000))
+    rq = np.einsum("ij,ij->j", x, S @ x) / np.einsum("ij,ij->j", x, x)
+    assert lam <= rq.min() + 1e-12
+
+
 @pytest.mark.parametrize("weights,seed", [("unit", 0), ("unit", 1), ("pm1", 2), ("pm1", 3)])
 def test_bruteforce_cut_below_sdp_bound(weights, seed):
     n = 12
