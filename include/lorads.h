@@ -13,12 +13,12 @@
  *     L_rho(R, y) = <C, RR^T> - y^T (A(RR^T) - b) + rho/2 ||A(RR^T) - b||^2,
  *     grad_R L    = 2 (C - A*(y~)) R  with  y~ = y - rho (A(RR^T) - b),
  * and the multiplier step of Sec. 2.1 is y <- y~.  The error measures of
- * Sec. 4.1 (err1, err2, err3) are written with the dual slack C - A*(y).
+ * Sec. 4.2 (err1, err2, err3) are written with the dual slack C - A*(y).
  *
  * Constraint convention (single-entry constraints).  Constraint k is one
  * triplet (i <= j, a):  <A_k, X> = a X_ii  (i == j)  or  2 a X_ij  (i < j).
- * This covers the MaxCut SDP of Sec. 4.2 (X_ii = 1) and the matrix-completion
- * SDP of Sec. 4.3.  Constraints with several triplets (general SDPs, Sec. 4.4)
+ * This covers the MaxCut SDP of Sec. 4.3 (X_ii = 1) and the matrix-completion
+ * SDP of Sec. 4.4.  Constraints with several triplets (general SDPs, Sec. 4.5)
  * are rejected with LORADS_ERR_UNSUPPORTED.
  *
  * Layout.  Every n x r factor (R, D, U, V, outputs) is row-major with a
@@ -77,7 +77,7 @@ typedef enum {
                               the rounded direction) */
 } lorads_prec;
 
-/* Solver constants.  The paper fixes tol (Sec. 4.1), the time limit (Sec. 4.1)
+/* Solver constants.  The paper fixes tol (Sec. 4.2), the time limit (Sec. 4.2)
  * and the rank rule (App. A.1); the remaining values are this library's
  * readings of what the paper leaves open. */
 typedef struct {
@@ -199,7 +199,7 @@ lorads_status lorads_linesearch_coeffs(lorads_ctx* ctx, const void* R, const voi
 lorads_status lorads_solve(lorads_ctx* ctx, const double* R0, int32_t r0, int32_t r0_on_device,
                            const double* y0, lorads_result* res);
 
-/* sigma_min(C - A*(y)), the dual-slack eigenvalue behind err2 of Sec. 4.1 (which the
+/* sigma_min(C - A*(y)), the dual-slack eigenvalue behind err2 of Sec. 4.2 (which the
  * paper evaluates on the CPU), by a `steps`-step Lanczos run on the GPU with the
  * library's FP64 SpMM; the start vector is drawn from SplitMix64(seed).  The smallest
  * Ritz value is returned (an upper bound that converges to sigma_min).
@@ -378,7 +378,7 @@ void lorads_batch_destroy(lorads_batch* b);
 
 /* ------------------------------------------------------------------ learned warm start
  * A small message-passing network that predicts a starting factor R0 (unit rows, the
- * feasible set of the MaxCut constraints X_ii = 1 of Sec. 4.2) from the pattern of C, to
+ * feasible set of the MaxCut constraints X_ii = 1 of Sec. 4.3) from the pattern of C, to
  * replace the random start of the solve.  The paper has no such network; it is trained
  * on the factors R* that lorads_solve / lorads_batch_solve return.  Definition (F = 16,
  * H = 32, w_ij = C_ij for i != j, s_i = sum_j |w_ij|, deg_i = #{j != i: C_ij stored}):

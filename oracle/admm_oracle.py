@@ -35,11 +35,11 @@ Readings where the paper is silent (all are parameters of ``AdmmParams``):
   * CG stop: ||r_k||_F <= cg_rel * ||r_0||_F, at most cg_max steps (the
     tolerance epsilon and cap K of Algorithm 2 are not given);
   * switch: the ALM stage runs with its own stopping test (err1 and |err3|,
-    Sec. 4.1) at the looser tolerance switch_err1; the ADMM stage then starts
+    Sec. 4.2) at the looser tolerance switch_err1; the ADMM stage then starts
     from U = V = R and the ALM stage's y;
   * rho: the ALM stage's last rho, held fixed through the ADMM stage (no
     schedule is given for it);
-  * stop: the errors of Sec. 4.1 at R = (U + V)/2, whose X = R R^T is positive
+  * stop: the errors of Sec. 4.2 at R = (U + V)/2, whose X = R R^T is positive
     semidefinite; err1 and |err3| <= tol, as in the ALM stage.
 
 Parity pins: tests/test_admm_oracle.py -- the operator against the dense
@@ -120,7 +120,7 @@ def cg(P: O.Problem, V: np.ndarray, X0: np.ndarray, rhs: np.ndarray, rho: float,
 def admm_stage(P: O.Problem, R: np.ndarray, y: np.ndarray, rho: float, params: AdmmParams | None = None,
                record: list | None = None):
     """The ADMM stage of Eq. (2.2) from U = V = R.  Returns a dict with the
-    averaged factor R = (U + V)/2, U, V, y, the errors of Sec. 4.1 at R and the
+    averaged factor R = (U + V)/2, U, V, y, the errors of Sec. 4.2 at R and the
     iteration and CG-step counts."""
     prm = params or AdmmParams()
     t0 = time.perf_counter()

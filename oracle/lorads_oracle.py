@@ -11,7 +11,7 @@ polynomial root finder, no fusion and no reordering of the algorithm's steps.
 Sign convention.  The body of the paper writes the Lagrangian as
 <C,RR^T> + <A(RR^T)-b, lam> + rho/2 ||A(RR^T)-b||^2 with the ascent step
 lam += rho (A(RR^T)-b) (Eq. (1.2), Sec. 2.1), while the line-search appendix
-and the error formulas (Sec. 4.1) use lam^T (b - A(X)) and C - A*(lam).  Only
+and the error formulas (Sec. 4.2) use lam^T (b - A(X)) and C - A*(lam).  Only
 the latter pair is consistent, so this module uses the standard dual variable
 y (= -lam of the body):
 
@@ -223,7 +223,7 @@ def lbfgs_direction(G: np.ndarray, S: list, Y: list, scaling: int = 0) -> np.nda
 # ----------------------------------------------------------------------------- errors
 
 def sigma_min(P: Problem, y: np.ndarray, dense_limit: int = 3000) -> float:
-    """Smallest eigenvalue of the dual slack C - A*(y) (Sec. 4.1, err2)."""
+    """Smallest eigenvalue of the dual slack C - A*(y) (Sec. 4.2, err2)."""
     S = (P.C - adjoint(P, y)).tocsr()
     if P.n <= dense_limit:
         return float(np.linalg.eigvalsh(S.toarray())[0])
@@ -234,7 +234,7 @@ def sigma_min(P: Problem, y: np.ndarray, dense_limit: int = 3000) -> float:
 
 
 def errors(P: Problem, R: np.ndarray, y: np.ndarray, with_err2: bool = False):
-    """Error measures of Sec. 4.1 with the readings used by the solver:
+    """Error measures of Sec. 4.2 with the readings used by the solver:
     err1 normalised by 1 + ||b||_inf, err3 signed, err2 by 1 + ||vec C||_1."""
     z = constraint_map(P, R, R) - P.b
     obj = objective(P, R)
@@ -299,7 +299,7 @@ class Params:
     """Solver constants.  The paper leaves all but ``tol`` and the rank rule
     unspecified (it defers them to the CPU LoRADS paper); the values below are
     the readings the GPU library uses too."""
-    tol: float = 1e-5                 # epsilon of Sec. 4.1
+    tol: float = 1e-5                 # epsilon of Sec. 4.2
     lbfgs_mem: int = 4                # T of Algorithm 1
     max_inner: int = 500              # K of Algorithm 1 (per outer step)
     max_outer: int = 200
@@ -316,7 +316,7 @@ class Params:
                                       # 2: as 1, capped by inner_progress * ||G|| at the loop start
     inner_progress: float = 0.1
     seed: int = 0
-    time_limit: float = 1e4           # seconds (Sec. 4.1)
+    time_limit: float = 1e4           # seconds (Sec. 4.2)
 
 
 def auto_rho(P: Problem) -> float:
@@ -388,7 +388,7 @@ def solve(P: Problem, R0: np.ndarray, params: Params | None = None,
                 Yh.clear()
             R, G = R_new, G_new
         total_inner += k
-        # ---- multiplier step (Sec. 2.1) and error check (Sec. 4.1)
+        # ---- multiplier step (Sec. 2.1) and error check (Sec. 4.2)
         z = constraint_map(P, R, R) - P.b
         y = y - rho * z
         err1_new = float(np.linalg.norm(z)) / (1.0 + bnorm_inf)

@@ -979,7 +979,7 @@ extern "C" lorads_status lorads_solve(lorads_ctx* ctx, const double* R0, int32_t
                    LORADS_ERR_INVALID_ARG;
     }
     if (res && res->status == 0 && s != LORADS_OK) res->status = s;
-    // err2 of Sec. 4.1 at the returned multiplier: sigma_min(C - A*(y)) by Lanczos
+    // err2 of Sec. 4.2 at the returned multiplier: sigma_min(C - A*(y)) by Lanczos
     if (ctx->prm.compute_err2 && ctx->st.have_solution && (s == LORADS_OK || s == LORADS_ERR_MAXITER)) {
         double sig = 0.0;
         const lorads_status ls = run_lanczos(ctx, ctx->st.y, ctx->prm.lanczos_steps, ctx->prm.seed, &sig);

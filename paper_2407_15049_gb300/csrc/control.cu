@@ -2,7 +2,7 @@
 // scalar pieces of the method: the line-search coefficients and cubic root of
 // App. A.2, the L-BFGS two-loop recursion of Algorithm 1 carried out on the
 // Gram data of the stored pairs, the multiplier/penalty step of Sec. 2.1 and
-// the error measures of Sec. 4.1.  All in FP64 on one block; the partial sums
+// the error measures of Sec. 4.2.  All in FP64 on one block; the partial sums
 // of the streaming kernels are folded in a fixed order (deterministic).
 #include <math.h>
 #include "control.h"
@@ -86,7 +86,7 @@ __global__ void k_ctrl_hist(Ctrl* c, int mode, const double* part_upd, int nb_up
 
 // ---------------------------------------------------------------- outer kernel
 // Multiplier step of Sec. 2.1 has been applied by the constraint pass (y <- y~);
-// here: err1 = ||A(RR^T) - b|| / (1 + ||b||_inf), err3 of Sec. 4.1, stop test,
+// here: err1 = ||A(RR^T) - b|| / (1 + ||b||_inf), err3 of Sec. 4.2, stop test,
 // penalty growth when err1 did not shrink enough, and the rank-update request
 // of App. A.1 when the inner loop hit its cap in consecutive outer steps.
 __global__ void k_ctrl_outer(Ctrl* c, const double* part_cons, int nb_cons, const double* part_obj, int nb_obj) {

@@ -13,13 +13,13 @@ the CUDA library nor the oracle is used):
 * the constraint values A(R R^T) (Sec. 2 notation: <A_k, X> with the
   single-entry convention <A_k, X> = a X_ii, or 2 a X_ij for i != j).
 
-Instances: the MaxCut SDP of Sec. 4.2 on a triangle with weights +1, -1, +1
-(C = -L/4, X_ii = 1); a 2 x 2 matrix-completion SDP of Sec. 4.3 (C = I of
+Instances: the MaxCut SDP of Sec. 4.3 on a triangle with weights +1, -1, +1
+(C = -L/4, X_ii = 1); a 2 x 2 matrix-completion SDP of Sec. 4.4 (C = I of
 order 4, two sampled entries, X_{i,2+j} + X_{2+j,i} = 2 M_ij); and a generic
 instance with a mixed-sign C, one diagonal and two off-diagonal constraints.
 
 ``maxcut_sdp_values.txt`` holds closed-form optimal values of the MaxCut SDP
-(max <L/4, X>, diag X = 1, X PSD) of Sec. 4.2 for unit weights: n^2/4 on the
+(max <L/4, X>, diag X = 1, X PSD) of Sec. 4.3 for unit weights: n^2/4 on the
 complete graph K_n (X = (n I - J)/(n - 1) attains the bound <L/4, X> <= n^2/4);
 (n/2)(1 + cos(pi/n)) on an odd cycle C_n (vectors at consecutive angles
 pi (n-1)/n, the classical value of the cycle's relaxation); |E| on a bipartite

@@ -14,7 +14,7 @@ Exchange format (the primal SDP of Eq. (1.1): min <C,X> s.t. <A_k,X> = b_k, X ps
   ``row <= col``; constraint k is  <A_k, X> = sum a * X_ij * (1 if i == j else 2).
 * ``b`` float64 (m).
 
-Workloads (Sec. 4.2 MaxCut SDP and Sec. 4.3 matrix-completion SDP):
+Workloads (Sec. 4.3 MaxCut SDP and Sec. 4.4 matrix-completion SDP):
 
 * MaxCut: C = -L/4 with L the weighted graph Laplacian, constraints X_ii = 1
   (one diagonal triplet per row, b = 1).  The reported SDP value is -<C,X>.
@@ -176,7 +176,7 @@ def cycle_graph(n: int):
 # ----------------------------------------------------------------------------- instances
 
 def maxcut_instance(n: int, edges) -> SDPInstance:
-    """MaxCut SDP of Sec. 4.2 written as a minimisation: C = -L(G,w)/4, X_ii = 1."""
+    """MaxCut SDP of Sec. 4.3 written as a minimisation: C = -L(G,w)/4, X_ii = 1."""
     i, j, w = edges
     deg = np.zeros(n, dtype=np.float64)
     np.add.at(deg, i, w)
@@ -193,7 +193,7 @@ def maxcut_instance(n: int, edges) -> SDPInstance:
 
 
 def mc_instance(n1: int, n2: int, rank: int, n_samples: int, seed: int) -> SDPInstance:
-    """Matrix-completion SDP of Sec. 4.3 with M = U V^T, U, V iid N(0,1) of rank ``rank``.
+    """Matrix-completion SDP of Sec. 4.4 with M = U V^T, U, V iid N(0,1) of rank ``rank``.
 
     Omega is drawn uniformly without replacement.  X = [[W1, Y^T-block], ...] has
     order n1 + n2; constraint k <-> (i, j): X_{i, n1+j} + X_{n1+j, i} = 2 M_ij.
