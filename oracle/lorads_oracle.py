@@ -317,6 +317,8 @@ class Params:
     inner_progress: float = 0.1
     seed: int = 0
     time_limit: float = 1e4           # seconds (Sec. 4.2)
+    stop_rule: int = 0                # 0: err1 and |err3| <= tol; 1: err1 <= tol alone (the
+                                      # primal-feasibility stop that precedes re-opt, Sec. 4.1)
 
 
 def auto_rho(P: Problem) -> float:
@@ -396,7 +398,7 @@ def solve(P: Problem, R0: np.ndarray, params: Params | None = None,
         if record is not None:
             record.append(dict(outer=outer, inner=k, rho=rho, err1=err1_new,
                                err3=e["err3"], obj=e["primal_obj"], r=R.shape[1]))
-        if err1_new <= prm.tol and abs(e["err3"]) <= prm.tol:
+        if err1_new <= prm.tol and (prm.stop_rule == 1 or abs(e["err3"]) <= prm.tol):
             status = "ok"
             err1 = err1_new
             break
