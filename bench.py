@@ -84,6 +84,9 @@ def _args():
     ap.add_argument("--instance-time-limit", type=float, default=60.0,
                     help="batched solve: per-instance time limit (s); instances past it count as unsolved")
     ap.add_argument("--tune-iters", type=int, default=20, help="batched solve: iterations per autotuner probe")
+    ap.add_argument("--spmm-vs-cusparse", type=int, default=0, metavar="N",
+                    help="informational: time C D of the library's SpMM and of cuSPARSE (torch CSR @ dense) "
+                         "on the ER graph with N vertices (degree 4, r = 24, FP32) and exit")
     return ap.parse_args()
 
 
@@ -645,8 +648,58 @@ def run_batch(args):
     return 0
 
 
+def spmm_vs_cusparse(n: int) -> int:
+    """C D with the library's SpMM entry point and with cuSPARSE (torch's CSR
+    matmul) on the same CSR and D: CUDA events over 20 calls after 3, outputs
+    compared.  Informational comparator, not a bench line."""
+    import torch
+    import workloads as W
+    import paper_2407_15049_gb300 as L
+    L.load()
+    r = 24
+    inst = W.maxcut_instance(n, W.er_graph(n, 2 * n, 0, "pm1"))
+    s = torch.cuda.current_stream()
+    ctx = L.lorads_create(inst, stream=s.cuda_stream)
+    try:
+        ld = L.padded_ld(r)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(0)
+        D = torch.randn(n, ld, dtype=torch.float32, device="cuda", generator=g)
+        out = torch.empty_like(D)
+        Cs = torch.sparse_csr_tensor(torch.as_tensor(inst.rowptr, device="cuda").to(torch.int32),
+                                     torch.as_tensor(inst.colind, device="cuda").to(torch.int32),
+                                     torch.as_tensor(inst.val, device="cuda").to(torch.float32), size=(n, n))
+        nnz = int(inst.rowptr[-1])
+        alg = nnz * 8 + 4 * (n + 1) + 2 * n * ld * 4
+
+        def timeit(fn, reps=20):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                fn()
+            e1.record(s)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        t_lib = timeit(lambda: L.lorads_spmm(ctx, D, None, out, r=r))
+        ref = Cs @ D
+        t_cus = timeit(lambda: torch.mm(Cs, D))
+        diff = (out - ref).abs().max().item() / ref.abs().max().item()
+    finally:
+        L.lorads_destroy(ctx)
+    print(json.dumps({"comparator": "spmm_vs_cusparse", "n": n, "r": r, "nnz": nnz, "library_ms": t_lib,
+                      "cusparse_ms": t_cus, "library_GBps": alg / t_lib / 1e6, "cusparse_GBps": alg / t_cus / 1e6,
+                      "max_rel_diff": diff}), flush=True)
+    return 0
+
+
 def main():
     args = _args()
+    if args.spmm_vs_cusparse:
+        return spmm_vs_cusparse(args.spmm_vs_cusparse)
     if args.workload in BATCH_WORKLOADS:
         return run_batch(args)
     if args.impl == "reference":
