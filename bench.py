@@ -46,6 +46,8 @@ WORKLOADS = {
                           desc="MaxCut SDP, Erdos-Renyi n=1e6, M=2e6 edges (avg degree 4), w in {-1,+1}, r=20"),
     "maxcut_er_1e5": dict(n=100_000, edges=200_000, weights="pm1", r=17, seed=0,
                           desc="MaxCut SDP, Erdos-Renyi n=1e5, M=2e5 edges (avg degree 4), w in {-1,+1}, r=17"),
+    "maxcut_torus_1e6": dict(n=1_000_000, edges=2_000_000, weights="pm1", r=20, seed=0, graph="torus", side=1000,
+                             desc="MaxCut SDP, 1000x1000 torus (4-regular, wraparound), w in {-1,+1}, r=20"),
 }
 BATCH_WORKLOADS = {
     "serving_batch_512": dict(count=512, seed=0,
@@ -56,7 +58,8 @@ BATCH_WORKLOADS = {
 BATCH_METRIC = "instances/s to rel. KKT 1e-5, one persistent launch (512 mixed MaxCut / matrix-completion SDPs)"
 # iterations to tolerance used to scale the reference arm's per-iteration time when no
 # GPU run of the same invocation provides it (measured on the GPU solve of maxcut_er_1e7)
-DEFAULT_ITERS_TO_TOL = {"maxcut_er_1e7": 8352, "maxcut_er_1e6": 6381, "maxcut_er_1e5": 5000}
+DEFAULT_ITERS_TO_TOL = {"maxcut_er_1e7": 8352, "maxcut_er_1e6": 6381, "maxcut_er_1e5": 5000,
+                       "maxcut_torus_1e6": 5271}
 
 
 def _args():
@@ -96,7 +99,10 @@ def build_instance(name):
     import workloads as W
     cfg = WORKLOADS[name]
     t = time.perf_counter()
-    edges = W.er_graph(cfg["n"], cfg["edges"], cfg["seed"], cfg["weights"])
+    if cfg.get("graph") == "torus":
+        edges = W.torus_graph(cfg["side"], cfg["seed"], cfg["weights"])
+    else:
+        edges = W.er_graph(cfg["n"], cfg["edges"], cfg["seed"], cfg["weights"])
     inst = W.maxcut_instance(cfg["n"], edges)
     R0 = W.initial_factor(inst, cfg["r"], cfg["seed"] + 1)
     return inst, R0, time.perf_counter() - t
@@ -199,13 +205,14 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernels are unchanged."""
+def ncu_traffic(kernel: str, prec: str):
+    """DRAM bytes of the committed ncu capture, if the kernels are unchanged and
+    the capture ran in the same precision form."""
     p = ROOT / "profiles" / "traffic.json"
     if not p.exists():
         return None
     d = json.loads(p.read_text())
-    if d.get("source_hash") != kernel_source_hash():
+    if d.get("source_hash") != kernel_source_hash() or d.get("prec", "mixed") != prec:
         return None
     return d.get("kernels", {}).get(kernel)
 
@@ -267,13 +274,20 @@ def run_reference(args):
     return 0
 
 
+def _l2_policy(cfg) -> str:
+    r_bytes = cfg["n"] * cfg["r"] * 8
+    if r_bytes > 129e6:
+        return f"inputs larger than L2 (R alone is {r_bytes / 1e6:,.0f} MB at FP64)"
+    return f"inputs smaller than L2 (R is {r_bytes / 1e6:,.0f} MB at FP64): timings include L2 reuse"
+
+
 def _config(args):
     cfg = WORKLOADS[args.workload]
     return {"workload": args.workload, "description": cfg["desc"], "n": cfg["n"], "m": cfg["n"],
             "nnz_C": cfg["n"] + 2 * cfg["edges"], "rank": cfg["r"], "solver_precision": args.prec,
             "start": ("learned warm start (network trained before timing; prediction timed)"
                       if args.warm_start == "gnn" else "cold (seeded unit-norm Gaussian rows)"), "tolerance": 1e-5,
-            "l2_policy": "inputs larger than L2 (R alone is 1.9 GB at FP64)",
+            "l2_policy": _l2_policy(cfg),
             "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -437,10 +451,13 @@ def run_native(args):
     if hot:
         dom = max(hot, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["solve_launches"])
         ach = kernels[dom]["GBps"]
-        tr = ncu_traffic(dom)
+        tr = ncu_traffic(dom, args.prec)
         roofline = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                     "frac": ach / peak, "peak_kind": peak_kind,
-                    "traffic": None if tr is None else tr.get("dram_bytes_per_launch_scaled"),
+                    # DRAM bytes per unit from the committed capture, times this workload's units
+                    # (the streaming passes move every operand once: traffic grows with n * ld)
+                    "traffic": (None if tr is None or not tr.get("measured_units")
+                                else tr["dram_bytes_measured"] / tr["measured_units"] * cfg["n"] * ld),
                     "algorithmic_bytes_per_launch": kernels[dom]["algorithmic_bytes"],
                     "avg_launch_ms": kernels[dom]["avg_ms"]}
         spmm = kernels.get("k_spmm_c(CD,ls)")
