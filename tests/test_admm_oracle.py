@@ -108,6 +108,24 @@ def test_cg_reaches_the_dense_solution(name):
     np.testing.assert_allclose(X, want, rtol=0, atol=1e-9 * np.abs(want).max())
 
 
+@pytest.mark.parametrize("name", list(INST))
+def test_cg_terminates_within_the_distinct_eigenvalue_count(name):
+    """frakA_V = rho I + rho sum_k v_k v_k^T has at most m + 1 distinct
+    eigenvalues, so exact-arithmetic CG (Algorithm 2) ends within m + 1 steps;
+    in FP64 it is at the dense solution to ~1e-8 after them (a wrong alpha or
+    beta does not)."""
+    P = O.Problem(INST[name])
+    rng = np.random.default_rng(8)
+    V = rng.standard_normal((P.n, 3))
+    y = rng.standard_normal(P.m)
+    rho = 1.1
+    rhs = A.system_rhs(P, V, y, rho)
+    assert P.m + 1 < V.size                        # fewer steps than unknowns
+    want = np.linalg.solve(_dense_operator(P, V, rho), rhs.reshape(-1)).reshape(V.shape)
+    X, steps = A.cg(P, V, np.zeros_like(V), rhs, rho, cg_rel=0.0, cg_max=P.m + 1)
+    assert np.abs(X - want).max() <= 1e-8 * np.abs(want).max()
+
+
 def test_block_steps_lower_the_lagrangian():
     P = O.Problem(INST["maxcut_er"])
     R = W.initial_factor(INST["maxcut_er"], 4, 5)
