@@ -15,6 +15,11 @@ tolerance with the iteration count of the solve.
 Multi-GPU (torchrun): replicas only -- every rank solves its own copy of the
 workload (the single-instance path has no exchange step); value is the max
 over ranks.
+
+Other workloads: --workload maxcut_er_1e6 / maxcut_er_1e5 / maxcut_torus_1e6
+(same line), serving_batch_512 (the batched persistent solve, instances/s);
+--spmm-vs-cusparse N prints an informational comparison of the library's SpMM
+with cuSPARSE on the ER graph with N vertices instead of a bench line.
 """
 from __future__ import annotations
 
