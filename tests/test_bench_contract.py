@@ -27,3 +27,24 @@ def test_reference_arm_prints_one_json_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"]
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_algorithmic_bytes_of_the_benchmark_kernels():
+    """The roofline numerators of the default workload (n = 1e7, ld = 24,
+    5e7 stored entries, mixed: w_R = 8, w_D = 4, T = 4), written out from the
+    per-launch formulas: every operand read or written once."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench", ROOT / "bench.py")
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    n, ld, nnz, m = 10_000_000, 24, 50_000_000, 10_000_000
+    kb = lambda fam: bench.kernel_bytes(fam, n, ld, nnz, m, 8, 4, 4)   # noqa: E731
+    per_row = 4 + 8 + 8 + 8
+    # step update: R, C R (8 B) read + written; D, C D, old G read; G, s, y written (4 B);
+    # the 3 older (s, y) pairs read (4 B); per-row constraint scalars
+    assert kb("k_update(step)") == n * ld * (4 * 8 + 6 * 4 + 2 * 3 * 4) + n * per_row == 19_480_000_000
+    # direction: G and 2T history slots read, D written
+    assert kb("k_dir") == n * ld * 4 * (2 + 2 * 4) == 9_600_000_000
+    # line-search SpMM: column indices + FP32 values, row pointers, own D and C D rows,
+    # R row (8 B), per-row scalars
+    assert kb("k_spmm_c(CD,ls)") == nnz * 8 + (n + 1) * 8 + n * ld * (2 * 4 + 8) + n * per_row == 4_600_000_008
