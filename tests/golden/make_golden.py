@@ -15,8 +15,9 @@ the CUDA library nor the oracle is used):
 
 Instances: the MaxCut SDP of Sec. 4.3 on a triangle with weights +1, -1, +1
 (C = -L/4, X_ii = 1); a 2 x 2 matrix-completion SDP of Sec. 4.4 (C = I of
-order 4, two sampled entries, X_{i,2+j} + X_{2+j,i} = 2 M_ij); and a generic
-instance with a mixed-sign C, one diagonal and two off-diagonal constraints.
+order 4, two sampled entries, X_{i,2+j} + X_{2+j,i} = 2 M_ij); a generic
+instance with a mixed-sign C, one diagonal and two off-diagonal constraints;
+and one whose constraints have several entries each (general SDPs, Sec. 4.5).
 
 ``maxcut_sdp_values.txt`` holds closed-form optimal values of the MaxCut SDP
 (max <L/4, X>, diag X = 1, X PSD) of Sec. 4.3 for unit weights: n^2/4 on the
@@ -73,6 +74,12 @@ def _cases():
         triplets=[(0, 1, 1, S.Rational(3, 2)), (1, 0, 2, 1), (2, 2, 3, -half)], b=[1, -1, 2],
         R=[[1, 0], [1, 1], [0, -2], [3, 1]], D=[[1, -1], [0, 2], [1, 1], [-1, 0]],
         y=[2, -half, 1], rho=S.Rational(5, 4)))
+    # a constraint with several entries (general SDPs, Sec. 4.5): k = 0 has three
+    cases.append(dict(
+        name="multi_entry_4", n=4, C=Cg, edges=None,
+        triplets=[(0, 0, 0, 1), (0, 1, 3, -S.Rational(3, 2)), (0, 2, 2, 2), (1, 0, 1, half), (1, 3, 3, 1)],
+        b=[3, -2], R=[[1, -1], [2, 0], [0, 1], [1, 1]], D=[[0, 2], [1, -1], [1, 0], [-2, 1]],
+        y=[-half, S.Rational(3, 2)], rho=S.Rational(2, 3)))
     return cases
 
 

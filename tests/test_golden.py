@@ -66,8 +66,8 @@ def _instance(c):
         aval=trip[:, 3].astype(np.float64), b=b, kind="generic")
 
 
-def test_fixture_has_the_three_instances():
-    assert [c["name"] for c in CASES] == ["maxcut_triangle", "mc_2x2", "generic_4"]
+def test_fixture_has_the_four_instances():
+    assert [c["name"] for c in CASES] == ["maxcut_triangle", "mc_2x2", "generic_4", "multi_entry_4"]
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c["name"] for c in CASES])
