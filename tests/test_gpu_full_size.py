@@ -102,15 +102,32 @@ def coef_scales(P, R, D, y, rho):
     return a, np.array([s1, s2, s3, s4])
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_full_size_linesearch_coeffs(full, prec):
-    inst, P, ctx = full
-    R, Rr = _factor(N, R_COLS, 103, prec)
-    D, Dr = _factor(N, R_COLS, 104, prec)
+@pytest.fixture(scope="module")
+def linesearch_case(full):
+    """R, D with FP32-representable entries (so that both storage forms hold the
+    same values), y, rho and the oracle's a1..a4 with their term scales: one
+    oracle pass serves both precisions."""
+    inst, P, _ = full
+    R = np.random.default_rng(103).standard_normal((N, R_COLS)).astype(np.float32).astype(np.float64)
+    D = np.random.default_rng(104).standard_normal((N, R_COLS)).astype(np.float32).astype(np.float64)
     y = np.random.default_rng(5).standard_normal(inst.m)
     rho = 3.5
-    a_gpu, tau_gpu = L.lorads_linesearch_coeffs(ctx, R, D, torch.as_tensor(y, device="cuda"), rho, r=R_COLS)
-    a_ref, scale = coef_scales(P, Rr, Dr, y, rho)
+    a_ref, scale = coef_scales(P, R, D, y, rho)
+    return R, D, y, rho, a_ref, scale
+
+
+def _device(X, prec):
+    t = torch.zeros((X.shape[0], L.padded_ld(X.shape[1])), dtype=DT[prec], device="cuda")
+    t[:, :X.shape[1]] = torch.as_tensor(X, device="cuda").to(DT[prec])
+    return t
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_linesearch_coeffs(full, linesearch_case, prec):
+    inst, P, ctx = full
+    R, D, y, rho, a_ref, scale = linesearch_case
+    a_gpu, tau_gpu = L.lorads_linesearch_coeffs(ctx, _device(R, prec), _device(D, prec),
+                                                torch.as_tensor(y, device="cuda"), rho, r=R_COLS)
     assert np.all(np.abs(a_gpu - a_ref) <= TOL[prec] * scale), (a_gpu, a_ref, scale)
     assert tau_gpu == pytest.approx(O.quartic_step(a_gpu), rel=1e-9, abs=1e-300)
 
