@@ -3,14 +3,22 @@
 Erdos-Renyi graph with n = 10^7 vertices (average degree 4, weights in {-1,+1},
 rank r = 24), plus the roofline of its dominant kernel.
 
-A step is one full solve (init + L-BFGS/ALM iterations to rel. KKT <= 1e-5)
-from the same seeded R0 with the problem already resident in HBM; `e2e`
-repeats it through the public C ABI from host buffers (upload of C, A, b and
-R0 inside the timed region, download of R and y at the end).
+A step is one full solve (init + L-BFGS/ALM iterations to rel. KKT <= 1e-5,
+err2 by Lanczos included) with the problem already resident in HBM; timed step
+k starts from its own seeded unit-row factor (seed 1 + k, drawn on the device
+before the timed region), so the steps form a seed sweep of the iteration
+count.  Warm-up steps are solves capped at --warmup-iters L-BFGS iterations
+(graph capture, caches, clocks).  The timed loop stops early, before starting
+a solve that would end past --time-budget seconds; `steps` reports the solves
+actually timed.  `e2e` repeats one solve through the public C ABI from host
+buffers (upload of C, A, b and R0 inside the timed region, download of R and y
+at the end).
 
---impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (L-BFGS iterations of the n = 10^7 solve), scaled to a time to
-tolerance with the iteration count of the solve.
+The CPU baseline and --impl reference time the FP64 CPU oracle on a bounded
+sample: L-BFGS iterations on an Erdos-Renyi graph with n = 10^6 of the same
+family (average degree 4, w in {-1,+1}, same rank), whose per-iteration work
+is linear in n and in the stored entries, scaled by n_workload / 10^6 and by
+the iteration count to tolerance.
 
 Multi-GPU (torchrun): replicas only -- every rank solves its own copy of the
 workload (the single-instance path has no exchange step); value is the max
@@ -42,6 +50,7 @@ for _var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
 
 ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
+T_START = time.perf_counter()
 
 METRIC = "time to rel. KKT 1e-5 (MaxCut n=1e7); SpMM+A(RRᵀ) HBM GB/s vs 8 TB/s"
 WORKLOADS = {
@@ -65,6 +74,16 @@ BATCH_METRIC = "instances/s to rel. KKT 1e-5, one persistent launch (512 mixed M
 # GPU run of the same invocation provides it (measured on the GPU solve of maxcut_er_1e7)
 DEFAULT_ITERS_TO_TOL = {"maxcut_er_1e7": 8352, "maxcut_er_1e6": 6381, "maxcut_er_1e5": 5000,
                        "maxcut_torus_1e6": 5271}
+# seconds of one solve to tolerance measured on a GB300 (bench default workload and form);
+# plan_seconds uses it to check that the driver's --steps 20 --warmup 5 run fits its limit
+MEASURED_SOLVE_S = {"maxcut_er_1e7": 69.1}
+# fixed legs of a default run on the GPU host (seconds, upper estimates): interpreter and
+# CUDA start, instance generation, upload, per-kernel profile, one e2e solve on top of its
+# solve time, CPU-baseline sample
+FIXED_LEGS_S = {"start": 60.0, "generate": 90.0, "create": 10.0, "profile": 20.0, "e2e_extra": 30.0,
+                "cpu_baseline": 60.0}
+DRIVER_LIMIT_S = 1800.0
+DEFAULT_TIME_BUDGET_S = 1100.0
 
 
 def _args():
@@ -78,7 +97,14 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=1, help="end-to-end steps")
     ap.add_argument("--profile-iters", type=int, default=200,
                     help="L-BFGS iterations of the CUDA-event-timed solve used for per-kernel durations")
-    ap.add_argument("--cpu-iters", type=int, default=2, help="oracle L-BFGS iterations per CPU sample")
+    ap.add_argument("--cpu-iters", type=int, default=2,
+                    help="oracle L-BFGS iterations of the CPU-baseline sample (reference arm: per step)")
+    ap.add_argument("--cpu-sample-n", type=int, default=1_000_000,
+                    help="vertices of the same-family graph the oracle is sampled on (0: the workload itself)")
+    ap.add_argument("--warmup-iters", type=int, default=60,
+                    help="L-BFGS iterations of each (capped) warm-up solve")
+    ap.add_argument("--time-budget", type=float, default=DEFAULT_TIME_BUDGET_S,
+                    help="seconds of timed solves: no solve starts that would end past it (at least one runs)")
     ap.add_argument("--iters-to-tol", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
@@ -199,7 +225,7 @@ def kernel_bytes(fam: str, n: int, ld: int, nnz: int, m: int, wR: int, wD: int, 
 
 
 # sources that define the single-instance streaming kernels (their device code)
-KERNEL_SOURCES = ("common.cuh", "dfloat.cuh", "kernels.cuh", "launch.cuh", "launch_decl.h", "update_tma.cuh",
+KERNEL_SOURCES = ("common.cuh", "dfloat.cuh", "kernels.cuh", "launch.cuh", "launch_decl.h",
                   "kern_mixed.cu")
 
 
@@ -239,44 +265,87 @@ def host_cpu() -> str:
     return f"{platform.machine()}, {os.cpu_count()} logical CPUs" + (f", {model}" if model else "")
 
 
-def oracle_sample(inst, R0, iters: int):
-    """Seconds per L-BFGS iteration of the FP64 oracle on the full instance."""
+def plan_seconds(steps: int, warmup: int, per_solve_s: float, budget_s: float, warmup_frac: float = 0.02) -> dict:
+    """Wall-time plan of a default run: the fixed legs, `warmup` capped solves
+    (a small fraction of a solve each), the timed solves (the loop starts no solve
+    that would end past budget_s, so at most floor(budget_s / per_solve_s) and at
+    least one run) and one e2e solve."""
+    timed_steps = max(1, min(steps, int(budget_s // per_solve_s)))
+    timed = timed_steps * per_solve_s
+    total = sum(FIXED_LEGS_S.values()) + warmup * warmup_frac * per_solve_s + timed + per_solve_s
+    return {"timed_steps": timed_steps, "timed_s": timed, "total_s": total, "limit_s": DRIVER_LIMIT_S,
+            "fits_in_driver_run": total <= 0.85 * DRIVER_LIMIT_S}
+
+
+def sample_instance(name: str, n_sample: int):
+    """The oracle's sample: the workload itself (n_sample = 0 or >= its n) or an
+    Erdos-Renyi graph of the same family with n_sample vertices (same average
+    degree and weights), seed 0, plus its seeded unit-row start of the same rank."""
+    import workloads as W
+    cfg = WORKLOADS[name]
+    if not n_sample or n_sample >= cfg["n"] or cfg.get("graph") == "torus":
+        inst, R0, _ = build_instance(name)
+        return inst, R0, 1.0
+    edges = W.er_graph(n_sample, int(round(cfg["edges"] * n_sample / cfg["n"])), 0, cfg["weights"])
+    inst = W.maxcut_instance(n_sample, edges)
+    return inst, W.initial_factor(inst, cfg["r"], 1), cfg["n"] / n_sample
+
+
+def oracle_overhead(P, R0):
+    """Seconds of the oracle's solve around its inner loop (start-up products, the
+    multiplier step and the error measures): one outer step with no iteration."""
     from oracle import lorads_oracle as O
-    P = O.Problem(inst)
+    t = time.perf_counter()
+    O.solve(P, R0, O.Params(max_outer=1, max_inner=0, tol=1e-300))
+    return time.perf_counter() - t
+
+
+def oracle_iteration_seconds(P, R0, iters: int, overhead: float):
+    """Seconds per L-BFGS iteration of the FP64 oracle: one outer step with `iters`
+    iterations, less the solve's fixed overhead."""
+    from oracle import lorads_oracle as O
     t = time.perf_counter()
     O.solve(P, R0, O.Params(max_outer=1, max_inner=iters, tol=1e-300))
-    return (time.perf_counter() - t) / iters
+    return max(time.perf_counter() - t - overhead, 1e-9) / iters
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    inst, R0, gen_s = build_instance(args.workload)
+    from oracle import lorads_oracle as O
+    inst, R0, scale = sample_instance(args.workload, args.cpu_sample_n)
+    P = O.Problem(inst)
     iters_to_tol = args.iters_to_tol or DEFAULT_ITERS_TO_TOL[args.workload]
-    for _ in range(args.warmup):
-        oracle_sample(inst, R0, 1)
+    overhead = statistics.median([oracle_overhead(P, R0) for _ in range(max(1, args.warmup))])
     per = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        per.append(oracle_sample(inst, R0, args.cpu_iters))
+        per.append(oracle_iteration_seconds(P, R0, args.cpu_iters, overhead))
     wall = time.perf_counter() - t0
-    s_iter = statistics.mean(per)
+    s_iter = statistics.mean(per) * scale
     value = s_iter * iters_to_tol
-    cores = 1
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": _config(args),
-        "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
-                         "sample": f"{args.cpu_iters} L-BFGS iterations of the n={WORKLOADS[args.workload]['n']:,} solve per step "
-                                   f"({s_iter:.2f} s/iteration, one thread on {host_cpu()}), scaled by "
-                                   f"{iters_to_tol} iterations to tolerance"},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+                         "sample": _sample_text(args, inst, scale, s_iter, iters_to_tol, "per step")},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _sample_text(args, inst, scale, s_iter, iters, what) -> str:
+    n_w = WORKLOADS[args.workload]["n"]
+    where = (f"the n={n_w:,} solve itself" if scale == 1.0 else
+             f"an Erdos-Renyi graph of the same family with n={inst.n:,} ({inst.nnz:,} stored entries, same "
+             f"rank), scaled by {scale:g} to n={n_w:,} (per-iteration work is linear in n and nnz)")
+    return (f"{args.cpu_iters} oracle L-BFGS iterations {what} on {where}, less the solve's fixed overhead: "
+            f"{s_iter:.2f} s/iteration at full size, one thread on {host_cpu()}; times {iters} iterations "
+            f"to tolerance")
 
 
 def _l2_policy(cfg) -> str:
@@ -359,23 +428,45 @@ def run_native(args):
             graph = WS.device_graph(inst)
             ldw = N.padded_ld(cfg["r"])
 
-            def start():
-                return net.predict(graph, feature_seed=0, ld=ldw)[:, :cfg["r"]].contiguous()
+            def start(seed):
+                return net.predict(graph, feature_seed=seed, ld=ldw)[:, :cfg["r"]].contiguous()
         else:
-            def start():
-                return R0_dev
-        results = []
+            def start(seed):
+                # seeded unit-norm Gaussian rows (the workload's start recipe), drawn on the device
+                g = torch.Generator(device="cuda")
+                g.manual_seed(seed)
+                Rs = torch.randn((inst.n, cfg["r"]), dtype=torch.float64, device="cuda", generator=g)
+                Rs /= torch.linalg.vector_norm(Rs, dim=1, keepdim=True)
+                return Rs
+        # warm-up: solves capped at a few iterations (graph capture, caches, clocks)
         for _ in range(args.warmup):
-            results.append(L.lorads_solve(ctx, start(), on_device=True))
+            L.lorads_solve(ctx, start(0), on_device=True, max_total_inner=args.warmup_iters)
+        # starting factors of the timed solves (seeds 1..K): random starts are drawn before the
+        # timed region, the network's predictions inside it (part of the warm-started method)
+        starts = [start(1 + k) for k in range(args.steps)] if warm is None else None
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        timed, step_s = [], []
         with ClockSampler(local) as clk:
             barrier()
+            t_wall = time.perf_counter()
             ev0.record(stream)
-            timed = [L.lorads_solve(ctx, start(), on_device=True) for _ in range(args.steps)]
+            for k in range(args.steps):
+                e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e_a.record(stream)
+                timed.append(L.lorads_solve(ctx, starts[k] if starts else start(1 + k), on_device=True))
+                e_b.record(stream)
+                e_b.synchronize()
+                step_s.append(e_a.elapsed_time(e_b) / 1e3)
+                spent = time.perf_counter() - t_wall
+                # start no solve that would end past the budget (the slowest so far as the estimate)
+                if k + 1 < args.steps and spent + max(step_s) > args.time_budget:
+                    break
             ev1.record(stream)
             barrier()
         elapsed = ev0.elapsed_time(ev1) / 1e3
+        steps_timed = len(timed)
+        del starts
         cold = None
         if warm is not None and args.compare_cold:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -423,7 +514,7 @@ def run_native(args):
             e2e_times.append(time.perf_counter() - t)
             d2h = Rh.nbytes + yh.nbytes
 
-    per_step = elapsed / args.steps
+    per_step = elapsed / steps_timed
     e2e_mean = statistics.mean(e2e_times) if e2e_times else None
     if world > 1:
         per_step, e2e_mean = max_over_ranks([per_step, e2e_mean], world)
@@ -469,16 +560,20 @@ def run_native(args):
         if spmm:
             roofline["spmm"] = {"achieved": spmm["GBps"], "frac": spmm["GBps"] / peak,
                                 "frac_of_8TBps": spmm["GBps"] / 8000.0, "avg_launch_ms": spmm["avg_ms"]}
+    iters_mean = statistics.mean(r["inner_iters"] for r in timed)
     cpu = None
     if not args.no_cpu_baseline:
-        s_iter = oracle_sample(inst, R0, args.cpu_iters)
-        iters = last["inner_iters"]
-        cpu = {"value": s_iter * iters, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_iters} L-BFGS iterations of the same n={cfg['n']:,} solve ({s_iter:.2f} s/iteration, "
-                         f"one thread on {host_cpu()}), scaled by the {iters} iterations this solve needed"}
+        from oracle import lorads_oracle as O
+        s_inst, s_R0, scale = sample_instance(args.workload, args.cpu_sample_n)
+        P = O.Problem(s_inst)
+        s_iter = oracle_iteration_seconds(P, s_R0, args.cpu_iters, oracle_overhead(P, s_R0)) * scale
+        cpu = {"value": s_iter * iters_mean, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": _sample_text(args, s_inst, scale, s_iter, round(iters_mean),
+                                      "(the mean L-BFGS iteration count of the timed GPU solves)")}
+    plan = plan_seconds(args.steps, args.warmup, MEASURED_SOLVE_S.get(args.workload, per_step), args.time_budget)
     line = {
-        "metric": METRIC, "value": per_step, "unit": "s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
+        "metric": METRIC, "value": per_step, "unit": "s", "n_gpus": world, "steps": steps_timed,
+        "steps_requested": args.steps, "warmup": args.warmup, "warmup_iters": args.warmup_iters, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None,
         "dtype": {"fp64": "f64", "mixed": "f32 (+double-float R, CR)", "df64": "double-float (2xf32)",
                   "fp32": "f32"}[args.prec],
@@ -488,6 +583,17 @@ def run_native(args):
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
         "solve": {k: last[k] for k in ("status_name", "primal_obj", "dual_obj", "err1", "err2", "err3", "sigma_min",
                                        "rho", "rank", "outer_iters", "inner_iters", "seconds")},
+        "per_step": {"start_seed": list(range(1, steps_timed + 1)), "seconds": step_s,
+                     "inner_iters": [r["inner_iters"] for r in timed],
+                     "outer_iters": [r["outer_iters"] for r in timed],
+                     "status": [r["status_name"] for r in timed],
+                     "primal_obj": [r["primal_obj"] for r in timed],
+                     "max_rel_kkt": [max(r["err1"], abs(r["err3"]), max(r["err2"], 0.0)) for r in timed]},
+        "spread": {"seconds_min": min(step_s), "seconds_median": statistics.median(step_s),
+                   "seconds_max": max(step_s), "iters_mean": iters_mean},
+        "consistency": {"timed_wall_s": elapsed, "time_budget_s": args.time_budget,
+                        "wall_s_total": time.perf_counter() - T_START, "plan": plan,
+                        "fits_in_driver_run": (time.perf_counter() - T_START) <= DRIVER_LIMIT_S},
         "sdp_value": -last["primal_obj"],
         "warm_start": None if warm is None else {
             "kind": "learned (3-layer message passing, bf16 activations)", "training": {

@@ -103,15 +103,14 @@ typedef struct {
     int32_t lbfgs_scaling;     /* 0: initial matrix I (Algorithm 1 as printed); 1 (default): gamma I, gamma = <s,y>/<y,y> */
     int32_t rho_policy;        /* rho grows when err1 did not shrink by infeas_decrease: 0 always; 1 only
                                   after a converged inner loop; 2 (default) also after a capped loop that raised err1 */
-    int32_t kernel_variant;    /* kernel forms, bit flags: 0 register-staged row update; bit 0: TMA-staged (bulk copies into
-                                  shared memory, one block per SM) where it applies; bits 1, 2: the
-                                  register-staged step update with 1 or 2 more resident blocks per SM
-                                  (bit 1: one more block, measured 16% faster at n = 1e7); bit 3: the
-                                  line-search SpMM loads each row group's next row bounds one iteration
-                                  ahead and prefetches that row's entries, rows and scalars into L2
-                                  (measured 6% faster at n = 1e7); bit 4: the step update (with bit 1 or 2)
-                                  prefetches each group's next row into L2 (measured 1% slower).  Bits 3
-                                  and 4 change no arithmetic.  Default 10 = bits 1 and 3. */
+    int32_t kernel_variant;    /* kernel forms, bit flags (bit 0 unused): bits 1, 2: the register-staged step
+                                  update with 1 or 2 more resident blocks per SM (bit 1: one more block,
+                                  measured 16% faster at n = 1e7); bit 3: the line-search SpMM loads each row
+                                  group's next row bounds one iteration ahead and prefetches that row's
+                                  entries, rows and scalars into L2 (measured 6% faster at n = 1e7); bit 4:
+                                  the step update (with bit 1 or 2) prefetches each group's next row into L2
+                                  (measured 1% slower).  Bits 3 and 4 change no arithmetic.  Default 10 =
+                                  bits 1 and 3. */
     int32_t inner_scale;       /* inner stop ||G||_F <= thr, z = A(RR^T) - b, e = tol (1 + ||b||_inf):
                                   0: thr = inner_rel max(||z||, e);  1: thr = inner_rel max(rho ||z||, e);
                                   2 (default): thr = max(e, min(inner_rel rho ||z||, inner_progress ||G_0||)) */
@@ -257,13 +256,20 @@ int32_t lorads_kernel_counts(const lorads_ctx* ctx, const char** names, int64_t*
  *   out               device double[5]: a1, a2, a3, a4, tau (as lorads_linesearch_coeffs).
  *   cuda_stream       stream to run on (NULL = legacy default stream).  Asynchronous.
  * Inputs are not validated beyond sizes and pointers: pass what lorads_create accepts.
+ * In particular every constraint must have exactly one triplet: the per-constraint
+ * products of the line search are formed per triplet, so a constraint with several
+ * triplets gives wrong coefficients (no error is returned).
  * Scratch: one fixed device array inside the library (2 x 1024 x 7 doubles, 114,688
  * bytes) that every GPU loading the library keeps until exit.  It is shared by all
  * calls on a device, so calls that overlap on the GPU race and must be ordered by the
  * caller; nothing needs clearing between calls.  The first call on each device looks
- * up the array's device address (cudaGetSymbolAddress, with that device current);
- * make that first call before starting any stream capture.  Sizes beyond the limits
- * above return LORADS_ERR_INVALID_ARG; the message is in lorads_noalloc_error().
+ * up the array's device address (cudaGetSymbolAddress, with that device current) and
+ * caches it per device ordinal; make that first call before starting any stream
+ * capture.  The library's kernels load on their first launch, one variant per row
+ * width: a caller that captures the call should make one call with each ld it will use
+ * beforehand.  After cudaDeviceReset on a device the cached address is stale: do not
+ * call this entry point on that device again in the same process.  Sizes beyond the
+ * limits above return LORADS_ERR_INVALID_ARG; the message is in lorads_noalloc_error().
  * Calls no allocation routine. */
 lorads_status lorads_linesearch_coeffs_noalloc(int64_t n, const int64_t* c_rowptr, const int32_t* c_colind,
                                                const double* c_val, int64_t m, const int32_t* a_con,

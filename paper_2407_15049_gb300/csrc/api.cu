@@ -512,17 +512,10 @@ struct Driver {
     int nb_rows, nb_flat, nb_off, nb_all;
     int64_t nunits;
 
-    int nb_upd;                 // grid of the row update (TMA path or register path)
-    bool tma;
-
     Driver(lorads_ctx* ctx) : c(ctx), st(ctx->st), s(ctx->solve_stream) { refresh(); }
 
     void refresh() {
         nb_rows = row_blocks(c, c->n, st.sh.L);
-        const int tb = (c->m_off == 0 && (c->prm.kernel_variant & 1) && std::is_same<TD, TDIR>::value)
-                           ? tma_update_blocks<TR, TD>(c->n, st.ld, c->num_sms) : 0;
-        tma = tb > 0;
-        nb_upd = tma ? tb : nb_rows;
         nunits = c->n * (int64_t)st.ld / 4;
         nb_flat = flat_blocks(c, nunits);
         nb_off = row_blocks(c, std::max<int64_t>(c->m_off, 1), st.sh.L);
@@ -612,13 +605,12 @@ struct Driver {
             timed(FAM_SPMM_A, [&] { launch_spmm_a<TR, TD>(w); });
         }
         UpdateArgs u{p(), c->m_off == 0, true, st.R, st.CR, st.D, st.CD, st.G, c->m_off ? st.W : nullptr, st.hist,
-                     st.slot_stride, st.ld, st.sh, st.y, st.ydf, st.zrow, c->ctrl, part_of(c, PART_UPD), nb_upd, c->ctrl, PH_STEP, s,
+                     st.slot_stride, st.ld, st.sh, st.y, st.ydf, st.zrow, c->ctrl, part_of(c, PART_UPD), nb_rows, c->ctrl, PH_STEP, s,
                      (c->prm.kernel_variant & 4) ? 2 : ((c->prm.kernel_variant & 2) ? 1 : 0),
                      (c->prm.kernel_variant & 16) ? 1 : 0};
-        if (tma) timed(FAM_UPDATE, [&] { launch_update_tma<TR, TD>(u, c->ctrl); });
-        else timed(FAM_UPDATE, [&] { launch_update<TR, TD, TDIR>(u); });
+        timed(FAM_UPDATE, [&] { launch_update<TR, TD, TDIR>(u); });
         timed(FAM_HIST, [&] {
-            ctrl_hist(s, c->ctrl, HIST_STEP, part_of(c, PART_UPD), nb_upd,
+            ctrl_hist(s, c->ctrl, HIST_STEP, part_of(c, PART_UPD), nb_rows,
                       c->m_off ? part_of(c, PART_YTIL) : nullptr, nb_off);
         });
     }
@@ -901,10 +893,6 @@ lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0,
         drv.enqueue_init();
     }
     if ((s = check_launch(ctx, "solve init"))) return s;
-    if (!prepare_update_tma<TR, TD>(st.ld)) {
-        cudaGetLastError();
-        ctx->prm.kernel_variant &= ~1;          // fall back to the register-staged row update
-    }
     if (P.verbose >= 2) return run_profiled<TR, TD, TDIR>(ctx, prec, t0, res);
     if ((s = capture<TR, TD, TDIR>(ctx))) return s;
     // ---- iterate: launch the graph in batches, poll the status of the previous batch

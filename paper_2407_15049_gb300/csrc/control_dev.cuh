@@ -233,7 +233,8 @@ __device__ inline void finish_inner_test(Ctrl* c) {
     else if (c->inner_scale == 1) thr = c->inner_rel * fmax(c->rho * zn, floor_);
     else thr = fmax(floor_, fmin(c->inner_rel * c->rho * zn, c->inner_progress * c->gnorm0));
     const double gn = sqrt(fmax(c->gnorm2, 0.0));
-    if (!isfinite(gn) || !isfinite(zn)) {
+    // tested on the sums themselves: fmax(NaN, 0) is 0
+    if (!isfinite(c->gnorm2) || !isfinite(c->znorm2)) {
         c->status = 5;                          // LORADS_ERR_NUMERIC
         c->solve_done = 1;
         return;
@@ -353,7 +354,7 @@ __device__ inline void ctrl_outer_apply(Ctrl* c, const double* sc, const double*
     c->dual_obj = dual;
     c->outer += 1;
     c->last_iter_rho = c->rho;
-    if (!isfinite(err1) || !isfinite(err3)) {
+    if (!isfinite(sc[PC_ZZ]) || !isfinite(err3)) {
         c->status = 5;
         c->solve_done = 1;
         return;

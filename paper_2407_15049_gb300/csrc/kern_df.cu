@@ -8,5 +8,4 @@ LORADS_INSTANTIATE_CONS(dfloat, dfloat)
 LORADS_INSTANTIATE_DIR(dfloat)
 LORADS_INSTANTIATE_STEP(dfloat, dfloat)
 LORADS_INSTANTIATE_UPDATE(dfloat, dfloat)
-LORADS_INSTANTIATE_TMA(dfloat, dfloat)
 }  // namespace lorads

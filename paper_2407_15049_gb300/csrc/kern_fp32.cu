@@ -8,5 +8,4 @@ LORADS_INSTANTIATE_CONS(float, float)
 LORADS_INSTANTIATE_DIR(float)
 LORADS_INSTANTIATE_STEP(float, float)
 LORADS_INSTANTIATE_UPDATE(float, float)
-LORADS_INSTANTIATE_TMA(float, float)
 }  // namespace lorads

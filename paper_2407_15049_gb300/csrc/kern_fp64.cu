@@ -8,5 +8,4 @@ LORADS_INSTANTIATE_CONS(double, double)
 LORADS_INSTANTIATE_DIR(double)
 LORADS_INSTANTIATE_STEP(double, double)
 LORADS_INSTANTIATE_UPDATE(double, double)
-LORADS_INSTANTIATE_TMA(double, double)
 }  // namespace lorads

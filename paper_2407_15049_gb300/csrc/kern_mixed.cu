@@ -9,5 +9,4 @@ LORADS_INSTANTIATE_SPMM_A(dfloat, float)
 LORADS_INSTANTIATE_CONS(dfloat, float)
 LORADS_INSTANTIATE_STEP(dfloat, float)
 LORADS_INSTANTIATE_UPDATE(dfloat, float)
-LORADS_INSTANTIATE_TMA(dfloat, float)
 }  // namespace lorads

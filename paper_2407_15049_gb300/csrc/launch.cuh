@@ -5,7 +5,6 @@
 
 #include "kernels.cuh"
 #include "launch_decl.h"
-#include "update_tma.cuh"
 
 namespace lorads {
 
@@ -128,55 +127,6 @@ void launch_update(const UpdateArgs& a) {
                 a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph);
     })
 }
-
-// ---- TMA-staged row update
-template <typename TR, typename TD>
-size_t tma_smem_bytes(int ld, int* L_out = nullptr) {
-    Shape sh;
-    if (!shape_for_ld(ld, &sh)) return 0;
-    if (L_out) *L_out = sh.L;
-    return (size_t)kTmaStages * tma_stage_bytes<TR, TD>(kThreads / sh.L, ld);
-}
-
-template <typename TR, typename TD>
-int tma_update_blocks(int64_t n, int ld, int num_sms) {
-    int L = 1;
-    const size_t bytes = tma_smem_bytes<TR, TD>(ld, &L);
-    if (bytes == 0 || bytes > 200 * 1024) return 0;            // one block per SM must fit
-    const int64_t ntiles = (n + kThreads / L - 1) / (kThreads / L);
-    return (int)(ntiles < num_sms ? ntiles : num_sms);
-}
-
-// Allows the dynamic shared memory of every row-width variant (one block per SM).
-template <typename TR, typename TD>
-bool prepare_update_tma(int) {
-    const int bytes = 200 * 1024;
-    cudaError_t e = cudaSuccess;
-    for (int cpl = 1; cpl <= kMaxCPL; ++cpl) {
-        LORADS_CPL_SWITCH(cpl, {
-            const cudaError_t ei =
-                cudaFuncSetAttribute(k_update_tma<TR, TD, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-            if (ei != cudaSuccess) e = ei;
-        })
-    }
-    return e == cudaSuccess;
-}
-
-template <typename TR, typename TD>
-void launch_update_tma(const UpdateArgs& a, Ctrl* ctrl) {
-    const size_t bytes = tma_smem_bytes<TR, TD>(a.ld);
-    LORADS_CPL_SWITCH(a.sh.CPL, {
-        k_update_tma<TR, TD, CPL><<<a.blocks, kThreads, bytes, a.stream>>>(
-            a.p, static_cast<TR*>(a.R), static_cast<TR*>(a.CR), static_cast<const TD*>(a.D),
-            static_cast<const TD*>(a.CD), static_cast<TD*>(a.G), static_cast<TD*>(a.hist), a.slot_stride, a.ld,
-            a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, ctrl, a.part, a.gate, a.ph);
-    })
-}
-
-#define LORADS_INSTANTIATE_TMA(TR, TD)                                                  \
-    template void launch_update_tma<TR, TD>(const UpdateArgs&, Ctrl*);                 \
-    template int tma_update_blocks<TR, TD>(int64_t, int, int);                         \
-    template bool prepare_update_tma<TR, TD>(int);
 
 #define LORADS_INSTANTIATE_SPMM_C(TX, TO, TR) template void launch_spmm_c<TX, TO, TR>(const SpmmCArgs&);
 #define LORADS_INSTANTIATE_SPMM_A(TX, TO) template void launch_spmm_a<TX, TO>(const SpmmAArgs&);

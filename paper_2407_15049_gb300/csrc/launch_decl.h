@@ -65,11 +65,6 @@ template <typename TU, typename TV> void launch_cons(const ConsArgs& a);
 template <typename TD, typename TDIR = TD> void launch_dir(const DirArgs& a);
 template <typename TR, typename TD, typename TDIR = TD> void launch_step(const StepArgs& a);
 template <typename TR, typename TD, typename TDIR = TD> void launch_update(const UpdateArgs& a);
-// TMA-staged row update (step + pair, no W term); `ctrl` receives the device error flag.
-// tma_update_blocks: grid of that kernel (0 = not applicable for this row width).
-template <typename TR, typename TD> void launch_update_tma(const UpdateArgs& a, Ctrl* ctrl);
-template <typename TR, typename TD> int tma_update_blocks(int64_t n, int ld, int num_sms);
-template <typename TR, typename TD> bool prepare_update_tma(int ld);
 
 using bf16 = __nv_bfloat16;
 
@@ -106,14 +101,6 @@ extern template void launch_spmm_c<bf16, float, dfloat>(const SpmmCArgs&);
 extern template void launch_cons<dfloat, bf16>(const ConsArgs&);
 extern template void launch_step<dfloat, float, bf16>(const StepArgs&);
 extern template void launch_update<dfloat, float, bf16>(const UpdateArgs&);
-#define LORADS_DECLARE_TMA(TR, TD)                                                    \
-    extern template void launch_update_tma<TR, TD>(const UpdateArgs&, Ctrl*);         \
-    extern template int tma_update_blocks<TR, TD>(int64_t, int, int);                 \
-    extern template bool prepare_update_tma<TR, TD>(int);
-LORADS_DECLARE_TMA(double, double)
-LORADS_DECLARE_TMA(dfloat, float)
-LORADS_DECLARE_TMA(dfloat, dfloat)
-LORADS_DECLARE_TMA(float, float)
 // kern_bf16.cu: bf16 storage, FP32 arithmetic (standalone entry points)
 extern template void launch_spmm_c<bf16, float, bf16>(const SpmmCArgs&);
 extern template void launch_spmm_a<bf16, float>(const SpmmAArgs&);

@@ -17,6 +17,12 @@
 // every call overwrites all the partial slots it later reads, so nothing needs
 // clearing.  Every GPU that loads this library holds the array until the
 // process exits.
+//
+// The address of the array on each device is looked up once, on the first
+// call with that device current, and cached per device ordinal.  A
+// cudaDeviceReset (or any teardown of the device's primary context) unloads
+// the module; the cached address is then stale, so a process that resets a
+// device must not call this entry point on that device afterwards.
 #include <mutex>
 #include <string>
 
@@ -114,6 +120,11 @@ extern "C" lorads_status lorads_linesearch_coeffs_noalloc(
     double* part_cons = scratch + kNoallocParts;
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
 
+    // Each triplet is passed to the constraint pass as its own constraint, so the
+    // per-constraint products q1_k q2_k, q1_k^2, q2_k^2 of App. A.2 are formed per
+    // triplet.  That equals the per-constraint sums only when every constraint has
+    // exactly one triplet (the input lorads_create accepts); several triplets of
+    // one constraint would give wrong coefficients, not an error.
     ProbDev p{};
     p.n = n;
     p.m = m;

@@ -1,7 +1,7 @@
 """Writes the exact fixtures ``lagrangian_exact.txt`` and ``maxcut_sdp_values.txt``
 of this folder.
 
-For three tiny SDPs with integer factors, the fixture holds, as exact
+For four tiny SDPs with integer factors, the fixture holds, as exact
 fractions obtained by symbolic expansion of the definitions (sympy; neither
 the CUDA library nor the oracle is used):
 
@@ -11,7 +11,13 @@ the CUDA library nor the oracle is used):
 * the coefficients of L_rho(R + tau D, y) - L_rho(R, y)
   = a1 tau^4 + a2 tau^3 + a3 tau^2 + a4 tau  (exact line search, App. A.2);
 * the constraint values A(R R^T) (Sec. 2 notation: <A_k, X> with the
-  single-entry convention <A_k, X> = a X_ii, or 2 a X_ij for i != j).
+  single-entry convention <A_k, X> = a X_ii, or 2 a X_ij for i != j);
+* the error measures of Sec. 4.2 at (R, y) with the readings the solver uses:
+  <C, X>, b^T y, err1 = ||A(X) - b||_2 / (1 + ||b||_inf) (and its 1 + ||b||_1
+  form), the signed err3 = (<C,X> - b^T y) / (1 + |<C,X>| + |b^T y|), and
+  err2 = |min(0, sigma_min(C - A*(y)))| / (1 + ||vec C||_1), sigma_min taken as
+  the smallest real root of the exact characteristic polynomial of the rational
+  matrix C - A*(y), to 30 digits.
 
 Instances: the MaxCut SDP of Sec. 4.3 on a triangle with weights +1, -1, +1
 (C = -L/4, X_ii = 1); a 2 x 2 matrix-completion SDP of Sec. 4.4 (C = I of
@@ -97,6 +103,36 @@ def _lagrangian(case, R, y, rho):
     return obj - sum(yk * zk for yk, zk in zip(y, z)) + rho / 2 * sum(zk * zk for zk in z)
 
 
+def _adjoint(case, y):
+    """A*(y) = sum_k y_k A_k, A_k symmetric with a at (i, j) and (j, i)."""
+    n = case["n"]
+    M = S.zeros(n, n)
+    for k, i, j, a in case["triplets"]:
+        M[i, j] += y[k] * a
+        if i != j:
+            M[j, i] += y[k] * a
+    return M
+
+
+def _errors(case, R, y):
+    X = R * R.T
+    n = case["n"]
+    z = [zk - bk for zk, bk in zip(_constraint_map(case, X), case["b"])]
+    obj = sum(case["C"][i, j] * X[i, j] for i in range(n) for j in range(n))
+    dual = sum(S.nsimplify(bk) * yk for bk, yk in zip(case["b"], y))
+    bmax = max(abs(S.nsimplify(v)) for v in case["b"])
+    b1 = sum(abs(S.nsimplify(v)) for v in case["b"])
+    znorm = S.sqrt(sum(zk * zk for zk in z))
+    slack = case["C"] - _adjoint(case, y)
+    lam = S.Symbol("lam")
+    roots = S.Poly(slack.charpoly(lam).as_expr(), lam).nroots(n=30)
+    smin = min(S.re(v) for v in roots)
+    c1 = sum(abs(case["C"][i, j]) for i in range(n) for j in range(n))
+    return dict(obj=obj, by=dual, err1=(znorm / (1 + bmax)).evalf(30), err1_l1=(znorm / (1 + b1)).evalf(30),
+                err3=(obj - dual) / (1 + abs(obj) + abs(dual)), smin=smin,
+                err2=(abs(min(S.Integer(0), smin)) / (1 + c1)).evalf(30))
+
+
 def _block(rows) -> str:
     return "; ".join(" ".join(_frac(v) for v in row) for row in rows)
 
@@ -108,6 +144,7 @@ def main() -> None:
         "# L = <C,RR^T> - y^T(A(RR^T)-b) + rho/2||A(RR^T)-b||^2  (Sec. 2, Eq. (1.2), y = -lambda);",
         "# a1..a4: L(R + tau D) - L(R) = a1 tau^4 + a2 tau^3 + a3 tau^2 + a4 tau  (App. A.2);",
         "# G = dL/dR; z = A(RR^T).  Matrices: rows separated by ';'.",
+        "# obj = <C,RR^T>, by = b^T y, err1/err1_l1/err3/err2 of Sec. 4.2, smin = sigma_min(C - A*(y)).",
     ]
     for case in _cases():
         n = case["n"]
@@ -135,6 +172,9 @@ def main() -> None:
                   f"rho {_frac(rho)}", f"L {_frac(L0)}",
                   "a " + " ".join(_frac(c) for c in coeffs),
                   f"G {_block(G)}", "z " + " ".join(_frac(v) for v in z)]
+        e = _errors(case, R, y)
+        lines += [f"obj {_frac(e['obj'])}", f"by {_frac(e['by'])}", f"err1 {e['err1']}", f"err1_l1 {e['err1_l1']}",
+                  f"err3 {_frac(e['err3'])}", f"smin {S.N(e['smin'], 30)}", f"err2 {e['err2']}"]
     (HERE / "lagrangian_exact.txt").write_text("\n".join(lines) + "\n")
     vals = ["# Closed-form MaxCut SDP values, unit weights (written by tests/golden/make_golden.py).",
             "# family size value expression"]

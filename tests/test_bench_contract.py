@@ -48,3 +48,28 @@ def test_algorithmic_bytes_of_the_benchmark_kernels():
     # line-search SpMM: column indices + FP32 values, row pointers, own D and C D rows,
     # R row (8 B), per-row scalars
     assert kb("k_spmm_c(CD,ls)") == nnz * 8 + (n + 1) * 8 + n * ld * (2 * 4 + 8) + n * per_row == 4_600_000_008
+
+
+def _bench():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench", ROOT / "bench.py")
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    return bench
+
+
+def test_default_run_fits_the_driver_limit():
+    """The driver runs `bench.py --gpus 1 --steps 20 --warmup 5` under an 1800 s
+    limit.  From the last measured solve time, the fixed legs, the capped warm-up
+    solves, the timed solves the budget admits and the e2e solve stay well inside
+    it; and even a solve twice as slow cannot push the run past the limit, because
+    the timed loop starts no solve that would end past its budget."""
+    bench = _bench()
+    per = bench.MEASURED_SOLVE_S["maxcut_er_1e7"]
+    budget = bench.DEFAULT_TIME_BUDGET_S
+    plan = bench.plan_seconds(20, 5, per, budget)
+    assert plan["fits_in_driver_run"], plan
+    assert plan["timed_steps"] >= 10
+    slow = bench.plan_seconds(20, 5, 2 * per, budget)
+    assert slow["total_s"] <= bench.DRIVER_LIMIT_S, slow
+    assert bench.plan_seconds(20, 5, 40.0, budget)["timed_steps"] == 20

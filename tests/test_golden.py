@@ -85,3 +85,23 @@ def test_oracle_matches_exact_definitions(case):
     a_exact = np.array([_num(t) for t in case["a"].split()])
     a, _ = O.linesearch_coeffs(P, R, D, y, rho)
     np.testing.assert_allclose(a, a_exact, rtol=1e-14, atol=1e-13)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c["name"] for c in CASES])
+def test_error_measures_match_exact_values(case):
+    """errors() against Sec. 4.2's measures evaluated exactly (sympy): <C,X> and
+    b^T y as fractions, err1 in both normalisations, the signed err3, and err2
+    from the smallest root of the exact characteristic polynomial of C - A*(y).
+    A wrong denominator, a sign of err3 or of y in the dual slack, or a dropped
+    off-diagonal half of A*(y) fails one of them."""
+    P = O.Problem(_instance(case))
+    R = _matrix(case["R"])
+    y = np.array([_num(t) for t in case["y"].split()])
+    e = O.errors(P, R, y, with_err2=True)
+    assert e["primal_obj"] == pytest.approx(_num(case["obj"]), rel=1e-14, abs=1e-14)
+    assert e["dual_obj"] == pytest.approx(_num(case["by"]), rel=1e-14, abs=1e-14)
+    assert e["err1"] == pytest.approx(float(case["err1"]), rel=1e-14)
+    assert e["err1_l1"] == pytest.approx(float(case["err1_l1"]), rel=1e-14)
+    assert e["err3"] == pytest.approx(_num(case["err3"]), rel=1e-14, abs=1e-15)
+    assert e["sigma_min"] == pytest.approx(float(case["smin"]), rel=1e-12, abs=1e-13)
+    assert e["err2"] == pytest.approx(float(case["err2"]), rel=1e-12, abs=1e-13)

@@ -265,3 +265,36 @@ def test_prefetch_variant_follows_oracle_trajectory():
     res, R, y = _gpu_solve(inst, R0, prec="fp64", kernel_variant=2 | 8 | 16, **caps)
     assert res["inner_iters"] == ref["inner"]
     assert np.max(np.abs(R - ref["R"])) <= 1e-9 * np.abs(ref["R"]).max()
+
+
+# ---- Algorithm 1 as printed: initial matrix H0 = I (lbfgs_scaling = 0)
+
+@pytest.mark.parametrize("k", [1, 5, 30])
+@pytest.mark.parametrize("kind", ["maxcut", "mc"])
+def test_trajectory_literal_lbfgs_matches_oracle(kind, k):
+    """With the identity as the initial matrix of the two-loop recursion (the
+    form Algorithm 1 prints), the GPU iterate follows the oracle's."""
+    if kind == "maxcut":
+        inst = W.maxcut_instance(1000, W.er_graph(1000, 4000, 0, "unit"))
+        R0 = W.initial_factor(inst, 10, 1)
+    else:
+        inst = W.mc_instance(60, 80, 3, 2500, seed=2)
+        R0 = W.initial_factor(inst, 12, 4)
+    caps = dict(max_outer=1, max_inner=k, tol=1e-300, lbfgs_scaling=0)
+    ref = O.solve(O.Problem(inst), R0, O.Params(**caps))
+    res, R, y = _gpu_solve(inst, R0, **caps)
+    assert res["inner_iters"] == ref["inner"]
+    assert np.max(np.abs(R - ref["R"])) <= 1e-9 * np.abs(ref["R"]).max() * max(1, k / 10)
+    assert np.max(np.abs(y - ref["y"])) <= 1e-8 * (1 + np.abs(ref["y"]).max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_literal_lbfgs_converges_to_oracle_objective(prec):
+    """Algorithm 1 as printed (H0 = I), run to rel. KKT 1e-5 on ER n = 1000 at
+    r = 30: both sides reach the SDP optimum and agree to 1e-5."""
+    n = 1000
+    inst = W.maxcut_instance(n, W.er_graph(n, 4 * n, 0, "unit"))
+    ref, res, R, y = _converged_pair(inst, 30, 1, prec=prec, lbfgs_scaling=0)
+    assert ref["status"] == "ok" and res["status_name"] == "LORADS_OK", res
+    assert res["err1"] <= 1e-5 and abs(res["err3"]) <= 1e-5
+    assert res["primal_obj"] == pytest.approx(ref["primal_obj"], rel=1e-5)

@@ -1,8 +1,11 @@
 """lorads_linesearch_coeffs_noalloc: the context-free line-search entry point for
 callers that cannot allocate device memory (graph capture, foreign allocators,
 latency-critical loops).  Its scratch is a fixed device array inside the
-library, so the test checks it against the context entry point on two calls
-in a row (the second sees the first call's leftovers in that array).
+library, so the test checks it against the context entry point and against
+the FP64 oracle's coefficients of App. A.2 on two calls in a row (the second
+sees the first call's leftovers in that array), on small instances and on one
+of 300,000 rows, where both reduction grids hit the 1024-block cap and every
+block's grid-stride loop covers several row tiles.
 
 This file is named to be collected last.
 """
@@ -33,12 +36,20 @@ def _scales(P, R, D, y, rho):
                      2 * float(np.sum(CRabs * np.abs(D))) + float(w @ np.abs(q1))])
 
 
-@pytest.mark.parametrize("name", ["mixed_1031", "maxcut_er_2001"])
+def _instance(name):
+    if name == "mixed_1031":
+        return mixed_instance(1031, seed=9)
+    if name == "maxcut_er_2001":
+        return W.maxcut_instance(2001, W.er_graph(2001, 4002, 3, "pm1"))
+    # 300,000 rows at ld = 12: 64 rows per 256-thread block, 4,688 row tiles > 1024 blocks
+    return W.maxcut_instance(300_000, W.er_graph(300_000, 600_000, 7, "pm1"))
+
+
+@pytest.mark.parametrize("name", ["mixed_1031", "maxcut_er_2001", "maxcut_er_300000"])
 def test_noalloc_matches_context_entry_point(name):
     L.build()
     lib = L.load()
-    inst = (mixed_instance(1031, seed=9) if name == "mixed_1031"
-            else W.maxcut_instance(2001, W.er_graph(2001, 4002, 3, "pm1")))
+    inst = _instance(name)
     P = O.Problem(inst)
     r = 10
     ld = L.padded_ld(r)
@@ -77,6 +88,9 @@ def test_noalloc_matches_context_entry_point(name):
             scale = _scales(P, Rh, Dh, yh, rho)
             assert np.all(np.abs(got[:4] - a_ref) <= 1e-12 * scale), (call, got[:4], a_ref)
             assert got[4] == pytest.approx(tau_ref, rel=1e-9, abs=1e-300)
+            a_orc, _ = O.linesearch_coeffs(P, Rh, Dh, yh, rho)
+            assert np.all(np.abs(got[:4] - a_orc) <= 1e-12 * scale), (call, got[:4], a_orc)
+            assert got[4] == pytest.approx(O.quartic_step(a_orc), rel=1e-9, abs=1e-300)
     finally:
         L.lorads_destroy(ctx)
 
