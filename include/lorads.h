@@ -114,6 +114,12 @@ typedef struct {
     int32_t inner_scale;       /* inner stop ||G||_F <= thr, z = A(RR^T) - b, e = tol (1 + ||b||_inf):
                                   0: thr = inner_rel max(||z||, e);  1: thr = inner_rel max(rho ||z||, e);
                                   2 (default): thr = max(e, min(inner_rel rho ||z||, inner_progress ||G_0||)) */
+    double  admm_switch;       /* two-stage solve (Sec. 2): 0 (default) runs the ALM stage alone; > 0 stops the
+                                  ALM stage once err1 and |err3| <= max(admm_switch, tol) and finishes with the
+                                  splitting ADMM stage of Sec. 2.2 from U = V = R, the ALM stage's y and rho */
+    double  cg_rel;            /* ADMM block steps: conjugate gradients (Algorithm 2) stop at ||r|| <= cg_rel ||r_0|| (1e-2) */
+    int32_t cg_max;            /* ... or after cg_max steps (50) */
+    int32_t admm_max_iter;     /* ADMM iterations (U step, V step, multiplier step) at most (20000) */
 } lorads_params;
 
 typedef struct {
@@ -130,6 +136,8 @@ typedef struct {
     int32_t inner_iters;       /* L-BFGS directions computed, all outer steps */
     int32_t status;            /* lorads_status of the solve */
     int64_t kernel_launches;   /* kernels this library launched during the solve (graph nodes included) */
+    int32_t admm_iters;        /* iterations of the ADMM stage (0: the ALM stage met the tolerance or admm_switch = 0) */
+    int32_t cg_steps;          /* conjugate-gradient steps of the ADMM stage, both block steps summed */
 } lorads_result;
 
 /* Fills *p with the defaults listed above. */
@@ -197,6 +205,40 @@ lorads_status lorads_linesearch_coeffs(lorads_ctx* ctx, const void* R, const voi
  * The solution stays in the context (lorads_get_solution). Synchronous. */
 lorads_status lorads_solve(lorads_ctx* ctx, const double* R0, int32_t r0, int32_t r0_on_device,
                            const double* y0, lorads_result* res);
+
+/* ------------------------------------------------------------------ splitting (ADMM) stage
+ * Sec. 2.2: with X = U V^T and L_rho(U, V, y) = <C, U V^T> - y^T (A(U V^T) - b)
+ * + rho/2 ||A(U V^T) - b||^2 + rho/2 ||U - V||_F^2 (Eq. (1.3) in the sign of y), the steps of
+ * Eq. (2.2) are U <- argmin_U L_rho, V <- argmin_V L_rho, y <- y - rho (A(U V^T) - b); each
+ * argmin is the positive definite system of Eq. (2.3), for the U step
+ *     frakA_V(U) = rho A*(A(U V^T)) V + rho U  =  frakb_V = -C V + A*(y) V + rho A*(b) V + rho V,
+ * solved by the conjugate gradients of Algorithm 2 from the current iterate (the V step
+ * exchanges U and V).  The stage reports R = (U + V)/2 and stops when err1 and |err3| of
+ * Sec. 4.2 at R are <= tol. */
+
+/* out = frakA_V(X) = rho A*(A(X V^T)) V + rho X (the left side of Eq. (2.3)).
+ *   V, X, out   device, n x ld, double (prec LORADS_FP64) or float (LORADS_FP32); out must
+ *               alias neither V nor X.   rho > 0.
+ * Asynchronous on the context stream; allocates nothing. */
+lorads_status lorads_admm_operator(lorads_ctx* ctx, const void* V, const void* X, int32_t r, int32_t ld,
+                                   double rho, void* out, int32_t prec);
+
+/* Solves frakA_V(X) = frakb_V(y) by Algorithm 2 in place, from the X given: stops at
+ * ||r|| <= cg_rel ||r_0|| or after cg_max steps (the parameters of the stage).
+ *   V, X        device, n x ld, double (LORADS_FP64) or float (LORADS_FP32); X is overwritten.
+ *   y           device double[m].   rho > 0.   steps_out (host, may be NULL): CG steps taken.
+ * The work arrays (three n x ld vectors and one m-vector) are allocated on the first call
+ * and kept by the context for later calls and solves.  Synchronous. */
+lorads_status lorads_admm_cg(lorads_ctx* ctx, const void* V, void* X, const double* y, double rho, int32_t r,
+                             int32_t ld, double cg_rel, int32_t cg_max, int32_t* steps_out, int32_t prec);
+
+/* Runs the ADMM stage alone from U = V = R0 with multiplier y0 and penalty rho (held fixed),
+ * in the precision form of params.prec, for at most params.admm_max_iter iterations with
+ * params.cg_rel / params.cg_max.  R0, r0, r0_on_device, y0 as in lorads_solve (y0 host, NULL:
+ * zeros).  res: R = (U + V)/2 and y stay in the context (lorads_get_solution); inner_iters = 0.
+ * Synchronous. */
+lorads_status lorads_admm_stage(lorads_ctx* ctx, const double* R0, int32_t r0, int32_t r0_on_device,
+                                const double* y0, double rho, lorads_result* res);
 
 /* sigma_min(C - A*(y)), the dual-slack eigenvalue behind err2 of Sec. 4.2 (which the
  * paper evaluates on the CPU), by a `steps`-step Lanczos run on the GPU with the

@@ -8,7 +8,7 @@ from . import _native
 from ._native import (  # noqa: F401
     LoradsError, default_params, lorads_create, lorads_destroy, lorads_spmm, lorads_constraint_eval,
     lorads_linesearch_coeffs, lorads_solve, lorads_get_solution, lorads_problem_info, padded_ld,
-    lorads_kernel_times, lorads_dual_min_eig,
+    lorads_kernel_times, lorads_dual_min_eig, lorads_admm_operator, lorads_admm_cg, lorads_admm_stage,
     lorads_batch_create, lorads_batch_solve, lorads_batch_tune, lorads_batch_set_shape,
     lorads_batch_get_solution, lorads_batch_destroy, lorads_batch_phase_times,
     lorads_gnn_param_count, lorads_gnn_create, lorads_gnn_get_params, lorads_gnn_set_params, lorads_gnn_predict,
@@ -21,7 +21,8 @@ __all__ = [
     "lorads_constraint_eval", "lorads_linesearch_coeffs", "lorads_solve", "lorads_get_solution",
     "lorads_problem_info", "padded_ld", "load", "build", "lorads_kernel_times", "lorads_dual_min_eig",
     "lorads_batch_create", "lorads_batch_solve", "lorads_batch_tune", "lorads_batch_set_shape",
-    "lorads_batch_get_solution", "lorads_batch_destroy",
+    "lorads_batch_get_solution", "lorads_batch_destroy", "lorads_admm_operator", "lorads_admm_cg",
+    "lorads_admm_stage",
 ]
 
 

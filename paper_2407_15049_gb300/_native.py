@@ -41,7 +41,8 @@ class lorads_params(C.Structure):
         ("check_every", C.c_int32), ("seed", C.c_uint64), ("compute_err2", C.c_int32),
         ("lanczos_steps", C.c_int32), ("verbose", C.c_int32), ("reserved", C.c_int32),
         ("lbfgs_scaling", C.c_int32), ("rho_policy", C.c_int32), ("kernel_variant", C.c_int32),
-        ("inner_scale", C.c_int32),
+        ("inner_scale", C.c_int32), ("admm_switch", C.c_double), ("cg_rel", C.c_double), ("cg_max", C.c_int32),
+        ("admm_max_iter", C.c_int32),
     ]
 
 
@@ -51,6 +52,7 @@ class lorads_result(C.Structure):
         ("err2", C.c_double), ("err3", C.c_double), ("sigma_min", C.c_double), ("rho", C.c_double),
         ("seconds", C.c_double), ("rank", C.c_int32), ("outer_iters", C.c_int32),
         ("inner_iters", C.c_int32), ("status", C.c_int32), ("kernel_launches", C.c_int64),
+        ("admm_iters", C.c_int32), ("cg_steps", C.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -102,6 +104,10 @@ SIGNATURES = {
                                                    _VP, _VP, C.c_int32, C.c_int32, _VP, C.c_double, _VP, _VP]),
     "lorads_noalloc_error": (C.c_char_p, []),
     "lorads_dual_min_eig": (C.c_int, [_VP, _VP, C.c_int32, C.c_uint64, _DP]),
+    "lorads_admm_operator": (C.c_int, [_VP, _VP, _VP, C.c_int32, C.c_int32, C.c_double, _VP, C.c_int32]),
+    "lorads_admm_cg": (C.c_int, [_VP, _VP, _VP, _VP, C.c_double, C.c_int32, C.c_int32, C.c_double, C.c_int32,
+                                 _I32P, C.c_int32]),
+    "lorads_admm_stage": (C.c_int, [_VP, _VP, C.c_int32, C.c_int32, _VP, C.c_double, C.POINTER(lorads_result)]),
     "lorads_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, _I64P, _I64P, _I64P, _I32P, _DP, _I32P,
                                       _I32P, _I32P, _DP, _DP, _I32P, _DP, C.POINTER(lorads_params), C.c_void_p]),
     "lorads_batch_solve": (C.c_int, [_VP, C.POINTER(lorads_result), C.POINTER(lorads_batch_stats)]),
@@ -266,6 +272,47 @@ def lorads_solve(ctx, R0=None, y0: np.ndarray | None = None, r0: int = 0, on_dev
     out = res.as_dict()
     out["status_name"] = STATUS_NAMES.get(res.status, str(res.status))
     if st not in (LORADS_OK, 5, 6, 7) or (raise_on_status and st != LORADS_OK):
+        _check(ctx, st)
+    return out
+
+
+def lorads_admm_operator(ctx, V, X, out, rho: float, r: int | None = None) -> None:
+    """out = rho A*(A(X V^T)) V + rho X on device tensors (n x ld, float64 or float32)."""
+    ld = V.shape[1]
+    _check(ctx, load().lorads_admm_operator(ctx, _dptr(V), _dptr(X), int(r or ld), int(ld), float(rho), _dptr(out),
+                                            _prec_of(V)))
+
+
+def lorads_admm_cg(ctx, V, X, y, rho: float, cg_rel: float = 1e-2, cg_max: int = 50, r: int | None = None) -> int:
+    """Solves rho A*(A(X V^T)) V + rho X = -C V + A*(y) V + rho A*(b) V + rho V by CG in
+    place from X; returns the number of CG steps."""
+    ld = V.shape[1]
+    steps = C.c_int32()
+    _check(ctx, load().lorads_admm_cg(ctx, _dptr(V), _dptr(X), _dptr(y), float(rho), int(r or ld), int(ld),
+                                      float(cg_rel), int(cg_max), C.byref(steps), _prec_of(V)))
+    return steps.value
+
+
+def lorads_admm_stage(ctx, R0, y0: np.ndarray | None, rho: float, on_device: bool = False) -> dict:
+    """Runs the ADMM stage alone from U = V = R0, multiplier y0 and penalty rho."""
+    lib = load()
+    res = lorads_result()
+    keep = []
+    if on_device or not isinstance(R0, np.ndarray):
+        rp, r0v, dev = C.c_void_p(_dptr(R0)), int(R0.shape[1]), 1
+    else:
+        R0 = np.ascontiguousarray(R0, dtype=np.float64)
+        keep.append(R0)
+        rp, r0v, dev = C.c_void_p(R0.ctypes.data), int(R0.shape[1]), 0
+    yp = None
+    if y0 is not None:
+        y0 = np.ascontiguousarray(y0, dtype=np.float64)
+        keep.append(y0)
+        yp = C.c_void_p(y0.ctypes.data)
+    st = lib.lorads_admm_stage(ctx, rp, r0v, dev, yp, float(rho), C.byref(res))
+    out = res.as_dict()
+    out["status_name"] = STATUS_NAMES.get(res.status, str(res.status))
+    if st not in (LORADS_OK, 5, 6, 7):
         _check(ctx, st)
     return out
 

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/lorads.h"
+#include "admm.h"
 #include "common.cuh"
 #include "control.h"
 #include "kernels.cuh"
@@ -50,6 +51,24 @@ struct SolverState {
     double* zk = nullptr;               // same for the off-diagonal constraints (by constraint)
     cudaGraphExec_t exec = nullptr;
     bool have_solution = false;
+};
+
+// Work arrays of the splitting (ADMM) stage: block iterates U, V (type of R),
+// CG vectors r, p, Q (work type), the m-vector w = y - rho (A(X V^T) - b) and
+// the stage's device control block; one captured graph per ADMM iteration.
+struct AdmmState {
+    int rtype = -1, wtype = -1, ld = 0;
+    size_t esR = 0, esW = 0;
+    void* U = nullptr;
+    void* V = nullptr;
+    void* r = nullptr;
+    void* p = nullptr;
+    void* Q = nullptr;
+    void* om = nullptr;
+    AdmmCtrl* ac = nullptr;
+    AdmmCtrl* h_ac = nullptr;           // pinned
+    cudaGraphExec_t exec = nullptr;
+    int64_t graph_nodes = 0;
 };
 
 // Per-kernel-family CUDA-event timing of the host-stepped (verbose >= 2) solve.
@@ -110,6 +129,7 @@ struct lorads_ctx {
     Ctrl* ctrl = nullptr;
     Ctrl* h_ctrl = nullptr;             // pinned, 2 slots
     SolverState st;
+    AdmmState admm;
     Prof* prof = nullptr;
     bool prof_valid = false;
     bool prof_active = false;
@@ -236,6 +256,10 @@ extern "C" void lorads_default_params(lorads_params* p) {
     p->rho_policy = 2;
     p->inner_scale = 2;
     p->kernel_variant = 10;
+    p->admm_switch = 0.0;
+    p->cg_rel = 1e-2;
+    p->cg_max = 50;
+    p->admm_max_iter = 20000;
 }
 
 extern "C" const char* lorads_create_error(void) { return g_create_error.c_str(); }
@@ -250,12 +274,19 @@ void free_state(SolverState& st) {
     dfree(st.y); dfree(st.ytil); dfree(st.zrow); dfree(st.zk); dfree(st.ydf);
     st = SolverState();
 }
+void free_admm(AdmmState& a) {
+    if (a.exec) cudaGraphExecDestroy(a.exec);
+    dfree(a.U); dfree(a.V); dfree(a.r); dfree(a.p); dfree(a.Q); dfree(a.om); dfree(a.ac);
+    if (a.h_ac) cudaFreeHost(a.h_ac);
+    a = AdmmState();
+}
 }  // namespace
 
 extern "C" void lorads_destroy(lorads_ctx* ctx) {
     if (!ctx) return;
     if (ctx->solve_stream) cudaStreamSynchronize(ctx->solve_stream);
     free_state(ctx->st);
+    free_admm(ctx->admm);
     dfree(ctx->c_rowptr); dfree(ctx->c_col); dfree(ctx->c_val); dfree(ctx->c_val32); dfree(ctx->c_valdf);
     dfree(ctx->dk); dfree(ctx->da); dfree(ctx->da32); dfree(ctx->da_df); dfree(ctx->b_df);
     dfree(ctx->a_rowptr); dfree(ctx->a_col); dfree(ctx->a_k); dfree(ctx->a_a);
@@ -369,6 +400,12 @@ extern "C" lorads_status lorads_create(lorads_ctx** out, int64_t n, const int64_
         return LORADS_ERR_INVALID_ARG;
     }
     if (ctx->prm.check_every < 1) ctx->prm.check_every = 1;
+    if (!(ctx->prm.admm_switch >= 0.0) || !(ctx->prm.cg_rel > 0.0 && ctx->prm.cg_rel < 1.0) ||
+        ctx->prm.cg_max < 1 || ctx->prm.admm_max_iter < 0) {
+        g_create_error = "need admm_switch >= 0, 0 < cg_rel < 1, cg_max >= 1 and admm_max_iter >= 0";
+        delete ctx;
+        return LORADS_ERR_INVALID_ARG;
+    }
     ctx->stream = static_cast<cudaStream_t>(cuda_stream);
     lorads_status s = validate_and_build(ctx, n, c_rowptr, c_colind, c_val, m, nnz_a, a_con, a_row, a_col, a_val, b);
     if (s == LORADS_OK) s = dalloc(ctx, &ctx->part, (size_t)NPART * ctx->max_blocks * kPartStride);
@@ -828,12 +865,12 @@ lorads_status run_profiled(lorads_ctx* ctx, int prec, std::chrono::steady_clock:
     return fill_result(ctx, t0, timed_out, res);
 }
 
+// Allocates the solver state for the starting rank and loads R <- R0 (or the
+// device random start) and y <- y0 (or 0), with the double-float mirror of y.
 template <typename TR, typename TD, typename TDIR = TD>
-lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0, int32_t r0_on_device,
-                        const double* y0, lorads_result* res) {
-    const auto t0 = std::chrono::steady_clock::now();
+lorads_status start_state(lorads_ctx* ctx, int prec, const double* R0, int32_t r0, int32_t r0_on_device,
+                          const double* y0) {
     const lorads_params& P = ctx->prm;
-    ctx->launches = 0;
     lorads_status s;
     int r = r0;
     if (r <= 0) r = std::max(1, (int)std::ceil(std::log2((double)std::max<int64_t>(ctx->m, 2))));
@@ -866,6 +903,199 @@ lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0,
         convert<double, dfloat>(ss, ctx->m, 1, 1, 1, st.y, st.ydf, flat_blocks(ctx, ctx->m));
         ctx->launches += 1;
     }
+    return check_launch(ctx, "start");
+}
+
+// ---------------------------------------------------------------- ADMM stage (Sec. 2.2)
+template <typename T>
+constexpr int type_code() {
+    return std::is_same<T, double>::value ? 0 : (std::is_same<T, dfloat>::value ? 1 : 2);
+}
+
+template <typename TR, typename TW>
+lorads_status admm_alloc(lorads_ctx* ctx, int ld) {
+    AdmmState& a = ctx->admm;
+    if (a.U && a.rtype == type_code<TR>() && a.wtype == type_code<TW>() && a.ld == ld) return LORADS_OK;
+    free_admm(a);
+    const size_t nl = (size_t)ctx->n * ld;
+    lorads_status s;
+    if ((s = dalloc(ctx, reinterpret_cast<TR**>(&a.U), nl))) return s;
+    if ((s = dalloc(ctx, reinterpret_cast<TR**>(&a.V), nl))) return s;
+    if ((s = dalloc(ctx, reinterpret_cast<TW**>(&a.r), nl))) return s;
+    if ((s = dalloc(ctx, reinterpret_cast<TW**>(&a.p), nl))) return s;
+    if ((s = dalloc(ctx, reinterpret_cast<TW**>(&a.Q), nl))) return s;
+    if ((s = dalloc(ctx, reinterpret_cast<double**>(&a.om), ctx->m))) return s;
+    if ((s = dalloc(ctx, &a.ac, 1))) return s;
+    if (cudaMallocHost(&a.h_ac, sizeof(AdmmCtrl)) != cudaSuccess) {
+        cudaGetLastError();
+        a.h_ac = nullptr;
+        return set_err(ctx, "pinned allocation failed"), LORADS_ERR_OOM;
+    }
+    CK(cudaMemset(a.r, 0, nl * sizeof(TW)));
+    CK(cudaMemset(a.p, 0, nl * sizeof(TW)));
+    CK(cudaMemset(a.Q, 0, nl * sizeof(TW)));
+    a.rtype = type_code<TR>();
+    a.wtype = type_code<TW>();
+    a.ld = ld;
+    a.esR = sizeof(TR);
+    a.esW = sizeof(TW);
+    return LORADS_OK;
+}
+
+AdmmRows admm_rows(const lorads_ctx* ctx, int ld, const Shape& sh, cudaStream_t s) {
+    AdmmRows r;
+    r.p = &ctx->pd;
+    r.ld = ld;
+    r.sh = sh;
+    r.nb_rows = row_blocks(ctx, ctx->n, sh.L);
+    r.nb_cons = row_blocks(ctx, ctx->m, sh.L);
+    r.nb_flat = flat_blocks(ctx, ctx->n * (int64_t)ld / 4);
+    r.stream = s;
+    return r;
+}
+
+// One block step of Eq. (2.2): X <- the CG solution of frakA_Vf(X) = frakb_Vf(y)
+// (Algorithm 2 from the current X, at most cg_max steps).  Returns kernels enqueued.
+template <typename TR, typename TW>
+int64_t admm_enqueue_block(lorads_ctx* ctx, const AdmmRows& rows, void* X, const void* Vf, double* y,
+                           dfloat* ydf, int cg_max) {
+    AdmmState& a = ctx->admm;
+    cudaStream_t s = rows.stream;
+    double* pr = part_of(ctx, PART_LS);
+    double* pq = part_of(ctx, PART_DIR);
+    double* pu = part_of(ctx, PART_UPD);
+    admm_omega<TR>(rows, X, Vf, y, ydf, a.om, a.ac);
+    admm_resid<TR, TW>(rows, X, Vf, a.om, a.r, a.p, a.ac, pr);
+    admm_cg_init(s, a.ac, pr, rows.nb_rows);
+    for (int k = 0; k < cg_max; ++k) {
+        admm_op<TR, TW>(rows, Vf, a.r, a.p, a.Q, a.ac, 0.0, 1, pq);
+        admm_alpha(s, a.ac, pq, rows.nb_rows);
+        admm_upd<TR, TW>(rows, X, a.p, a.r, a.Q, a.ac, pu);
+        admm_beta(s, a.ac, pu, rows.nb_flat);
+    }
+    return 3 + (int64_t)cg_max * (ctx->m_off ? 5 : 4);
+}
+
+// Multiplier step and the errors of Sec. 4.2 at R = (U + V)/2.
+template <typename TR>
+int64_t admm_enqueue_outer(lorads_ctx* ctx, const AdmmRows& rows) {
+    AdmmState& a = ctx->admm;
+    SolverState& st = ctx->st;
+    cudaStream_t s = rows.stream;
+    admm_yupd<TR>(rows, a.U, a.V, st.y, st.ydf, a.ac, part_of(ctx, PART_YTIL));
+    admm_avg<TR>(rows, a.U, a.V, st.R);
+    SpmmCArgs o{ctx->pd, st.R, st.CR, rows.ld, rows.sh, nullptr, 1, EPI_OBJ, st.R, st.y, nullptr, nullptr, nullptr,
+                0.0, part_of(ctx, PART_OBJ), rows.nb_rows, nullptr, PH_ALWAYS, s};
+    launch_spmm_c<TR, TR, TR>(o);
+    ConsArgs z{ctx->pd, CONS_ZZ, 0, ctx->m, st.R, st.R, rows.ld, rows.sh, nullptr, nullptr, nullptr, nullptr,
+               nullptr, 0.0, part_of(ctx, PART_CONS), rows.nb_cons, nullptr, PH_ALWAYS, s};
+    launch_cons<TR, TR>(z);
+    admm_outer(s, a.ac, part_of(ctx, PART_YTIL), rows.nb_cons, part_of(ctx, PART_CONS), rows.nb_cons,
+               part_of(ctx, PART_OBJ), rows.nb_rows);
+    return 5;
+}
+
+// The ADMM stage from U = V = R (the solver state), multiplier y of the state,
+// penalty rho (fixed): one captured graph per ADMM iteration (U step, V step,
+// multiplier step and errors), launched until the device control block says done.
+template <typename TR, typename TW>
+lorads_status run_admm(lorads_ctx* ctx, double rho, std::chrono::steady_clock::time_point t0, lorads_result* res) {
+    SolverState& st = ctx->st;
+    const lorads_params& P = ctx->prm;
+    lorads_status s;
+    if ((s = admm_alloc<TR, TW>(ctx, st.ld))) return s;
+    AdmmState& a = ctx->admm;
+    cudaStream_t ss = ctx->solve_stream;
+    const size_t bytes = (size_t)ctx->n * st.ld * sizeof(TR);
+    CK(cudaMemcpyAsync(a.U, st.R, bytes, cudaMemcpyDeviceToDevice, ss));
+    CK(cudaMemcpyAsync(a.V, st.R, bytes, cudaMemcpyDeviceToDevice, ss));
+    AdmmCtrl h{};
+    h.rho = rho;
+    h.cg_rel = P.cg_rel;
+    h.tol = P.tol;
+    h.bnorm_inf = ctx->bnorm_inf;
+    h.cg_max = P.cg_max;
+    h.max_iter = P.admm_max_iter;
+    h.status = LORADS_ERR_MAXITER;
+    CK(cudaMemcpyAsync(a.ac, &h, sizeof(AdmmCtrl), cudaMemcpyHostToDevice, ss));
+    *a.h_ac = h;
+    bool timed_out = false;
+    if (P.admm_max_iter > 0) {
+        if (a.exec) {
+            cudaGraphExecDestroy(a.exec);
+            a.exec = nullptr;
+        }
+        const AdmmRows rows = admm_rows(ctx, st.ld, st.sh, ss);
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(ss, cudaStreamCaptureModeThreadLocal));
+        int64_t nodes = admm_enqueue_block<TR, TW>(ctx, rows, a.U, a.V, st.y, st.ydf, P.cg_max);
+        nodes += admm_enqueue_block<TR, TW>(ctx, rows, a.V, a.U, st.y, st.ydf, P.cg_max);
+        nodes += admm_enqueue_outer<TR>(ctx, rows);
+        cudaError_t e = cudaStreamEndCapture(ss, &g);
+        if (e != cudaSuccess) {
+            ctx->err = std::string("ADMM graph capture: ") + cudaGetErrorString(e);
+            cudaGetLastError();
+            return LORADS_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&a.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ctx->err = std::string("ADMM graph instantiate: ") + cudaGetErrorString(e);
+            return LORADS_ERR_CUDA;
+        }
+        a.graph_nodes = nodes;
+        for (;;) {
+            CK(cudaGraphLaunch(a.exec, ss));
+            ctx->launches += a.graph_nodes;
+            CK(cudaMemcpyAsync(a.h_ac, a.ac, sizeof(AdmmCtrl), cudaMemcpyDeviceToHost, ss));
+            CK(cudaStreamSynchronize(ss));
+            const AdmmCtrl& hc = *a.h_ac;
+            if (P.verbose == 1)
+                std::fprintf(stderr, "[lorads] admm %d cg %d err1 %.3e err3 %.3e obj %.10g t %.3fs\n", hc.iters,
+                             hc.cg_total, hc.err1, hc.err3, hc.primal_obj,
+                             std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+            if (hc.done) break;
+            if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > P.time_limit) {
+                timed_out = true;
+                break;
+            }
+        }
+    }
+    st.have_solution = true;
+    const AdmmCtrl& hc = *a.h_ac;
+    const lorads_status fs = timed_out ? LORADS_ERR_TIMEOUT : (lorads_status)hc.status;
+    if (res) {
+        if (hc.iters > 0) {
+            res->primal_obj = hc.primal_obj;
+            res->dual_obj = hc.dual_obj;
+            res->err1 = hc.err1;
+            res->err3 = hc.err3;
+        }
+        res->rho = rho;
+        res->rank = st.r;
+        res->admm_iters = hc.iters;
+        res->cg_steps = hc.cg_total;
+        res->status = fs;
+        res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        res->kernel_launches = ctx->launches;
+    }
+    return fs;
+}
+
+template <typename TR, typename TD, typename TDIR>
+lorads_status run_graph(lorads_ctx* ctx, int prec, std::chrono::steady_clock::time_point t0, lorads_result* res);
+
+template <typename TR, typename TD, typename TDIR = TD>
+lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0, int32_t r0_on_device,
+                        const double* y0, lorads_result* res) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const lorads_params& P = ctx->prm;
+    ctx->launches = 0;
+    lorads_status s;
+    if ((s = start_state<TR, TD, TDIR>(ctx, prec, R0, r0, r0_on_device, y0))) return s;
+    cudaStream_t ss = ctx->solve_stream;
+    // two-stage solve: the ALM stage stops at the switch tolerance
+    const double alm_tol = P.admm_switch > 0 ? std::max(P.admm_switch, P.tol) : P.tol;
     // control block
     Ctrl h{};
     h.rho = P.rho0 > 0 ? P.rho0 : 1.0 / ctx->mean_abs_c;
@@ -877,7 +1107,7 @@ lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0,
     h.lbfgs_scaling = P.lbfgs_scaling;
     h.rho_policy = P.rho_policy;
     h.inner_scale = P.inner_scale;
-    h.tol = P.tol;
+    h.tol = alm_tol;
     h.inner_rel = P.inner_rel;
     h.inner_progress = P.inner_progress;
     h.bnorm1 = ctx->bnorm1;
@@ -893,7 +1123,24 @@ lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0,
         drv.enqueue_init();
     }
     if ((s = check_launch(ctx, "solve init"))) return s;
-    if (P.verbose >= 2) return run_profiled<TR, TD, TDIR>(ctx, prec, t0, res);
+    lorads_result alm{};
+    lorads_status fs;
+    if (P.verbose >= 2) fs = run_profiled<TR, TD, TDIR>(ctx, prec, t0, &alm);
+    else fs = run_graph<TR, TD, TDIR>(ctx, prec, t0, &alm);
+    if (fs == LORADS_OK && P.admm_switch > 0 && !(alm.err1 <= P.tol && std::fabs(alm.err3) <= P.tol))
+        fs = run_admm<TR, TD>(ctx, alm.rho, t0, &alm);
+    if (res) *res = alm;
+    return fs;
+}
+
+// The ALM stage on the captured iteration graph: launch it in batches, poll the
+// status of the previous batch, grow the rank when the device asks.
+template <typename TR, typename TD, typename TDIR>
+lorads_status run_graph(lorads_ctx* ctx, int prec, std::chrono::steady_clock::time_point t0, lorads_result* res) {
+    const lorads_params& P = ctx->prm;
+    SolverState& st = ctx->st;
+    cudaStream_t ss = ctx->solve_stream;
+    lorads_status s;
     if ((s = capture<TR, TD, TDIR>(ctx))) return s;
     // ---- iterate: launch the graph in batches, poll the status of the previous batch
     int slot = 0;
@@ -945,6 +1192,7 @@ lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0,
 
 namespace {
 lorads_status run_lanczos(lorads_ctx* ctx, const double* ydev, int k, uint64_t seed, double* sigma_out);
+lorads_status finish_err2(lorads_ctx* ctx, lorads_status s, lorads_result* res);
 }  // namespace
 
 extern "C" lorads_status lorads_solve(lorads_ctx* ctx, const double* R0, int32_t r0, int32_t r0_on_device,
@@ -966,8 +1214,14 @@ extern "C" lorads_status lorads_solve(lorads_ctx* ctx, const double* R0, int32_t
             return set_err(ctx, "params.prec must be FP64, MIXED, DF64, FP32 or MIXED_BF16 for lorads_solve"),
                    LORADS_ERR_INVALID_ARG;
     }
+    return finish_err2(ctx, s, res);
+}
+
+namespace {
+
+// err2 of Sec. 4.2 at the returned multiplier: sigma_min(C - A*(y)) by Lanczos.
+lorads_status finish_err2(lorads_ctx* ctx, lorads_status s, lorads_result* res) {
     if (res && res->status == 0 && s != LORADS_OK) res->status = s;
-    // err2 of Sec. 4.2 at the returned multiplier: sigma_min(C - A*(y)) by Lanczos
     if (ctx->prm.compute_err2 && ctx->st.have_solution && (s == LORADS_OK || s == LORADS_ERR_MAXITER)) {
         double sig = 0.0;
         const lorads_status ls = run_lanczos(ctx, ctx->st.y, ctx->prm.lanczos_steps, ctx->prm.seed, &sig);
@@ -979,6 +1233,110 @@ extern "C" lorads_status lorads_solve(lorads_ctx* ctx, const double* R0, int32_t
         }
     }
     return s;
+}
+
+template <typename TR, typename TD, typename TDIR = TD>
+lorads_status run_stage(lorads_ctx* ctx, int prec, const double* R0, int32_t r0, int32_t r0_on_device,
+                        const double* y0, double rho, lorads_result* res) {
+    const auto t0 = std::chrono::steady_clock::now();
+    ctx->launches = 0;
+    lorads_status s;
+    if ((s = start_state<TR, TD, TDIR>(ctx, prec, R0, r0, r0_on_device, y0))) return s;
+    lorads_result out{};
+    s = run_admm<TR, TD>(ctx, rho, t0, &out);
+    if (res) *res = out;
+    return s;
+}
+
+template <typename TR, typename TW>
+lorads_status run_admm_cg(lorads_ctx* ctx, const void* V, void* X, const double* y, double rho, int ld,
+                          const Shape& sh, double cg_rel, int cg_max, int32_t* steps_out) {
+    lorads_status s;
+    if ((s = admm_alloc<TR, TW>(ctx, ld))) return s;
+    AdmmState& a = ctx->admm;
+    AdmmCtrl h{};
+    h.rho = rho;
+    h.cg_rel = cg_rel;
+    h.cg_max = cg_max;
+    h.tol = ctx->prm.tol;
+    h.bnorm_inf = ctx->bnorm_inf;
+    h.max_iter = 1;
+    h.status = LORADS_OK;
+    CK(cudaMemcpyAsync(a.ac, &h, sizeof(AdmmCtrl), cudaMemcpyHostToDevice, ctx->stream));
+    const AdmmRows rows = admm_rows(ctx, ld, sh, ctx->stream);
+    admm_enqueue_block<TR, TW>(ctx, rows, X, V, const_cast<double*>(y), nullptr, cg_max);
+    if ((s = check_launch(ctx, "lorads_admm_cg launch"))) return s;
+    CK(cudaMemcpyAsync(a.h_ac, a.ac, sizeof(AdmmCtrl), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (steps_out) *steps_out = a.h_ac->cg_k;
+    if (a.h_ac->status == LORADS_ERR_NUMERIC) return set_err(ctx, "non-finite CG residual"), LORADS_ERR_NUMERIC;
+    return LORADS_OK;
+}
+
+lorads_status check_admm_factors(lorads_ctx* ctx, int32_t r, int32_t ld, int32_t prec, double rho, Shape* sh) {
+    lorads_status s = check_factor_args(ctx, r, ld, prec, sh);
+    if (s) return s;
+    if (prec != LORADS_FP64 && prec != LORADS_FP32)
+        return set_err(ctx, "prec must be LORADS_FP64 or LORADS_FP32"), LORADS_ERR_INVALID_ARG;
+    if (!(rho > 0.0) || !std::isfinite(rho)) return set_err(ctx, "rho must be finite and > 0"), LORADS_ERR_INVALID_ARG;
+    return LORADS_OK;
+}
+
+}  // namespace
+
+extern "C" lorads_status lorads_admm_operator(lorads_ctx* ctx, const void* V, const void* X, int32_t r, int32_t ld,
+                                              double rho, void* out, int32_t prec) {
+    if (!ctx) return LORADS_ERR_INVALID_ARG;
+    Shape sh;
+    lorads_status s = check_admm_factors(ctx, r, ld, prec, rho, &sh);
+    if (s) return s;
+    if (!V || !X || !out || !aligned16(V) || !aligned16(X) || !aligned16(out))
+        return set_err(ctx, "V, X and out must be 16-byte aligned device pointers"), LORADS_ERR_INVALID_ARG;
+    if (out == V || out == X) return set_err(ctx, "out must alias neither V nor X"), LORADS_ERR_INVALID_ARG;
+    const AdmmRows rows = admm_rows(ctx, ld, sh, ctx->stream);
+    if (prec == LORADS_FP64)
+        admm_op<double, double>(rows, V, nullptr, const_cast<void*>(X), out, nullptr, rho, 0, part_of(ctx, PART_MISC));
+    else
+        admm_op<float, float>(rows, V, nullptr, const_cast<void*>(X), out, nullptr, rho, 0, part_of(ctx, PART_MISC));
+    return check_launch(ctx, "lorads_admm_operator launch");
+}
+
+extern "C" lorads_status lorads_admm_cg(lorads_ctx* ctx, const void* V, void* X, const double* y, double rho,
+                                        int32_t r, int32_t ld, double cg_rel, int32_t cg_max, int32_t* steps_out,
+                                        int32_t prec) {
+    if (!ctx) return LORADS_ERR_INVALID_ARG;
+    Shape sh;
+    lorads_status s = check_admm_factors(ctx, r, ld, prec, rho, &sh);
+    if (s) return s;
+    if (!V || !X || !y || !aligned16(V) || !aligned16(X))
+        return set_err(ctx, "V, X (16-byte aligned) and y must be device pointers"), LORADS_ERR_INVALID_ARG;
+    if (V == X) return set_err(ctx, "X must not alias V"), LORADS_ERR_INVALID_ARG;
+    if (!(cg_rel > 0.0 && cg_rel < 1.0) || cg_max < 1)
+        return set_err(ctx, "need 0 < cg_rel < 1 and cg_max >= 1"), LORADS_ERR_INVALID_ARG;
+    if (prec == LORADS_FP64) return run_admm_cg<double, double>(ctx, V, X, y, rho, ld, sh, cg_rel, cg_max, steps_out);
+    return run_admm_cg<float, float>(ctx, V, X, y, rho, ld, sh, cg_rel, cg_max, steps_out);
+}
+
+extern "C" lorads_status lorads_admm_stage(lorads_ctx* ctx, const double* R0, int32_t r0, int32_t r0_on_device,
+                                           const double* y0, double rho, lorads_result* res) {
+    if (!ctx) return LORADS_ERR_INVALID_ARG;
+    if (res) std::memset(res, 0, sizeof(*res));
+    if (R0 && r0 < 1) return set_err(ctx, "r0 must be >= 1 when R0 is given"), LORADS_ERR_INVALID_ARG;
+    if (!(rho > 0.0) || !std::isfinite(rho)) return set_err(ctx, "rho must be finite and > 0"), LORADS_ERR_INVALID_ARG;
+    const int prec = ctx->prm.prec;
+    lorads_status s;
+    switch (prec) {
+        case LORADS_FP64: s = run_stage<double, double>(ctx, prec, R0, r0, r0_on_device, y0, rho, res); break;
+        case LORADS_MIXED: s = run_stage<dfloat, float>(ctx, prec, R0, r0, r0_on_device, y0, rho, res); break;
+        case LORADS_DF64: s = run_stage<dfloat, dfloat>(ctx, prec, R0, r0, r0_on_device, y0, rho, res); break;
+        case LORADS_FP32: s = run_stage<float, float>(ctx, prec, R0, r0, r0_on_device, y0, rho, res); break;
+        case LORADS_MIXED_BF16:
+            s = run_stage<dfloat, float, __nv_bfloat16>(ctx, prec, R0, r0, r0_on_device, y0, rho, res);
+            break;
+        default:
+            return set_err(ctx, "params.prec must be FP64, MIXED, DF64, FP32 or MIXED_BF16"), LORADS_ERR_INVALID_ARG;
+    }
+    return finish_err2(ctx, s, res);
 }
 
 extern "C" lorads_status lorads_get_solution(lorads_ctx* ctx, double* R_host, int64_t R_capacity, int32_t* rank_out,
