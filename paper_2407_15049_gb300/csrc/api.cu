@@ -33,6 +33,7 @@ struct SolverState {
     int prec = -1;
     int r = 0, ld = 0;
     Shape sh{1, 1};
+    Shape sh_ls{1, 1};                  // lane shape of the line-search SpMM (kernel_variant bit 5)
     size_t esR = 0, esD = 0;
     int rtype = 0;                      // storage of R: 0 double, 1 double-float, 2 float
     void* R = nullptr;
@@ -546,13 +547,14 @@ struct Driver {
     lorads_ctx* c;
     SolverState& st;
     cudaStream_t s;
-    int nb_rows, nb_flat, nb_off, nb_all;
+    int nb_rows, nb_ls, nb_flat, nb_off, nb_all;
     int64_t nunits;
 
     Driver(lorads_ctx* ctx) : c(ctx), st(ctx->st), s(ctx->solve_stream) { refresh(); }
 
     void refresh() {
         nb_rows = row_blocks(c, c->n, st.sh.L);
+        nb_ls = row_blocks(c, c->n, st.sh_ls.L);
         nunits = c->n * (int64_t)st.ld / 4;
         nb_flat = flat_blocks(c, nunits);
         nb_off = row_blocks(c, std::max<int64_t>(c->m_off, 1), st.sh.L);
@@ -620,8 +622,8 @@ struct Driver {
         DirArgs d{nunits, st.G, st.D, st.hist, st.slot_stride, c->ctrl, part_of(c, PART_DIR), nb_flat, c->ctrl,
                   PH_INNER, s};
         timed(FAM_DIR, [&] { launch_dir<TD, TDIR>(d); });
-        SpmmCArgs ls{p(), st.D, st.CD, st.ld, st.sh, nullptr, 1, EPI_LS, st.R, st.y, st.zrow, st.ydf, c->ctrl, 0.0,
-                     part_of(c, PART_LS), nb_rows, c->ctrl, PH_INNER, s, (c->prm.kernel_variant & 8) ? 1 : 0};
+        SpmmCArgs ls{p(), st.D, st.CD, st.ld, st.sh_ls, nullptr, 1, EPI_LS, st.R, st.y, st.zrow, st.ydf, c->ctrl, 0.0,
+                     part_of(c, PART_LS), nb_ls, c->ctrl, PH_INNER, s, (c->prm.kernel_variant & 8) ? 1 : 0};
         timed(FAM_SPMM_LS, [&] { launch_spmm_c<TDIR, TD, TR>(ls); });
         if (c->m_off) {
             ConsArgs cl{p(), CONS_LS, c->m_diag, c->m, st.R, st.D, st.ld, st.sh, st.y, nullptr, st.zk, st.ydf, c->ctrl, 0.0,
@@ -629,7 +631,7 @@ struct Driver {
             timed(FAM_CONS_LS, [&] { launch_cons<TR, TDIR>(cl); });
         }
         timed(FAM_ROOT, [&] {
-            ctrl_root(s, c->ctrl, part_of(c, PART_DIR), nb_flat, part_of(c, PART_LS), nb_rows,
+            ctrl_root(s, c->ctrl, part_of(c, PART_DIR), nb_flat, part_of(c, PART_LS), nb_ls,
                       c->m_off ? part_of(c, PART_CONS_LS) : nullptr, nb_off);
         });
         if (c->m_off) {
@@ -686,6 +688,8 @@ lorads_status alloc_state(lorads_ctx* ctx, int prec, int r) {
     st.r = r;
     st.ld = ld;
     st.sh = sh;
+    st.sh_ls = sh;
+    if (ctx->prm.kernel_variant & 32) shape_narrow(ld, &st.sh_ls);
     st.esR = sizeof(TR);
     st.esD = sizeof(TD);
     st.rtype = std::is_same<TR, double>::value ? 0 : (std::is_same<TR, dfloat>::value ? 1 : 2);

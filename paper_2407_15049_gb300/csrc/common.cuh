@@ -38,6 +38,29 @@ inline bool shape_for_ld(int ld, Shape* s) {
     return s->CPL <= kMaxCPL;
 }
 
+// Narrow row groups for the gather-bound SpMM: the fewest lanes per row (a
+// power of two, at most kMaxCPL units each) whose idle unit slots do not exceed
+// those of shape_for_ld.  More rows per warp means more independent row gathers
+// in flight (ld = 24: 2 lanes x 3 units, 16 rows per warp, no idle lane, instead
+// of 8 lanes with 2 idle and 4 rows per warp).  Element sums are unchanged: each
+// output element is still accumulated by one lane in the order of the stored entries.
+inline bool shape_narrow(int ld, Shape* s) {
+    Shape d;
+    if (!shape_for_ld(ld, &d)) return false;
+    const int waste = d.L * d.CPL - d.Q;
+    for (int L = 1; L <= d.L; L <<= 1) {
+        const int cpl = (d.Q + L - 1) / L;
+        if (cpl <= kMaxCPL && L * cpl - d.Q <= waste) {
+            s->L = L;
+            s->Q = d.Q;
+            s->CPL = cpl;
+            return true;
+        }
+    }
+    *s = d;
+    return true;
+}
+
 // Row width used for rank r: r rounded up to a multiple of 4.
 inline int padded_ld(int r) { return (r + 3) / 4 * 4; }
 

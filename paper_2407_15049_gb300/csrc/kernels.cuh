@@ -274,7 +274,7 @@ k_spmm_c_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld,
             const int64_t e_ = s_cur >= 0 ? e_cur : __ldg(p.c_rowptr + i + 1);
             // nonzeros in flight per lane: with one unit per lane, all the gathers of a
             // row of up to 8 stored entries are issued together (masked slots load nothing)
-            constexpr int UN = CPL == 1 ? 8 : 2;
+            constexpr int UN = CPL == 1 ? 8 : (CPL == 2 ? 4 : 3);
             for (; s < e_; s += UN) {
                 if (CPL != 1 && s + UN > e_) break;
                 int j[UN];
@@ -960,12 +960,13 @@ k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __
 // One launch per body over the hardware grid; a kernel of the captured
 // iteration graph first checks the phase flags of the control block.
 
-// Resident blocks per SM the SpMM over C is compiled for: 4 (64 registers,
-// no spills) for float rows with one unit per lane, where the pass is bound by
-// the latency of its dependent loads; otherwise left to the compiler.
+// Resident blocks per SM the SpMM over C is compiled for: for float rows 4 (64
+// registers, no spills) with one unit per lane and 3 (85 registers) with more,
+// where the pass is bound by the latency of its dependent loads; otherwise left
+// to the compiler.
 template <typename TX, typename TO, int CPL>
 constexpr int spmm_min_blocks() {
-    return (CPL == 1 && std::is_same_v<TX, float> && std::is_same_v<TO, float>) ? 4 : 1;
+    return (std::is_same_v<TX, float> && std::is_same_v<TO, float>) ? (CPL == 1 ? 4 : 3) : 1;
 }
 
 template <typename TX, typename TO, typename TR, int CPL, int EPI>

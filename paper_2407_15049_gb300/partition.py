@@ -1,0 +1,111 @@
+"""Row partition of the SpMM (C - A*(v)) R across ranks: the exchange plan.
+
+The hot path shards naturally by rows: rank q owns a contiguous block of rows
+of C, R and every n x r iterate.  One SpMM needs, besides the rank's own rows
+of R (or D), the *halo* rows: rows j owned by other ranks with C_ij stored for
+some own row i.  Because C is symmetric, the rows rank q must send to rank p
+are exactly its own rows that have a stored column in p's block, so every rank
+builds both its receive and its send lists from its own rows, with no request
+round.  The per-iteration exchange is then one neighbour send/receive of those
+rows per SpMM (D changes every L-BFGS iteration), and the scalar reductions
+(the line-search sums, the L-BFGS Gram entries, err1 / err3) are one small
+all-reduce of a few dozen doubles.
+
+This module holds index bookkeeping and the exchange only: no arithmetic of
+the method.  It is not wired into the single-GPU library (each box of this
+build has one GPU); its plan and exchange are tested with gloo ranks on the
+CPU.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def row_ranges(n: int, world: int) -> list[tuple[int, int]]:
+    """Contiguous, nearly equal row blocks [lo, hi) for ranks 0..world-1."""
+    bounds = [(n * q) // world for q in range(world + 1)]
+    return [(bounds[q], bounds[q + 1]) for q in range(world)]
+
+
+def owner_of(rows: np.ndarray, ranges: list[tuple[int, int]]) -> np.ndarray:
+    """Rank owning each global row."""
+    starts = np.array([lo for lo, _ in ranges])
+    return np.searchsorted(starts, rows, side="right") - 1
+
+
+@dataclass
+class HaloPlan:
+    """What one rank holds, receives and sends for one SpMM over C."""
+    rank: int
+    world: int
+    lo: int
+    hi: int
+    # own rows of C with columns renumbered: own rows 0..n_own-1, then halo rows in
+    # receive order (owner rank, then global row)
+    rowptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+    recv: dict = field(default_factory=dict)      # owner rank -> global rows received from it (sorted)
+    send: dict = field(default_factory=dict)      # peer rank -> own global rows sent to it (sorted)
+
+    @property
+    def n_own(self) -> int:
+        return self.hi - self.lo
+
+    @property
+    def n_halo(self) -> int:
+        return int(sum(len(v) for v in self.recv.values()))
+
+
+def build_plan(rowptr: np.ndarray, colind: np.ndarray, val: np.ndarray, n: int, world: int,
+               rank: int) -> HaloPlan:
+    """Plan of `rank` from the rows of the symmetric CSR matrix C it owns."""
+    ranges = row_ranges(n, world)
+    lo, hi = ranges[rank]
+    s0, s1 = int(rowptr[lo]), int(rowptr[hi])
+    cols = np.asarray(colind[s0:s1], dtype=np.int64)
+    own = (cols >= lo) & (cols < hi)
+    remote = np.unique(cols[~own])
+    owners = owner_of(remote, ranges)
+    recv = {int(q): remote[owners == q] for q in np.unique(owners)}
+    # halo numbering: by owner rank, then by global row (np.unique sorts both)
+    new_col = np.where(own, cols - lo, 0)
+    if remote.size:
+        pos = np.searchsorted(remote, cols[~own])
+        new_col[~own] = (hi - lo) + pos
+    # symmetric C: own row i goes to rank p iff row i has a stored column in p's block
+    send = {}
+    col_owner = owner_of(cols, ranges)
+    row_of_entry = np.repeat(np.arange(lo, hi), np.diff(np.asarray(rowptr[lo:hi + 1], dtype=np.int64)))
+    for p in np.unique(col_owner[col_owner != rank]):
+        send[int(p)] = np.unique(row_of_entry[col_owner == p])
+    return HaloPlan(rank=rank, world=world, lo=lo, hi=hi,
+                    rowptr=np.asarray(rowptr[lo:hi + 1], dtype=np.int64) - s0, col=new_col,
+                    val=np.asarray(val[s0:s1]), recv=recv, send=send)
+
+
+def exchange(plan: HaloPlan, X_own, dist) -> "object":
+    """Halo rows of X (a torch tensor holding this rank's rows, n_own x ld) in the
+    plan's halo order, by one send/receive per neighbouring rank (torch.distributed
+    point-to-point; any backend).  Returns an n_halo x ld tensor."""
+    import torch
+    ld = X_own.shape[1]
+    ops = []
+    out = {}
+    for p, rows in sorted(plan.recv.items()):
+        buf = torch.empty((len(rows), ld), dtype=X_own.dtype, device=X_own.device)
+        out[p] = buf
+        ops.append(dist.P2POp(dist.irecv, buf, p))
+    sends = []
+    for p, rows in sorted(plan.send.items()):
+        payload = X_own[torch.as_tensor(rows - plan.lo, device=X_own.device)].contiguous()
+        sends.append(payload)
+        ops.append(dist.P2POp(dist.isend, payload, p))
+    if ops:
+        for req in dist.batch_isend_irecv(ops):
+            req.wait()
+    if not out:
+        return torch.empty((0, ld), dtype=X_own.dtype, device=X_own.device)
+    return torch.cat([out[p] for p in sorted(out)], dim=0)
