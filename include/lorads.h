@@ -120,6 +120,13 @@ typedef struct {
     double  cg_rel;            /* ADMM block steps: conjugate gradients (Algorithm 2) stop at ||r|| <= cg_rel ||r_0|| (1e-2) */
     int32_t cg_max;            /* ... or after cg_max steps (50) */
     int32_t admm_max_iter;     /* ADMM iterations (U step, V step, multiplier step) at most (20000) */
+    int32_t reopt_level;       /* re-opt of Sec. 4.1 with the final criteria of Sec. 4.2: 0 (default) off; 1: the ALM
+                                  solve stops on err1 <= tol alone, then while err1 (1 + ||b||_1 normalisation)
+                                  or |err3| of the original problem exceed tol, C is scaled by reopt_factor
+                                  (compounding) and the scaled problem is solved again from R, rho and the scaled
+                                  y; 2: err2 must hold too (GPU Lanczos).  Takes precedence over admm_switch. */
+    int32_t max_reopt;         /* re-opt rounds at most (5) */
+    double  reopt_factor;      /* scale of C per round, in (0, 1) (0.1) */
 } lorads_params;
 
 typedef struct {
@@ -138,6 +145,9 @@ typedef struct {
     int64_t kernel_launches;   /* kernels this library launched during the solve (graph nodes included) */
     int32_t admm_iters;        /* iterations of the ADMM stage (0: the ALM stage met the tolerance or admm_switch = 0) */
     int32_t cg_steps;          /* conjugate-gradient steps of the ADMM stage, both block steps summed */
+    int32_t reopt_rounds;      /* re-opt rounds taken */
+    int32_t reserved_r;
+    double  reopt_scale;       /* final scale of C in the re-opt rounds (1: none) */
 } lorads_result;
 
 /* Fills *p with the defaults listed above. */

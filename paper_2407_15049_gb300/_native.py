@@ -42,7 +42,8 @@ class lorads_params(C.Structure):
         ("lanczos_steps", C.c_int32), ("verbose", C.c_int32), ("reserved", C.c_int32),
         ("lbfgs_scaling", C.c_int32), ("rho_policy", C.c_int32), ("kernel_variant", C.c_int32),
         ("inner_scale", C.c_int32), ("admm_switch", C.c_double), ("cg_rel", C.c_double), ("cg_max", C.c_int32),
-        ("admm_max_iter", C.c_int32),
+        ("admm_max_iter", C.c_int32), ("reopt_level", C.c_int32), ("max_reopt", C.c_int32),
+        ("reopt_factor", C.c_double),
     ]
 
 
@@ -52,7 +53,8 @@ class lorads_result(C.Structure):
         ("err2", C.c_double), ("err3", C.c_double), ("sigma_min", C.c_double), ("rho", C.c_double),
         ("seconds", C.c_double), ("rank", C.c_int32), ("outer_iters", C.c_int32),
         ("inner_iters", C.c_int32), ("status", C.c_int32), ("kernel_launches", C.c_int64),
-        ("admm_iters", C.c_int32), ("cg_steps", C.c_int32),
+        ("admm_iters", C.c_int32), ("cg_steps", C.c_int32), ("reopt_rounds", C.c_int32),
+        ("reserved_r", C.c_int32), ("reopt_scale", C.c_double),
     ]
 
     def as_dict(self) -> dict:

@@ -104,6 +104,7 @@ struct lorads_ctx {
     int64_t* c_rowptr = nullptr;
     int32_t* c_col = nullptr;
     double* c_val = nullptr;
+    double* c_val0 = nullptr;           // C as uploaded, kept once re-opt scales c_val
     float* c_val32 = nullptr;
     dfloat* c_valdf = nullptr;
     int32_t* dk = nullptr;
@@ -261,6 +262,9 @@ extern "C" void lorads_default_params(lorads_params* p) {
     p->cg_rel = 1e-2;
     p->cg_max = 50;
     p->admm_max_iter = 20000;
+    p->reopt_level = 0;
+    p->max_reopt = 5;
+    p->reopt_factor = 0.1;
 }
 
 extern "C" const char* lorads_create_error(void) { return g_create_error.c_str(); }
@@ -288,7 +292,7 @@ extern "C" void lorads_destroy(lorads_ctx* ctx) {
     if (ctx->solve_stream) cudaStreamSynchronize(ctx->solve_stream);
     free_state(ctx->st);
     free_admm(ctx->admm);
-    dfree(ctx->c_rowptr); dfree(ctx->c_col); dfree(ctx->c_val); dfree(ctx->c_val32); dfree(ctx->c_valdf);
+    dfree(ctx->c_rowptr); dfree(ctx->c_col); dfree(ctx->c_val); dfree(ctx->c_val0); dfree(ctx->c_val32); dfree(ctx->c_valdf);
     dfree(ctx->dk); dfree(ctx->da); dfree(ctx->da32); dfree(ctx->da_df); dfree(ctx->b_df);
     dfree(ctx->a_rowptr); dfree(ctx->a_col); dfree(ctx->a_k); dfree(ctx->a_a);
     dfree(ctx->k_row); dfree(ctx->k_col); dfree(ctx->k_a); dfree(ctx->k_id); dfree(ctx->b);
@@ -402,8 +406,10 @@ extern "C" lorads_status lorads_create(lorads_ctx** out, int64_t n, const int64_
     }
     if (ctx->prm.check_every < 1) ctx->prm.check_every = 1;
     if (!(ctx->prm.admm_switch >= 0.0) || !(ctx->prm.cg_rel > 0.0 && ctx->prm.cg_rel < 1.0) ||
-        ctx->prm.cg_max < 1 || ctx->prm.admm_max_iter < 0) {
-        g_create_error = "need admm_switch >= 0, 0 < cg_rel < 1, cg_max >= 1 and admm_max_iter >= 0";
+        ctx->prm.cg_max < 1 || ctx->prm.admm_max_iter < 0 || ctx->prm.reopt_level < 0 || ctx->prm.reopt_level > 2 ||
+        ctx->prm.max_reopt < 0 || !(ctx->prm.reopt_factor > 0.0 && ctx->prm.reopt_factor < 1.0)) {
+        g_create_error = "need admm_switch >= 0, 0 < cg_rel < 1, cg_max >= 1, admm_max_iter >= 0, reopt_level in "
+                         "[0, 2], max_reopt >= 0 and 0 < reopt_factor < 1";
         delete ctx;
         return LORADS_ERR_INVALID_ARG;
     }
@@ -539,6 +545,8 @@ extern "C" lorads_status lorads_linesearch_coeffs(lorads_ctx* ctx, const void* R
 
 // ============================================================== solver
 namespace {
+
+lorads_status run_lanczos(lorads_ctx* ctx, const double* ydev, int k, uint64_t seed, double* sigma_out);
 
 template <typename TR, typename TD, typename TDIR = TD>
 struct Driver {
@@ -816,6 +824,7 @@ lorads_status fill_result(lorads_ctx* ctx, std::chrono::steady_clock::time_point
         res->status = final_status;
         res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         res->kernel_launches = ctx->launches;
+        res->reopt_scale = 1.0;
     }
     return final_status;
 }
@@ -1089,20 +1098,13 @@ lorads_status run_admm(lorads_ctx* ctx, double rho, std::chrono::steady_clock::t
 template <typename TR, typename TD, typename TDIR>
 lorads_status run_graph(lorads_ctx* ctx, int prec, std::chrono::steady_clock::time_point t0, lorads_result* res);
 
-template <typename TR, typename TD, typename TDIR = TD>
-lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0, int32_t r0_on_device,
-                        const double* y0, lorads_result* res) {
-    const auto t0 = std::chrono::steady_clock::now();
+// Uploads a fresh control block (penalty rho, stop tolerance and rule) and
+// enqueues the start of an ALM solve from the state's R and y.
+template <typename TR, typename TD, typename TDIR>
+lorads_status start_alm(lorads_ctx* ctx, double rho, double tol, int stop_rule) {
     const lorads_params& P = ctx->prm;
-    ctx->launches = 0;
-    lorads_status s;
-    if ((s = start_state<TR, TD, TDIR>(ctx, prec, R0, r0, r0_on_device, y0))) return s;
-    cudaStream_t ss = ctx->solve_stream;
-    // two-stage solve: the ALM stage stops at the switch tolerance
-    const double alm_tol = P.admm_switch > 0 ? std::max(P.admm_switch, P.tol) : P.tol;
-    // control block
     Ctrl h{};
-    h.rho = P.rho0 > 0 ? P.rho0 : 1.0 / ctx->mean_abs_c;
+    h.rho = rho;
     h.lbfgs_mem = P.lbfgs_mem;
     h.total_limit = ctx->iter_limit > 0 ? (int)std::min<int64_t>(ctx->iter_limit, INT32_MAX) : 0;
     h.max_inner = P.max_inner;
@@ -1111,7 +1113,8 @@ lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0,
     h.lbfgs_scaling = P.lbfgs_scaling;
     h.rho_policy = P.rho_policy;
     h.inner_scale = P.inner_scale;
-    h.tol = alm_tol;
+    h.stop_rule = stop_rule;
+    h.tol = tol;
     h.inner_rel = P.inner_rel;
     h.inner_progress = P.inner_progress;
     h.bnorm1 = ctx->bnorm1;
@@ -1121,17 +1124,111 @@ lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0,
     h.infeas_decrease = P.infeas_decrease;
     h.status = LORADS_ERR_MAXITER;
     for (int q = 0; q < kMaxMem; ++q) h.order[q] = q;
-    CK(cudaMemcpyAsync(ctx->ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, ss));
-    {
-        Driver<TR, TD, TDIR> drv(ctx);
-        drv.enqueue_init();
+    CK(cudaMemcpyAsync(ctx->ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, ctx->solve_stream));
+    Driver<TR, TD, TDIR> drv(ctx);
+    drv.enqueue_init();
+    return check_launch(ctx, "solve init");
+}
+
+template <typename TR, typename TD, typename TDIR>
+lorads_status run_alm(lorads_ctx* ctx, int prec, std::chrono::steady_clock::time_point t0, lorads_result* res) {
+    if (ctx->prm.verbose >= 2) return run_profiled<TR, TD, TDIR>(ctx, prec, t0, res);
+    return run_graph<TR, TD, TDIR>(ctx, prec, t0, res);
+}
+
+// Re-opt (Sec. 4.1) after an ALM solve that stopped on primal feasibility
+// alone: while the final criteria of the chosen level (Sec. 4.2; level 1: err1
+// with 1 + ||b||_1 and |err3|; level 2: also err2) fail on the original
+// problem, scale C by reopt_factor (compounding), keep R and rho, scale y with
+// C, and solve the scaled problem again with the same stop.  At the end y and C
+// are those of the original problem again.
+template <typename TR, typename TD, typename TDIR>
+lorads_status run_reopt(lorads_ctx* ctx, int prec, std::chrono::steady_clock::time_point t0, lorads_result* res) {
+    const lorads_params& P = ctx->prm;
+    SolverState& st = ctx->st;
+    cudaStream_t ss = ctx->solve_stream;
+    const int nbc = flat_blocks(ctx, ctx->nnz_c), nbm = flat_blocks(ctx, ctx->m);
+    double scale = 1.0;
+    int rounds = 0;
+    int64_t inner = res->inner_iters, outer = res->outer_iters;
+    lorads_status s = LORADS_OK;
+    bool met = false;
+    double obj = 0, by = 0, err3 = 0;
+    for (;;) {
+        // errors of the original problem: <C, X> = <sC, X>/s, b^T y = b^T (s y)/s
+        obj = res->primal_obj / scale;
+        by = res->dual_obj / scale;
+        err3 = (obj - by) / (1.0 + std::fabs(obj) + std::fabs(by));
+        const double err1_l1 = res->err1 * (1.0 + ctx->bnorm_inf) / (1.0 + ctx->bnorm1);
+        met = err1_l1 <= P.tol && std::fabs(err3) <= P.tol;
+        if (met && P.reopt_level >= 2) {
+            double sig = 0.0;           // sigma_min(sC - A*(s y)) = s sigma_min(C - A*(y))
+            if ((s = run_lanczos(ctx, st.y, P.lanczos_steps, P.seed, &sig))) break;
+            met = std::max(0.0, -sig / scale) / (1.0 + ctx->cnorm1) <= P.tol;
+        }
+        if (met || rounds >= P.max_reopt) break;
+        if (!ctx->c_val0) {
+            if ((s = dalloc(ctx, &ctx->c_val0, (size_t)ctx->nnz_c))) break;
+            CK(cudaMemcpyAsync(ctx->c_val0, ctx->c_val, (size_t)ctx->nnz_c * sizeof(double),
+                               cudaMemcpyDeviceToDevice, ss));
+        }
+        const double s_new = scale * P.reopt_factor;
+        scale_c(ss, ctx->nnz_c, ctx->c_val0, s_new, ctx->c_val, ctx->c_val32, ctx->c_valdf, nbc);
+        rescale_y(ss, ctx->m, st.y, st.ydf, scale, s_new, nbm);
+        ctx->launches += 2;
+        scale = s_new;
+        rounds += 1;
+        if ((s = start_alm<TR, TD, TDIR>(ctx, res->rho, P.tol, 1))) break;
+        lorads_result r2{};
+        s = run_alm<TR, TD, TDIR>(ctx, prec, t0, &r2);
+        inner += r2.inner_iters;
+        outer += r2.outer_iters;
+        *res = r2;
+        if (s != LORADS_OK) break;
     }
-    if ((s = check_launch(ctx, "solve init"))) return s;
+    if (scale != 1.0) {
+        rescale_y(ss, ctx->m, st.y, st.ydf, scale, 1.0, nbm);
+        scale_c(ss, ctx->nnz_c, ctx->c_val0, 1.0, ctx->c_val, ctx->c_val32, ctx->c_valdf, nbc);
+        ctx->launches += 2;
+        CK(cudaStreamSynchronize(ss));
+        if (s == LORADS_OK) {
+            obj = res->primal_obj / scale;
+            by = res->dual_obj / scale;
+            err3 = (obj - by) / (1.0 + std::fabs(obj) + std::fabs(by));
+        }
+    }
+    res->primal_obj = obj;
+    res->dual_obj = by;
+    res->err3 = err3;
+    res->inner_iters = (int32_t)std::min<int64_t>(inner, INT32_MAX);
+    res->outer_iters = (int32_t)std::min<int64_t>(outer, INT32_MAX);
+    res->reopt_rounds = rounds;
+    res->reopt_scale = scale;
+    res->kernel_launches = ctx->launches;
+    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (s == LORADS_OK && !met) s = LORADS_ERR_MAXITER;
+    res->status = s;
+    return s;
+}
+
+template <typename TR, typename TD, typename TDIR = TD>
+lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0, int32_t r0_on_device,
+                        const double* y0, lorads_result* res) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const lorads_params& P = ctx->prm;
+    ctx->launches = 0;
+    lorads_status s;
+    if ((s = start_state<TR, TD, TDIR>(ctx, prec, R0, r0, r0_on_device, y0))) return s;
+    // two-stage solve: the ALM stage stops at the switch tolerance; re-opt: the
+    // first solve stops on primal feasibility alone
+    const double alm_tol = (P.admm_switch > 0 && P.reopt_level <= 0) ? std::max(P.admm_switch, P.tol) : P.tol;
+    const double rho0 = P.rho0 > 0 ? P.rho0 : 1.0 / ctx->mean_abs_c;
+    if ((s = start_alm<TR, TD, TDIR>(ctx, rho0, alm_tol, P.reopt_level > 0 ? 1 : 0))) return s;
     lorads_result alm{};
-    lorads_status fs;
-    if (P.verbose >= 2) fs = run_profiled<TR, TD, TDIR>(ctx, prec, t0, &alm);
-    else fs = run_graph<TR, TD, TDIR>(ctx, prec, t0, &alm);
-    if (fs == LORADS_OK && P.admm_switch > 0 && !(alm.err1 <= P.tol && std::fabs(alm.err3) <= P.tol))
+    lorads_status fs = run_alm<TR, TD, TDIR>(ctx, prec, t0, &alm);
+    if (fs == LORADS_OK && P.reopt_level > 0)
+        fs = run_reopt<TR, TD, TDIR>(ctx, prec, t0, &alm);
+    else if (fs == LORADS_OK && P.admm_switch > 0 && !(alm.err1 <= P.tol && std::fabs(alm.err3) <= P.tol))
         fs = run_admm<TR, TD>(ctx, alm.rho, t0, &alm);
     if (res) *res = alm;
     return fs;

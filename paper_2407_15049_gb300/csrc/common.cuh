@@ -251,6 +251,7 @@ struct Ctrl {
     int lbfgs_scaling;
     int rho_policy;
     int inner_scale;
+    int stop_rule;              // 0: err1 and |err3| <= tol; 1: err1 <= tol alone (the stop before re-opt)
     // outer-loop state
     double tol, inner_rel, inner_progress, gnorm0, bnorm1, bnorm_inf;
     double rho_growth, rho_max, infeas_decrease;

@@ -172,6 +172,28 @@ __global__ void k_random_start(int64_t n, int ld, int r, uint64_t seed, int unit
     }
 }
 
+// Re-opt (Sec. 4.1): C <- s C_0 in every stored precision (FP64 product, then
+// the float and double-float mirrors of it, as lorads_create builds them).
+__global__ void k_scale_c(int64_t nnz, const double* c0, double s, double* c, float* c32, dfloat* cdf) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x) {
+        const double v = c0[q] * s;
+        c[q] = v;
+        c32[q] = (float)v;
+        const float h = (float)v;
+        cdf[q] = dfloat(h, (float)(v - (double)h));
+    }
+}
+
+// y <- (y / s_old) s_new (the multiplier of the original problem, rescaled), and
+// its double-float mirror
+__global__ void k_rescale_y(int64_t m, double* y, dfloat* ydf, double s_old, double s_new) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (y[k] / s_old) * s_new;
+        y[k] = v;
+        if (ydf != nullptr) ydf[k] = dfloat(v);
+    }
+}
+
 template <typename TI, typename TO>
 __global__ void k_convert(int64_t n, int ld_in, int ld_out, int r, const TI* in, TO* out) {
     const int64_t total = n * (int64_t)ld_out;
@@ -329,6 +351,15 @@ void random_start(cudaStream_t s, int64_t n, int ld, int r, uint64_t seed, int u
 template void random_start<double>(cudaStream_t, int64_t, int, int, uint64_t, int, double, void*, int);
 template void random_start<float>(cudaStream_t, int64_t, int, int, uint64_t, int, double, void*, int);
 template void random_start<dfloat>(cudaStream_t, int64_t, int, int, uint64_t, int, double, void*, int);
+
+void scale_c(cudaStream_t s, int64_t nnz, const double* c0, double scale, double* c, float* c32, dfloat* cdf,
+             int blocks) {
+    k_scale_c<<<blocks, 256, 0, s>>>(nnz, c0, scale, c, c32, cdf);
+}
+
+void rescale_y(cudaStream_t s, int64_t m, double* y, dfloat* ydf, double s_old, double s_new, int blocks) {
+    k_rescale_y<<<blocks, 256, 0, s>>>(m, y, ydf, s_old, s_new);
+}
 
 template <typename TI, typename TO>
 void convert(cudaStream_t s, int64_t n, int ld_in, int ld_out, int r, const void* in, void* out, int blocks) {

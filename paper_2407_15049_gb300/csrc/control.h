@@ -36,6 +36,9 @@ void rank_columns(cudaStream_t s, int64_t n, int ld, int r_old, int r_new, doubl
 template <typename T>
 void random_start(cudaStream_t s, int64_t n, int ld, int r, uint64_t seed, int unit_rows, double scale, void* X,
                   int blocks);
+void scale_c(cudaStream_t s, int64_t nnz, const double* c0, double scale, double* c, float* c32, dfloat* cdf,
+             int blocks);
+void rescale_y(cudaStream_t s, int64_t m, double* y, dfloat* ydf, double s_old, double s_new, int blocks);
 template <typename TI, typename TO>
 void convert(cudaStream_t s, int64_t n, int ld_in, int ld_out, int r, const void* in, void* out, int blocks);
 

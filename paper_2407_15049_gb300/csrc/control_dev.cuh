@@ -359,7 +359,7 @@ __device__ inline void ctrl_outer_apply(Ctrl* c, const double* sc, const double*
         c->solve_done = 1;
         return;
     }
-    if (err1 <= c->tol && fabs(err3) <= c->tol) {
+    if (err1 <= c->tol && (c->stop_rule == 1 || fabs(err3) <= c->tol)) {
         c->status = 0;
         c->solve_done = 1;
         return;

@@ -1,0 +1,96 @@
+"""GPU re-opt (Sec. 4.1, with the stopping criteria of Sec. 4.2) against the FP64
+oracle's procedure (oracle/reopt_oracle.py) on the same inputs.
+
+* The odd cycle C_7: the primal-feasibility stop leaves err3 above tol; one
+  round (C scaled by 0.1) reaches the closed-form SDP value
+  (n/2)(1 + cos(pi/n)) with the level-1 criteria, and err2 too at level 2.
+* Short inner loops (max_inner = 5) on ER graphs make the first stop early:
+  the GPU takes the oracle's number of rounds, ends with its status (level 2
+  runs out of rounds on the 500-vertex graph), its objective and, after the
+  multiplier is mapped back to the original problem, its y.
+* When the criteria hold after the first stop, no round is taken.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import lorads_oracle as O
+from oracle import reopt_oracle as RO
+from tests._util import rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_2407_15049_gb300 as L  # noqa: E402
+
+PREC = {"fp64": L.LORADS_FP64, "mixed": L.LORADS_MIXED}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    L.build()
+
+
+def _gpu(inst, R0, prec, **kw):
+    ctx = L.lorads_create(inst, L.default_params(prec=PREC[prec], **kw))
+    try:
+        res = L.lorads_solve(ctx, R0)
+        R, y = L.lorads_get_solution(ctx, inst.n, inst.m)
+    finally:
+        L.lorads_destroy(ctx)
+    return res, R, y
+
+
+@pytest.mark.parametrize("level", [1, 2])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_odd_cycle_reaches_the_closed_form(level, prec):
+    inst = W.maxcut_instance(7, W.cycle_graph(7))
+    R0 = W.initial_factor(inst, 3, 1)
+    ref = RO.solve_reopt(O.Problem(inst), R0, level=level)
+    res, R, y = _gpu(inst, R0, prec, reopt_level=level, compute_err2=1)
+    assert ref["rounds"] == 1
+    assert res["status_name"] == "LORADS_OK", res
+    assert res["reopt_rounds"] == ref["rounds"]
+    assert res["reopt_scale"] == pytest.approx(0.1, rel=1e-15)
+    value = 3.5 * (1 + math.cos(math.pi / 7))
+    assert -res["primal_obj"] == pytest.approx(value, rel=1e-6)
+    assert abs(res["err3"]) <= 1e-5 and res["err1"] <= 1e-5
+    if level == 2:
+        assert res["err2"] <= 1e-5
+    # the multiplier is the original problem's: the duality gap closes on C itself
+    e = O.errors(O.Problem(inst), R, y)
+    assert e["err3"] == pytest.approx(res["err3"], abs=1e-9)
+
+
+@pytest.mark.parametrize("case", [("er200", 1), ("er500", 1), ("er500", 2)])
+def test_rounds_and_result_match_oracle(case):
+    name, level = case
+    if name == "er200":
+        inst = W.maxcut_instance(200, W.er_graph(200, 600, 2, "pm1"))
+        R0 = W.initial_factor(inst, 8, 1)
+    else:
+        inst = W.maxcut_instance(500, W.er_graph(500, 1500, 4, "unit"))
+        R0 = W.initial_factor(inst, 9, 1)
+    ref = RO.solve_reopt(O.Problem(inst), R0, level=level, params=O.Params(max_inner=5))
+    res, R, y = _gpu(inst, R0, "fp64", reopt_level=level, max_inner=5)
+    assert ref["rounds"] >= 2
+    assert res["reopt_rounds"] == ref["rounds"]
+    assert res["status_name"] == ("LORADS_OK" if ref["status"] == "ok" else "LORADS_ERR_MAXITER"), res
+    assert res["reopt_scale"] == pytest.approx(ref["scale"], rel=1e-12)
+    assert res["inner_iters"] == ref["inner"]
+    assert res["primal_obj"] == pytest.approx(ref["primal_obj"], rel=1e-8)
+    assert res["err3"] == pytest.approx(ref["err3"], rel=1e-5, abs=1e-10)
+    assert rel_err(y, ref["y"]) <= 1e-6
+
+
+def test_no_round_when_the_criteria_hold():
+    inst = W.maxcut_instance(1000, W.er_graph(1000, 4000, 0, "unit"))
+    R0 = W.initial_factor(inst, 10, 1)
+    ref = RO.solve_reopt(O.Problem(inst), R0, level=2)
+    res, _, _ = _gpu(inst, R0, "fp64", reopt_level=2, compute_err2=1)
+    assert ref["rounds"] == 0 and res["reopt_rounds"] == 0
+    assert res["status_name"] == "LORADS_OK"
+    assert res["primal_obj"] == pytest.approx(ref["primal_obj"], rel=1e-7)
+    assert res["err2"] <= 1e-5
