@@ -54,7 +54,7 @@ T_START = time.perf_counter()
 
 METRIC = "time to rel. KKT 1e-5 (MaxCut n=1e7); SpMM+A(RRᵀ) HBM GB/s vs 8 TB/s"
 WORKLOADS = {
-    "maxcut_er_1e7": dict(n=10_000_000, edges=20_000_000, weights="pm1", r=24, seed=0,
+    "maxcut_er_1e7": dict(n=10_000_000, edges=20_000_000, weights="pm1", r=24, seed=0, admm_switch=3e-4,
                           desc="MaxCut SDP, Erdos-Renyi n=1e7, M=2e7 edges (avg degree 4), w in {-1,+1}, r=24"),
     "maxcut_er_1e6": dict(n=1_000_000, edges=2_000_000, weights="pm1", r=20, seed=0,
                           desc="MaxCut SDP, Erdos-Renyi n=1e6, M=2e6 edges (avg degree 4), w in {-1,+1}, r=20"),
@@ -62,7 +62,12 @@ WORKLOADS = {
                           desc="MaxCut SDP, Erdos-Renyi n=1e5, M=2e5 edges (avg degree 4), w in {-1,+1}, r=17"),
     "maxcut_torus_1e6": dict(n=1_000_000, edges=2_000_000, weights="pm1", r=20, seed=0, graph="torus", side=1000,
                              desc="MaxCut SDP, 1000x1000 torus (4-regular, wraparound), w in {-1,+1}, r=20"),
+    "mc_5e4_rank3": dict(kind="mc", side=50_000, rank=3, n=100_000, m=2_704_945, r=22, seed=0, admm_switch=1e-3,
+                         desc="matrix-completion SDP: M = U V^T, U, V in R^{50000x3} iid N(0,1), |Omega| = "
+                              "ceil(5 n ln n) = 2,704,945 uniform samples, X of order 1e5, C = I, r = 22"),
 }
+# metric of each workload's line (the benchmark's own metric for the MaxCut workloads)
+MC_METRIC = "time to rel. KKT 1e-5 (matrix completion 5e4 x 5e4, |Omega| 2.7e6)"
 BATCH_WORKLOADS = {
     "serving_batch_512": dict(count=512, seed=0,
                               desc="512 uneven SDPs: ~3/4 MaxCut on ER graphs (n log-uniform in [200, 20000], "
@@ -71,19 +76,22 @@ BATCH_WORKLOADS = {
 }
 BATCH_METRIC = "instances/s to rel. KKT 1e-5, one persistent launch (512 mixed MaxCut / matrix-completion SDPs)"
 # iterations to tolerance used to scale the reference arm's per-iteration time when no
-# GPU run of the same invocation provides it (measured on the GPU solve of maxcut_er_1e7)
-DEFAULT_ITERS_TO_TOL = {"maxcut_er_1e7": 8352, "maxcut_er_1e6": 6381, "maxcut_er_1e5": 5000,
-                       "maxcut_torus_1e6": 5271}
+# GPU run of the same invocation provides it (L-BFGS iterations of the GPU two-stage solve
+# of maxcut_er_1e7 at switch 3e-4, mean over start seeds 1-3; its two ADMM iterations,
+# 8 CG steps, are not counted)
+DEFAULT_ITERS_TO_TOL = {"maxcut_er_1e7": 4690, "maxcut_er_1e6": 6381, "maxcut_er_1e5": 5000,
+                       "maxcut_torus_1e6": 5271, "mc_5e4_rank3": 236}
 # seconds of one solve to tolerance measured on a GB300 (bench default workload and form);
 # plan_seconds uses it to check that the driver's --steps 20 --warmup 5 run fits its limit
-MEASURED_SOLVE_S = {"maxcut_er_1e7": 69.1}
+MEASURED_SOLVE_S = {"maxcut_er_1e7": 43.0}
 # fixed legs of a default run on the GPU host (seconds, upper estimates): interpreter and
 # CUDA start, instance generation, upload, per-kernel profile, one e2e solve on top of its
 # solve time, CPU-baseline sample
-FIXED_LEGS_S = {"start": 60.0, "generate": 90.0, "create": 10.0, "profile": 20.0, "e2e_extra": 30.0,
-                "cpu_baseline": 60.0}
+FIXED_LEGS_S = {"start": 40.0, "generate": 30.0, "create": 10.0, "profile": 20.0, "e2e_extra": 20.0,
+                "cpu_baseline": 40.0, "fp64_same_run": 420.0}
 DRIVER_LIMIT_S = 1800.0
-DEFAULT_TIME_BUDGET_S = 1100.0
+DEFAULT_TIME_BUDGET_S = 800.0
+FP64_SAME_RUN_LIMIT_S = 400.0
 
 
 def _args():
@@ -94,6 +102,11 @@ def _args():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", default="maxcut_er_1e7", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS))
     ap.add_argument("--prec", default="mixed", choices=["fp64", "mixed", "df64", "fp32"])
+    ap.add_argument("--admm-switch", type=float, default=None,
+                    help="two-stage solve: err1/|err3| at which the ALM stage hands over to the ADMM stage "
+                         "(0: ALM only; default: the workload's)")
+    ap.add_argument("--reopt-level", type=int, default=0, choices=[0, 1, 2],
+                    help="re-opt of Sec. 4.1 with the level-1/2 final criteria")
     ap.add_argument("--e2e-steps", type=int, default=1, help="end-to-end steps")
     ap.add_argument("--profile-iters", type=int, default=200,
                     help="L-BFGS iterations of the CUDA-event-timed solve used for per-kernel durations")
@@ -103,6 +116,10 @@ def _args():
                     help="vertices of the same-family graph the oracle is sampled on (0: the workload itself)")
     ap.add_argument("--warmup-iters", type=int, default=60,
                     help="L-BFGS iterations of each (capped) warm-up solve")
+    ap.add_argument("--fp64-same-run", type=int, default=None,
+                    help="1: after the timed solves, one cold solve of the plain FP64 form from the first timed "
+                         "start (bounded by a time limit), reported beside the headline (default: on for "
+                         "the n=1e7 MaxCut workload)")
     ap.add_argument("--time-budget", type=float, default=DEFAULT_TIME_BUDGET_S,
                     help="seconds of timed solves: no solve starts that would end past it (at least one runs)")
     ap.add_argument("--iters-to-tol", type=int, default=None)
@@ -121,7 +138,12 @@ def _args():
     ap.add_argument("--spmm-vs-cusparse", type=int, default=0, metavar="N",
                     help="informational: time C D of the library's SpMM and of cuSPARSE (torch CSR @ dense) "
                          "on the ER graph with N vertices (degree 4, r = 24, FP32) and exit")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.fp64_same_run is None:
+        args.fp64_same_run = 1 if (args.workload == "maxcut_er_1e7" and args.prec != "fp64") else 0
+    if args.admm_switch is None:
+        args.admm_switch = WORKLOADS.get(args.workload, {}).get("admm_switch", 0.0)
+    return args
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -130,6 +152,10 @@ def build_instance(name):
     import workloads as W
     cfg = WORKLOADS[name]
     t = time.perf_counter()
+    if cfg.get("kind") == "mc":
+        inst, _ = W.config_instance(name, cfg["seed"])
+        R0 = W.initial_factor(inst, cfg["r"], cfg["seed"] + 1)
+        return inst, R0, time.perf_counter() - t
     if cfg.get("graph") == "torus":
         edges = W.torus_graph(cfg["side"], cfg["seed"], cfg["weights"])
     else:
@@ -205,10 +231,22 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power)}
 
 
-def kernel_bytes(fam: str, n: int, ld: int, nnz: int, m: int, wR: int, wD: int, T: int) -> float:
-    """Algorithmic bytes of one launch (each operand read or written once)."""
+def kernel_bytes(fam: str, n: int, ld: int, nnz: int, m: int, wR: int, wD: int, T: int, m_off: int = 0) -> float:
+    """Algorithmic bytes of one launch (each operand read or written once).  m_off:
+    off-diagonal constraints (matrix completion: all of them), each a gathered pair of rows."""
     nl = n * ld
     row_meta = 4 + 8 + 8 + 8                      # dk, da, y, b per row
+    if m_off > 0:
+        if fam == "k_cons(ls)":                   # i, j, coefficient, id, y, cached z; rows of R and D at i, j
+            return m_off * (4 + 4 + 8 + 4 + 8 + 8 + 2 * ld * (wR + wD))
+        if fam == "k_cons(ytil)":                 # i, j, coefficient, id, y, b; y~ and z written; rows of R
+            return m_off * (4 + 4 + 8 + 4 + 8 + 8 + 8 + 8 + 2 * ld * wR)
+        if fam == "k_spmm_a":                     # pattern (2 entries per constraint): column, id, coefficient,
+            return 8 * (n + 1) + 2 * m_off * (4 + 4 + 8 + 8 + ld * wR) + nl * wD   # y~, gathered row; W out
+        if fam == "k_step":                       # R, C R read and written; D, C D read
+            return nl * (4 * wR + 2 * wD)
+        if fam == "k_update(step)" and m_off == m:    # no diagonal constraint: R, C R read (the step is k_step)
+            return nl * (2 * wR + 6 * wD + 2 * (T - 1) * wD)
     if fam == "k_spmm_c(CD,ls)":
         return nnz * (4 + (8 if wD == 8 else 4)) + (n + 1) * 8 + nl * (2 * wD + wR) + n * row_meta
     if fam == "k_spmm_c(CR,obj)":
@@ -326,7 +364,7 @@ def run_reference(args):
     s_iter = statistics.mean(per) * scale
     value = s_iter * iters_to_tol
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+        "impl": "reference", "metric": _metric(args), "value": value, "unit": "s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": _config(args),
@@ -355,12 +393,36 @@ def _l2_policy(cfg) -> str:
     return f"inputs smaller than L2 (R is {r_bytes / 1e6:,.0f} MB at FP64): timings include L2 reuse"
 
 
+def _mc_recovery(inst, obj: float) -> dict:
+    """The matrix-completion SDP's optimum is 2 ||M||_* (w.h.p. at |Omega| = 5 n ln n): the
+    nuclear norm of M = U V^T from the singular values of R_u R_v^T (QR of U and of V)."""
+    import numpy as np
+    U, V = inst.meta["U"], inst.meta["V"]
+    ru = np.linalg.qr(U, mode="r")
+    rv = np.linalg.qr(V, mode="r")
+    nuc = float(np.sum(np.linalg.svd(ru @ rv.T, compute_uv=False)))
+    return {"two_nuclear_norm": 2 * nuc, "objective": obj, "rel_gap": (obj - 2 * nuc) / (2 * nuc)}
+
+
+def _metric(args) -> str:
+    return MC_METRIC if WORKLOADS[args.workload].get("kind") == "mc" else METRIC
+
+
 def _config(args):
     cfg = WORKLOADS[args.workload]
-    return {"workload": args.workload, "description": cfg["desc"], "n": cfg["n"], "m": cfg["n"],
-            "nnz_C": cfg["n"] + 2 * cfg["edges"], "rank": cfg["r"], "solver_precision": args.prec,
-            "start": ("learned warm start (network trained before timing; prediction timed)"
-                      if args.warm_start == "gnn" else "cold (seeded unit-norm Gaussian rows)"), "tolerance": 1e-5,
+    mc = cfg.get("kind") == "mc"
+    if mc:
+        start = "cold (seeded Gaussian rows scaled to ||R0||_F^2 = ||b||_1 / 2)"
+    elif args.warm_start == "gnn":
+        start = "learned warm start (network trained before timing; prediction timed)"
+    else:
+        start = "cold (seeded unit-norm Gaussian rows)"
+    return {"workload": args.workload, "description": cfg["desc"], "n": cfg["n"], "m": cfg["m"] if mc else cfg["n"],
+            "nnz_C": cfg["n"] if mc else cfg["n"] + 2 * cfg["edges"], "rank": cfg["r"],
+            "solver_precision": args.prec, "start": start, "tolerance": 1e-5,
+            "two_stage": ({"admm_switch": args.admm_switch, "cg_rel": 1e-2, "cg_max": 50}
+                          if args.admm_switch > 0 else None),
+            "reopt_level": args.reopt_level,
             "l2_policy": _l2_policy(cfg),
             "parallelism": f"replicas x{args.gpus}"}
 
@@ -401,7 +463,8 @@ def run_native(args):
     stream = torch.cuda.Stream()
     # rel. KKT = max(err1, err2, err3): err2 (Lanczos on C - A*(y)) is evaluated at the
     # end of every timed solve
-    params = L.default_params(prec=prec_code, compute_err2=1)
+    params = L.default_params(prec=prec_code, compute_err2=1, admm_switch=args.admm_switch,
+                              reopt_level=args.reopt_level)
 
     def barrier():
         torch.cuda.synchronize()
@@ -431,13 +494,23 @@ def run_native(args):
             def start(seed):
                 return net.predict(graph, feature_seed=seed, ld=ldw)[:, :cfg["r"]].contiguous()
         else:
-            def start(seed):
-                # seeded unit-norm Gaussian rows (the workload's start recipe), drawn on the device
-                g = torch.Generator(device="cuda")
-                g.manual_seed(seed)
-                Rs = torch.randn((inst.n, cfg["r"]), dtype=torch.float64, device="cuda", generator=g)
+            start = None
+
+        def cold_start(seed):
+            # seeded Gaussian rows drawn on the device, scaled as the workload's start recipe:
+            # unit rows (MaxCut) or ||R0||_F^2 = ||b||_1 / 2 (matrix completion)
+            g = torch.Generator(device="cuda")
+            g.manual_seed(seed)
+            Rs = torch.randn((inst.n, cfg["r"]), dtype=torch.float64, device="cuda", generator=g)
+            if inst.kind == "mc":
+                target = max(0.5 * float(np.abs(inst.b).sum()), 1.0)
+                Rs *= math.sqrt(target) / torch.linalg.vector_norm(Rs)
+            else:
                 Rs /= torch.linalg.vector_norm(Rs, dim=1, keepdim=True)
-                return Rs
+            return Rs
+
+        if start is None:
+            start = cold_start
         # warm-up: solves capped at a few iterations (graph capture, caches, clocks)
         for _ in range(args.warmup):
             L.lorads_solve(ctx, start(0), on_device=True, max_total_inner=args.warmup_iters)
@@ -489,6 +562,30 @@ def run_native(args):
             prof = L.lorads_kernel_times(pctx)
             L.lorads_destroy(pctx)
         L.lorads_destroy(ctx)
+        # the plain FP64 form on the same workload and start as the first timed solve
+        fp64 = None
+        if args.fp64_same_run:
+            fctx = L.lorads_create(inst, L.default_params(prec=L.LORADS_FP64, compute_err2=1,
+                                                          admm_switch=args.admm_switch, reopt_level=args.reopt_level,
+                                                          time_limit=FP64_SAME_RUN_LIMIT_S),
+                                   stream=stream.cuda_stream)
+            f0 = cold_start(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rf = L.lorads_solve(fctx, f0, on_device=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            L.lorads_destroy(fctx)
+            del f0
+            first = timed[0]
+            fp64 = {"seconds": e0.elapsed_time(e1) / 1e3, "start": "cold, seed 1 (the first timed step's "
+                    "start when that is cold)", "time_limit_s": FP64_SAME_RUN_LIMIT_S,
+                    **{k: rf[k] for k in ("status_name", "primal_obj", "err1", "err2", "err3", "inner_iters",
+                                          "outer_iters", "admm_iters", "cg_steps")},
+                    "mixed_same_start": {"seconds": step_s[0], "primal_obj": first["primal_obj"],
+                                         "inner_iters": first["inner_iters"]},
+                    "rel_obj_diff_mixed_vs_fp64": (first["primal_obj"] - rf["primal_obj"]) / abs(rf["primal_obj"]),
+                    "speedup_mixed_vs_fp64": (e0.elapsed_time(e1) / 1e3) / step_s[0]}
         del R0_dev
         # end to end through the C ABI from host buffers
         e2e_steps = args.e2e_steps
@@ -533,8 +630,9 @@ def run_native(args):
     per_inner = {"k_dir", "k_spmm_c(CD,ls)", "k_ctrl_root", "k_update(step)", "k_ctrl_hist", "k_cons(ls)",
                  "k_step", "k_spmm_a", "k_cons(ytil)"}
     kernels = {}
+    m_off = int(np.sum(inst.row != inst.col))
     for name, (ms, cnt) in prof.items():
-        b = kernel_bytes(name, inst.n, ld, inst.nnz, inst.m, wR, wD, params.lbfgs_mem)
+        b = kernel_bytes(name, inst.n, ld, inst.nnz, inst.m, wR, wD, params.lbfgs_mem, m_off)
         solve_launches = last["inner_iters"] if name in per_inner else last["outer_iters"]
         kernels[name] = {"avg_ms": ms, "profiled_launches": cnt, "solve_launches": solve_launches,
                          "share": None, "algorithmic_bytes": None if math.isnan(b) else b,
@@ -572,7 +670,7 @@ def run_native(args):
                                       "(the mean L-BFGS iteration count of the timed GPU solves)")}
     plan = plan_seconds(args.steps, args.warmup, MEASURED_SOLVE_S.get(args.workload, per_step), args.time_budget)
     line = {
-        "metric": METRIC, "value": per_step, "unit": "s", "n_gpus": world, "steps": steps_timed,
+        "metric": _metric(args), "value": per_step, "unit": "s", "n_gpus": world, "steps": steps_timed,
         "steps_requested": args.steps, "warmup": args.warmup, "warmup_iters": args.warmup_iters, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None,
         "dtype": {"fp64": "f64", "mixed": "f32 (+double-float R, CR)", "df64": "double-float (2xf32)",
@@ -582,9 +680,11 @@ def run_native(args):
         "gpu_launches": int(launches),
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
         "solve": {k: last[k] for k in ("status_name", "primal_obj", "dual_obj", "err1", "err2", "err3", "sigma_min",
-                                       "rho", "rank", "outer_iters", "inner_iters", "seconds")},
+                                       "rho", "rank", "outer_iters", "inner_iters", "admm_iters", "cg_steps",
+                                       "reopt_rounds", "seconds")},
         "per_step": {"start_seed": list(range(1, steps_timed + 1)), "seconds": step_s,
                      "inner_iters": [r["inner_iters"] for r in timed],
+                     "admm_iters": [r["admm_iters"] for r in timed], "cg_steps": [r["cg_steps"] for r in timed],
                      "outer_iters": [r["outer_iters"] for r in timed],
                      "status": [r["status_name"] for r in timed],
                      "primal_obj": [r["primal_obj"] for r in timed],
@@ -594,10 +694,12 @@ def run_native(args):
         "consistency": {"timed_wall_s": elapsed, "time_budget_s": args.time_budget,
                         "wall_s_total": time.perf_counter() - T_START, "plan": plan,
                         "fits_in_driver_run": (time.perf_counter() - T_START) <= DRIVER_LIMIT_S},
-        "sdp_value": -last["primal_obj"],
+        "sdp_value": last["primal_obj"] if inst.kind == "mc" else -last["primal_obj"],
+        "mc_recovery": _mc_recovery(inst, last["primal_obj"]) if inst.kind == "mc" else None,
         "warm_start": None if warm is None else {
             "kind": "learned (3-layer message passing, bf16 activations)", "training": {
                 k: v for k, v in warm.items() if k != "batch_stats"}, "cold_start_same_run": cold},
+        "fp64_same_run": fp64,
         "kernels": kernels, "setup_s": {"generate": gen_s, "create": create_s},
     }
     print(json.dumps(line), flush=True)

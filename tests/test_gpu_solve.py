@@ -254,6 +254,39 @@ def test_prefetch_variants_are_bit_identical(prec):
     assert np.array_equal(Ra, Rb) and np.array_equal(ya, yb)
 
 
+@pytest.mark.parametrize("prec", ["mixed", "mixed_bf16"])
+def test_shared_memory_partials_variant_is_bit_identical(prec):
+    """The step update with its partial sums in shared memory (kernel_variant bit 7,
+    six blocks per SM) performs the same operations in the same order as the
+    register form: bit-identical iterates and multipliers."""
+    n = 60_000
+    inst = W.maxcut_instance(n, W.er_graph(n, 2 * n, 3, "pm1"))
+    R0 = W.initial_factor(inst, 12, 5)
+    caps = dict(max_outer=2, max_inner=15, tol=1e-300)
+    res0, Ra, ya = _gpu_solve(inst, R0, prec=prec, kernel_variant=2 | 8, **caps)
+    res1, Rb, yb = _gpu_solve(inst, R0, prec=prec, kernel_variant=2 | 8 | 128, **caps)
+    assert res0["inner_iters"] == res1["inner_iters"] > 15
+    assert np.array_equal(Ra, Rb) and np.array_equal(ya, yb)
+
+
+@pytest.mark.parametrize("kv", [2 | 8 | 32, 2 | 8 | 128])
+def test_kernel_variants_follow_oracle_trajectory(kv):
+    """Narrow lane groups in the line-search SpMM (bit 5: other reduction order)
+    and shared-memory partials (bit 7): FP64 iterates after 5 steps equal the
+    oracle's; in the mixed form a capped solve stays within 1e-6 of the default."""
+    n = 60_000
+    inst = W.maxcut_instance(n, W.er_graph(n, 2 * n, 3, "pm1"))
+    R0 = W.initial_factor(inst, 24, 5)
+    caps = dict(max_outer=1, max_inner=5, tol=1e-300)
+    ref = O.solve(O.Problem(inst), R0, O.Params(**caps))
+    res, R, y = _gpu_solve(inst, R0, prec="fp64", kernel_variant=kv, **caps)
+    assert res["inner_iters"] == ref["inner"]
+    assert np.max(np.abs(R - ref["R"])) <= 1e-9 * np.abs(ref["R"]).max()
+    res_m, Rm, _ = _gpu_solve(inst, R0, prec="mixed", kernel_variant=kv, **caps)
+    res_d, Rd, _ = _gpu_solve(inst, R0, prec="mixed", **caps)
+    assert np.max(np.abs(Rm - Rd)) <= 1e-6 * np.abs(Rd).max()
+
+
 def test_prefetch_variant_follows_oracle_trajectory():
     """FP64 with both prefetch forms, several grid passes per kernel: the iterate
     after 5 L-BFGS steps equals the oracle's."""
