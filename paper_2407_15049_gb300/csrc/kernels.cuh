@@ -784,28 +784,21 @@ constexpr int update_min_blocks() {
     return (CPL == 1 && !std::is_same_v<arith_t<TR>, double>) ? 3 : 2;
 }
 
-// SMEM_ACC: the 14 per-thread partial sums live in shared memory (one padded
-// row of floats per thread, conflict-free) instead of registers, so that more
-// blocks fit per SM; double-float partials only.
-constexpr int kUpdAccStride = 2 * PU_N + 1;          // floats per thread (odd: no bank conflicts)
-
-template <typename TR, typename TD, int CPL, bool STEP, bool HIST, typename TDIR = TD, bool SMEM_ACC = false>
+template <typename TR, typename TD, int CPL, bool STEP, bool HIST, typename TDIR = TD>
 __device__ __forceinline__ void
 k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __restrict__ D,
          const TD* __restrict__ CD, TD* __restrict__ G, const TD* __restrict__ W,
          TD* __restrict__ hist, int64_t slot_stride, int ld, int L, int Q,
          const double* __restrict__ y, const dfloat* __restrict__ ydf, void* __restrict__ zrow_v,
-         const Ctrl* ctrl, double* __restrict__ part, VGrid vg, int pf = 0, float* acc_smem = nullptr) {
+         const Ctrl* ctrl, double* __restrict__ part, VGrid vg, int pf = 0) {
     using AR = arith_t<TR>;
     using AD = arith_t<TD>;
     using PA = part_t<TR, TD>;
     using RS = rowscalar_t<TR, TD>;             // per-row scalars (no FP64 off the FP64 path)
     using ZS = zrow_t<TD, TR>;
-    static_assert(!SMEM_ACC || std::is_same_v<PA, dfloat>, "shared-memory partials are double-float");
     ZS* __restrict__ zrow = static_cast<ZS*>(zrow_v);
     const RS rho_r = RS(ctrl->rho);
-    PA accq_reg[SMEM_ACC ? 1 : PU_N];
-    PA* const accq = SMEM_ACC ? reinterpret_cast<PA*>(acc_smem + threadIdx.x * kUpdAccStride) : accq_reg;
+    PA accq[PU_N];
 #pragma unroll
     for (int q = 0; q < PU_N; ++q) accq[q] = PA(0);
     const double taud = ctrl->tau;
@@ -960,14 +953,7 @@ k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __
             }
         }
     }
-    if constexpr (SMEM_ACC) {
-        PA fin[PU_N];
-#pragma unroll
-        for (int q = 0; q < PU_N; ++q) fin[q] = accq[q];
-        block_partials<PU_N>(fin, part, vg.pslot);
-    } else {
-        block_partials<PU_N>(accq_reg, part, vg.pslot);
-    }
+    block_partials<PU_N>(accq, part, vg.pslot);
 }
 
 // ================================================================== kernels
@@ -1051,22 +1037,6 @@ k_update_step_occ(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR
     if (gated_off(gate, ph)) return;
     k_update_body<TR, TD, CPL, true, true, TDIR>(p, R, CR, D, CD, G, W, hist, slot_stride, ld, L, Q, y, ydf, zrow_v, ctrl,
                                            part, hw_grid(), pf);
-}
-
-// The step update with its partial sums in shared memory: 6 resident blocks per SM
-// (42 registers) instead of 4 (double-float partials only).
-template <typename TR, typename TD, int CPL, typename TDIR = TD>
-__global__ void __launch_bounds__(kThreads, 6)
-k_update_step_smem(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __restrict__ D,
-                   const TD* __restrict__ CD, TD* __restrict__ G, const TD* __restrict__ W,
-                   TD* __restrict__ hist, int64_t slot_stride, int ld, int L, int Q,
-                   const double* __restrict__ y, const dfloat* __restrict__ ydf, void* __restrict__ zrow_v,
-                   const Ctrl* ctrl, double* __restrict__ part, const Ctrl* gate, int ph, int pf) {
-    __shared__ float acc[kThreads * kUpdAccStride];
-    if (gated_off(gate, ph)) return;
-    if constexpr (std::is_same_v<part_t<TR, TD>, dfloat>)
-        k_update_body<TR, TD, CPL, true, true, TDIR, true>(p, R, CR, D, CD, G, W, hist, slot_stride, ld, L, Q, y, ydf,
-                                                           zrow_v, ctrl, part, hw_grid(), pf, acc);
 }
 
 }  // namespace lorads

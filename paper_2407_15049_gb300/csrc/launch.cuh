@@ -110,10 +110,7 @@ void launch_update(const UpdateArgs& a) {
     const TD* W = static_cast<const TD*>(a.W);
     TD* H = static_cast<TD*>(a.hist);
     LORADS_CPL_SWITCH(a.sh.CPL, {
-        if (a.step && a.hist_on && a.extra_blocks == 3 && std::is_same_v<part_t<TR, TD>, dfloat>)
-            k_update_step_smem<TR, TD, CPL, TDIR><<<a.blocks, kThreads, 0, a.stream>>>(
-                a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph, a.prefetch);
-        else if (a.step && a.hist_on && a.extra_blocks == 1)
+        if (a.step && a.hist_on && a.extra_blocks == 1)
             k_update_step_occ<TR, TD, CPL, 1, TDIR><<<a.blocks, kThreads, 0, a.stream>>>(
                 a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph, a.prefetch);
         else if (a.step && a.hist_on && a.extra_blocks == 2)
