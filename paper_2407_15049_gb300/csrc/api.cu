@@ -120,6 +120,7 @@ struct lorads_ctx {
     int32_t* k_col = nullptr;
     double* k_a = nullptr;
     int32_t* k_id = nullptr;
+    int64_t* k_ptr = nullptr;           // general form: triplet range of each list position
     double* b = nullptr;
     dfloat* k_adf = nullptr;
     dfloat* a_adf = nullptr;
@@ -295,7 +296,7 @@ extern "C" void lorads_destroy(lorads_ctx* ctx) {
     dfree(ctx->c_rowptr); dfree(ctx->c_col); dfree(ctx->c_val); dfree(ctx->c_val0); dfree(ctx->c_val32); dfree(ctx->c_valdf);
     dfree(ctx->dk); dfree(ctx->da); dfree(ctx->da32); dfree(ctx->da_df); dfree(ctx->b_df);
     dfree(ctx->a_rowptr); dfree(ctx->a_col); dfree(ctx->a_k); dfree(ctx->a_a);
-    dfree(ctx->k_row); dfree(ctx->k_col); dfree(ctx->k_a); dfree(ctx->k_id); dfree(ctx->b);
+    dfree(ctx->k_row); dfree(ctx->k_col); dfree(ctx->k_a); dfree(ctx->k_id); dfree(ctx->k_ptr); dfree(ctx->b);
     dfree(ctx->k_adf); dfree(ctx->a_adf);
     dfree(ctx->part); dfree(ctx->small); dfree(ctx->ctrl);
     if (ctx->h_small) cudaFreeHost(ctx->h_small);
@@ -358,12 +359,14 @@ lorads_status validate_and_build(lorads_ctx* ctx, int64_t n, const int64_t* rp, 
         if ((s = upload(ctx, &ctx->a_k, hp.a_k.data(), hp.a_k.size()))) return s;
         if ((s = upload(ctx, &ctx->a_a, hp.a_a.data(), hp.a_a.size()))) return s;
     }
-    if ((s = upload(ctx, &ctx->k_row, hp.k_row.data(), m))) return s;
-    if ((s = upload(ctx, &ctx->k_col, hp.k_col.data(), m))) return s;
-    if ((s = upload(ctx, &ctx->k_a, hp.k_a.data(), m))) return s;
+    const size_t n_trip = hp.k_row.size();       // m, or the triplet count of the general form
+    if ((s = upload(ctx, &ctx->k_row, hp.k_row.data(), n_trip))) return s;
+    if ((s = upload(ctx, &ctx->k_col, hp.k_col.data(), n_trip))) return s;
+    if ((s = upload(ctx, &ctx->k_a, hp.k_a.data(), n_trip))) return s;
     if ((s = upload(ctx, &ctx->k_id, hp.k_id.data(), m))) return s;
+    if (!hp.k_ptr.empty() && (s = upload(ctx, &ctx->k_ptr, hp.k_ptr.data(), m + 1))) return s;
     if ((s = upload(ctx, &ctx->b, b, m))) return s;
-    if ((s = upload(ctx, &ctx->k_adf, hp.k_adf.data(), m))) return s;
+    if ((s = upload(ctx, &ctx->k_adf, hp.k_adf.data(), n_trip))) return s;
     if (m_off > 0 && (s = upload(ctx, &ctx->a_adf, hp.a_adf.data(), hp.a_adf.size()))) return s;
     ProbDev& p = ctx->pd;
     p.n = n; p.m = m;
@@ -371,7 +374,7 @@ lorads_status validate_and_build(lorads_ctx* ctx, int64_t n, const int64_t* rp, 
     p.c_valdf = ctx->c_valdf;
     p.dk = ctx->dk; p.da = ctx->da; p.da32 = ctx->da32; p.da_df = ctx->da_df; p.b_df = ctx->b_df;
     p.a_rowptr = ctx->a_rowptr; p.a_col = ctx->a_col; p.a_k = ctx->a_k; p.a_a = ctx->a_a;
-    p.k_row = ctx->k_row; p.k_col = ctx->k_col; p.k_a = ctx->k_a; p.k_id = ctx->k_id;
+    p.k_row = ctx->k_row; p.k_col = ctx->k_col; p.k_a = ctx->k_a; p.k_id = ctx->k_id; p.k_ptr = ctx->k_ptr;
     p.m_diag = m_diag; p.m_off = m_off;
     p.b = ctx->b;
     p.k_adf = ctx->k_adf;
@@ -1016,6 +1019,9 @@ lorads_status run_admm(lorads_ctx* ctx, double rho, std::chrono::steady_clock::t
     SolverState& st = ctx->st;
     const lorads_params& P = ctx->prm;
     lorads_status s;
+    if (ctx->pd.k_ptr != nullptr)
+        return set_err(ctx, "the ADMM stage takes constraints of one triplet each (the general form is solved by "
+                            "the ALM stage)"), LORADS_ERR_UNSUPPORTED;
     if ((s = admm_alloc<TR, TW>(ctx, st.ld))) return s;
     AdmmState& a = ctx->admm;
     cudaStream_t ss = ctx->solve_stream;
@@ -1221,14 +1227,16 @@ lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0,
     if ((s = start_state<TR, TD, TDIR>(ctx, prec, R0, r0, r0_on_device, y0))) return s;
     // two-stage solve: the ALM stage stops at the switch tolerance; re-opt: the
     // first solve stops on primal feasibility alone
-    const double alm_tol = (P.admm_switch > 0 && P.reopt_level <= 0) ? std::max(P.admm_switch, P.tol) : P.tol;
+    // (the general form, constraints with several triplets, runs the ALM stage alone)
+    const bool two_stage = P.admm_switch > 0 && P.reopt_level <= 0 && ctx->pd.k_ptr == nullptr;
+    const double alm_tol = two_stage ? std::max(P.admm_switch, P.tol) : P.tol;
     const double rho0 = P.rho0 > 0 ? P.rho0 : 1.0 / ctx->mean_abs_c;
     if ((s = start_alm<TR, TD, TDIR>(ctx, rho0, alm_tol, P.reopt_level > 0 ? 1 : 0))) return s;
     lorads_result alm{};
     lorads_status fs = run_alm<TR, TD, TDIR>(ctx, prec, t0, &alm);
     if (fs == LORADS_OK && P.reopt_level > 0)
         fs = run_reopt<TR, TD, TDIR>(ctx, prec, t0, &alm);
-    else if (fs == LORADS_OK && P.admm_switch > 0 && !(alm.err1 <= P.tol && std::fabs(alm.err3) <= P.tol))
+    else if (fs == LORADS_OK && two_stage && !(alm.err1 <= P.tol && std::fabs(alm.err3) <= P.tol))
         fs = run_admm<TR, TD>(ctx, alm.rho, t0, &alm);
     if (res) *res = alm;
     return fs;
@@ -1394,6 +1402,8 @@ extern "C" lorads_status lorads_admm_operator(lorads_ctx* ctx, const void* V, co
     if (!V || !X || !out || !aligned16(V) || !aligned16(X) || !aligned16(out))
         return set_err(ctx, "V, X and out must be 16-byte aligned device pointers"), LORADS_ERR_INVALID_ARG;
     if (out == V || out == X) return set_err(ctx, "out must alias neither V nor X"), LORADS_ERR_INVALID_ARG;
+    if (ctx->pd.k_ptr != nullptr)
+        return set_err(ctx, "the ADMM operator takes constraints of one triplet each"), LORADS_ERR_UNSUPPORTED;
     const AdmmRows rows = admm_rows(ctx, ld, sh, ctx->stream);
     if (prec == LORADS_FP64)
         admm_op<double, double>(rows, V, nullptr, const_cast<void*>(X), out, nullptr, rho, 0, part_of(ctx, PART_MISC));
@@ -1414,6 +1424,8 @@ extern "C" lorads_status lorads_admm_cg(lorads_ctx* ctx, const void* V, void* X,
     if (V == X) return set_err(ctx, "X must not alias V"), LORADS_ERR_INVALID_ARG;
     if (!(cg_rel > 0.0 && cg_rel < 1.0) || cg_max < 1)
         return set_err(ctx, "need 0 < cg_rel < 1 and cg_max >= 1"), LORADS_ERR_INVALID_ARG;
+    if (ctx->pd.k_ptr != nullptr)
+        return set_err(ctx, "the ADMM block step takes constraints of one triplet each"), LORADS_ERR_UNSUPPORTED;
     if (prec == LORADS_FP64) return run_admm_cg<double, double>(ctx, V, X, y, rho, ld, sh, cg_rel, cg_max, steps_out);
     return run_admm_cg<float, float>(ctx, V, X, y, rho, ld, sh, cg_rel, cg_max, steps_out);
 }

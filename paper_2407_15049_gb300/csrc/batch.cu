@@ -371,6 +371,9 @@ extern "C" lorads_status lorads_batch_create(lorads_batch** out, int32_t count, 
         lorads_status s = build_host_prob(&hp[i], &e, n, rp, c_colind + nnz_at, c_val + nnz_at, m, m, a_con + k_at,
                                           a_row + k_at, a_col + k_at, a_val + k_at, b_in + k_at);
         if (s != LORADS_OK) return fail(s, "instance " + std::to_string(i) + ": " + e);
+        if (!hp[i].k_ptr.empty())
+            return fail(LORADS_ERR_UNSUPPORTED, "instance " + std::to_string(i) + ": several constraints on one "
+                        "entry (the general form) is solved by lorads_solve, not by the batched solve");
         rp_at += n + 1;
         nnz_at += nnz;
         k_at += m;

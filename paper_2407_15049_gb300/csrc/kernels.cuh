@@ -30,11 +30,15 @@ struct ProbDev {
     const int32_t* a_col;
     const int32_t* a_k;
     const double* a_a;
-    // constraint list, diagonal constraints first: (row <= col, coef, original index)
+    // constraint list, fused diagonal constraints first: triplets (row <= col, coef) in
+    // list order and the constraint of each list position.  k_ptr (general form,
+    // constraints with several triplets): position q owns triplets k_ptr[q]..k_ptr[q+1]-1;
+    // null: position q is triplet q.
     const int32_t* k_row;
     const int32_t* k_col;
     const double* k_a;
     const int32_t* k_id;
+    const int64_t* k_ptr;
     int64_t m_diag, m_off;
     const double* b;
     // double-float mirrors of the constraint coefficients (list order and pattern
@@ -527,11 +531,139 @@ k_spmm_a_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld,
 //   CONS_ZZ  : partial |z|^2
 enum { CONS_EVAL = 0, CONS_LS = 1, CONS_YTIL = 2, CONS_YUPD = 3, CONS_ZZ = 4 };
 
+// General form of the constraint pass: list position q is one constraint whose
+// triplets t (i <= j, a) are summed with the weights of the triplet convention:
+//   <A_k, U V^T> = sum_t a (u_i.v_j + [i != j] u_j.v_i),
+// and, with f = 1 (i == j) or 2, z = sum_t f a r_i.r_j - b_k, q1 = sum_t f a
+// (r_i.d_j + d_i.r_j) / (1 + [i == j]) ... written per triplet as in the single-triplet
+// path, then the same per-constraint formulas.  Each lane accumulates its share of
+// every triplet's dots; the group sum follows the triplet loop (no shuffle inside
+// the loop, whose trip count differs between the groups of a warp).
+template <typename TU, typename TV, int CPL, int MODE>
+__device__ __forceinline__ void
+k_cons_general(ProbDev p, int64_t k0, int64_t k1, const TU* __restrict__ U, const TV* __restrict__ V, int ld, int L,
+               int Q, double* y, void* __restrict__ out, void* zk, dfloat* ydf, const Ctrl* ctrl, double rho_arg,
+               double* __restrict__ part, VGrid vg) {
+    constexpr int NQ = MODE == CONS_LS ? PL_N : PC_N;
+    using PA = part_t<TU, TV>;
+    PA accq[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) accq[q] = PA(0);
+    const double rho = ctrl ? ctrl->rho : rho_arg;
+    const bool same = (const void*)U == (const void*)V;
+    using AU = wide_t<TU, TU>;
+    using AW = wide_t<TU, TV>;
+    using AV = wide_t<TV, TV>;
+    using CS = std::conditional_t<std::is_same_v<PA, double>, double, dfloat>;
+    const CS rho_c = CS(rho);
+    CS* zkc = static_cast<CS*>(zk);
+    RowLoop rl(L, vg);
+    const int64_t cnt = k1 - k0;
+    for (int64_t base = rl.first; base < cnt; base += rl.stride) {
+        const int64_t q = k0 + base + rl.gw;
+        const bool act = q < k1;
+        // per-lane weighted dots: z part (f a u_i.u_j), q1 part, q2 part / EVAL value
+        AU s_z = AU(0);
+        AW s_1 = AW(0);
+        AV s_2 = AV(0);
+        if (act) {
+            const int64_t t0 = __ldg(p.k_ptr + q), t1 = __ldg(p.k_ptr + q + 1);
+            for (int64_t t = t0; t < t1; ++t) {
+                const int i = __ldg(p.k_row + t), j = __ldg(p.k_col + t);
+                const bool dg = i == j;
+                const double a = __ldg(p.k_a + t);
+                const double fa = dg ? a : 2.0 * a;
+                Unit<TU> ui[CPL], uj[CPL];
+                load_row<TU, CPL>(ui, U, i, ld, L, Q, rl.lig);
+                if (!dg) load_row<TU, CPL>(uj, U, j, ld, L, Q, rl.lig);
+                if constexpr (MODE == CONS_EVAL) {
+                    if (same) {
+                        s_z = s_z + AU(fa) * (dg ? dot_units<AU>(ui, ui) : dot_units<AU>(ui, uj));
+                    } else {
+                        Unit<TV> vi[CPL], vj[CPL];
+                        load_row<TV, CPL>(vi, V, i, ld, L, Q, rl.lig);
+                        if (dg) {
+                            s_1 = s_1 + AW(a) * dot_units<AW>(ui, vi);
+                        } else {
+                            load_row<TV, CPL>(vj, V, j, ld, L, Q, rl.lig);
+                            s_1 = s_1 + AW(a) * (dot_units<AW>(ui, vj) + dot_units<AW>(uj, vi));
+                        }
+                    }
+                } else {
+                    if (MODE != CONS_LS || zk == nullptr)
+                        s_z = s_z + AU(fa) * (dg ? dot_units<AU>(ui, ui) : dot_units<AU>(ui, uj));
+                    if constexpr (MODE == CONS_LS) {
+                        Unit<TV> vi[CPL], vj[CPL];
+                        load_row<TV, CPL>(vi, V, i, ld, L, Q, rl.lig);
+                        if (dg) {
+                            const AW d = dot_units<AW>(ui, vi);
+                            s_1 = s_1 + AW(fa) * (d + d);
+                            s_2 = s_2 + AV(fa) * dot_units<AV>(vi, vi);
+                        } else {
+                            load_row<TV, CPL>(vj, V, j, ld, L, Q, rl.lig);
+                            s_1 = s_1 + AW(fa) * (dot_units<AW>(ui, vj) + dot_units<AW>(vi, uj));
+                            s_2 = s_2 + AV(fa) * dot_units<AV>(vi, vj);
+                        }
+                    }
+                }
+            }
+        }
+        s_z = group_sum(s_z, L);
+        s_1 = group_sum(s_1, L);
+        s_2 = group_sum(s_2, L);
+        if (act && rl.lig == 0) {
+            const int k = __ldg(p.k_id + q);
+            if constexpr (MODE == CONS_EVAL) {
+                static_cast<double*>(out)[k] = same ? double(s_z) : double(s_1);
+            } else {
+                CS yk = CS(0.0), bk;
+                if constexpr (MODE != CONS_ZZ) {
+                    if constexpr (std::is_same_v<CS, double>) yk = y[k];
+                    else yk = ydf ? ld_scalar<CS>(y, ydf, k) : CS(y[k]);
+                }
+                if constexpr (std::is_same_v<CS, double>) bk = __ldg(p.b + k);
+                else bk = p.b_df ? ld_scalar<CS>(p.b, p.b_df, k) : CS(__ldg(p.b + k));
+                const CS z = (MODE == CONS_LS && zk != nullptr) ? zkc[k] : CS(s_z) - bk;
+                if constexpr (MODE == CONS_LS) {
+                    const CS yt = yk - rho_c * z;
+                    const CS q1 = CS(s_1);
+                    const CS q2 = CS(s_2);
+                    accq[PL_YQ1] += PA(yt * q1);
+                    accq[PL_YQ2] += PA(yt * q2);
+                    accq[PL_Q1Q1] += PA(q1 * q1);
+                    accq[PL_Q1Q2] += PA(q1 * q2);
+                    accq[PL_Q2Q2] += PA(q2 * q2);
+                } else {
+                    accq[PC_ZZ] += PA(z * z);
+                    if constexpr (MODE == CONS_YTIL) {
+                        static_cast<CS*>(out)[k] = yk - rho_c * z;
+                        if (zk != nullptr) zkc[k] = z;
+                    } else if constexpr (MODE == CONS_YUPD) {
+                        const CS yn = yk - rho_c * z;
+                        y[k] = double(yn);
+                        if constexpr (std::is_same_v<CS, dfloat>) {
+                            if (ydf != nullptr) ydf[k] = yn;
+                        } else {
+                            if (ydf != nullptr) ydf[k] = dfloat(yn);
+                        }
+                        accq[PC_BY] += PA(bk * yn);
+                    }
+                }
+            }
+        }
+    }
+    if constexpr (MODE != CONS_EVAL) block_partials<NQ>(accq, part, vg.pslot);
+}
+
 template <typename TU, typename TV, int CPL, int MODE>
 __device__ __forceinline__ void
 k_cons_body(ProbDev p, int64_t k0, int64_t k1, const TU* __restrict__ U, const TV* __restrict__ V, int ld, int L, int Q,
        double* y, void* __restrict__ out, void* zk, dfloat* ydf, const Ctrl* ctrl, double rho_arg,
        double* __restrict__ part, VGrid vg) {
+    if (p.k_ptr != nullptr) {
+        k_cons_general<TU, TV, CPL, MODE>(p, k0, k1, U, V, ld, L, Q, y, out, zk, ydf, ctrl, rho_arg, part, vg);
+        return;
+    }
     constexpr int NQ = MODE == CONS_LS ? PL_N : PC_N;
     using PA = part_t<TU, TV>;
     PA accq[NQ];

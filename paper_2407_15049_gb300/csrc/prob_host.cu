@@ -46,13 +46,9 @@ lorads_status build_host_prob(HostProb* hp, std::string* err, int64_t n, const i
     }
     hp->cnorm1 = sum_abs;
     hp->mean_abs_c = cnt_nz ? sum_abs / (double)cnt_nz : 1.0;
-    // constraints
-    if (nnz_a != m)
-        return set_err("every constraint must be a single triplet (nnz_a == m); constraints with several "
-                            "entries are not supported"),
-               LORADS_ERR_UNSUPPORTED;
-    std::vector<int32_t> seen(m, 0);
-    std::vector<int32_t> trip_of(m, -1);
+    // constraints: validate every triplet, then group the triplets by constraint
+    if (nnz_a < m) return set_err("every constraint needs at least one triplet (nnz_a >= m)"), LORADS_ERR_INVALID_ARG;
+    std::vector<int64_t> kstart(m + 1, 0);
     for (int64_t t = 0; t < nnz_a; ++t) {
         const int32_t k = acon[t], i = arow[t], j = acol[t];
         if (k < 0 || k >= m) return set_err("a_con out of range"), LORADS_ERR_INVALID_ARG;
@@ -60,8 +56,25 @@ lorads_status build_host_prob(HostProb* hp, std::string* err, int64_t n, const i
             return set_err("constraint triplet needs 0 <= a_row <= a_col < n"), LORADS_ERR_INVALID_ARG;
         if (!std::isfinite(aval[t]) || aval[t] == 0.0)
             return set_err("constraint coefficient must be finite and nonzero"), LORADS_ERR_INVALID_ARG;
-        if (seen[k]++) return set_err("constraint with several triplets"), LORADS_ERR_UNSUPPORTED;
-        trip_of[k] = (int32_t)t;
+        kstart[k + 1]++;
+    }
+    for (int64_t k = 0; k < m; ++k) {
+        if (kstart[k + 1] == 0) return set_err("constraint " + std::to_string(k) + " has no triplet"), LORADS_ERR_INVALID_ARG;
+        kstart[k + 1] += kstart[k];
+    }
+    std::vector<int32_t> trip(nnz_a);           // triplet ids grouped by constraint, input order within
+    {
+        std::vector<int64_t> fill(kstart.begin(), kstart.end() - 1);
+        for (int64_t t = 0; t < nnz_a; ++t) trip[fill[acon[t]]++] = (int32_t)t;
+    }
+    // two triplets of one constraint on the same entry are one entry with the summed coefficient
+    for (int64_t k = 0; k < m; ++k) {
+        if (kstart[k + 1] - kstart[k] < 2) continue;
+        std::vector<int64_t> keys;
+        for (int64_t q = kstart[k]; q < kstart[k + 1]; ++q) keys.push_back((int64_t)arow[trip[q]] * n + acol[trip[q]]);
+        std::sort(keys.begin(), keys.end());
+        if (std::adjacent_find(keys.begin(), keys.end()) != keys.end())
+            return set_err("constraint " + std::to_string(k) + " lists one entry twice"), LORADS_ERR_INVALID_ARG;
     }
     double bmax = 0.0, b1 = 0.0;
     for (int64_t k = 0; k < m; ++k) {
@@ -71,58 +84,75 @@ lorads_status build_host_prob(HostProb* hp, std::string* err, int64_t n, const i
     }
     hp->bnorm_inf = bmax;
     hp->bnorm1 = b1;
-    // diagonal constraints by row
+    // General form (Sec. 4.5: constraints with several entries, or several constraints
+    // on one entry): constraint list positions carry triplet ranges (k_ptr).  Otherwise
+    // every constraint is one triplet and position = triplet.
+    bool general = nnz_a > m;
+    // diagonal constraints of one triplet, at most one per row: fused into the row passes
     std::vector<int32_t> dk(n, -1);
     std::vector<double> da(n, 0.0);
+    std::vector<char> fused(m, 0);
     int64_t m_diag = 0;
-    std::vector<int64_t> offkeys;
     for (int64_t k = 0; k < m; ++k) {
-        const int32_t t = trip_of[k];
-        const int32_t i = arow[t], j = acol[t];
-        if (i == j) {
-            if (dk[i] >= 0) return set_err("two constraints on the same diagonal entry"), LORADS_ERR_UNSUPPORTED;
-            dk[i] = (int32_t)k;
-            da[i] = aval[t];
-            ++m_diag;
+        if (kstart[k + 1] - kstart[k] != 1) continue;
+        const int32_t t = trip[kstart[k]];
+        const int32_t i = arow[t];
+        if (i != acol[t]) continue;
+        if (dk[i] >= 0) {
+            general = true;                     // a second one on this row stays in the list
+            continue;
         }
+        dk[i] = (int32_t)k;
+        da[i] = aval[t];
+        fused[k] = 1;
+        ++m_diag;
     }
     const int64_t m_off = m - m_diag;
-    // ordered constraint list: diagonal constraints by row, then off-diagonal by (row, col)
+    // the other constraints, ordered by the entry of their first triplet
+    std::vector<std::pair<int64_t, int32_t>> off;
+    off.reserve(m_off);
+    for (int64_t k = 0; k < m; ++k)
+        if (!fused[k]) {
+            const int32_t t = trip[kstart[k]];
+            off.emplace_back((int64_t)arow[t] * n + acol[t], (int32_t)k);
+        }
+    std::sort(off.begin(), off.end());
+    for (size_t q = 1; q < off.size() && !general; ++q)
+        if (off[q].first == off[q - 1].first) general = true;     // several constraints on one entry
+    // ordered constraint list: fused diagonal constraints by row, then the others
     std::vector<int32_t> order;
     order.reserve(m);
     for (int64_t i = 0; i < n; ++i)
         if (dk[i] >= 0) order.push_back(dk[i]);
-    {
-        std::vector<std::pair<int64_t, int32_t>> off;
-        off.reserve(m_off);
-        for (int64_t k = 0; k < m; ++k) {
-            const int32_t t = trip_of[k];
-            if (arow[t] != acol[t]) off.emplace_back((int64_t)arow[t] * n + acol[t], (int32_t)k);
-        }
-        std::sort(off.begin(), off.end());
-        for (size_t q = 1; q < off.size(); ++q)
-            if (off[q].first == off[q - 1].first)
-                return set_err("two constraints on the same off-diagonal entry"), LORADS_ERR_UNSUPPORTED;
-        for (auto& pr : off) order.push_back(pr.second);
-    }
-    std::vector<int32_t> k_row(m), k_col(m), k_id(m);
-    std::vector<double> k_a(m);
+    for (auto& pr : off) order.push_back(pr.second);
+    // triplets in list order; k_ptr (general form) maps a list position to its range
+    std::vector<int32_t> k_row, k_col, k_id(m);
+    std::vector<double> k_a;
+    std::vector<int64_t> k_ptr;
+    if (general) k_ptr.assign(m + 1, 0);
     for (int64_t q = 0; q < m; ++q) {
         const int32_t k = order[q];
-        const int32_t t = trip_of[k];
-        k_row[q] = arow[t];
-        k_col[q] = acol[t];
-        k_a[q] = aval[t];
         k_id[q] = k;
+        for (int64_t u = kstart[k]; u < kstart[k + 1]; ++u) {
+            const int32_t t = trip[u];
+            k_row.push_back(arow[t]);
+            k_col.push_back(acol[t]);
+            k_a.push_back(aval[t]);
+        }
+        if (general) k_ptr[q + 1] = (int64_t)k_row.size();
     }
-    // off-diagonal constraint pattern (symmetric, sorted by column within a row)
+    // pattern of the listed constraints (symmetric, sorted by column within a row):
+    // slot (row i, column j) per entry of A_k, i.e. two per off-diagonal triplet and
+    // one per diagonal triplet (general form only)
     std::vector<int64_t> a_rp(n + 1, 0);
     std::vector<int32_t> a_col, a_k;
     std::vector<double> a_a;
     if (m_off > 0) {
-        for (int64_t q = m_diag; q < m; ++q) {
-            a_rp[k_row[q] + 1]++;
-            a_rp[k_col[q] + 1]++;
+        const int64_t t0 = general ? k_ptr[m_diag] : m_diag;
+        const int64_t t1 = (int64_t)k_row.size();
+        for (int64_t t = t0; t < t1; ++t) {
+            a_rp[k_row[t] + 1]++;
+            if (k_row[t] != k_col[t]) a_rp[k_col[t] + 1]++;
         }
         for (int64_t i = 0; i < n; ++i) a_rp[i + 1] += a_rp[i];
         const int64_t nz = a_rp[n];
@@ -130,12 +160,20 @@ lorads_status build_host_prob(HostProb* hp, std::string* err, int64_t n, const i
         a_k.resize(nz);
         a_a.resize(nz);
         std::vector<int64_t> fill(a_rp.begin(), a_rp.end() - 1);
-        for (int64_t q = m_diag; q < m; ++q) {
-            const int32_t i = k_row[q], j = k_col[q];
+        int64_t q = m_diag;
+        for (int64_t t = t0; t < t1; ++t) {
+            if (general) {
+                while (k_ptr[q + 1] <= t) ++q;
+            } else {
+                q = t;
+            }
+            const int32_t i = k_row[t], j = k_col[t];
             int64_t s = fill[i]++;
-            a_col[s] = j; a_k[s] = k_id[q]; a_a[s] = k_a[q];
-            s = fill[j]++;
-            a_col[s] = i; a_k[s] = k_id[q]; a_a[s] = k_a[q];
+            a_col[s] = j; a_k[s] = k_id[q]; a_a[s] = k_a[t];
+            if (i != j) {
+                s = fill[j]++;
+                a_col[s] = i; a_k[s] = k_id[q]; a_a[s] = k_a[t];
+            }
         }
         // sort each row by column
         std::vector<int64_t> idx;
@@ -143,15 +181,16 @@ lorads_status build_host_prob(HostProb* hp, std::string* err, int64_t n, const i
             const int64_t s0 = a_rp[i], s1 = a_rp[i + 1];
             if (s1 - s0 < 2) continue;
             idx.resize(s1 - s0);
-            for (int64_t q = 0; q < s1 - s0; ++q) idx[q] = s0 + q;
+            for (int64_t u = 0; u < s1 - s0; ++u) idx[u] = s0 + u;
             std::sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return a_col[x] < a_col[y]; });
             std::vector<int32_t> tc(s1 - s0), tk(s1 - s0);
             std::vector<double> ta(s1 - s0);
-            for (int64_t q = 0; q < s1 - s0; ++q) { tc[q] = a_col[idx[q]]; tk[q] = a_k[idx[q]]; ta[q] = a_a[idx[q]]; }
-            for (int64_t q = 0; q < s1 - s0; ++q) { a_col[s0 + q] = tc[q]; a_k[s0 + q] = tk[q]; a_a[s0 + q] = ta[q]; }
+            for (int64_t u = 0; u < s1 - s0; ++u) { tc[u] = a_col[idx[u]]; tk[u] = a_k[idx[u]]; ta[u] = a_a[idx[u]]; }
+            for (int64_t u = 0; u < s1 - s0; ++u) { a_col[s0 + u] = tc[u]; a_k[s0 + u] = tk[u]; a_a[s0 + u] = ta[u]; }
         }
         hp->nnz_aoff = nz;
     }
+    hp->k_ptr = std::move(k_ptr);
     hp->n = n; hp->m = m; hp->nnz_c = nnz; hp->m_diag = m_diag; hp->m_off = m_off;
     hp->rp = rp; hp->ci = ci; hp->cv = cv; hp->b = b;
     hp->cv32.assign(cv, cv + nnz);

@@ -1,5 +1,5 @@
 // Host-side validation and layout of one problem instance (the primal SDP
-// min <C,X> s.t. <A_k,X> = b_k of Sec. 2, with single-entry constraints):
+// min <C,X> s.t. <A_k,X> = b_k of Sec. 2, constraints given as triplets):
 // the checks of lorads_create and the derived arrays every solver uploads.
 #pragma once
 
@@ -32,9 +32,14 @@ struct HostProb {
     std::vector<int64_t> a_rp;
     std::vector<int32_t> a_col, a_k;
     std::vector<double> a_a;
-    // constraint list: diagonal constraints by row, then off-diagonal by (row, col)
+    // constraint list: fused diagonal constraints by row, then the others by the entry
+    // of their first triplet.  k_id: constraint of each list position.  k_row, k_col,
+    // k_a: the triplets in list order; with k_ptr (general form: a constraint with
+    // several triplets, or several constraints on one entry) position q owns triplets
+    // k_ptr[q] .. k_ptr[q+1]-1, otherwise position q is triplet q.
     std::vector<int32_t> k_row, k_col, k_id;
     std::vector<double> k_a;
+    std::vector<int64_t> k_ptr;
     // double-float mirrors of k_a and a_a
     std::vector<dfloat> k_adf, a_adf;
 };

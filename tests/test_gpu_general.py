@@ -1,0 +1,157 @@
+"""GPU parity on general constraints (the class of Sec. 4.5): constraints with
+several entries, several constraints on one entry, and a dense C.
+
+Instances: the Lovasz theta SDP (tr X = 1 over all n diagonal entries, X_ij = 0 on
+the edges, C = -J), and MaxCut SDPs with added constraints summing several
+off-diagonal entries plus X_00 + X_11 = 2 over entries the row constraints
+already fix.
+
+* Kernels: the constraint map, (C - A*(v)) R and the line-search coefficients
+  against the FP64 oracle (1e-12 FP64, 1e-5 FP32).
+* Trajectory: 1, 5 and 30 L-BFGS steps equal the oracle's (FP64).
+* Convergence: theta(C_5) = sqrt 5, theta(C_7), theta(Petersen) = 4 in FP64 and
+  the mixed form, and the oracle's objective on the MaxCut instance.
+* The two-stage switch falls back to the ALM stage alone on this form.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import lorads_oracle as O
+from tests._util import rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_2407_15049_gb300 as L  # noqa: E402
+
+PREC = {"fp64": L.LORADS_FP64, "mixed": L.LORADS_MIXED, "df64": L.LORADS_DF64, "fp32": L.LORADS_FP32}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    L.build()
+
+
+def _instance(name):
+    if name == "theta_petersen":
+        return W.theta_instance(10, W.petersen_graph())
+    if name == "theta_c7":
+        return W.theta_instance(7, W.cycle_graph(7))
+    if name == "theta_er60":
+        return W.theta_instance(60, W.er_graph(60, 200, 4, "unit"))
+    return W.maxcut_with_sums(300, W.er_graph(300, 900, 2, "pm1"), 4, 12, 3)
+
+
+def _dev(a, dtype, ld):
+    t = torch.zeros((a.shape[0], ld), dtype=dtype, device="cuda")
+    t[:, :a.shape[1]] = torch.as_tensor(a, dtype=dtype, device="cuda")
+    return t
+
+
+def _start(inst, r, seed):
+    """Seeded Gaussian start: ||R0||_F = 1 for theta (tr X = 1), unit rows otherwise (X_ii = 1)."""
+    R0 = np.random.default_rng(seed).standard_normal((inst.n, r))
+    if inst.kind == "theta":
+        return R0 / np.linalg.norm(R0)
+    return R0 / np.linalg.norm(R0, axis=1, keepdims=True)
+
+
+NAMES = ["theta_petersen", "theta_er60", "maxcut_sums_300"]
+
+
+@pytest.mark.parametrize("r", [1, 6, 17])
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_kernels_match_oracle(name, r, prec):
+    inst = _instance(name)
+    P = O.Problem(inst)
+    rng = np.random.default_rng(r + 1)
+    U, V, D = (rng.standard_normal((inst.n, r)) for _ in range(3))
+    v = rng.standard_normal(inst.m)
+    y = rng.standard_normal(inst.m)
+    rho = 1.7
+    ld = L.padded_ld(r)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    ctx = L.lorads_create(inst)
+    try:
+        out = torch.zeros(inst.m, dtype=torch.float64, device="cuda")
+        L.lorads_constraint_eval(ctx, _dev(U, dt, ld), _dev(V, dt, ld), out, r=r)
+        torch.cuda.synchronize()
+        assert rel_err(out.cpu().numpy(), O.constraint_map(P, U, V)) <= tol
+        sp = torch.zeros((inst.n, ld), dtype=dt, device="cuda")
+        L.lorads_spmm(ctx, _dev(U, dt, ld), torch.as_tensor(v, device="cuda"), sp, r=r)
+        torch.cuda.synchronize()
+        assert rel_err(sp.double().cpu().numpy()[:, :r], O.spmm(P, U, v)) <= tol
+        a, _ = L.lorads_linesearch_coeffs(ctx, _dev(U, dt, ld), _dev(D, dt, ld), torch.as_tensor(y, device="cuda"),
+                                          rho, r=r)
+    finally:
+        L.lorads_destroy(ctx)
+    a_ref, parts = O.linesearch_coeffs(P, U, D, y, rho)
+    # cancellation-aware scale of each coefficient: the magnitudes of its terms
+    q1, q2, q0 = parts["q1"], parts["q2"], parts["q0"]
+    w = np.abs(y) + rho * np.abs(q0)
+    Cabs = abs(P.C)
+    scale = np.array([0.5 * rho * float(q2 @ q2), rho * float(np.abs(q1) @ np.abs(q2)),
+                      float(np.sum((Cabs @ np.abs(D)) * np.abs(D))) + float(w @ np.abs(q2)) + 0.5 * rho * float(q1 @ q1),
+                      2 * float(np.sum((Cabs @ np.abs(U)) * np.abs(D))) + float(w @ np.abs(q1))])
+    assert np.all(np.abs(a - a_ref) <= tol * scale), (a, a_ref)
+
+
+@pytest.mark.parametrize("k", [1, 5, 30])
+@pytest.mark.parametrize("name", ["theta_er60", "maxcut_sums_300"])
+def test_trajectory_matches_oracle(name, k):
+    inst = _instance(name)
+    R0 = _start(inst, 6, 2)
+    caps = dict(max_outer=1, max_inner=k, tol=1e-300)
+    ref = O.solve(O.Problem(inst), R0, O.Params(**caps))
+    ctx = L.lorads_create(inst, L.default_params(prec=L.LORADS_FP64, **caps))
+    try:
+        res = L.lorads_solve(ctx, R0)
+        R, y = L.lorads_get_solution(ctx, inst.n, inst.m)
+    finally:
+        L.lorads_destroy(ctx)
+    assert res["inner_iters"] == ref["inner"]
+    assert np.max(np.abs(R - ref["R"])) <= 1e-9 * np.abs(ref["R"]).max() * max(1, k / 10)
+    assert np.max(np.abs(y - ref["y"])) <= 1e-8 * (1 + np.abs(ref["y"]).max())
+
+
+@pytest.mark.parametrize("name", ["C5", "C7", "petersen"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "df64"])
+def test_theta_closed_forms(name, prec):
+    if name == "petersen":
+        inst, value = W.theta_instance(10, W.petersen_graph()), 4.0
+    else:
+        n = int(name[1:])
+        c = math.cos(math.pi / n)
+        inst, value = W.theta_instance(n, W.cycle_graph(n)), n * c / (1 + c)
+    R0 = _start(inst, 3, 1)
+    ctx = L.lorads_create(inst, L.default_params(prec=PREC[prec], compute_err2=1))
+    try:
+        res = L.lorads_solve(ctx, R0)
+    finally:
+        L.lorads_destroy(ctx)
+    assert res["status_name"] == "LORADS_OK", res
+    assert -res["primal_obj"] == pytest.approx(value, rel=1e-5)
+    assert res["err1"] <= 1e-5 and abs(res["err3"]) <= 1e-5 and res["err2"] <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_maxcut_with_sums_converges_to_oracle_objective(prec):
+    inst = _instance("maxcut_sums_300")
+    R0 = _start(inst, 20, 1)
+    ref = O.solve(O.Problem(inst), R0, O.Params())
+    ctx = L.lorads_create(inst, L.default_params(prec=PREC[prec], admm_switch=1e-3))
+    try:
+        res = L.lorads_solve(ctx, R0)
+        R, _ = L.lorads_get_solution(ctx, inst.n, inst.m)
+    finally:
+        L.lorads_destroy(ctx)
+    assert ref["status"] == "ok" and res["status_name"] == "LORADS_OK", res
+    assert res["admm_iters"] == 0                    # this form runs the ALM stage alone
+    assert res["primal_obj"] == pytest.approx(ref["primal_obj"], rel=1e-6 if prec == "fp64" else 2e-5)
+    z = O.constraint_map(O.Problem(inst), R, R) - inst.b
+    assert np.linalg.norm(z) / (1 + np.abs(inst.b).max()) <= 1.0001e-5

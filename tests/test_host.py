@@ -100,20 +100,34 @@ def test_rejects_lower_triangle_triplet(lib):
     _expect("LORADS_ERR_INVALID_ARG", inst)
 
 
-def test_rejects_multi_entry_constraint(lib):
+def test_rejects_constraint_without_triplet(lib):
     inst = _maxcut()
     inst.con = inst.con.copy()
     inst.con[1] = 0                    # constraint 0 gets two triplets, constraint 1 none
-    msg = _expect("LORADS_ERR_UNSUPPORTED", inst)
-    assert "triplet" in msg
+    msg = _expect("LORADS_ERR_INVALID_ARG", inst)
+    assert "no triplet" in msg
 
 
-def test_rejects_duplicate_entry_constraints(lib):
+def test_rejects_an_entry_listed_twice_in_one_constraint(lib):
+    inst = W.theta_instance(5, W.cycle_graph(5))
+    inst.row = inst.row.copy()
+    inst.col = inst.col.copy()
+    inst.row[1], inst.col[1] = inst.row[0], inst.col[0]     # tr X lists X_00 twice
+    msg = _expect("LORADS_ERR_INVALID_ARG", inst)
+    assert "twice" in msg
+
+
+def test_batch_rejects_the_general_form(lib):
+    """Several constraints on one entry are the general form: lorads_solve takes it,
+    the batched solve does not (host check, before any device call)."""
     inst = W.mc_instance(4, 5, 2, 6, seed=1)
     inst.row = inst.row.copy()
     inst.col = inst.col.copy()
     inst.row[1], inst.col[1] = inst.row[0], inst.col[0]
-    _expect("LORADS_ERR_UNSUPPORTED", inst)
+    with pytest.raises(N.LoradsError) as ei:
+        N.lorads_batch_create([inst])
+    assert N.STATUS_NAMES[ei.value.status] == "LORADS_ERR_UNSUPPORTED"
+    assert "general form" in str(ei.value)
 
 
 def test_rejects_empty_problem(lib):

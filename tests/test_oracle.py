@@ -337,3 +337,22 @@ def test_matrix_completion_recovers_nuclear_norm():
     R = res["R"]
     Mhat = R[:n1] @ R[n1:].T
     assert np.linalg.norm(Mhat - M) <= 1e-2 * np.linalg.norm(M)
+
+
+@pytest.mark.parametrize("name", ["C5", "C7", "petersen"])
+def test_lovasz_theta_closed_forms(name):
+    """Constraints with several entries (tr X = 1 over n diagonal entries) and a
+    dense C = -J: the Lovasz theta SDP reaches its closed-form values,
+    theta(C_n) = n cos(pi/n) / (1 + cos(pi/n)) for odd n (sqrt 5 for the pentagon)
+    and theta(Petersen) = 4."""
+    if name == "petersen":
+        inst, value = W.theta_instance(10, W.petersen_graph()), 4.0
+    else:
+        n = int(name[1:])
+        c = math.cos(math.pi / n)
+        inst, value = W.theta_instance(n, W.cycle_graph(n)), n * c / (1 + c)
+    R0 = np.random.default_rng(1).standard_normal((inst.n, 3))
+    R0 /= np.linalg.norm(R0)
+    res = O.solve(O.Problem(inst), R0, O.Params())
+    assert res["status"] == "ok"
+    assert -res["primal_obj"] == pytest.approx(value, rel=1e-5)

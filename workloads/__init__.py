@@ -20,6 +20,10 @@ Workloads (Sec. 4.3 MaxCut SDP and Sec. 4.4 matrix-completion SDP):
   (one diagonal triplet per row, b = 1).  The reported SDP value is -<C,X>.
 * Matrix completion: X has order n1 + n2, C = I, constraint k <-> (i, j) in
   Omega is  X_{i,n1+j} + X_{n1+j,i} = 2 M_ij  (one off-diagonal triplet).
+* General constraints (the class of Sec. 4.5, constraints with several
+  entries): the Lovasz theta SDP of a graph, max <J, X> s.t. tr X = 1 and
+  X_ij = 0 on the edges (C = -J, one constraint of n diagonal triplets), and
+  MaxCut instances with added constraints over several entries.
 
 Random numbers come from numpy's PCG64 (``numpy.random.default_rng(seed)``).
 """
@@ -33,7 +37,7 @@ import numpy as np
 __all__ = [
     "SDPInstance", "er_graph", "torus_graph", "complete_graph", "cycle_graph",
     "bipartite_torus_graph", "maxcut_instance", "mc_instance", "initial_factor",
-    "rank_log2", "config_instance",
+    "rank_log2", "config_instance", "theta_instance", "maxcut_with_sums",
 ]
 
 
@@ -226,6 +230,68 @@ def mc_instance(n1: int, n2: int, rank: int, n_samples: int, seed: int) -> SDPIn
         col=(n1 + sj).astype(np.int32), aval=np.ones(m), b=2.0 * mvals,
         kind="mc", meta={"n1": n1, "n2": n2, "U": U, "V": V},
     )
+
+
+def theta_instance(n: int, edges) -> SDPInstance:
+    """Lovasz theta SDP of a graph: min <-J, X> s.t. tr X = 1 (constraint 0: n
+    diagonal triplets, b = 1) and X_ij = 0 for every edge (one triplet (i, j, 1/2),
+    b = 0).  C = -J is stored in full (n^2 entries).  The value is theta(G)."""
+    i, j, _ = (np.asarray(x) for x in edges)
+    lo, hi = np.minimum(i, j).astype(np.int64), np.maximum(i, j).astype(np.int64)
+    keys = np.unique(lo * n + hi)
+    lo, hi = keys // n, keys % n
+    rowptr = np.arange(n + 1, dtype=np.int64) * n
+    colind = np.tile(np.arange(n, dtype=np.int32), n)
+    val = -np.ones(n * n)
+    m = 1 + len(lo)
+    con = np.concatenate([np.zeros(n, dtype=np.int32), np.arange(1, m, dtype=np.int32)])
+    row = np.concatenate([np.arange(n), lo]).astype(np.int32)
+    col = np.concatenate([np.arange(n), hi]).astype(np.int32)
+    aval = np.concatenate([np.ones(n), 0.5 * np.ones(len(lo))])
+    b = np.concatenate([[1.0], np.zeros(len(lo))])
+    return SDPInstance(n=n, rowptr=rowptr, colind=colind, val=val, m=m, con=con, row=row, col=col, aval=aval, b=b,
+                       kind="theta")
+
+
+def petersen_graph():
+    """The Petersen graph (10 vertices, 15 edges, unit weights): theta = 4."""
+    outer = [(k, (k + 1) % 5) for k in range(5)]
+    spokes = [(k, k + 5) for k in range(5)]
+    inner = [(5 + k, 5 + (k + 2) % 5) for k in range(5)]
+    e = np.array(outer + spokes + inner)
+    return e[:, 0], e[:, 1], np.ones(len(e))
+
+
+def maxcut_with_sums(n: int, edges, groups: int, size: int, seed: int) -> SDPInstance:
+    """A MaxCut SDP (X_ii = 1) with `groups` added constraints over several entries
+    each: sum of X_ij over `size` random off-diagonal pairs = 0, and one constraint
+    X_00 + X_11 = 2 on two entries the diagonal constraints already fix.  X = I is
+    feasible for all of them."""
+    base = maxcut_instance(n, edges)
+    rng = np.random.default_rng(seed)
+    con, row, col, aval, b = [base.con], [base.row], [base.col], [base.aval], [base.b]
+    k = base.m
+    for _ in range(groups):
+        a = rng.integers(0, n, 3 * size)
+        c = rng.integers(0, n, 3 * size)
+        ok = a != c
+        lo, hi = np.minimum(a[ok], c[ok]), np.maximum(a[ok], c[ok])
+        keys = np.unique(lo.astype(np.int64) * n + hi)[:size]
+        con.append(np.full(len(keys), k, dtype=np.int32))
+        row.append((keys // n).astype(np.int32))
+        col.append((keys % n).astype(np.int32))
+        aval.append(rng.uniform(0.5, 1.5, len(keys)))
+        b.append([0.0])
+        k += 1
+    con.append(np.array([k, k], dtype=np.int32))
+    row.append(np.array([0, 1], dtype=np.int32))
+    col.append(np.array([0, 1], dtype=np.int32))
+    aval.append(np.ones(2))
+    b.append([2.0])
+    k += 1
+    return SDPInstance(n=n, rowptr=base.rowptr, colind=base.colind, val=base.val, m=k,
+                       con=np.concatenate(con), row=np.concatenate(row), col=np.concatenate(col),
+                       aval=np.concatenate(aval), b=np.concatenate(b).astype(np.float64), kind="generic")
 
 
 def rank_log2(k: int) -> int:
