@@ -47,13 +47,15 @@ __global__ void k_admm_cg_init(AdmmCtrl* ac, const double* part_r, int nb) {
     ac->cg_active = (sqrt(fmax(rr, 0.0)) > ac->eps && rr > 0.0) ? 1 : 0;
 }
 
-__global__ void k_admm_alpha(AdmmCtrl* ac, const double* part_q, int nb) {
+__global__ void k_admm_alpha(AdmmCtrl* ac, const double* part_q, int nb, const double* part_w, int nb_w) {
     if (!ac->cg_active) return;
-    __shared__ double s[PQ_N];
+    __shared__ double s[PQ_N + 1];
     fold_sum(part_q, nb, PQ_N, s);
+    if (part_w != nullptr) fold_sum(part_w, nb_w, 1, s + PQ_N);
+    else if (threadIdx.x == 0) s[PQ_N] = 0.0;
     __syncthreads();
     if (threadIdx.x != 0) return;
-    const double pq = ac->rho * (s[PQ_PP] + s[PQ_WW]);
+    const double pq = ac->rho * (s[PQ_PP] + s[PQ_WW] + s[PQ_N]);
     const double alpha = ac->rr / pq;
     if (!(pq > 0.0) || !isfinite(alpha)) {
         ac->cg_active = 0;                  // no positive curvature left: keep the iterate
@@ -158,8 +160,11 @@ void admm_resid(const AdmmRows& a, const void* X, const void* V, const void* om,
 
 template <typename TR, typename TW>
 void admm_op(const AdmmRows& a, const void* V, const void* r, void* pd, void* Q, const AdmmCtrl* ac,
-             double rho_arg, int update_p, double* part) {
-    const bool fuse = update_p && a.p->m_off == 0;
+             double rho_arg, int update_p, double* part, void* w, double* part_w) {
+    // general form: the row pass covers p's update, rho p and the fused diagonal
+    // constraints; the listed constraints follow in two passes (w, then A*(w) V)
+    const bool general = a.p->k_ptr != nullptr;
+    const bool fuse = update_p && (a.p->m_off == 0 || general);
     if (update_p && !fuse) {
         const int64_t nunits = a.p->n * (int64_t)a.ld / 4;
         k_admm_pupd<TW><<<a.nb_flat, kThreads, 0, a.stream>>>(nunits, static_cast<const TW*>(r),
@@ -174,6 +179,12 @@ void admm_op(const AdmmRows& a, const void* V, const void* r, void* pd, void* Q,
             k_admm_op<TR, TW, CPL, false><<<a.nb_rows, kThreads, 0, a.stream>>>(
                 *a.p, static_cast<const TR*>(V), a.ld, a.sh.L, a.sh.Q, static_cast<const TW*>(r),
                 static_cast<TW*>(pd), static_cast<TW*>(Q), ac, rho_arg, part);
+        if (general && a.p->m_off > 0 && ac != nullptr) {
+            k_admm_opw<TR, TW, CPL><<<a.nb_cons, kThreads, 0, a.stream>>>(
+                *a.p, static_cast<const TR*>(V), a.ld, a.sh.L, a.sh.Q, static_cast<const TW*>(pd), w, ac, part_w);
+            k_admm_opq<TR, TW, CPL><<<a.nb_rows, kThreads, 0, a.stream>>>(
+                *a.p, static_cast<const TR*>(V), a.ld, a.sh.L, a.sh.Q, w, static_cast<TW*>(Q), ac);
+        }
     })
 }
 
@@ -196,8 +207,8 @@ void admm_avg(const AdmmRows& a, const void* U, const void* V, void* R) {
 void admm_cg_init(cudaStream_t s, AdmmCtrl* ac, const double* part_r, int nb) {
     k_admm_cg_init<<<1, 256, 0, s>>>(ac, part_r, nb);
 }
-void admm_alpha(cudaStream_t s, AdmmCtrl* ac, const double* part_q, int nb) {
-    k_admm_alpha<<<1, 256, 0, s>>>(ac, part_q, nb);
+void admm_alpha(cudaStream_t s, AdmmCtrl* ac, const double* part_q, int nb, const double* part_w, int nb_w) {
+    k_admm_alpha<<<1, 256, 0, s>>>(ac, part_q, nb, part_w, nb_w);
 }
 void admm_beta(cudaStream_t s, AdmmCtrl* ac, const double* part_r, int nb) {
     k_admm_beta<<<1, 256, 0, s>>>(ac, part_r, nb);
@@ -219,7 +230,7 @@ void admm_outer(cudaStream_t s, AdmmCtrl* ac, const double* part_y, int nb_y, co
     template void admm_resid<TR, TW>(const AdmmRows&, const void*, const void*, const void*, void*, void*,  \
                                      const AdmmCtrl*, double*);                                              \
     template void admm_op<TR, TW>(const AdmmRows&, const void*, const void*, void*, void*, const AdmmCtrl*,  \
-                                  double, int, double*);                                                     \
+                                  double, int, double*, void*, double*);                                     \
     template void admm_upd<TR, TW>(const AdmmRows&, void*, const void*, void*, const void*, const AdmmCtrl*, \
                                    double*);
 

@@ -76,7 +76,25 @@ k_admm_cons(ProbDev p, const TR* __restrict__ X, const TR* __restrict__ V, int l
             j = __ldg(p.k_col + t);
         }
         AR s = AR(0);
-        if (act) {
+        if (act && p.k_ptr != nullptr) {
+            // general form: list position t is one constraint, sum over its triplets
+            // (the coefficient is applied per triplet; a = 1 below)
+            const int64_t u0 = __ldg(p.k_ptr + t), u1 = __ldg(p.k_ptr + t + 1);
+            for (int64_t u = u0; u < u1; ++u) {
+                const int iu = __ldg(p.k_row + u), ju = __ldg(p.k_col + u);
+                Unit<TR> xi[CPL], vj[CPL];
+                load_row<TR, CPL>(xi, X, iu, ld, L, Q, rl.lig);
+                load_row<TR, CPL>(vj, V, ju, ld, L, Q, rl.lig);
+                AR d = dot_units<AR>(xi, vj);
+                if (iu != ju) {
+                    Unit<TR> xj[CPL], vi[CPL];
+                    load_row<TR, CPL>(xj, X, ju, ld, L, Q, rl.lig);
+                    load_row<TR, CPL>(vi, V, iu, ld, L, Q, rl.lig);
+                    d = d + dot_units<AR>(xj, vi);
+                }
+                s = s + AR(ld_cs<CS>(p.k_a, p.k_adf, u)) * d;
+            }
+        } else if (act) {
             Unit<TR> xi[CPL], vj[CPL];
             load_row<TR, CPL>(xi, X, i, ld, L, Q, rl.lig);
             load_row<TR, CPL>(vj, V, j, ld, L, Q, rl.lig);
@@ -91,7 +109,7 @@ k_admm_cons(ProbDev p, const TR* __restrict__ X, const TR* __restrict__ V, int l
         s = group_sum(s, L);
         if (act && rl.lig == 0) {
             const int k = __ldg(p.k_id + t);
-            const CS a = ld_cs<CS>(p.k_a, p.k_adf, t);
+            const CS a = p.k_ptr != nullptr ? CS(1.0) : ld_cs<CS>(p.k_a, p.k_adf, t);
             const CS bk = ld_cs<CS>(p.b, p.b_df, k);
             const CS z = a * CS(s) - bk;
             const CS yk = ld_cs<CS>(y, ydf, k);
@@ -295,7 +313,8 @@ k_admm_op(ProbDev p, const TR* __restrict__ V, int ld, int L, int Q, const TW* _
             if (rl.lig == 0) accq[PQ_WW] += PA(w * w);
         }
         // off-diagonal constraints of row i: w = a (p_i.v_j + p_j.v_i), Q_i += a w v_j
-        if (act && p.m_off > 0) {
+        // (single-triplet form; the general form adds these terms in k_admm_opw/opq)
+        if (act && p.m_off > 0 && p.k_ptr == nullptr) {
             const int64_t a0 = __ldg(p.a_rowptr + i), a1 = __ldg(p.a_rowptr + i + 1);
             for (int64_t s = a0; s < a1; ++s) {
                 const int j = __ldg(p.a_col + s);
@@ -334,6 +353,101 @@ k_admm_op(ProbDev p, const TR* __restrict__ V, int ld, int L, int Q, const TW* _
         }
     }
     block_partials<PQ_N>(accq, part);
+}
+
+// ------------------------------------------------------------------ general form
+// w_k = <A_k, p V^T> for the listed constraints (positions m_diag..m-1; each a sum
+// over its triplets), stored by constraint; partial sum of w_k^2.
+template <typename TR, typename TW, int CPL>
+__global__ void __launch_bounds__(kThreads)
+k_admm_opw(ProbDev p, const TR* __restrict__ V, int ld, int L, int Q, const TW* __restrict__ pd,
+           void* __restrict__ w_v, const AdmmCtrl* __restrict__ ac, double* __restrict__ part) {
+    if (!ac->cg_active) return;
+    using AW = arith_t<TW>;
+    using CS = admm_cs_t<TR>;
+    using PA = part_t<TW, TW>;
+    CS* __restrict__ w = static_cast<CS*>(w_v);
+    PA acc[1] = {PA(0)};
+    RowLoop rl(L, hw_grid());
+    const int64_t cnt = p.m - p.m_diag;
+    for (int64_t base = rl.first; base < cnt; base += rl.stride) {
+        const int64_t q = p.m_diag + base + rl.gw;
+        const bool act = q < p.m;
+        AW s = AW(0);
+        if (act) {
+            const int64_t u0 = __ldg(p.k_ptr + q), u1 = __ldg(p.k_ptr + q + 1);
+            for (int64_t u = u0; u < u1; ++u) {
+                const int i = __ldg(p.k_row + u), j = __ldg(p.k_col + u);
+                Unit<TW> pi[CPL];
+                Unit<TR> vj[CPL];
+                load_row<TW, CPL>(pi, pd, i, ld, L, Q, rl.lig);
+                load_row<TR, CPL>(vj, V, j, ld, L, Q, rl.lig);
+                AW d = AW(0);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) d = fma(AW(pi[c].v[e]), AW(vj[c].v[e]), d);
+                if (i != j) {
+                    Unit<TW> pj[CPL];
+                    Unit<TR> vi[CPL];
+                    load_row<TW, CPL>(pj, pd, j, ld, L, Q, rl.lig);
+                    load_row<TR, CPL>(vi, V, i, ld, L, Q, rl.lig);
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) d = fma(AW(pj[c].v[e]), AW(vi[c].v[e]), d);
+                }
+                s = fma(AW(ld_cs<CS>(p.k_a, p.k_adf, u)), d, s);
+            }
+        }
+        s = group_sum(s, L);
+        if (act && rl.lig == 0) {
+            w[__ldg(p.k_id + q)] = CS(s);
+            acc[0] += PA(s * s);
+        }
+    }
+    block_partials<1>(acc, part);
+}
+
+// Q_i += rho sum over the slots (j, k, a) of row i of a w_k v_j (A*(w) V of the listed
+// constraints).
+template <typename TR, typename TW, int CPL>
+__global__ void __launch_bounds__(kThreads)
+k_admm_opq(ProbDev p, const TR* __restrict__ V, int ld, int L, int Q, const void* __restrict__ w_v,
+           TW* __restrict__ Qo, const AdmmCtrl* __restrict__ ac) {
+    if (!ac->cg_active) return;
+    using AW = arith_t<TW>;
+    using CS = admm_cs_t<TR>;
+    const CS* __restrict__ w = static_cast<const CS*>(w_v);
+    const AW rho = AW(ac->rho);
+    RowLoop rl(L, hw_grid());
+    for (int64_t base = rl.first; base < p.n; base += rl.stride) {
+        const int64_t i = base + rl.gw;
+        if (i >= p.n) continue;
+        AW acc[CPL][4];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[c][e] = AW(0);
+        const int64_t s0 = __ldg(p.a_rowptr + i), s1 = __ldg(p.a_rowptr + i + 1);
+        for (int64_t s = s0; s < s1; ++s) {
+            const int j = __ldg(p.a_col + s);
+            const AW c_w = AW(ld_cs<CS>(p.a_a, p.a_adf, s) * w[__ldg(p.a_k + s)]);
+            Unit<TR> vj[CPL];
+            load_row<TR, CPL>(vj, V, j, ld, L, Q, rl.lig);
+#pragma unroll
+            for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[c][e] = fma(c_w, AW(vj[c].v[e]), acc[c][e]);
+        }
+        Unit<TW> q[CPL];
+        load_row<TW, CPL>(q, Qo, i, ld, L, Q, rl.lig);
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) q[c].v[e] = fma(rho, acc[c][e], AW(q[c].v[e]));
+        store_row<TW, CPL>(q, Qo, i, ld, L, Q, rl.lig);
+    }
 }
 
 // ------------------------------------------------------------------ update pass

@@ -39,9 +39,12 @@ template <typename TR> void admm_yupd(const AdmmRows& a, const void* U, const vo
 template <typename TR, typename TW> void admm_resid(const AdmmRows& a, const void* X, const void* V,
                                                     const void* om, void* r, void* pd, const AdmmCtrl* ac,
                                                     double* part);
-// one CG operator application (p update first when update_p), Q = frakA_V(p); partials PQ_*
+// one CG operator application (p update first when update_p), Q = frakA_V(p); partials PQ_*;
+// general form (constraints with several triplets): w (m-vector, scratch) and part_w
+// (its sum of squares) for the listed constraints
 template <typename TR, typename TW> void admm_op(const AdmmRows& a, const void* V, const void* r, void* pd, void* Q,
-                                                 const AdmmCtrl* ac, double rho_arg, int update_p, double* part);
+                                                 const AdmmCtrl* ac, double rho_arg, int update_p, double* part,
+                                                 void* w, double* part_w);
 // X += alpha p, r -= alpha Q; partial ||r||^2
 template <typename TR, typename TW> void admm_upd(const AdmmRows& a, void* X, const void* pd, void* r, const void* Q,
                                                   const AdmmCtrl* ac, double* part);
@@ -50,7 +53,7 @@ template <typename TR> void admm_avg(const AdmmRows& a, const void* U, const voi
 
 // single-block control kernels (FP64)
 void admm_cg_init(cudaStream_t s, AdmmCtrl* ac, const double* part_r, int nb);
-void admm_alpha(cudaStream_t s, AdmmCtrl* ac, const double* part_q, int nb);
+void admm_alpha(cudaStream_t s, AdmmCtrl* ac, const double* part_q, int nb, const double* part_w, int nb_w);
 void admm_beta(cudaStream_t s, AdmmCtrl* ac, const double* part_r, int nb);
 void admm_outer(cudaStream_t s, AdmmCtrl* ac, const double* part_y, int nb_y, const double* part_zz, int nb_zz,
                 const double* part_obj, int nb_obj);

@@ -983,13 +983,17 @@ int64_t admm_enqueue_block(lorads_ctx* ctx, const AdmmRows& rows, void* X, const
     admm_omega<TR>(rows, X, Vf, y, ydf, a.om, a.ac);
     admm_resid<TR, TW>(rows, X, Vf, a.om, a.r, a.p, a.ac, pr);
     admm_cg_init(s, a.ac, pr, rows.nb_rows);
+    // general form: w of the listed constraints reuses the m-vector of the start
+    // residual (read only by admm_resid, before the first CG step)
+    const bool general = ctx->pd.k_ptr != nullptr && ctx->m_off > 0;
+    double* pw = general ? part_of(ctx, PART_CONS_LS) : nullptr;
     for (int k = 0; k < cg_max; ++k) {
-        admm_op<TR, TW>(rows, Vf, a.r, a.p, a.Q, a.ac, 0.0, 1, pq);
-        admm_alpha(s, a.ac, pq, rows.nb_rows);
+        admm_op<TR, TW>(rows, Vf, a.r, a.p, a.Q, a.ac, 0.0, 1, pq, a.om, pw);
+        admm_alpha(s, a.ac, pq, rows.nb_rows, pw, rows.nb_cons);
         admm_upd<TR, TW>(rows, X, a.p, a.r, a.Q, a.ac, pu);
         admm_beta(s, a.ac, pu, rows.nb_flat);
     }
-    return 3 + (int64_t)cg_max * (ctx->m_off ? 5 : 4);
+    return 3 + (int64_t)cg_max * (general ? 6 : (ctx->m_off ? 5 : 4));
 }
 
 // Multiplier step and the errors of Sec. 4.2 at R = (U + V)/2.
@@ -1019,9 +1023,6 @@ lorads_status run_admm(lorads_ctx* ctx, double rho, std::chrono::steady_clock::t
     SolverState& st = ctx->st;
     const lorads_params& P = ctx->prm;
     lorads_status s;
-    if (ctx->pd.k_ptr != nullptr)
-        return set_err(ctx, "the ADMM stage takes constraints of one triplet each (the general form is solved by "
-                            "the ALM stage)"), LORADS_ERR_UNSUPPORTED;
     if ((s = admm_alloc<TR, TW>(ctx, st.ld))) return s;
     AdmmState& a = ctx->admm;
     cudaStream_t ss = ctx->solve_stream;
@@ -1227,8 +1228,7 @@ lorads_status run_solve(lorads_ctx* ctx, int prec, const double* R0, int32_t r0,
     if ((s = start_state<TR, TD, TDIR>(ctx, prec, R0, r0, r0_on_device, y0))) return s;
     // two-stage solve: the ALM stage stops at the switch tolerance; re-opt: the
     // first solve stops on primal feasibility alone
-    // (the general form, constraints with several triplets, runs the ALM stage alone)
-    const bool two_stage = P.admm_switch > 0 && P.reopt_level <= 0 && ctx->pd.k_ptr == nullptr;
+    const bool two_stage = P.admm_switch > 0 && P.reopt_level <= 0;
     const double alm_tol = two_stage ? std::max(P.admm_switch, P.tol) : P.tol;
     const double rho0 = P.rho0 > 0 ? P.rho0 : 1.0 / ctx->mean_abs_c;
     if ((s = start_alm<TR, TD, TDIR>(ctx, rho0, alm_tol, P.reopt_level > 0 ? 1 : 0))) return s;
@@ -1406,9 +1406,11 @@ extern "C" lorads_status lorads_admm_operator(lorads_ctx* ctx, const void* V, co
         return set_err(ctx, "the ADMM operator takes constraints of one triplet each"), LORADS_ERR_UNSUPPORTED;
     const AdmmRows rows = admm_rows(ctx, ld, sh, ctx->stream);
     if (prec == LORADS_FP64)
-        admm_op<double, double>(rows, V, nullptr, const_cast<void*>(X), out, nullptr, rho, 0, part_of(ctx, PART_MISC));
+        admm_op<double, double>(rows, V, nullptr, const_cast<void*>(X), out, nullptr, rho, 0, part_of(ctx, PART_MISC),
+                                nullptr, nullptr);
     else
-        admm_op<float, float>(rows, V, nullptr, const_cast<void*>(X), out, nullptr, rho, 0, part_of(ctx, PART_MISC));
+        admm_op<float, float>(rows, V, nullptr, const_cast<void*>(X), out, nullptr, rho, 0, part_of(ctx, PART_MISC),
+                              nullptr, nullptr);
     return check_launch(ctx, "lorads_admm_operator launch");
 }
 
@@ -1424,8 +1426,6 @@ extern "C" lorads_status lorads_admm_cg(lorads_ctx* ctx, const void* V, void* X,
     if (V == X) return set_err(ctx, "X must not alias V"), LORADS_ERR_INVALID_ARG;
     if (!(cg_rel > 0.0 && cg_rel < 1.0) || cg_max < 1)
         return set_err(ctx, "need 0 < cg_rel < 1 and cg_max >= 1"), LORADS_ERR_INVALID_ARG;
-    if (ctx->pd.k_ptr != nullptr)
-        return set_err(ctx, "the ADMM block step takes constraints of one triplet each"), LORADS_ERR_UNSUPPORTED;
     if (prec == LORADS_FP64) return run_admm_cg<double, double>(ctx, V, X, y, rho, ld, sh, cg_rel, cg_max, steps_out);
     return run_admm_cg<float, float>(ctx, V, X, y, rho, ld, sh, cg_rel, cg_max, steps_out);
 }
