@@ -386,8 +386,10 @@ typedef struct {
  *   R0                        NULL (rows drawn on the device as in lorads_solve) or the
  *                             n_i x r0_i row-major FP64 starting factors one after the other.
  *   p                         parameters (NULL = defaults); prec must be LORADS_FP64,
- *                             LORADS_MIXED or LORADS_FP32; compute_err2, check_every and
- *                             kernel_variant do not apply.
+ *                             LORADS_MIXED or LORADS_FP32; compute_err2, check_every,
+ *                             kernel_variant and reopt_level do not apply; admm_switch > 0 runs
+ *                             the ADMM stage of Sec. 2.2 after each instance's ALM stage, inside
+ *                             the same launch (single-triplet constraints only, as below).
  * All inputs are host memory and are copied.  Each instance is validated as by
  * lorads_create; the first failure names the instance (lorads_batch_create_error). */
 lorads_status lorads_batch_create(lorads_batch** out, int32_t count, const int64_t* n, const int64_t* m,

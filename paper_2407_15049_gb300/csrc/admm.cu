@@ -32,19 +32,7 @@ __global__ void k_admm_cg_init(AdmmCtrl* ac, const double* part_r, int nb) {
     __shared__ double s[PA_N];
     fold_sum(part_r, nb, PA_N, s);
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    const double rr = s[PA_RR];
-    ac->cg_k = 0;
-    ac->rr = rr;
-    ac->eps = ac->cg_rel * sqrt(fmax(rr, 0.0));
-    if (!isfinite(rr)) {
-        ac->cg_active = 0;
-        ac->status = 5;                     // LORADS_ERR_NUMERIC
-        ac->done = 1;
-        return;
-    }
-    // Algorithm 2 returns the start when its residual already meets the test
-    ac->cg_active = (sqrt(fmax(rr, 0.0)) > ac->eps && rr > 0.0) ? 1 : 0;
+    if (threadIdx.x == 0) admm_cg_init_apply(ac, s[PA_RR]);
 }
 
 __global__ void k_admm_alpha(AdmmCtrl* ac, const double* part_q, int nb, const double* part_w, int nb_w) {
@@ -54,14 +42,7 @@ __global__ void k_admm_alpha(AdmmCtrl* ac, const double* part_q, int nb, const d
     if (part_w != nullptr) fold_sum(part_w, nb_w, 1, s + PQ_N);
     else if (threadIdx.x == 0) s[PQ_N] = 0.0;
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    const double pq = ac->rho * (s[PQ_PP] + s[PQ_WW] + s[PQ_N]);
-    const double alpha = ac->rr / pq;
-    if (!(pq > 0.0) || !isfinite(alpha)) {
-        ac->cg_active = 0;                  // no positive curvature left: keep the iterate
-        return;
-    }
-    ac->alpha = alpha;
+    if (threadIdx.x == 0) admm_alpha_apply(ac, s[PQ_PP], s[PQ_WW] + s[PQ_N]);
 }
 
 __global__ void k_admm_beta(AdmmCtrl* ac, const double* part_r, int nb) {
@@ -69,22 +50,7 @@ __global__ void k_admm_beta(AdmmCtrl* ac, const double* part_r, int nb) {
     __shared__ double s[PA_N];
     fold_sum(part_r, nb, PA_N, s);
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    const double rr_new = s[PA_RR];
-    ac->cg_k += 1;
-    ac->cg_total += 1;
-    if (!isfinite(rr_new)) {
-        ac->cg_active = 0;
-        ac->status = 5;
-        ac->done = 1;
-        return;
-    }
-    if (sqrt(fmax(rr_new, 0.0)) <= ac->eps || ac->cg_k >= ac->cg_max) {
-        ac->cg_active = 0;
-        return;
-    }
-    ac->beta = rr_new / ac->rr;
-    ac->rr = rr_new;
+    if (threadIdx.x == 0) admm_beta_apply(ac, s[PA_RR]);
 }
 
 __global__ void k_admm_outer(AdmmCtrl* ac, const double* part_y, int nb_y, const double* part_zz, int nb_zz,
@@ -94,27 +60,7 @@ __global__ void k_admm_outer(AdmmCtrl* ac, const double* part_y, int nb_y, const
     fold_sum(part_zz, nb_zz, PC_N, sz);
     fold_sum(part_obj, nb_obj, PO_N, so);
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    if (ac->done) return;                   // a block step already failed
-    const double err1 = sqrt(fmax(sz[PC_ZZ], 0.0)) / (1.0 + ac->bnorm_inf);
-    const double obj = so[PO_CRR];
-    const double dual = sy[PY_BY];
-    const double err3 = (obj - dual) / (1.0 + fabs(obj) + fabs(dual));
-    ac->err1 = err1;
-    ac->err3 = err3;
-    ac->primal_obj = obj;
-    ac->dual_obj = dual;
-    ac->iters += 1;
-    if (!isfinite(sz[PC_ZZ]) || !isfinite(err3)) {
-        ac->status = 5;
-        ac->done = 1;
-    } else if (err1 <= ac->tol && fabs(err3) <= ac->tol) {
-        ac->status = 0;
-        ac->done = 1;
-    } else if (ac->iters >= ac->max_iter) {
-        ac->status = 6;                     // LORADS_ERR_MAXITER
-        ac->done = 1;
-    }
+    if (threadIdx.x == 0) admm_outer_apply(ac, sz[PC_ZZ], sy[PY_BY], so[PO_CRR]);
 }
 
 }  // namespace

@@ -51,22 +51,90 @@ __device__ __forceinline__ CS ld_cs(const double* d, const dfloat* df, int64_t k
     else return df ? ld_scalar<dfloat>(d, df, k) : dfloat(__ldg(d + k));
 }
 
+// ------------------------------------------------------------------ control (one thread)
+// Algorithm 2's start: ||r_0|| and the stop threshold eps = cg_rel ||r_0||.
+__device__ inline void admm_cg_init_apply(AdmmCtrl* ac, double rr) {
+    ac->cg_k = 0;
+    ac->rr = rr;
+    ac->eps = ac->cg_rel * sqrt(fmax(rr, 0.0));
+    if (!isfinite(rr)) {
+        ac->cg_active = 0;
+        ac->status = 5;                     // LORADS_ERR_NUMERIC
+        ac->done = 1;
+        return;
+    }
+    // Algorithm 2 returns the start when its residual already meets the test
+    ac->cg_active = (sqrt(fmax(rr, 0.0)) > ac->eps && rr > 0.0) ? 1 : 0;
+}
+
+// alpha = <r,r> / <p, frakA_V(p)>, <p, frakA_V(p)> = rho (||p||^2 + ||A(p V^T)||^2)
+__device__ inline void admm_alpha_apply(AdmmCtrl* ac, double pp, double ww) {
+    const double pq = ac->rho * (pp + ww);
+    const double alpha = ac->rr / pq;
+    if (!(pq > 0.0) || !isfinite(alpha)) {
+        ac->cg_active = 0;                  // no positive curvature left: keep the iterate
+        return;
+    }
+    ac->alpha = alpha;
+}
+
+// ||r_new||: the stop test, else beta = <r_new, r_new> / <r, r>
+__device__ inline void admm_beta_apply(AdmmCtrl* ac, double rr_new) {
+    ac->cg_k += 1;
+    ac->cg_total += 1;
+    if (!isfinite(rr_new)) {
+        ac->cg_active = 0;
+        ac->status = 5;
+        ac->done = 1;
+        return;
+    }
+    if (sqrt(fmax(rr_new, 0.0)) <= ac->eps || ac->cg_k >= ac->cg_max) {
+        ac->cg_active = 0;
+        return;
+    }
+    ac->beta = rr_new / ac->rr;
+    ac->rr = rr_new;
+}
+
+// After the multiplier step and R = (U + V)/2: err1 and err3 of Sec. 4.2 at R
+// (zz = ||A(RR^T) - b||^2, by = b^T y, obj = <C R, R>), the stop test and the cap.
+__device__ inline void admm_outer_apply(AdmmCtrl* ac, double zz, double by, double obj) {
+    if (ac->done) return;                   // a block step already failed
+    const double err1 = sqrt(fmax(zz, 0.0)) / (1.0 + ac->bnorm_inf);
+    const double err3 = (obj - by) / (1.0 + fabs(obj) + fabs(by));
+    ac->err1 = err1;
+    ac->err3 = err3;
+    ac->primal_obj = obj;
+    ac->dual_obj = by;
+    ac->iters += 1;
+    if (!isfinite(zz) || !isfinite(err3)) {
+        ac->status = 5;
+        ac->done = 1;
+    } else if (err1 <= ac->tol && fabs(err3) <= ac->tol) {
+        ac->status = 0;
+        ac->done = 1;
+    } else if (ac->iters >= ac->max_iter) {
+        ac->status = 6;                     // LORADS_ERR_MAXITER
+        ac->done = 1;
+    }
+}
+
 // ------------------------------------------------------------------ constraint pass
 // One group of L lanes per constraint t (list order):
 //   s = <A_k, X V^T> = a x_i.v_i (i == j) or a (x_i.v_j + x_j.v_i),  z = s - b_k.
 // MODE 0: w_k = y_k - rho z  (written to om, scalar type CS)
 // MODE 1: y_k <- y_k - rho z (and the double-float mirror); partials z^2, b_k y_k.
 template <typename TR, int CPL, int MODE>
-__global__ void __launch_bounds__(kThreads)
-k_admm_cons(ProbDev p, const TR* __restrict__ X, const TR* __restrict__ V, int ld, int L, int Q,
+__device__ __forceinline__ void
+k_admm_cons_body(ProbDev p, const TR* __restrict__ X, const TR* __restrict__ V, int ld, int L, int Q,
             double* y, dfloat* ydf, void* __restrict__ om, const AdmmCtrl* __restrict__ ac,
-            double* __restrict__ part) {
+            double* __restrict__ part, VGrid vg) {
     using AR = arith_t<TR>;
     using CS = admm_cs_t<TR>;
     using PA = part_t<TR, TR>;
     PA accq[PY_N] = {PA(0), PA(0)};
     const CS rho = CS(ac->rho);
-    RowLoop rl(L, hw_grid());
+    RowLoop rl(L, vg);
     for (int64_t base = rl.first; base < p.m; base += rl.stride) {
         const int64_t t = base + rl.gw;
         const bool act = t < p.m;
@@ -124,17 +192,17 @@ k_admm_cons(ProbDev p, const TR* __restrict__ X, const TR* __restrict__ V, int l
             }
         }
     }
-    if constexpr (MODE == 1) block_partials<PY_N>(accq, part);
+    if constexpr (MODE == 1) block_partials<PY_N>(accq, part, vg.pslot);
 }
 
 // ------------------------------------------------------------------ residual pass
 // r = p = -(C - A*(w)) V + rho (V - X) row by row (Algorithm 2's r_0 and p_0);
 // partial ||r||^2 of the stored values.
 template <typename TR, typename TW, int CPL>
-__global__ void __launch_bounds__(kThreads)
-k_admm_resid(ProbDev p, const TR* __restrict__ X, const TR* __restrict__ V, int ld, int L, int Q,
+__device__ __forceinline__ void
+k_admm_resid_body(ProbDev p, const TR* __restrict__ X, const TR* __restrict__ V, int ld, int L, int Q,
              const void* __restrict__ om_v, TW* __restrict__ r, TW* __restrict__ pd,
-             const AdmmCtrl* __restrict__ ac, double* __restrict__ part) {
+             const AdmmCtrl* __restrict__ ac, double* __restrict__ part, VGrid vg) {
     using AR = arith_t<TR>;
     using AW = arith_t<TW>;
     using CS = admm_cs_t<TR>;
@@ -143,7 +211,7 @@ k_admm_resid(ProbDev p, const TR* __restrict__ X, const TR* __restrict__ V, int 
     const AR* __restrict__ cv = cvals<AR>(p);
     const AR rho = AR(ac->rho);
     PA acc_rr[PA_N] = {PA(0)};
-    RowLoop rl(L, hw_grid());
+    RowLoop rl(L, vg);
     for (int64_t base = rl.first; base < p.n; base += rl.stride) {
         const int64_t i = base + rl.gw;
         if (i >= p.n) continue;
@@ -220,19 +288,19 @@ k_admm_resid(ProbDev p, const TR* __restrict__ X, const TR* __restrict__ V, int 
         store_row<TW, CPL>(ro, pd, i, ld, L, Q, rl.lig);
         acc_rr[PA_RR] += PA(rr);
     }
-    block_partials<PA_N>(acc_rr, part);
+    block_partials<PA_N>(acc_rr, part, vg.pslot);
 }
 
 // ------------------------------------------------------------------ p update
 // p = r + beta p (CG steps after the first), for the path with off-diagonal
 // constraints whose operator pass gathers neighbouring rows of p.
 template <typename TW>
-__global__ void __launch_bounds__(kThreads)
-k_admm_pupd(int64_t nunits, const TW* __restrict__ r, TW* __restrict__ pd, const AdmmCtrl* __restrict__ ac) {
+__device__ __forceinline__ void
+k_admm_pupd_body(int64_t nunits, const TW* __restrict__ r, TW* __restrict__ pd, const AdmmCtrl* __restrict__ ac, VGrid vg) {
     if (!ac->cg_active || ac->cg_k == 0) return;
     using AW = arith_t<TW>;
     const AW beta = AW(ac->beta);
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nunits; u += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t u = vg.bid * (int64_t)blockDim.x + threadIdx.x; u < nunits; u += (int64_t)vg.nblk * blockDim.x) {
         Unit<TW> ru, pu;
         ru.load_stream(r + 4 * u);
         pu.load(pd + 4 * u);
@@ -250,10 +318,10 @@ k_admm_pupd(int64_t nunits, const TW* __restrict__ r, TW* __restrict__ pd, const
 // off-diagonal constraints, whose rows would read neighbours' p).
 // With ac == nullptr (standalone operator) the pass runs with rho_arg and no update.
 template <typename TR, typename TW, int CPL, bool FUSE_P>
-__global__ void __launch_bounds__(kThreads)
-k_admm_op(ProbDev p, const TR* __restrict__ V, int ld, int L, int Q, const TW* __restrict__ r,
+__device__ __forceinline__ void
+k_admm_op_body(ProbDev p, const TR* __restrict__ V, int ld, int L, int Q, const TW* __restrict__ r,
           TW* __restrict__ pd, TW* __restrict__ Qo, const AdmmCtrl* __restrict__ ac, double rho_arg,
-          double* __restrict__ part) {
+          double* __restrict__ part, VGrid vg) {
     if (ac != nullptr && !ac->cg_active) return;
     using AW = arith_t<TW>;
     using CS = admm_cs_t<TR>;
@@ -263,7 +331,7 @@ k_admm_op(ProbDev p, const TR* __restrict__ V, int ld, int L, int Q, const TW* _
     const bool upd = FUSE_P && ac != nullptr && ac->cg_k > 0;
     const AW beta = upd ? AW(ac->beta) : AW(0);
     PA accq[PQ_N] = {PA(0), PA(0)};
-    RowLoop rl(L, hw_grid());
+    RowLoop rl(L, vg);
     for (int64_t base = rl.first; base < p.n; base += rl.stride) {
         const int64_t i = base + rl.gw;
         const bool act = i < p.n;
@@ -352,23 +420,23 @@ k_admm_op(ProbDev p, const TR* __restrict__ V, int ld, int L, int Q, const TW* _
             accq[PQ_PP] += PA(pp);
         }
     }
-    block_partials<PQ_N>(accq, part);
+    block_partials<PQ_N>(accq, part, vg.pslot);
 }
 
 // ------------------------------------------------------------------ general form
 // w_k = <A_k, p V^T> for the listed constraints (positions m_diag..m-1; each a sum
 // over its triplets), stored by constraint; partial sum of w_k^2.
 template <typename TR, typename TW, int CPL>
-__global__ void __launch_bounds__(kThreads)
-k_admm_opw(ProbDev p, const TR* __restrict__ V, int ld, int L, int Q, const TW* __restrict__ pd,
-           void* __restrict__ w_v, const AdmmCtrl* __restrict__ ac, double* __restrict__ part) {
+__device__ __forceinline__ void
+k_admm_opw_body(ProbDev p, const TR* __restrict__ V, int ld, int L, int Q, const TW* __restrict__ pd,
+           void* __restrict__ w_v, const AdmmCtrl* __restrict__ ac, double* __restrict__ part, VGrid vg) {
     if (!ac->cg_active) return;
     using AW = arith_t<TW>;
     using CS = admm_cs_t<TR>;
     using PA = part_t<TW, TW>;
     CS* __restrict__ w = static_cast<CS*>(w_v);
     PA acc[1] = {PA(0)};
-    RowLoop rl(L, hw_grid());
+    RowLoop rl(L, vg);
     const int64_t cnt = p.m - p.m_diag;
     for (int64_t base = rl.first; base < cnt; base += rl.stride) {
         const int64_t q = p.m_diag + base + rl.gw;
@@ -406,21 +474,21 @@ k_admm_opw(ProbDev p, const TR* __restrict__ V, int ld, int L, int Q, const TW* 
             acc[0] += PA(s * s);
         }
     }
-    block_partials<1>(acc, part);
+    block_partials<1>(acc, part, vg.pslot);
 }
 
 // Q_i += rho sum over the slots (j, k, a) of row i of a w_k v_j (A*(w) V of the listed
 // constraints).
 template <typename TR, typename TW, int CPL>
-__global__ void __launch_bounds__(kThreads)
-k_admm_opq(ProbDev p, const TR* __restrict__ V, int ld, int L, int Q, const void* __restrict__ w_v,
-           TW* __restrict__ Qo, const AdmmCtrl* __restrict__ ac) {
+__device__ __forceinline__ void
+k_admm_opq_body(ProbDev p, const TR* __restrict__ V, int ld, int L, int Q, const void* __restrict__ w_v,
+           TW* __restrict__ Qo, const AdmmCtrl* __restrict__ ac, VGrid vg) {
     if (!ac->cg_active) return;
     using AW = arith_t<TW>;
     using CS = admm_cs_t<TR>;
     const CS* __restrict__ w = static_cast<const CS*>(w_v);
     const AW rho = AW(ac->rho);
-    RowLoop rl(L, hw_grid());
+    RowLoop rl(L, vg);
     for (int64_t base = rl.first; base < p.n; base += rl.stride) {
         const int64_t i = base + rl.gw;
         if (i >= p.n) continue;
@@ -453,9 +521,9 @@ k_admm_opq(ProbDev p, const TR* __restrict__ V, int ld, int L, int Q, const void
 // ------------------------------------------------------------------ update pass
 // X += alpha p, r -= alpha Q; partial ||r||^2 (flat over units of 4 elements).
 template <typename TR, typename TW>
-__global__ void __launch_bounds__(kThreads)
-k_admm_upd(int64_t nunits, TR* __restrict__ X, const TW* __restrict__ pd, TW* __restrict__ r,
-           const TW* __restrict__ Qo, const AdmmCtrl* __restrict__ ac, double* __restrict__ part) {
+__device__ __forceinline__ void
+k_admm_upd_body(int64_t nunits, TR* __restrict__ X, const TW* __restrict__ pd, TW* __restrict__ r,
+           const TW* __restrict__ Qo, const AdmmCtrl* __restrict__ ac, double* __restrict__ part, VGrid vg) {
     if (!ac->cg_active) return;
     using AR = arith_t<TR>;
     using AW = arith_t<TW>;
@@ -464,7 +532,7 @@ k_admm_upd(int64_t nunits, TR* __restrict__ X, const TW* __restrict__ pd, TW* __
     const AW alpha_w = AW(ac->alpha);
     PA acc[PA_N] = {PA(0)};
     AW rr = AW(0);
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nunits; u += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t u = vg.bid * (int64_t)blockDim.x + threadIdx.x; u < nunits; u += (int64_t)vg.nblk * blockDim.x) {
         Unit<TR> xu;
         Unit<TW> pu, ru, qu;
         xu.load_stream(X + 4 * u);
@@ -482,15 +550,15 @@ k_admm_upd(int64_t nunits, TR* __restrict__ X, const TW* __restrict__ pd, TW* __
         ru.store_stream(r + 4 * u);
     }
     acc[PA_RR] += PA(rr);
-    block_partials<PA_N>(acc, part);
+    block_partials<PA_N>(acc, part, vg.pslot);
 }
 
 // R = (U + V) / 2 (flat), the factor whose X = R R^T the stage reports.
 template <typename TR>
-__global__ void __launch_bounds__(kThreads)
-k_admm_avg(int64_t nunits, const TR* __restrict__ U, const TR* __restrict__ V, TR* __restrict__ R) {
+__device__ __forceinline__ void
+k_admm_avg_body(int64_t nunits, const TR* __restrict__ U, const TR* __restrict__ V, TR* __restrict__ R, VGrid vg) {
     using AR = arith_t<TR>;
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nunits; u += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t u = vg.bid * (int64_t)blockDim.x + threadIdx.x; u < nunits; u += (int64_t)vg.nblk * blockDim.x) {
         Unit<TR> a, b;
         a.load_stream(U + 4 * u);
         b.load_stream(V + 4 * u);
@@ -498,6 +566,67 @@ k_admm_avg(int64_t nunits, const TR* __restrict__ U, const TR* __restrict__ V, T
         for (int e = 0; e < 4; ++e) a.v[e] = AR(0.5f) * (AR(a.v[e]) + AR(b.v[e]));
         a.store(R + 4 * u);
     }
+}
+
+
+// ------------------------------------------------------------------ kernels
+// One launch per body over the hardware grid (the batched solve runs the bodies
+// over the blocks of one instance).
+template <typename TR, int CPL, int MODE>
+__global__ void __launch_bounds__(kThreads)
+k_admm_cons(ProbDev p, const TR* __restrict__ X, const TR* __restrict__ V, int ld, int L, int Q,
+            double* y, dfloat* ydf, void* __restrict__ om, const AdmmCtrl* __restrict__ ac,
+            double* __restrict__ part) {
+    k_admm_cons_body<TR, CPL, MODE>(p, X, V, ld, L, Q, y, ydf, om, ac, part, hw_grid());
+}
+
+template <typename TR, typename TW, int CPL>
+__global__ void __launch_bounds__(kThreads)
+k_admm_resid(ProbDev p, const TR* __restrict__ X, const TR* __restrict__ V, int ld, int L, int Q,
+             const void* __restrict__ om_v, TW* __restrict__ r, TW* __restrict__ pd,
+             const AdmmCtrl* __restrict__ ac, double* __restrict__ part) {
+    k_admm_resid_body<TR, TW, CPL>(p, X, V, ld, L, Q, om_v, r, pd, ac, part, hw_grid());
+}
+
+template <typename TW>
+__global__ void __launch_bounds__(kThreads)
+k_admm_pupd(int64_t nunits, const TW* __restrict__ r, TW* __restrict__ pd, const AdmmCtrl* __restrict__ ac) {
+    k_admm_pupd_body<TW>(nunits, r, pd, ac, hw_grid());
+}
+
+template <typename TR, typename TW, int CPL, bool FUSE_P>
+__global__ void __launch_bounds__(kThreads)
+k_admm_op(ProbDev p, const TR* __restrict__ V, int ld, int L, int Q, const TW* __restrict__ r,
+          TW* __restrict__ pd, TW* __restrict__ Qo, const AdmmCtrl* __restrict__ ac, double rho_arg,
+          double* __restrict__ part) {
+    k_admm_op_body<TR, TW, CPL, FUSE_P>(p, V, ld, L, Q, r, pd, Qo, ac, rho_arg, part, hw_grid());
+}
+
+template <typename TR, typename TW, int CPL>
+__global__ void __launch_bounds__(kThreads)
+k_admm_opw(ProbDev p, const TR* __restrict__ V, int ld, int L, int Q, const TW* __restrict__ pd,
+           void* __restrict__ w_v, const AdmmCtrl* __restrict__ ac, double* __restrict__ part) {
+    k_admm_opw_body<TR, TW, CPL>(p, V, ld, L, Q, pd, w_v, ac, part, hw_grid());
+}
+
+template <typename TR, typename TW, int CPL>
+__global__ void __launch_bounds__(kThreads)
+k_admm_opq(ProbDev p, const TR* __restrict__ V, int ld, int L, int Q, const void* __restrict__ w_v,
+           TW* __restrict__ Qo, const AdmmCtrl* __restrict__ ac) {
+    k_admm_opq_body<TR, TW, CPL>(p, V, ld, L, Q, w_v, Qo, ac, hw_grid());
+}
+
+template <typename TR, typename TW>
+__global__ void __launch_bounds__(kThreads)
+k_admm_upd(int64_t nunits, TR* __restrict__ X, const TW* __restrict__ pd, TW* __restrict__ r,
+           const TW* __restrict__ Qo, const AdmmCtrl* __restrict__ ac, double* __restrict__ part) {
+    k_admm_upd_body<TR, TW>(nunits, X, pd, r, Qo, ac, part, hw_grid());
+}
+
+template <typename TR>
+__global__ void __launch_bounds__(kThreads)
+k_admm_avg(int64_t nunits, const TR* __restrict__ U, const TR* __restrict__ V, TR* __restrict__ R) {
+    k_admm_avg_body<TR>(nunits, U, V, R, hw_grid());
 }
 
 }  // namespace lorads

@@ -100,7 +100,8 @@ void fill_ctrl0(const lorads_params& P, const HostProb& hp, int64_t iter_limit, 
     h->lbfgs_scaling = P.lbfgs_scaling;
     h->rho_policy = P.rho_policy;
     h->inner_scale = P.inner_scale;
-    h->tol = P.tol;
+    // two-stage solve: the ALM stage stops at the switch tolerance
+    h->tol = P.admm_switch > 0 ? std::max(P.admm_switch, P.tol) : P.tol;
     h->inner_rel = P.inner_rel;
     h->inner_progress = P.inner_progress;
     h->bnorm1 = hp.bnorm1;
@@ -270,6 +271,9 @@ lorads_status run_batch(lorads_batch* b, lorads_result* results, lorads_batch_st
             r.inner_iters = c.total_inner;
             r.status = c.status;
             r.kernel_launches = 1;
+            r.admm_iters = o.admm_iters;
+            r.cg_steps = o.cg_steps;
+            r.reopt_scale = 1.0;
         }
     }
     if (stats) {
@@ -404,6 +408,7 @@ extern "C" lorads_status lorads_batch_create(lorads_batch** out, int32_t count, 
         if (h.m_off) ss += align_up(nl * esD) + 2 * align_up(m * 8);
         ss += align_up(m * 8) + align_up(n * 8);                           // y, zrow
         if (!fp64) ss += align_up(m * 8);                                  // ydf
+        if (P.admm_switch > 0) ss += 2 * align_up(nl * esR) + align_up(m * 8);   // U, V, w (ADMM stage)
         state_off[i + 1] = state_off[i] + ss;
     }
     lorads_batch* b = new (std::nothrow) lorads_batch();
@@ -511,6 +516,16 @@ extern "C" lorads_status lorads_batch_create(lorads_batch** out, int32_t count, 
         I.y = static_cast<double*>(take(m * 8));
         I.zrow = take(n * 8);
         if (!fp64) I.ydf = static_cast<dfloat*>(take(m * 8));
+        if (P.admm_switch > 0) {
+            I.U = take(nl * esR);
+            I.V = take(nl * esR);
+            I.om = take(m * 8);
+            I.admm_on = 1;
+            I.admm_tol = P.tol;
+            I.cg_rel = P.cg_rel;
+            I.cg_max = P.cg_max;
+            I.admm_max_iter = P.admm_max_iter;
+        }
         I.slot_stride = (int64_t)nl;
         I.r0 = r0[i];
         I.ld_cap = ldcap[i];
@@ -684,7 +699,8 @@ extern "C" const char* lorads_batch_create_error(void) { return g_batch_create_e
 extern "C" int32_t lorads_batch_phase_times(const lorads_batch* b, int32_t i, const char** names, double* ms,
                                             int32_t cap) {
     static const char* const kNames[BP_N] = {"init", "direction", "spmm_ls", "cons_ls", "root", "step", "ytil",
-                                             "spmm_a", "update", "hist", "outer", "outer_gradient", "rank_update"};
+                                             "spmm_a", "update", "hist", "outer", "outer_gradient", "rank_update",
+                                             "admm"};
     if (!b || !b->have_solution || i < -1 || i >= b->count || cap < 1) return 0;
     const int k = std::min<int>(cap, BP_N);
     for (int q = 0; q < k; ++q) {

@@ -7,6 +7,7 @@
 #include <cooperative_groups.h>
 
 #include "../../include/lorads.h"
+#include "admm.cuh"
 #include "common.cuh"
 #include "control_dev.cuh"
 #include "kernels.cuh"
@@ -37,16 +38,24 @@ struct BInst {
     int r0, ld_cap, r_cap, unit_rows;
     double start_scale;
     uint64_t seed;
+    // splitting ADMM stage (Sec. 2.2) after the ALM stage (admm_on): block iterates
+    // U, V (n x ld_cap, type of R), the m-vector w, the final tolerance and CG limits
+    void* U;
+    void* V;
+    void* om;
+    int admm_on, cg_max, admm_max_iter;
+    double admm_tol, cg_rel;
 };
 
 // Per-instance result written by the kernel.
 // phases of the per-instance solve timed by the persistent kernel
 enum { BP_INIT = 0, BP_DIR, BP_LS, BP_CONS_LS, BP_ROOT, BP_STEP, BP_YTIL, BP_SPMM_A, BP_UPDATE, BP_HIST, BP_OUTER,
-       BP_GRAD, BP_RANK, BP_N };
+       BP_GRAD, BP_RANK, BP_ADMM, BP_N };
 
 struct BOut {
     Ctrl ctrl;
     int r, ld;
+    int admm_iters, cg_steps;
     long long t_begin, t_end;     // %globaltimer (ns)
     long long phase_ns[BP_N];     // time of each phase (thread 0 of the block, after its barrier)
 };
@@ -131,8 +140,9 @@ __device__ void batch_start(const BInst& I, TR* R, int r, int ld, const Team& tm
 
 // sp: this block's partial sums; tot: the team's sums (== sp for one block)
 template <typename TR, typename TD>
-__device__ void batch_solve_one(const BInst& I, const Ctrl& c0, BOut& o, Ctrl* c, double* sp, double* tot,
-                                int rows_per_warp, long long time_limit_ns, long long* ph, const Team tm) {
+__device__ void batch_solve_one(const BInst& I, const Ctrl& c0, BOut& o, Ctrl* c, AdmmCtrl* ac, double* sp,
+                                double* tot, int rows_per_warp, long long time_limit_ns, long long* ph,
+                                const Team tm) {
     using ZS = zrow_t<TD, TR>;
     // y~ and the cached z of the off-diagonal constraints: double-float unless FP64
     constexpr bool kYtilDf = !std::is_same<TR, double>::value;
@@ -349,6 +359,96 @@ __device__ void batch_solve_one(const BInst& I, const Ctrl& c0, BOut& o, Ctrl* c
         }
     }
     tm.sync();
+    // ---- the splitting ADMM stage (Sec. 2.2) when the ALM stage stopped at the switch
+    // tolerance: U = V = R, the ALM stage's y and rho (fixed); Algorithm 2's CG for each
+    // block step as a device loop; the direction, C D and gradient arrays hold r, p, Q.
+    int admm_iters = 0, cg_steps = 0;
+    if (I.admm_on && c->status == LORADS_OK && !(c->err1 <= I.admm_tol && fabs(c->err3) <= I.admm_tol)) {
+        enum { SA_R = SP_DIR, SA_Q = SP_LS };
+        TR* U = static_cast<TR*>(I.U);
+        TR* V = static_cast<TR*>(I.V);
+        TD* rv = D;
+        TD* pv = CD;
+        TD* Qv = G;
+        for (int64_t e = tm.tid(); e < p.n * ld; e += tm.nthreads()) {
+            U[e] = R[e];
+            V[e] = R[e];
+        }
+        if (tid == 0) {
+            *ac = AdmmCtrl{};
+            ac->rho = c->rho;
+            ac->cg_rel = I.cg_rel;
+            ac->cg_max = I.cg_max;
+            ac->tol = I.admm_tol;
+            ac->bnorm_inf = c->bnorm_inf;
+            ac->max_iter = I.admm_max_iter;
+            ac->status = LORADS_ERR_MAXITER;
+        }
+        tm.sync();
+        while (!ac->done) {
+            for (int half = 0; half < 2 && !ac->done; ++half) {
+                TR* X = half == 0 ? U : V;
+                const TR* Vf = half == 0 ? V : U;
+                k_admm_cons_body<TR, 1, 0>(p, X, Vf, ld, L, Q, y, ydf, I.om, ac, nullptr, vg);
+                tm.sync();
+                k_admm_resid_body<TR, TD, 1>(p, X, Vf, ld, L, Q, I.om, rv, pv, ac, sp + SA_R, vg);
+                reduce(SA_R, 1);
+                if (tid == 0) admm_cg_init_apply(ac, tot[SA_R]);
+                tm.sync();
+                while (ac->cg_active) {
+                    if (p.m_off > 0) {
+                        k_admm_pupd_body<TD>(nunits, rv, pv, ac, vg);
+                        tm.sync();
+                        k_admm_op_body<TR, TD, 1, false>(p, Vf, ld, L, Q, rv, pv, Qv, ac, 0.0, sp + SA_Q, vg);
+                    } else {
+                        k_admm_op_body<TR, TD, 1, true>(p, Vf, ld, L, Q, rv, pv, Qv, ac, 0.0, sp + SA_Q, vg);
+                    }
+                    reduce(SA_Q, PQ_N);
+                    if (tid == 0) admm_alpha_apply(ac, tot[SA_Q + PQ_PP], tot[SA_Q + PQ_WW]);
+                    tm.sync();
+                    if (!ac->cg_active) break;
+                    k_admm_upd_body<TR, TD>(nunits, X, pv, rv, Qv, ac, sp + SA_R, vg);
+                    reduce(SA_R, 1);
+                    if (tid == 0) admm_beta_apply(ac, tot[SA_R]);
+                    tm.sync();
+                }
+            }
+            if (ac->done) break;
+            // multiplier step, R = (U + V)/2, <C R, R> and ||A(RR^T) - b|| (Sec. 4.2 at R)
+            k_admm_cons_body<TR, 1, 1>(p, U, V, ld, L, Q, y, ydf, nullptr, ac, sp + SP_YT, vg);
+            tm.sync();
+            k_admm_avg_body<TR>(nunits, U, V, R, vg);
+            tm.sync();
+            spmm_cr();
+            tm.sync();
+            k_cons_body<TR, TR, 1, CONS_ZZ>(p, 0, p.m, R, R, ld, L, Q, y, nullptr, nullptr, nullptr, c, 0.0,
+                                            sp + SP_CONS, vg);
+            if (tid == 0) sp[SP_TIME] = tm.rank == 0 ? (double)(globaltimer_ns() - t_begin) : 0.0;
+            reduce(SP_CONS, PC_N + PO_N + 1);
+            reduce(SP_YT, PY_N);
+            if (tid == 0) {
+                admm_outer_apply(ac, tot[SP_CONS + PC_ZZ], tot[SP_YT + PY_BY], tot[SP_OBJ + PO_CRR]);
+                if (!ac->done && time_limit_ns > 0 && tot[SP_TIME] > (double)time_limit_ns) {
+                    ac->status = LORADS_ERR_TIMEOUT;
+                    ac->done = 1;
+                }
+            }
+            tm.sync();
+            tick(BP_ADMM);
+        }
+        if (tid == 0) {
+            if (ac->iters > 0) {
+                c->primal_obj = ac->primal_obj;
+                c->dual_obj = ac->dual_obj;
+                c->err1 = ac->err1;
+                c->err3 = ac->err3;
+            }
+            c->status = ac->status;
+        }
+        admm_iters = ac->iters;
+        cg_steps = ac->cg_total;
+        tm.sync();
+    }
     if (tm.rank == 0) {
         const int* src = reinterpret_cast<const int*>(c);
         int* dst = reinterpret_cast<int*>(&o.ctrl);
@@ -356,6 +456,8 @@ __device__ void batch_solve_one(const BInst& I, const Ctrl& c0, BOut& o, Ctrl* c
         if (tid == 0) {
             o.r = r;
             o.ld = ld;
+            o.admm_iters = admm_iters;
+            o.cg_steps = cg_steps;
             o.t_begin = t_begin;
             o.t_end = globaltimer_ns();
             for (int q = 0; q < BP_N; ++q) o.phase_ns[q] = ph[q];
@@ -374,6 +476,7 @@ k_batch_solve(const BInst* __restrict__ insts, const Ctrl* __restrict__ ctrl0, B
               const int* __restrict__ order, int count, int n_team, int* queues, int rows_per_warp,
               long long time_limit_ns) {
     __shared__ Ctrl c;
+    __shared__ AdmmCtrl ac;
     __shared__ double sp[SP_N];
     __shared__ double tot[SP_N];
     __shared__ long long s_ph[BP_N];
@@ -403,7 +506,7 @@ k_batch_solve(const BInst* __restrict__ insts, const Ctrl* __restrict__ ctrl0, B
             if (it >= count) return;
         }
         const int k = order[it];
-        batch_solve_one<TR, TD>(insts[k], ctrl0[k], out[k], &c, sp, tm.size > 1 ? tot : sp, rows_per_warp,
+        batch_solve_one<TR, TD>(insts[k], ctrl0[k], out[k], &c, &ac, sp, tm.size > 1 ? tot : sp, rows_per_warp,
                                 time_limit_ns, s_ph, tm);
     }
 }

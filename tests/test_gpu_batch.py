@@ -219,3 +219,29 @@ def test_batch_iteration_cap_reports_maxiter():
         L.lorads_batch_destroy(b)
     assert res[0]["status_name"] == "LORADS_ERR_MAXITER" and res[0]["inner_iters"] == 7
     assert res2[0]["status_name"] == "LORADS_OK"
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_two_stage_matches_oracle(prec):
+    """The ADMM stage of Sec. 2.2 inside the persistent launch (admm_switch): every
+    instance ends at rel. KKT 1e-5; the ALM -> ADMM hand-over and the ADMM iteration
+    count equal the oracle's two-stage solve on the stable instances, and the
+    objectives agree (FP64 1e-7 on those; 2e-5 otherwise, as for lorads_solve)."""
+    from oracle import admm_oracle as A
+    insts = [W.maxcut_instance(1000, W.er_graph(1000, 4000, 0, "unit")),
+             W.mc_instance(60, 80, 3, 2500, seed=2),
+             W.maxcut_instance(300, W.er_graph(300, 1200, 3, "unit"))]
+    R0 = [W.initial_factor(insts[0], 10, 1), W.initial_factor(insts[1], 12, 4), W.initial_factor(insts[2], 9, 5)]
+    res, stats, sols = _batch_run(insts, R0, prec=prec, admm_switch=1e-2)
+    for i, inst in enumerate(insts):
+        ref = A.solve_two_stage(O.Problem(inst), R0[i], O.Params(), A.AdmmParams(switch_err1=1e-2))
+        assert ref["status"] == "ok" and res[i]["status_name"] == "LORADS_OK", (i, res[i])
+        assert res[i]["err1"] <= 1e-5 and abs(res[i]["err3"]) <= 1e-5
+        if prec == "fp64" and i < 2:
+            assert res[i]["admm_iters"] == ref["admm_iters"], (i, res[i]["admm_iters"], ref["admm_iters"])
+            assert res[i]["primal_obj"] == pytest.approx(ref["primal_obj"], rel=1e-7)
+        else:
+            assert res[i]["primal_obj"] == pytest.approx(ref["primal_obj"], rel=2e-5)
+        R, _ = sols[i]
+        z = O.constraint_map(O.Problem(inst), R, R) - inst.b
+        assert np.linalg.norm(z) / (1 + np.abs(inst.b).max()) <= 1.0001e-5
