@@ -56,6 +56,8 @@ METRIC = "time to rel. KKT 1e-5 (MaxCut n=1e7); SpMM+A(RRᵀ) HBM GB/s vs 8 TB/s
 WORKLOADS = {
     "maxcut_er_1e7": dict(n=10_000_000, edges=20_000_000, weights="pm1", r=24, seed=0, admm_switch=3e-4,
                           desc="MaxCut SDP, Erdos-Renyi n=1e7, M=2e7 edges (avg degree 4), w in {-1,+1}, r=24"),
+    "maxcut_er_2e6": dict(n=2_000_000, edges=4_000_000, weights="pm1", r=24, seed=0,
+                          desc="MaxCut SDP, Erdos-Renyi n=2e6, M=4e6 edges (avg degree 4), w in {-1,+1}, r=24"),
     "maxcut_er_1e6": dict(n=1_000_000, edges=2_000_000, weights="pm1", r=20, seed=0,
                           desc="MaxCut SDP, Erdos-Renyi n=1e6, M=2e6 edges (avg degree 4), w in {-1,+1}, r=20"),
     "maxcut_er_1e5": dict(n=100_000, edges=200_000, weights="pm1", r=17, seed=0,
@@ -69,7 +71,7 @@ WORKLOADS = {
 # metric of each workload's line (the benchmark's own metric for the MaxCut workloads)
 MC_METRIC = "time to rel. KKT 1e-5 (matrix completion 5e4 x 5e4, |Omega| 2.7e6)"
 BATCH_WORKLOADS = {
-    "serving_batch_512": dict(count=512, seed=0,
+    "serving_batch_512": dict(count=512, seed=0, admm_switch=1e-3,
                               desc="512 uneven SDPs: ~3/4 MaxCut on ER graphs (n log-uniform in [200, 20000], "
                                    "average degree 3-20, w in {-1,+1}), ~1/4 matrix completion (side 100-5000, "
                                    "rank 2-5, |Omega| = 5 side ln side); r0 = ceil(log2 m)"),
@@ -135,6 +137,9 @@ def _args():
     ap.add_argument("--instance-time-limit", type=float, default=60.0,
                     help="batched solve: per-instance time limit (s); instances past it count as unsolved")
     ap.add_argument("--tune-iters", type=int, default=20, help="batched solve: iterations per autotuner probe")
+    ap.add_argument("--kernel-probe", type=int, default=0, metavar="ITERS",
+                    help="print the CUDA-event time of every kernel family over the first ITERS L-BFGS iterations "
+                         "of a host-stepped solve of the workload (twice) and exit: the target of ncu captures")
     ap.add_argument("--spmm-vs-cusparse", type=int, default=0, metavar="N",
                     help="informational: time C D of the library's SpMM and of cuSPARSE (torch CSR @ dense) "
                          "on the ER graph with N vertices (degree 4, r = 24, FP32) and exit")
@@ -142,7 +147,7 @@ def _args():
     if args.fp64_same_run is None:
         args.fp64_same_run = 1 if (args.workload == "maxcut_er_1e7" and args.prec != "fp64") else 0
     if args.admm_switch is None:
-        args.admm_switch = WORKLOADS.get(args.workload, {}).get("admm_switch", 0.0)
+        args.admm_switch = {**WORKLOADS, **BATCH_WORKLOADS}.get(args.workload, {}).get("admm_switch", 0.0)
     return args
 
 
@@ -708,10 +713,12 @@ def run_native(args):
     return 0
 
 
-def batch_bytes(inst, ld: int, wR: int, wD: int, T: int, inner: int, outer: int) -> float:
+def batch_bytes(inst, ld: int, wR: int, wD: int, T: int, inner: int, outer: int, cg_steps: int = 0) -> float:
     """Algorithmic bytes of one instance's batched solve: per L-BFGS iteration the
     direction, line-search SpMM / constraint pass and row update (each operand once),
-    per outer step the multiplier pass and C R."""
+    per outer step the multiplier pass and C R, per CG step of the ADMM stage the
+    operator pass (p, r read, p and Q written, V read; slot gathers of p and V) and the
+    update pass (X read and written, p, r, Q read, r written)."""
     n, m, nnz = inst.n, inst.m, inst.nnz
     fam = lambda f: kernel_bytes(f, n, ld, nnz, m, wR, wD, T)  # noqa: E731
     per_inner = fam("k_dir") + fam("k_spmm_c(CD,ls)") + fam("k_update(step)")
@@ -719,19 +726,24 @@ def batch_bytes(inst, ld: int, wR: int, wD: int, T: int, inner: int, outer: int)
     if m_off > 0:                       # constraint line-search pass, y~ pass, A*(y~) R
         per_inner += m_off * (4 * 4 + 8 * 3) + 2 * m_off * ld * (wR + wD) + 2 * m_off * ld * wR + n * ld * wD
     per_outer = fam("k_cons(yupd)") + fam("k_spmm_c(CR,obj)") + fam("k_update(grad)")
-    return per_inner * inner + per_outer * outer
+    per_cg = n * ld * (4 * wD + wR) + n * ld * (2 * wR + 4 * wD) + 2 * m_off * ld * (wD + wR)
+    return per_inner * inner + per_outer * outer + per_cg * cg_steps
 
 
-def _oracle_instance_seconds(inst, r0):
+def _oracle_instance_seconds(inst, r0, admm_switch: float = 0.0):
     from oracle import lorads_oracle as O
+    from oracle import admm_oracle as A
     import workloads as W
     R0 = W.initial_factor(inst, r0, 1)
     t = time.perf_counter()
-    ref = O.solve(O.Problem(inst), R0, O.Params())
+    if admm_switch > 0:
+        ref = A.solve_two_stage(O.Problem(inst), R0, O.Params(), A.AdmmParams(switch_err1=admm_switch))
+    else:
+        ref = O.solve(O.Problem(inst), R0, O.Params())
     return time.perf_counter() - t, ref
 
 
-def _batch_cpu_sample(B, budget_s: float = 20.0):
+def _batch_cpu_sample(B, budget_s: float = 20.0, admm_switch: float = 0.0):
     """The oracle on a seeded sample of the batch's instances, smallest first until
     about budget_s of CPU time: instances per second on that sample."""
     import numpy as np
@@ -742,7 +754,7 @@ def _batch_cpu_sample(B, budget_s: float = 20.0):
     for i in idx:
         if spent > budget_s:
             break
-        s, _ = _oracle_instance_seconds(B[i], W.rank_log2(B[i].m))
+        s, _ = _oracle_instance_seconds(B[i], W.rank_log2(B[i].m), admm_switch)
         spent += s
         done += 1
         names.append(f"{B[i].kind} n={B[i].n}")
@@ -766,7 +778,7 @@ def run_batch(args):
             return 0
         per = []
         for _ in range(args.steps):
-            v, spent, names = _batch_cpu_sample(B, budget_s=20.0)
+            v, spent, names = _batch_cpu_sample(B, budget_s=20.0, admm_switch=args.admm_switch)
             per.append((v, spent, names))
         v, spent, names = per[-1]
         line = {"impl": "reference", "metric": BATCH_METRIC, "value": v, "unit": "instances/s", "n_gpus": args.gpus,
@@ -786,7 +798,7 @@ def run_batch(args):
     import paper_2407_15049_gb300 as L
     L.load()
     prec_code = {"fp64": L.LORADS_FP64, "mixed": L.LORADS_MIXED, "fp32": L.LORADS_FP32}[args.prec]
-    params = L.default_params(prec=prec_code, time_limit=args.instance_time_limit)
+    params = L.default_params(prec=prec_code, time_limit=args.instance_time_limit, admm_switch=args.admm_switch)
     t = time.perf_counter()
     b = L.lorads_batch_create(B, params)
     create_s = time.perf_counter() - t
@@ -837,7 +849,7 @@ def run_batch(args):
     alg = 0.0
     for inst, r in zip(B, res):
         alg += batch_bytes(inst, L.padded_ld(max(r["rank"], 1)), wR, wD, params.lbfgs_mem, r["inner_iters"],
-                           r["outer_iters"])
+                           r["outer_iters"], r["cg_steps"])
     peak, peak_kind = measured_peaks()
     ach = alg / per_step / 1e9
     kinds = np.array([x.kind for x in B])
@@ -846,7 +858,7 @@ def run_batch(args):
     totals = {k: int(np.sum(kinds == k)) for k in ("maxcut", "mc")}
     cpu = None
     if not args.no_cpu_baseline:
-        v, spent, names = _batch_cpu_sample(B, budget_s=20.0)
+        v, spent, names = _batch_cpu_sample(B, budget_s=20.0, admm_switch=args.admm_switch)
         cpu = {"value": v, "unit": "instances/s", "cores": 1, "kind": "oracle",
                "sample": f"{len(names)} seeded instances of the batch, smallest first, solved to tolerance by "
                          f"the oracle ({spent:.1f} s, one thread on {host_cpu()}): " + ", ".join(names)}
@@ -858,6 +870,8 @@ def run_batch(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "description": cfg["desc"], "count": count,
                    "solver_precision": args.prec, "instance_time_limit_s": args.instance_time_limit,
+                   "two_stage": ({"admm_switch": args.admm_switch, "cg_rel": 1e-2, "cg_max": 50}
+                                 if args.admm_switch > 0 else None),
                    "tolerance": 1e-5, "shape": shape, "l2_policy": "state of all instances 1.1x L2 and up; "
                    "each launch restarts every instance from its start", "parallelism": f"replicas x{world}"},
         "e2e": {"value": count / e2e_s, "unit": "instances/s", "h2d_bytes_per_step": int(h2d),
@@ -866,6 +880,11 @@ def run_batch(args):
         "latency_ms": {"p50": stats["latency_p50_ms"], "p99": stats["latency_p99_ms"],
                        "max": stats["latency_max_ms"]},
         "solved": solved, "instances": totals, "inner_iters": stats["inner_iters"],
+        "admm": {"instances_with_stage": int(sum(1 for r in res if r["admm_iters"] > 0)),
+                 "admm_iters": int(sum(r["admm_iters"] for r in res)),
+                 "cg_steps": int(sum(r["cg_steps"] for r in res))},
+        "status_counts": {nm: int(sum(1 for r in res if r["status_name"] == nm))
+                          for nm in sorted({r["status_name"] for r in res})},
         "roofline": {"kernel": "k_batch_solve", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                      "frac": ach / peak, "peak_kind": peak_kind, "traffic": None,
                      "algorithmic_bytes_per_launch": alg, "avg_launch_ms": per_step * 1e3},
@@ -926,8 +945,30 @@ def spmm_vs_cusparse(n: int) -> int:
     return 0
 
 
+def kernel_probe(args) -> int:
+    """Per-kernel CUDA-event times of the first ITERS iterations of a host-stepped solve
+    (the same kernels and decisions as the graph path), twice; one JSON line each."""
+    import torch
+    import paper_2407_15049_gb300 as L
+    L.load()
+    code = {"fp64": L.LORADS_FP64, "mixed": L.LORADS_MIXED, "df64": L.LORADS_DF64, "fp32": L.LORADS_FP32}[args.prec]
+    inst, R0, _ = build_instance(args.workload)
+    R0d = torch.as_tensor(R0, device="cuda")
+    for rep in range(2):
+        ctx = L.lorads_create(inst, L.default_params(prec=code, verbose=2, max_outer=10**6, max_inner=args.kernel_probe,
+                                                     rank_update_threshold=10**6))
+        res = L.lorads_solve(ctx, R0d, on_device=True, max_total_inner=args.kernel_probe)
+        t = L.lorads_kernel_times(ctx)
+        L.lorads_destroy(ctx)
+        print(json.dumps({"workload": args.workload, "prec": args.prec, "rep": rep, "iters": res["inner_iters"],
+                          "kernels_ms": {k: v[0] for k, v in t.items()}}), flush=True)
+    return 0
+
+
 def main():
     args = _args()
+    if args.kernel_probe:
+        return kernel_probe(args)
     if args.spmm_vs_cusparse:
         return spmm_vs_cusparse(args.spmm_vs_cusparse)
     if args.workload in BATCH_WORKLOADS:
