@@ -111,8 +111,10 @@ typedef struct {
                                   the step update (with bit 1 or 2) prefetches each group's next row into L2
                                   (measured 1% slower); bit 5: the line-search SpMM with the fewest lanes
                                   per row that leaves none idle (ld = 24: 2 lanes x 3 units, 16 rows per
-                                  warp; measured 2.6% slower at n = 1e7).  Bits 3 and 4 change no
-                                  arithmetic, bit 5 only the order of the epilogue's sums.  Default 10 =
+                                  warp; measured 2.6% slower at n = 1e7); bit 6 (with bit 3): the
+                                  line-search SpMM loads row bounds two rows ahead and prefetches one
+                                  neighbour row of the next row per lane into L2.  Bits 3, 4 and 6 change
+                                  no arithmetic, bit 5 only the order of the epilogue's sums.  Default 10 =
                                   bits 1 and 3. */
     int32_t inner_scale;       /* inner stop ||G||_F <= thr, z = A(RR^T) - b, e = tol (1 + ||b||_inf):
                                   0: thr = inner_rel max(||z||, e);  1: thr = inner_rel max(rho ||z||, e);

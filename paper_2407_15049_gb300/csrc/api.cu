@@ -59,6 +59,7 @@ struct SolverState {
 // the stage's device control block; one captured graph per ADMM iteration.
 struct AdmmState {
     int rtype = -1, wtype = -1, ld = 0;
+    bool borrowed = false;              // U, V, r, p, Q, w live in the solver state's arrays
     size_t esR = 0, esW = 0;
     void* U = nullptr;
     void* V = nullptr;
@@ -280,9 +281,20 @@ void free_state(SolverState& st) {
     dfree(st.y); dfree(st.ytil); dfree(st.zrow); dfree(st.zk); dfree(st.ydf);
     st = SolverState();
 }
+// Frees what the ADMM state owns; arrays lent by the solver state stay.
+void release_admm_arrays(AdmmState& a) {
+    if (!a.borrowed) {
+        dfree(a.U); dfree(a.V); dfree(a.r); dfree(a.p); dfree(a.Q); dfree(a.om);
+    }
+    a.U = a.V = a.r = a.p = a.Q = a.om = nullptr;
+    a.borrowed = false;
+    a.rtype = a.wtype = -1;
+    a.ld = 0;
+}
 void free_admm(AdmmState& a) {
     if (a.exec) cudaGraphExecDestroy(a.exec);
-    dfree(a.U); dfree(a.V); dfree(a.r); dfree(a.p); dfree(a.Q); dfree(a.om); dfree(a.ac);
+    release_admm_arrays(a);
+    dfree(a.ac);
     if (a.h_ac) cudaFreeHost(a.h_ac);
     a = AdmmState();
 }
@@ -634,7 +646,8 @@ struct Driver {
                   PH_INNER, s};
         timed(FAM_DIR, [&] { launch_dir<TD, TDIR>(d); });
         SpmmCArgs ls{p(), st.D, st.CD, st.ld, st.sh_ls, nullptr, 1, EPI_LS, st.R, st.y, st.zrow, st.ydf, c->ctrl, 0.0,
-                     part_of(c, PART_LS), nb_ls, c->ctrl, PH_INNER, s, (c->prm.kernel_variant & 8) ? 1 : 0};
+                     part_of(c, PART_LS), nb_ls, c->ctrl, PH_INNER, s,
+                     (c->prm.kernel_variant & 8) ? ((c->prm.kernel_variant & 64) ? 2 : 1) : 0};
         timed(FAM_SPMM_LS, [&] { launch_spmm_c<TDIR, TD, TR>(ls); });
         if (c->m_off) {
             ConsArgs cl{p(), CONS_LS, c->m_diag, c->m, st.R, st.D, st.ld, st.sh, st.y, nullptr, st.zk, st.ydf, c->ctrl, 0.0,
@@ -928,31 +941,72 @@ constexpr int type_code() {
     return std::is_same<T, double>::value ? 0 : (std::is_same<T, dfloat>::value ? 1 : 2);
 }
 
+lorads_status admm_ctrl_alloc(lorads_ctx* ctx) {
+    AdmmState& a = ctx->admm;
+    lorads_status s;
+    if (!a.ac && (s = dalloc(ctx, &a.ac, 1))) return s;
+    if (!a.h_ac && cudaMallocHost(&a.h_ac, sizeof(AdmmCtrl)) != cudaSuccess) {
+        cudaGetLastError();
+        a.h_ac = nullptr;
+        return set_err(ctx, "pinned allocation failed"), LORADS_ERR_OOM;
+    }
+    return LORADS_OK;
+}
+
+// Work arrays of the stage for row width ld, owned by the context (kept for later calls).
 template <typename TR, typename TW>
 lorads_status admm_alloc(lorads_ctx* ctx, int ld) {
     AdmmState& a = ctx->admm;
-    if (a.U && a.rtype == type_code<TR>() && a.wtype == type_code<TW>() && a.ld == ld) return LORADS_OK;
-    free_admm(a);
+    if (a.U && !a.borrowed && a.rtype == type_code<TR>() && a.wtype == type_code<TW>() && a.ld == ld)
+        return LORADS_OK;
+    release_admm_arrays(a);
     const size_t nl = (size_t)ctx->n * ld;
     lorads_status s;
+    if ((s = admm_ctrl_alloc(ctx))) return s;
     if ((s = dalloc(ctx, reinterpret_cast<TR**>(&a.U), nl))) return s;
     if ((s = dalloc(ctx, reinterpret_cast<TR**>(&a.V), nl))) return s;
     if ((s = dalloc(ctx, reinterpret_cast<TW**>(&a.r), nl))) return s;
     if ((s = dalloc(ctx, reinterpret_cast<TW**>(&a.p), nl))) return s;
     if ((s = dalloc(ctx, reinterpret_cast<TW**>(&a.Q), nl))) return s;
     if ((s = dalloc(ctx, reinterpret_cast<double**>(&a.om), ctx->m))) return s;
-    if ((s = dalloc(ctx, &a.ac, 1))) return s;
-    if (cudaMallocHost(&a.h_ac, sizeof(AdmmCtrl)) != cudaSuccess) {
-        cudaGetLastError();
-        a.h_ac = nullptr;
-        return set_err(ctx, "pinned allocation failed"), LORADS_ERR_OOM;
-    }
     CK(cudaMemset(a.r, 0, nl * sizeof(TW)));
     CK(cudaMemset(a.p, 0, nl * sizeof(TW)));
     CK(cudaMemset(a.Q, 0, nl * sizeof(TW)));
     a.rtype = type_code<TR>();
     a.wtype = type_code<TW>();
     a.ld = ld;
+    a.esR = sizeof(TR);
+    a.esW = sizeof(TW);
+    return LORADS_OK;
+}
+
+// The stage after an ALM solve: its arrays are lent by the solver state, whose
+// L-BFGS history, gradient and C D are not needed any more: r = G, p = C D, Q, U
+// and V in the history slots, w in the z cache of the constraints (m doubles).
+// When the history is too small (short memory), owned arrays are used instead.
+template <typename TR, typename TW>
+lorads_status admm_bind(lorads_ctx* ctx) {
+    AdmmState& a = ctx->admm;
+    SolverState& st = ctx->st;
+    const size_t nl = (size_t)ctx->n * st.ld;
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t need = up(nl * sizeof(TW)) + 2 * up(nl * sizeof(TR));
+    const size_t have = nl * st.esD * 2 * (size_t)ctx->prm.lbfgs_mem;
+    if (need > have || st.esD != sizeof(TW)) return admm_alloc<TR, TW>(ctx, st.ld);
+    lorads_status s;
+    release_admm_arrays(a);
+    if ((s = admm_ctrl_alloc(ctx))) return s;
+    char* h = static_cast<char*>(st.hist);
+    a.r = st.G;
+    a.p = st.CD;
+    a.Q = h;
+    a.U = h + up(nl * sizeof(TW));
+    a.V = h + up(nl * sizeof(TW)) + up(nl * sizeof(TR));
+    a.om = st.zk;
+    a.borrowed = true;
+    a.rtype = type_code<TR>();
+    a.wtype = type_code<TW>();
+    a.ld = st.ld;
     a.esR = sizeof(TR);
     a.esW = sizeof(TW);
     return LORADS_OK;
@@ -1023,7 +1077,7 @@ lorads_status run_admm(lorads_ctx* ctx, double rho, std::chrono::steady_clock::t
     SolverState& st = ctx->st;
     const lorads_params& P = ctx->prm;
     lorads_status s;
-    if ((s = admm_alloc<TR, TW>(ctx, st.ld))) return s;
+    if ((s = admm_bind<TR, TW>(ctx))) return s;
     AdmmState& a = ctx->admm;
     cudaStream_t ss = ctx->solve_stream;
     const size_t bytes = (size_t)ctx->n * st.ld * sizeof(TR);

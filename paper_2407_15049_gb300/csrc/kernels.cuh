@@ -245,18 +245,28 @@ k_spmm_c_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld,
     // iteration ahead, and that row's entries, own-row streams and scalars are prefetched
     // into L2, so of its dependent load phases only the neighbour gathers wait on HBM.
     const bool own_row = EPI == EPI_LS || EPI == EPI_OBJ || (v != nullptr && p.dk != nullptr);
+    // With pf == 2 the bounds run two rows ahead: the stored entries of the row after
+    // next are prefetched, so that the next row's column indices are L2 hits one
+    // iteration early and each lane can prefetch one neighbour row of D for it.
     int64_t s_nx = -1, e_nx = -1;
+    int64_t s_n2 = -1, e_n2 = -1;
     for (int64_t base = rl.first; base < p.n; base += rl.stride) {
         const int64_t i = base + rl.gw;
         const bool act = i < p.n;
         const int64_t s_cur = s_nx, e_cur = e_nx;
         s_nx = -1;
         int k_nx = -1;
+        int jn = -1;
         if (pf != 0) {
             const int64_t nx = i + rl.stride;
             if (nx < p.n) {
-                s_nx = __ldg(p.c_rowptr + nx);
-                e_nx = __ldg(p.c_rowptr + nx + 1);
+                if (pf == 2 && s_n2 >= 0) {
+                    s_nx = s_n2;
+                    e_nx = e_n2;
+                } else {
+                    s_nx = __ldg(p.c_rowptr + nx);
+                    e_nx = __ldg(p.c_rowptr + nx + 1);
+                }
                 if (own_row) prefetch_row<TX, CPL>(X, nx, ld, L, Q, rl.lig);
                 if constexpr (EPI == EPI_LS) prefetch_row<TR, CPL>(R, nx, ld, L, Q, rl.lig);
                 if (p.dk != nullptr && rl.lig == 0) {
@@ -266,6 +276,15 @@ k_spmm_c_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld,
                     if constexpr (EPI == EPI_LS)
                         if (zrow != nullptr) prefetch_l2(zrow + nx);
                 }
+            }
+            if (pf == 2) {
+                const int64_t n2 = nx + rl.stride;
+                s_n2 = -1;
+                if (n2 < p.n) {
+                    s_n2 = __ldg(p.c_rowptr + n2);
+                    e_n2 = __ldg(p.c_rowptr + n2 + 1);
+                }
+                if (s_nx >= 0 && s_nx + rl.lig < e_nx) jn = __ldg(p.c_col + s_nx + rl.lig);
             }
         }
         A acc[CPL][4];
@@ -317,7 +336,20 @@ k_spmm_c_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld,
 #pragma unroll
                     for (int e = 0; e < 4; ++e) acc[c][e] = fma(w0, A(x0[c].v[e]), acc[c][e]);
             }
-            if (s_nx >= 0 && rl.lig < 2 && e_nx > s_nx) {
+            if (pf == 2) {
+                // one neighbour row of the next row (its first and last element), and the
+                // stored entries of the row after next
+                if (jn >= 0) {
+                    const TX* rowp = X + (int64_t)jn * ld;
+                    prefetch_l2(rowp);
+                    prefetch_l2(rowp + ld - 1);
+                }
+                if (s_n2 >= 0 && rl.lig < 2 && e_n2 > s_n2) {
+                    const int64_t q = rl.lig == 0 ? s_n2 : e_n2 - 1;
+                    prefetch_l2(p.c_col + q);
+                    prefetch_l2(cv + q);
+                }
+            } else if (s_nx >= 0 && rl.lig < 2 && e_nx > s_nx) {
                 // the next row's stored entries (first and last sector) and multiplier terms
                 const int64_t q = rl.lig == 0 ? s_nx : e_nx - 1;
                 prefetch_l2(p.c_col + q);

@@ -16,7 +16,8 @@ struct SpmmCArgs {
     const double* v; int write_out; int epi;
     const void* R; const double* y; const void* zrow; const dfloat* ydf; const Ctrl* ctrl; double rho; double* part;
     int blocks; const Ctrl* gate; int ph; cudaStream_t stream;
-    int prefetch = 0;   // 1: carry the next row's bounds and prefetch its entries and row terms into L2
+    int prefetch = 0;   // 1: carry the next row's bounds and prefetch its entries and row terms into L2;
+                        // 2: also the bounds of the row after next and one neighbour row of the next row
 };
 
 // v: double[m], or double-float[m] when v_df (weights then formed without FP64)

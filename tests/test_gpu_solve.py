@@ -252,6 +252,10 @@ def test_prefetch_variants_are_bit_identical(prec):
     res1, Rb, yb = _gpu_solve(inst, R0, prec=prec, kernel_variant=2 | 8 | 16, **caps)
     assert res0["inner_iters"] == res1["inner_iters"] > 15
     assert np.array_equal(Ra, Rb) and np.array_equal(ya, yb)
+    # bit 6: bounds two rows ahead and one neighbour row of the next row prefetched
+    res2, Rc, yc = _gpu_solve(inst, R0, prec=prec, kernel_variant=2 | 8 | 64, **caps)
+    assert res2["inner_iters"] == res0["inner_iters"]
+    assert np.array_equal(Ra, Rc) and np.array_equal(ya, yc)
 
 
 @pytest.mark.parametrize("kv", [2 | 8 | 32])
