@@ -96,10 +96,12 @@ def test_cg_matches_oracle(name, cg_rel):
     finally:
         L.lorads_destroy(ctx)
     assert k == k_ref
-    # a few steps: the iterates agree to rounding; 50 steps (the cap, reached at 1e-8):
-    # the CG recurrences amplify the rounding differences of the two reduction orders
-    # (measured 2.8e-10 on the MaxCut instance)
-    assert rel_err(Xd.cpu().numpy()[:, :r], X_ref) <= (1e-10 if k <= 10 else 1e-8)
+    # Algorithm 2 stops at a relative residual: the iterate it returns responds to
+    # rounding differences (another reduction order) through the Krylov polynomial;
+    # the bound is 10x the oracle's own response to a 1e-15 change of its right side
+    rhs = A.system_rhs(P, V, y, rho)
+    sens = max(rel_err(A.cg(P, V, X0, rhs * f, rho, cg_rel, 50)[0], X_ref) for f in (1 + 1e-15, 1 - 1e-15))
+    assert rel_err(Xd.cpu().numpy()[:, :r], X_ref) <= max(1e-10, 10 * sens)
 
 
 @pytest.mark.parametrize("name", ["maxcut_er_1000", "mc_60x80"])

@@ -144,7 +144,7 @@ def test_trained_network_starts_closer_to_the_optimum():
     try:
         hist = net.fit(train, epochs=60, lr=3e-3, seed=1)
         assert hist[-1] < 0.7 * hist[0], hist[::10]
-        gains = []
+        gains, iters = [], []
         for k in range(3):
             n = 900 + 100 * k
             inst = W.maxcut_instance(n, W.er_graph(n, 2 * n, 900 + k, "pm1"))
@@ -160,6 +160,19 @@ def test_trained_network_starts_closer_to_the_optimum():
             gap_rand = O.objective(Pb, Rr) - opt
             gains.append(gap_rand / gap_net)
             assert gap_net < gap_rand, (gap_net, gap_rand)
+            # started from the network's factor, the solve reaches the same optimum
+            # (both at rel. KKT 1e-5 with err2); the iteration counts are reported
+            ctx = L.lorads_create(inst, L.default_params(compute_err2=1))
+            try:
+                res_w = L.lorads_solve(ctx, R0)
+                res_c = L.lorads_solve(ctx, Rr)
+            finally:
+                L.lorads_destroy(ctx)
+            for rr in (res_w, res_c):
+                assert rr["status_name"] == "LORADS_OK", rr
+                assert max(rr["err1"], abs(rr["err3"]), rr["err2"]) <= 1e-5
+                assert rr["primal_obj"] == pytest.approx(opt, rel=1e-4)
+            iters.append((res_w["inner_iters"], res_c["inner_iters"]))
     finally:
         net.close()
-    print("objective-gap ratio random / network:", gains)
+    print("objective-gap ratio random / network:", gains, "iterations network / random start:", iters)
