@@ -56,6 +56,8 @@ METRIC = "time to rel. KKT 1e-5 (MaxCut n=1e7); SpMM+A(RRᵀ) HBM GB/s vs 8 TB/s
 WORKLOADS = {
     "maxcut_er_1e7": dict(n=10_000_000, edges=20_000_000, weights="pm1", r=24, seed=0, admm_switch=3e-4,
                           desc="MaxCut SDP, Erdos-Renyi n=1e7, M=2e7 edges (avg degree 4), w in {-1,+1}, r=24"),
+    "maxcut_er_4e6": dict(n=4_000_000, edges=8_000_000, weights="pm1", r=24, seed=0,
+                          desc="MaxCut SDP, Erdos-Renyi n=4e6, M=8e6 edges (avg degree 4), w in {-1,+1}, r=24"),
     "maxcut_er_2e6": dict(n=2_000_000, edges=4_000_000, weights="pm1", r=24, seed=0,
                           desc="MaxCut SDP, Erdos-Renyi n=2e6, M=4e6 edges (avg degree 4), w in {-1,+1}, r=24"),
     "maxcut_er_1e6": dict(n=1_000_000, edges=2_000_000, weights="pm1", r=20, seed=0,
@@ -64,6 +66,10 @@ WORKLOADS = {
                           desc="MaxCut SDP, Erdos-Renyi n=1e5, M=2e5 edges (avg degree 4), w in {-1,+1}, r=17"),
     "maxcut_torus_1e6": dict(n=1_000_000, edges=2_000_000, weights="pm1", r=20, seed=0, graph="torus", side=1000,
                              desc="MaxCut SDP, 1000x1000 torus (4-regular, wraparound), w in {-1,+1}, r=20"),
+    "maxcut_er_1p7e8": dict(n=170_000_000, edges=340_000_000, weights="pm1", r=28, seed=0, admm_switch=3e-4,
+                            lbfgs_mem=2, scale=True,
+                            desc="MaxCut SDP, Erdos-Renyi n=1.7e8, M=3.4e8 edges (avg degree 4), w in {-1,+1}, "
+                                 "r=28 fixed, two stored L-BFGS pairs (the order of the largest MaxCut of Table 4)"),
     "mc_5e4_rank3": dict(kind="mc", side=50_000, rank=3, n=100_000, m=2_704_945, r=22, seed=0, admm_switch=1e-3,
                          desc="matrix-completion SDP: M = U V^T, U, V in R^{50000x3} iid N(0,1), |Omega| = "
                               "ceil(5 n ln n) = 2,704,945 uniform samples, X of order 1e5, C = I, r = 22"),
@@ -130,7 +136,11 @@ def _args():
     ap.add_argument("--warm-start", choices=["none", "gnn"], default="none",
                     help="starting factor: seeded random rows, or the learned network (trained before timing "
                          "on solved ER graphs; its prediction is inside the timed region)")
+    ap.add_argument("--scale-time-limit", type=float, default=1500.0,
+                    help="time limit (s) of the solve of a scale workload")
     ap.add_argument("--train-graphs", type=int, default=96)
+    ap.add_argument("--train-max-n", type=int, default=30000,
+                    help="training graphs: n log-uniform in [1000, this]")
     ap.add_argument("--train-epochs", type=int, default=40)
     ap.add_argument("--compare-cold", action="store_true",
                     help="with --warm-start gnn: also time one solve from the random start")
@@ -153,7 +163,7 @@ def _args():
 
 # ----------------------------------------------------------------------------- helpers
 
-def build_instance(name):
+def build_instance(name, with_start: bool = True):
     import workloads as W
     cfg = WORKLOADS[name]
     t = time.perf_counter()
@@ -166,7 +176,7 @@ def build_instance(name):
     else:
         edges = W.er_graph(cfg["n"], cfg["edges"], cfg["seed"], cfg["weights"])
     inst = W.maxcut_instance(cfg["n"], edges)
-    R0 = W.initial_factor(inst, cfg["r"], cfg["seed"] + 1)
+    R0 = W.initial_factor(inst, cfg["r"], cfg["seed"] + 1) if with_start else None
     return inst, R0, time.perf_counter() - t
 
 
@@ -490,7 +500,7 @@ def run_native(args):
             rng = _np.random.default_rng(12345)
             train = []
             for k in range(args.train_graphs):
-                nk = int(round(_m.exp(rng.uniform(_m.log(1000), _m.log(30000)))))
+                nk = int(round(_m.exp(rng.uniform(_m.log(1000), _m.log(args.train_max_n)))))
                 train.append(W.maxcut_instance(nk, W.er_graph(nk, 2 * nk, 5000 + k, "pm1")))
             net, warm = WS.train_on_solved(train, cfg["r"], epochs=args.train_epochs)
             graph = WS.device_graph(inst)
@@ -973,10 +983,120 @@ def kernel_probe(args) -> int:
     return 0
 
 
+SCALE_HOST_NEED_GB = 100.0      # generation (~45 GB at 1.7e8) plus the host mirrors of lorads_create
+
+
+def _host_available_gb() -> float:
+    """Memory this process may still take: MemAvailable, capped by a cgroup v2 limit."""
+    avail = float("inf")
+    try:
+        for line in Path("/proc/meminfo").read_text().splitlines():
+            if line.startswith("MemAvailable:"):
+                avail = float(line.split()[1]) * 1024 / 1e9
+    except OSError:
+        pass
+    try:
+        lim = Path("/sys/fs/cgroup/memory.max").read_text().strip()
+        if lim != "max":
+            cur = float(Path("/sys/fs/cgroup/memory.current").read_text().strip())
+            avail = min(avail, (float(lim) - cur) / 1e9)
+    except (OSError, ValueError):
+        pass
+    return avail
+
+
+def scale_device_bytes(n: int, nnz: int, ld: int, T: int) -> float:
+    """Device bytes of a mixed-form solve of a MaxCut instance (one diagonal constraint per
+    row): the solver state (R, C R double-float; D, C D, G and 2T history slots FP32),
+    C (row pointers, columns, FP64 / FP32 / double-float values), the per-row constraint
+    arrays and their state, and the err2 Lanczos vectors (three n x 4 FP64 blocks)."""
+    nl = n * ld
+    state = nl * (2 * 8 + 3 * 4 + 2 * T * 4)
+    c = (n + 1) * 8 + nnz * (4 + 8 + 4 + 8)
+    rows = n * (4 + 8 + 4 + 8 + 8 + 4 + 4 + 8 + 4 + 8 + 8) + n * (8 + 8 + 8 + 4)
+    lanczos = 3 * n * 4 * 8
+    return float(state + c + rows + lanczos)
+
+
+def run_scale(args) -> int:
+    """One timed solve of a workload at the size of the largest MaxCut of Table 4: the
+    mixed form, the rank fixed at the workload's r and two stored L-BFGS pairs (the state
+    then fills most of HBM), the start drawn on the device.  Checks host and device memory
+    before it starts and prints an ``unavailable`` line when either is short."""
+    import torch
+    import paper_2407_15049_gb300 as L
+    cfg = WORKLOADS[args.workload]
+    n, r, T = cfg["n"], cfg["r"], cfg["lbfgs_mem"]
+    nnz = n + 2 * cfg["edges"]
+    ld = L.padded_ld(r)
+    head = {"metric": f"time to rel. KKT 1e-5 (MaxCut ER n={n:.2g}, r={r})", "workload": args.workload}
+    host = _host_available_gb()
+    need = scale_device_bytes(n, nnz, ld, T)
+    free_b, total_b = torch.cuda.mem_get_info()
+    if host < SCALE_HOST_NEED_GB or free_b < need + 4e9:
+        print(json.dumps({**head, "unavailable": f"memory: host {host:.0f} GB available (need "
+                          f"{SCALE_HOST_NEED_GB:.0f}), device {free_b / 1e9:.0f} GB free (need {need / 1e9:.0f} + 4)"}),
+              flush=True)
+        return 0
+    L.load()
+    inst, _, gen_s = build_instance(args.workload, with_start=False)
+    stream = torch.cuda.Stream()
+    params = L.default_params(prec=L.LORADS_MIXED, compute_err2=1, admm_switch=args.admm_switch,
+                              lbfgs_mem=T, rank_update_threshold=10**6, time_limit=args.scale_time_limit, seed=1)
+    with torch.cuda.stream(stream):
+        t = time.perf_counter()
+        ctx = L.lorads_create(inst, params, stream=stream.cuda_stream)
+        create_s = time.perf_counter() - t
+        # warm-up: a capped solve (graph capture, first launches)
+        L.lorads_solve(ctx, None, r0=r, max_total_inner=args.warmup_iters)
+        torch.cuda.synchronize()
+        used_b = total_b - torch.cuda.mem_get_info()[0]
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            res = L.lorads_solve(ctx, None, r0=r)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        L.lorads_destroy(ctx)
+    secs = ev0.elapsed_time(ev1) / 1e3
+    it_bytes = sum(kernel_bytes(f, n, ld, nnz, n, 8, 4, T) for f in ("k_dir", "k_spmm_c(CD,ls)", "k_update(step)"))
+    peak, kind = measured_peaks()
+    per_it = secs / max(res["inner_iters"], 1)
+    print(json.dumps({
+        **head, "value": secs, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 1, "warmup_iters": args.warmup_iters,
+        "higher_is_better": False, "dtype": "mixed (double-float R and C R, f32 work arrays)", "data": "synthetic",
+        "config": {"workload": args.workload, "description": cfg["desc"], "n": n, "m": n, "nnz_C": nnz, "rank": r,
+                   "lbfgs_mem": T, "rank_rule": "off (rank fixed)", "two_stage": {"admm_switch": args.admm_switch},
+                   "start": "cold (unit rows drawn on the device, seed 1)", "tolerance": 1e-5},
+        "solve": {k: res[k] for k in ("status_name", "inner_iters", "outer_iters", "admm_iters", "cg_steps",
+                                      "primal_obj", "err1", "err2", "err3", "rank")},
+        "per_iteration": {"ms_upper_bound": per_it * 1e3, "algorithmic_bytes": it_bytes,
+                          "algorithmic_gbs_lower_bound": it_bytes / per_it / 1e9,
+                          "frac_of_peak_lower_bound": it_bytes / per_it / 1e9 / peak, "peak_gbs": peak,
+                          "peak_kind": kind,
+                          "note": "solve time over L-BFGS iterations: the outer steps, the ADMM stage and the "
+                                  "final err2 are charged to the iterations too"},
+        "memory": {"device_used_gb": used_b / 1e9, "device_estimate_gb": need / 1e9,
+                   "device_total_gb": total_b / 1e9, "host_available_gb_at_start": host},
+        "setup_s": {"generate": gen_s, "create": create_s},
+        "clocks": clk.summary(),
+        "context": "Table 4 reports 158 s on an H100 for the k-mer graph kmer_A2a (n = 170,728,175); "
+                   "a different graph, machine and precision",
+    }), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     if args.kernel_probe:
         return kernel_probe(args)
+    if WORKLOADS.get(args.workload, {}).get("scale"):
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle is not run at this size "
+                              "(hours per iteration)"}), flush=True)
+            return 0
+        return run_scale(args)
     if args.spmm_vs_cusparse:
         return spmm_vs_cusparse(args.spmm_vs_cusparse)
     if args.workload in BATCH_WORKLOADS:

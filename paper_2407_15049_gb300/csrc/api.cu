@@ -34,7 +34,7 @@ struct SolverState {
     int r = 0, ld = 0;
     Shape sh{1, 1};
     Shape sh_ls{1, 1};                  // lane shape of the line-search SpMM (kernel_variant bit 5)
-    size_t esR = 0, esD = 0;
+    size_t esR = 0, esD = 0, esDir = 0;  // element bytes of R, of C D / G / history, of D
     int rtype = 0;                      // storage of R: 0 double, 1 double-float, 2 float
     void* R = nullptr;
     void* CR = nullptr;
@@ -716,6 +716,7 @@ lorads_status alloc_state(lorads_ctx* ctx, int prec, int r) {
     if (ctx->prm.kernel_variant & 32) shape_narrow(ld, &st.sh_ls);
     st.esR = sizeof(TR);
     st.esD = sizeof(TD);
+    st.esDir = sizeof(TDIR);
     st.rtype = std::is_same<TR, double>::value ? 0 : (std::is_same<TR, dfloat>::value ? 1 : 2);
     const size_t nl = (size_t)ctx->n * ld;
     lorads_status s;
@@ -981,16 +982,19 @@ lorads_status admm_alloc(lorads_ctx* ctx, int ld) {
 }
 
 // The stage after an ALM solve: its arrays are lent by the solver state, whose
-// L-BFGS history, gradient and C D are not needed any more: r = G, p = C D, Q, U
-// and V in the history slots, w in the z cache of the constraints (m doubles).
-// When the history is too small (short memory), owned arrays are used instead.
+// L-BFGS history, gradient, direction and C D are not needed any more: r = G,
+// p = C D, Q = D (or the first history bytes when D is stored narrower), U and V
+// in the history slots, w in the z cache of the constraints (m doubles).  With
+// two stored pairs of float history and double-float R the history holds U and V
+// exactly.  When it is too small, owned arrays are used instead.
 template <typename TR, typename TW>
 lorads_status admm_bind(lorads_ctx* ctx) {
     AdmmState& a = ctx->admm;
     SolverState& st = ctx->st;
-    const size_t nl = (size_t)ctx->n * st.ld;
-    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t need = up(nl * sizeof(TW)) + 2 * up(nl * sizeof(TR));
+    const size_t nl = (size_t)ctx->n * st.ld;     // a multiple of 4: every offset below is 16-byte aligned
+    const bool q_in_d = st.esDir == sizeof(TW);
+    const size_t q_bytes = q_in_d ? 0 : nl * sizeof(TW);
+    const size_t need = q_bytes + 2 * nl * sizeof(TR);
     const size_t have = nl * st.esD * 2 * (size_t)ctx->prm.lbfgs_mem;
     if (need > have || st.esD != sizeof(TW)) return admm_alloc<TR, TW>(ctx, st.ld);
     lorads_status s;
@@ -999,9 +1003,9 @@ lorads_status admm_bind(lorads_ctx* ctx) {
     char* h = static_cast<char*>(st.hist);
     a.r = st.G;
     a.p = st.CD;
-    a.Q = h;
-    a.U = h + up(nl * sizeof(TW));
-    a.V = h + up(nl * sizeof(TW)) + up(nl * sizeof(TR));
+    a.Q = q_in_d ? st.D : static_cast<void*>(h);
+    a.U = h + q_bytes;
+    a.V = h + q_bytes + nl * sizeof(TR);
     a.om = st.zk;
     a.borrowed = true;
     a.rtype = type_code<TR>();

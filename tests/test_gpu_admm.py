@@ -195,6 +195,33 @@ def test_two_stage_solve_matches_oracle(case, switch, prec):
         assert res["primal_obj"] == pytest.approx(ref["primal_obj"], rel=2e-5)
 
 
+@pytest.mark.parametrize("mem", [1, 2])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_two_stage_with_short_memory(mem, prec):
+    """With T = 1 or 2 stored pairs the stage takes its arrays from the solver state
+    (history, gradient, C D and the direction; for the mixed form at T = 2 the history
+    holds U and V exactly) or, mixed at T = 1, allocates its own: the result is the
+    oracle's two-stage solve with the same memory."""
+    inst = _instance("maxcut_er_1000")
+    P = O.Problem(inst)
+    R0 = W.initial_factor(inst, 10, 1)
+    ref = A.solve_two_stage(P, R0, O.Params(lbfgs_mem=mem), A.AdmmParams(switch_err1=1e-3))
+    ctx = L.lorads_create(inst, L.default_params(prec=PREC[prec], admm_switch=1e-3, lbfgs_mem=mem))
+    try:
+        res = L.lorads_solve(ctx, R0)
+    finally:
+        L.lorads_destroy(ctx)
+    assert ref["status"] == "ok" and res["status_name"] == "LORADS_OK", res
+    assert res["admm_iters"] >= 1
+    assert res["err1"] <= 1e-5 and abs(res["err3"]) <= 1e-5
+    if prec == "fp64":
+        assert res["inner_iters"] == ref["alm_inner"]
+        assert res["admm_iters"] == ref["admm_iters"]
+        assert res["primal_obj"] == pytest.approx(ref["primal_obj"], rel=1e-7)
+    else:
+        assert res["primal_obj"] == pytest.approx(ref["primal_obj"], rel=2e-5)
+
+
 def test_stage_rejects_bad_rho():
     inst = _instance("maxcut_er_1000")
     ctx = L.lorads_create(inst)

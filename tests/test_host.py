@@ -182,3 +182,42 @@ def test_workload_generators_shapes():
     mc = W.mc_instance(30, 40, 3, 200, seed=2)
     assert mc.n == 70 and mc.m == 200 and np.all(mc.col >= 30)
     assert W.rank_log2(1000) == 10 and W.rank_log2(10**6) == 20 and W.rank_log2(10**7) == 24
+
+
+@pytest.mark.parametrize("graph", ["er_pm1", "er_unit_isolated", "torus", "cycle", "complete", "uniform"])
+def test_counting_csr_equals_the_sparse_conversion(graph):
+    """The counting CSR build (sorted distinct pairs) gives the arrays of the general
+    sparse-matrix conversion bit for bit: same row pointers, columns and values."""
+    rng = np.random.default_rng(5)
+    if graph == "er_pm1":
+        n, e = 300, W.er_graph(300, 1200, 1, "pm1")
+    elif graph == "er_unit_isolated":
+        n, e = 500, W.er_graph(500, 120, 2, "unit")         # many rows without an edge
+    elif graph == "torus":
+        n, e = 144, W.torus_graph(12, 3)
+    elif graph == "cycle":
+        n, e = 9, W.cycle_graph(9)
+    elif graph == "complete":
+        n, e = 12, W.complete_graph(12)
+    else:
+        i, j, _ = W.er_graph(200, 900, 4, "unit")
+        n, e = 200, (i, j, rng.uniform(-1, 1, len(i)))
+    i, j, w = e
+    assert W._sorted_distinct_upper(np.asarray(i), np.asarray(j))
+    deg = np.bincount(np.concatenate([i, j]), weights=np.concatenate([w, w]), minlength=n)
+    a = W._sym_csr(n, i, j, np.asarray(w) / 4.0, -deg / 4.0)
+    b = W._sym_csr_upper_sorted(n, i, j, np.asarray(w) / 4.0, -deg / 4.0)
+    for x, y in zip(a, b):
+        assert x.dtype == y.dtype and np.array_equal(x, y)
+    inst = W.maxcut_instance(n, e)
+    assert np.array_equal(inst.colind, a[1]) and np.array_equal(inst.val, a[2])
+
+
+def test_unsorted_pairs_take_the_sparse_conversion():
+    i, j, w = W.er_graph(100, 300, 7, "pm1")
+    perm = np.random.default_rng(0).permutation(len(i))
+    assert not W._sorted_distinct_upper(i[perm], j[perm])
+    a = W.maxcut_instance(100, (i, j, w))
+    b = W.maxcut_instance(100, (i[perm], j[perm], w[perm]))
+    assert np.array_equal(a.rowptr, b.rowptr) and np.array_equal(a.colind, b.colind)
+    assert np.allclose(a.val, b.val, rtol=0, atol=1e-15)

@@ -179,14 +179,66 @@ def cycle_graph(n: int):
 
 # ----------------------------------------------------------------------------- instances
 
+def _sorted_distinct_upper(i: np.ndarray, j: np.ndarray) -> bool:
+    """True when every pair has i < j and the pairs are strictly increasing in (i, j)."""
+    if len(i) == 0:
+        return True
+    if not np.all(i < j):
+        return False
+    di = np.diff(i)
+    return bool(np.all((di > 0) | ((di == 0) & (np.diff(j) > 0))))
+
+
+def _sym_csr_upper_sorted(n: int, i: np.ndarray, j: np.ndarray, w: np.ndarray, diag: np.ndarray):
+    """The CSR of ``_sym_csr`` built by counting, for distinct pairs i < j sorted by
+    (i, j): row r holds the pairs whose larger end is r (columns ascending), then the
+    diagonal, then the pairs whose smaller end is r.  Linear memory, no sparse-matrix
+    conversion (graphs of 1e8 vertices and more)."""
+    i = np.asarray(i, dtype=np.int64)
+    j = np.asarray(j, dtype=np.int64)
+    w = np.asarray(w, dtype=np.float64)
+    cnt_up = np.bincount(i, minlength=n).astype(np.int64)
+    cnt_lo = np.bincount(j, minlength=n).astype(np.int64)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(cnt_lo + cnt_up + 1, out=rowptr[1:])
+    nnz = int(rowptr[-1])
+    colind = np.empty(nnz, dtype=np.int32)
+    val = np.empty(nnz, dtype=np.float64)
+    rows = np.arange(n, dtype=np.int64)
+    dpos = rowptr[:-1] + cnt_lo
+    colind[dpos] = rows.astype(np.int32)
+    val[dpos] = np.asarray(diag, dtype=np.float64)
+    del dpos
+    # upper entries: the pairs in their given order, k - (first pair of row i) after the diagonal
+    first_up = np.zeros(n, dtype=np.int64)
+    np.cumsum(cnt_up[:-1], out=first_up[1:])
+    pos = rowptr[:-1][i] + cnt_lo[i] + 1 + (np.arange(len(i), dtype=np.int64) - first_up[i])
+    colind[pos] = j.astype(np.int32)
+    val[pos] = w
+    del pos, first_up
+    # lower entries: the pairs ordered by (j, i) (distinct keys: any sort gives this order)
+    perm = np.argsort(j * n + i)
+    js = j[perm]
+    first_lo = np.zeros(n, dtype=np.int64)
+    np.cumsum(cnt_lo[:-1], out=first_lo[1:])
+    pos = rowptr[:-1][js] + (np.arange(len(js), dtype=np.int64) - first_lo[js])
+    colind[pos] = i[perm].astype(np.int32)
+    val[pos] = w[perm]
+    return rowptr, colind, val
+
+
 def maxcut_instance(n: int, edges) -> SDPInstance:
     """MaxCut SDP of Sec. 4.3 written as a minimisation: C = -L(G,w)/4, X_ii = 1."""
     i, j, w = edges
-    deg = np.zeros(n, dtype=np.float64)
-    np.add.at(deg, i, w)
-    np.add.at(deg, j, w)
+    w = np.asarray(w, dtype=np.float64)
+    # weighted degrees, each accumulated in the order of the pairs (i ends, then j ends)
+    deg = np.bincount(np.concatenate([np.asarray(i, np.int64), np.asarray(j, np.int64)]),
+                      weights=np.concatenate([w, w]), minlength=n)
     # L_ij = -w_ij, L_ii = sum_k w_ik  ->  C = -L/4
-    rowptr, colind, val = _sym_csr(n, i, j, w / 4.0, -deg / 4.0)
+    if _sorted_distinct_upper(np.asarray(i), np.asarray(j)):
+        rowptr, colind, val = _sym_csr_upper_sorted(n, i, j, w / 4.0, -deg / 4.0)
+    else:
+        rowptr, colind, val = _sym_csr(n, i, j, w / 4.0, -deg / 4.0)
     k = np.arange(n, dtype=np.int32)
     return SDPInstance(
         n=n, rowptr=rowptr, colind=colind, val=val, m=n,
