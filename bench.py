@@ -102,7 +102,7 @@ DEFAULT_TIME_BUDGET_S = 800.0
 FP64_SAME_RUN_LIMIT_S = 400.0
 
 
-def _args():
+def _args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1)
@@ -153,7 +153,7 @@ def _args():
     ap.add_argument("--spmm-vs-cusparse", type=int, default=0, metavar="N",
                     help="informational: time C D of the library's SpMM and of cuSPARSE (torch CSR @ dense) "
                          "on the ER graph with N vertices (degree 4, r = 24, FP32) and exit")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     if args.fp64_same_run is None:
         args.fp64_same_run = 1 if (args.workload == "maxcut_er_1e7" and args.prec != "fp64") else 0
     if args.admm_switch is None:
@@ -1032,11 +1032,14 @@ def run_scale(args) -> int:
     head = {"metric": f"time to rel. KKT 1e-5 (MaxCut ER n={n:.2g}, r={r})", "workload": args.workload}
     host = _host_available_gb()
     need = scale_device_bytes(n, nnz, ld, T)
+    if host < SCALE_HOST_NEED_GB:
+        print(json.dumps({**head, "unavailable": f"host memory: {host:.0f} GB available, "
+                          f"{SCALE_HOST_NEED_GB:.0f} GB needed"}), flush=True)
+        return 0
     free_b, total_b = torch.cuda.mem_get_info()
-    if host < SCALE_HOST_NEED_GB or free_b < need + 4e9:
-        print(json.dumps({**head, "unavailable": f"memory: host {host:.0f} GB available (need "
-                          f"{SCALE_HOST_NEED_GB:.0f}), device {free_b / 1e9:.0f} GB free (need {need / 1e9:.0f} + 4)"}),
-              flush=True)
+    if free_b < need + 4e9:
+        print(json.dumps({**head, "unavailable": f"device memory: {free_b / 1e9:.0f} GB free, "
+                          f"{need / 1e9:.0f} + 4 GB needed"}), flush=True)
         return 0
     L.load()
     inst, _, gen_s = build_instance(args.workload, with_start=False)

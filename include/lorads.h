@@ -72,9 +72,10 @@ typedef enum {
     LORADS_BF16 = 2,
     LORADS_MIXED = 3,  /* solve only: double-float R and C*R, FP32 direction/gradient/history */
     LORADS_DF64 = 4,   /* solve only: double-float (hi, lo float pairs, ~48-bit) everywhere */
-    LORADS_MIXED_BF16 = 5  /* solve only: MIXED with the search direction D stored in bf16 (rounded once
-                              when formed; the C D product, line search, step and stored pair all use
-                              the rounded direction) */
+    LORADS_MIXED_BF16 = 5  /* solve only: MIXED with the search direction D and the stored L-BFGS pairs
+                              in bf16 (each rounded once when formed; the C D product, line search and
+                              step use the rounded direction, the Gram dots and the two-loop recursion
+                              the rounded pairs); the gradient and C D stay FP32 */
 } lorads_prec;
 
 /* Solver constants.  The paper fixes tol (Sec. 4.2), the time limit (Sec. 4.2)
@@ -113,9 +114,14 @@ typedef struct {
                                   per row that leaves none idle (ld = 24: 2 lanes x 3 units, 16 rows per
                                   warp; measured 2.6% slower at n = 1e7); bit 6 (with bit 3): the
                                   line-search SpMM loads row bounds two rows ahead and prefetches one
-                                  neighbour row of the next row per lane into L2.  Bits 3, 4 and 6 change
-                                  no arithmetic, bit 5 only the order of the epilogue's sums.  Default 10 =
-                                  bits 1 and 3. */
+                                  neighbour row of the next row per lane into L2; bit 7 (with bit 1): the
+                                  step update in packed row groups of ld/4 lanes where that keeps more lanes
+                                  busy (ld = 24: 5 rows of 6 lanes per warp instead of 4 rows of 8 lanes);
+                                  bit 8 (without bit 5): the same packed groups in the line-search SpMM.
+                                  Bits 3, 4 and 6 change no arithmetic, bit 5 only the order of the
+                                  epilogue's sums, bits 7 and 8 the order of the row sums and of the
+                                  partial sums.
+                                  Default 10 = bits 1 and 3. */
     int32_t inner_scale;       /* inner stop ||G||_F <= thr, z = A(RR^T) - b, e = tol (1 + ||b||_inf):
                                   0: thr = inner_rel max(||z||, e);  1: thr = inner_rel max(rho ||z||, e);
                                   2 (default): thr = max(e, min(inner_rel rho ||z||, inner_progress ||G_0||)) */

@@ -34,7 +34,7 @@ struct SolverState {
     int r = 0, ld = 0;
     Shape sh{1, 1};
     Shape sh_ls{1, 1};                  // lane shape of the line-search SpMM (kernel_variant bit 5)
-    size_t esR = 0, esD = 0, esDir = 0;  // element bytes of R, of C D / G / history, of D
+    size_t esR = 0, esD = 0, esDir = 0;  // element bytes of R, of C D and G, of D and the history
     int rtype = 0;                      // storage of R: 0 double, 1 double-float, 2 float
     void* R = nullptr;
     void* CR = nullptr;
@@ -647,7 +647,8 @@ struct Driver {
         timed(FAM_DIR, [&] { launch_dir<TD, TDIR>(d); });
         SpmmCArgs ls{p(), st.D, st.CD, st.ld, st.sh_ls, nullptr, 1, EPI_LS, st.R, st.y, st.zrow, st.ydf, c->ctrl, 0.0,
                      part_of(c, PART_LS), nb_ls, c->ctrl, PH_INNER, s,
-                     (c->prm.kernel_variant & 8) ? ((c->prm.kernel_variant & 64) ? 2 : 1) : 0};
+                     (c->prm.kernel_variant & 8) ? ((c->prm.kernel_variant & 64) ? 2 : 1) : 0,
+                     (c->prm.kernel_variant & 256) ? 1 : 0};
         timed(FAM_SPMM_LS, [&] { launch_spmm_c<TDIR, TD, TR>(ls); });
         if (c->m_off) {
             ConsArgs cl{p(), CONS_LS, c->m_diag, c->m, st.R, st.D, st.ld, st.sh, st.y, nullptr, st.zk, st.ydf, c->ctrl, 0.0,
@@ -670,7 +671,7 @@ struct Driver {
         UpdateArgs u{p(), c->m_off == 0, true, st.R, st.CR, st.D, st.CD, st.G, c->m_off ? st.W : nullptr, st.hist,
                      st.slot_stride, st.ld, st.sh, st.y, st.ydf, st.zrow, c->ctrl, part_of(c, PART_UPD), nb_rows, c->ctrl, PH_STEP, s,
                      (c->prm.kernel_variant & 4) ? 2 : ((c->prm.kernel_variant & 2) ? 1 : 0),
-                     (c->prm.kernel_variant & 16) ? 1 : 0};
+                     (c->prm.kernel_variant & 16) ? 1 : 0, (c->prm.kernel_variant & 128) ? 1 : 0};
         timed(FAM_UPDATE, [&] { launch_update<TR, TD, TDIR>(u); });
         timed(FAM_HIST, [&] {
             ctrl_hist(s, c->ctrl, HIST_STEP, part_of(c, PART_UPD), nb_rows,
@@ -726,7 +727,7 @@ lorads_status alloc_state(lorads_ctx* ctx, int prec, int r) {
     if ((s = dalloc(ctx, reinterpret_cast<TDIR**>(&st.D), nl))) return s;
     if ((s = dalloc(ctx, reinterpret_cast<TD**>(&st.CD), nl))) return s;
     if ((s = dalloc(ctx, reinterpret_cast<TD**>(&st.G), nl))) return s;
-    if ((s = dalloc(ctx, reinterpret_cast<TD**>(&st.hist), nl * 2 * T))) return s;
+    if ((s = dalloc(ctx, reinterpret_cast<TDIR**>(&st.hist), nl * 2 * T))) return s;
     st.slot_stride = (int64_t)nl;
     if (ctx->m_off) {
         if ((s = dalloc(ctx, reinterpret_cast<TD**>(&st.W), nl))) return s;
@@ -743,7 +744,7 @@ lorads_status alloc_state(lorads_ctx* ctx, int prec, int r) {
     CK(cudaMemset(st.D, 0, nl * sizeof(TDIR)));
     CK(cudaMemset(st.CD, 0, nl * sizeof(TD)));
     CK(cudaMemset(st.G, 0, nl * sizeof(TD)));
-    CK(cudaMemset(st.hist, 0, nl * 2 * T * sizeof(TD)));
+    CK(cudaMemset(st.hist, 0, nl * 2 * T * sizeof(TDIR)));
     if (st.W) CK(cudaMemset(st.W, 0, nl * sizeof(TD)));
     return LORADS_OK;
 }
@@ -995,7 +996,7 @@ lorads_status admm_bind(lorads_ctx* ctx) {
     const bool q_in_d = st.esDir == sizeof(TW);
     const size_t q_bytes = q_in_d ? 0 : nl * sizeof(TW);
     const size_t need = q_bytes + 2 * nl * sizeof(TR);
-    const size_t have = nl * st.esD * 2 * (size_t)ctx->prm.lbfgs_mem;
+    const size_t have = nl * st.esDir * 2 * (size_t)ctx->prm.lbfgs_mem;
     if (need > have || st.esD != sizeof(TW)) return admm_alloc<TR, TW>(ctx, st.ld);
     lorads_status s;
     release_admm_arrays(a);

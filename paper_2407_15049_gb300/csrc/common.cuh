@@ -61,6 +61,13 @@ inline bool shape_narrow(int ld, Shape* s) {
     return true;
 }
 
+// Packed row groups (Q lanes, one unit each, floor(32/Q) rows per warp) keep more
+// lanes busy than the power-of-two groups of shape_for_ld (ld = 24: 30 of 32 lanes
+// instead of 24; ld = 20: 30 instead of 20; ld = 28: 28 either way).
+inline bool packed_rows_gain(const Shape& s) {
+    return s.CPL == 1 && s.Q <= 32 && (32 / s.Q) * s.Q > (32 / s.L) * s.Q;
+}
+
 // Row width used for rank r: r rounded up to a multiple of 4.
 inline int padded_ld(int r) { return (r + 3) / 4 * 4; }
 

@@ -128,20 +128,48 @@ __device__ __forceinline__ dfloat ldv(const dfloat* p) {
 }
 
 // Warp-uniform row loop: each warp owns 32/L consecutive rows per trip, so the
-// group shuffles below always see the full warp.
+// group shuffles below always see the full warp.  Packed groups (`dense`): L may
+// be any width up to 32 (one unit per lane, L = units per row); the warp holds
+// floor(32/L) rows and its last 32 mod L lanes take no row (`live` false), e.g.
+// ld = 24: 5 rows of 6 lanes instead of 4 rows of 8 lanes with 2 idle each.
 struct RowLoop {
-    int L, lig, gw, rows_per_warp;
+    int L, lig, gw, rows_per_warp, base_lane;
+    bool live;
     int64_t first, stride;
-    __device__ __forceinline__ RowLoop(int L_, VGrid vg) : L(L_) {
-        lig = threadIdx.x & (L - 1);
-        gw = (threadIdx.x & 31) / L;
-        rows_per_warp = 32 / L;
+    __device__ __forceinline__ RowLoop(int L_, VGrid vg, bool dense = false) : L(L_) {
+        const int lane = threadIdx.x & 31;
+        if (dense) {
+            gw = lane / L;
+            lig = lane - gw * L;
+            rows_per_warp = 32 / L;
+            live = gw < rows_per_warp;
+        } else {
+            lig = threadIdx.x & (L - 1);
+            gw = lane / L;
+            rows_per_warp = 32 / L;
+            live = true;
+        }
+        base_lane = live ? gw * L : 0;
         const int64_t warp = (vg.bid * (int64_t)blockDim.x + threadIdx.x) >> 5;
         const int64_t nwarps = ((int64_t)vg.nblk * blockDim.x) >> 5;
         first = warp * rows_per_warp;
         stride = nwarps * rows_per_warp;
     }
 };
+
+// Sum over the L lanes of a packed group, taken in lane order by every lane (the
+// same bits in each lane of the group); all 32 lanes take part in the shuffles.
+__device__ __forceinline__ float shfl_idx(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ double shfl_idx(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ dfloat shfl_idx(dfloat v, int src) {
+    return dfloat(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
+}
+template <typename V>
+__device__ __forceinline__ V group_sum_packed(V v, int L, int base_lane) {
+    V t = shfl_idx(v, base_lane);
+    for (int k = 1; k < L; ++k) t += shfl_idx(v, base_lane + k);
+    return t;
+}
 
 // Row helpers: lane `lig` of a group of L handles units c*L + lig < Q.
 // Units past Q are zero on load and skipped on store.
@@ -219,13 +247,14 @@ __device__ __forceinline__ A as_stored(A v) {
 //   EPI_OBJ: <C X, X> (objective with X = R)
 enum { EPI_NONE = 0, EPI_LS = 1, EPI_OBJ = 2 };
 
-template <typename TX, typename TO, typename TR, int CPL, int EPI>
+// PF (compile-time, so that the default form carries none of the others' code):
+// 0 none, 1 the next row's bounds and L2 prefetches, 2 also two rows ahead.
+template <typename TX, typename TO, typename TR, int CPL, int EPI, bool DENSE = false, int PF = 0>
 __device__ __forceinline__ void
 k_spmm_c_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int L, int Q,
          const double* __restrict__ v, int write_out,
          const TR* __restrict__ R, const double* __restrict__ y, const void* __restrict__ zrow_v,
-         const dfloat* __restrict__ ydf, const Ctrl* ctrl, double rho_arg, double* __restrict__ part, VGrid vg,
-         int pf = 0) {
+         const dfloat* __restrict__ ydf, const Ctrl* ctrl, double rho_arg, double* __restrict__ part, VGrid vg) {
     using A = arith_t<TO>;
     using TV = cval_t<TX>;
     using PA = part_t<TO, TR>;
@@ -240,7 +269,8 @@ k_spmm_c_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld,
     const double rho = ctrl ? ctrl->rho : rho_arg;
     const LS rho_s = LS(rho);
     const TV* __restrict__ cv = cvals<TV>(p);
-    RowLoop rl(L, vg);
+    static_assert(!DENSE || CPL == 1, "packed row groups hold one unit per lane");
+    RowLoop rl(L, vg, DENSE);
     // With pf: the bounds (and constraint index) of this group's next row are loaded one
     // iteration ahead, and that row's entries, own-row streams and scalars are prefetched
     // into L2, so of its dependent load phases only the neighbour gathers wait on HBM.
@@ -252,15 +282,15 @@ k_spmm_c_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld,
     int64_t s_n2 = -1, e_n2 = -1;
     for (int64_t base = rl.first; base < p.n; base += rl.stride) {
         const int64_t i = base + rl.gw;
-        const bool act = i < p.n;
+        const bool act = rl.live && i < p.n;
         const int64_t s_cur = s_nx, e_cur = e_nx;
         s_nx = -1;
         int k_nx = -1;
         int jn = -1;
-        if (pf != 0) {
+        if (PF != 0 && rl.live) {
             const int64_t nx = i + rl.stride;
             if (nx < p.n) {
-                if (pf == 2 && s_n2 >= 0) {
+                if (PF == 2 && s_n2 >= 0) {
                     s_nx = s_n2;
                     e_nx = e_n2;
                 } else {
@@ -277,7 +307,7 @@ k_spmm_c_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld,
                         if (zrow != nullptr) prefetch_l2(zrow + nx);
                 }
             }
-            if (pf == 2) {
+            if constexpr (PF == 2) {
                 const int64_t n2 = nx + rl.stride;
                 s_n2 = -1;
                 if (n2 < p.n) {
@@ -336,7 +366,7 @@ k_spmm_c_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld,
 #pragma unroll
                     for (int e = 0; e < 4; ++e) acc[c][e] = fma(w0, A(x0[c].v[e]), acc[c][e]);
             }
-            if (pf == 2) {
+            if constexpr (PF == 2) {
                 // one neighbour row of the next row (its first and last element), and the
                 // stored entries of the row after next
                 if (jn >= 0) {
@@ -425,9 +455,15 @@ k_spmm_c_body(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld,
             accq[PL_P2] += t_p2;
             if (zrow == nullptr) accq[PL_P1] += PA(AW(2) * t_p1);
             if (p.dk != nullptr) {
-                if (zrow == nullptr) t_rr = group_sum(t_rr, L);
-                t_rd = group_sum(t_rd, L);
-                t_dd = group_sum(t_dd, L);
+                if constexpr (DENSE) {
+                    if (zrow == nullptr) t_rr = group_sum_packed(t_rr, L, rl.base_lane);
+                    t_rd = group_sum_packed(t_rd, L, rl.base_lane);
+                    t_dd = group_sum_packed(t_dd, L, rl.base_lane);
+                } else {
+                    if (zrow == nullptr) t_rr = group_sum(t_rr, L);
+                    t_rd = group_sum(t_rd, L);
+                    t_dd = group_sum(t_dd, L);
+                }
                 if (act && rl.lig == 0) {
                     const int k = __ldg(p.dk + i);
                     if (k >= 0) {
@@ -850,11 +886,11 @@ k_cons_body(ProbDev p, int64_t k0, int64_t k1, const TU* __restrict__ U, const T
 // ================================================================== direction
 // D = cG G + sum_u (cS_u S_u + cY_u Y_u) over the stored pairs (the two-loop
 // recursion of Algorithm 1 carried out on coefficients); partials <G,D>, ||D||^2.
-// TDIR: storage of D (the direction may be stored narrower than G and the
-// history; <G,D> and ||D||^2 are then taken of the stored values).
+// TDIR: storage of D and of the stored pairs (they may be stored narrower than G;
+// <G,D> and ||D||^2 are then taken of the stored direction).
 template <typename TD, typename TDIR = TD>
 __device__ __forceinline__ void
-k_dir_body(int64_t nunits, const TD* __restrict__ G, TDIR* __restrict__ D, const TD* __restrict__ hist,
+k_dir_body(int64_t nunits, const TD* __restrict__ G, TDIR* __restrict__ D, const TDIR* __restrict__ hist,
       int64_t slot_stride, const Ctrl* ctrl, double* __restrict__ part, VGrid vg) {
     using A = arith_t<TD>;
     using PA = part_t<TD, TD>;
@@ -862,8 +898,8 @@ k_dir_body(int64_t nunits, const TD* __restrict__ G, TDIR* __restrict__ D, const
     const int mem = ctrl->mem_count;
     const A cG = A(ctrl->cG);
     A cS[kMaxMem], cY[kMaxMem];
-    const TD* Sp[kMaxMem];
-    const TD* Yp[kMaxMem];
+    const TDIR* Sp[kMaxMem];
+    const TDIR* Yp[kMaxMem];
 #pragma unroll
     for (int t = 0; t < kMaxMem; ++t) {
         const int s = ctrl->order[t];
@@ -881,7 +917,7 @@ k_dir_body(int64_t nunits, const TD* __restrict__ G, TDIR* __restrict__ D, const
 #pragma unroll
         for (int t = 0; t < kMaxMem; ++t) {
             if (t < mem) {
-                Unit<TD> s, y;
+                Unit<TDIR> s, y;
                 s.load_stream(Sp[t] + u * 4);
                 y.load_stream(Yp[t] + u * 4);
 #pragma unroll
@@ -948,11 +984,11 @@ constexpr int update_min_blocks() {
     return (CPL == 1 && !std::is_same_v<arith_t<TR>, double>) ? 3 : 2;
 }
 
-template <typename TR, typename TD, int CPL, bool STEP, bool HIST, typename TDIR = TD>
+template <typename TR, typename TD, int CPL, bool STEP, bool HIST, typename TDIR = TD, bool DENSE = false>
 __device__ __forceinline__ void
 k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __restrict__ D,
          const TD* __restrict__ CD, TD* __restrict__ G, const TD* __restrict__ W,
-         TD* __restrict__ hist, int64_t slot_stride, int ld, int L, int Q,
+         TDIR* __restrict__ hist, int64_t slot_stride, int ld, int L, int Q,
          const double* __restrict__ y, const dfloat* __restrict__ ydf, void* __restrict__ zrow_v,
          const Ctrl* ctrl, double* __restrict__ part, VGrid vg, int pf = 0) {
     using AR = arith_t<TR>;
@@ -969,10 +1005,10 @@ k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __
     const AR tau = AR(taud);
     const AD tau_d = AD(taud);
     int nold = 0;
-    TD* Snew = nullptr;
-    TD* Ynew = nullptr;
-    const TD* So[kMaxMem - 1];
-    const TD* Yo[kMaxMem - 1];
+    TDIR* Snew = nullptr;                       // pairs stored in the direction's type
+    TDIR* Ynew = nullptr;
+    const TDIR* So[kMaxMem - 1];
+    const TDIR* Yo[kMaxMem - 1];
     if constexpr (HIST) {
         nold = ctrl->old_count;
         const int ns = ctrl->new_slot;
@@ -985,17 +1021,18 @@ k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __
             Yo[t] = hist + (int64_t)(2 * s + 1) * slot_stride;
         }
     }
-    RowLoop rl(L, vg);
+    static_assert(!DENSE || CPL == 1, "packed row groups hold one unit per lane");
+    RowLoop rl(L, vg, DENSE);
     for (int64_t base = rl.first; base < p.n; base += rl.stride) {
         const int64_t i = base + rl.gw;
-        const bool act = i < p.n;
+        const bool act = rl.live && i < p.n;
         int knx = -1;                            // constraint of the next row, loaded one iteration ahead
         if (pf != 0) {
             // Prefetch the next row of this group into L2: the several dependent load
             // phases of that iteration (R..C D, the old G, each stored pair) then wait
             // on L2 instead of HBM.
             const int64_t nx = i + rl.stride;
-            if (nx < p.n) {
+            if (rl.live && nx < p.n) {
                 prefetch_row<TR, CPL>(R, nx, ld, L, Q, rl.lig);
                 prefetch_row<TR, CPL>(CR, nx, ld, L, Q, rl.lig);
                 if constexpr (STEP || HIST) prefetch_row<TDIR, CPL>(D, nx, ld, L, Q, rl.lig);
@@ -1006,8 +1043,8 @@ k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __
 #pragma unroll
                     for (int t = 0; t < kMaxMem - 1; ++t)
                         if (t < nold) {
-                            prefetch_row<TD, CPL>(So[t], nx, ld, L, Q, rl.lig);
-                            prefetch_row<TD, CPL>(Yo[t], nx, ld, L, Q, rl.lig);
+                            prefetch_row<TDIR, CPL>(So[t], nx, ld, L, Q, rl.lig);
+                            prefetch_row<TDIR, CPL>(Yo[t], nx, ld, L, Q, rl.lig);
                         }
                 }
                 if (p.dk != nullptr && rl.lig == 0) {
@@ -1045,7 +1082,8 @@ k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __
         // diagonal-constraint coefficient a_i y~_k of row i
         AR coef = AR(0);
         if (p.dk != nullptr) {
-            rr = group_sum(rr, L);
+            if constexpr (DENSE) rr = group_sum_packed(rr, L, rl.base_lane);
+            else rr = group_sum(rr, L);
             if (act) {
                 const int k = __ldg(p.dk + i);
                 if (k >= 0) {
@@ -1076,26 +1114,29 @@ k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __
                     }
                 }
             if constexpr (HIST) {
-                Unit<TD> gold[CPL], sn[CPL], yn[CPL];
+                // the new pair as stored (rounded to TDIR): the Gram dots below are those
+                // of the stored vectors, which the direction pass reads
+                Unit<TD> gold[CPL];
+                Unit<TDIR> sn[CPL], yn[CPL];
                 load_row_stream<TD, CPL>(gold, G, i, ld, L, Q, rl.lig);
 #pragma unroll
                 for (int c = 0; c < CPL; ++c)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        sn[c].v[e] = tau_d * AD(d[c].v[e]);
-                        yn[c].v[e] = AD(g[c].v[e]) - AD(gold[c].v[e]);
+                        sn[c].v[e] = as_stored<TDIR>(tau_d * AD(d[c].v[e]));
+                        yn[c].v[e] = as_stored<TDIR>(AD(g[c].v[e]) - AD(gold[c].v[e]));
                     }
-                store_row<TD, CPL>(sn, Snew, i, ld, L, Q, rl.lig);
-                store_row<TD, CPL>(yn, Ynew, i, ld, L, Q, rl.lig);
+                store_row<TDIR, CPL>(sn, Snew, i, ld, L, Q, rl.lig);
+                store_row<TDIR, CPL>(yn, Ynew, i, ld, L, Q, rl.lig);
                 accq[PU_GYN] += dot_units<AD>(g, yn);
                 accq[PU_SYN] += dot_units<AD>(sn, yn);
                 accq[PU_YYN] += dot_units<AD>(yn, yn);
 #pragma unroll
                 for (int t = 0; t < kMaxMem - 1; ++t) {
                     if (t < nold) {
-                        Unit<TD> so[CPL], yo[CPL];
-                        load_row_stream<TD, CPL>(so, So[t], i, ld, L, Q, rl.lig);
-                        load_row_stream<TD, CPL>(yo, Yo[t], i, ld, L, Q, rl.lig);
+                        Unit<TDIR> so[CPL], yo[CPL];
+                        load_row_stream<TDIR, CPL>(so, So[t], i, ld, L, Q, rl.lig);
+                        load_row_stream<TDIR, CPL>(yo, Yo[t], i, ld, L, Q, rl.lig);
                         PA* q = accq + PU_FIXED + PU_PER_OLD * t;
                         q[0] += dot_units<AD>(sn, yo);
                         q[1] += dot_units<AD>(so, yn);
@@ -1133,16 +1174,16 @@ constexpr int spmm_min_blocks() {
     return (std::is_same_v<TX, float> && std::is_same_v<TO, float>) ? (CPL == 1 ? 4 : 3) : 1;
 }
 
-template <typename TX, typename TO, typename TR, int CPL, int EPI>
+template <typename TX, typename TO, typename TR, int CPL, int EPI, bool DENSE = false, int PF = 0>
 __global__ void __launch_bounds__(kThreads, (spmm_min_blocks<TX, TO, CPL>()))
 k_spmm_c(ProbDev p, const TX* __restrict__ X, TO* __restrict__ out, int ld, int L, int Q,
          const double* __restrict__ v, int write_out,
          const TR* __restrict__ R, const double* __restrict__ y, const void* __restrict__ zrow_v,
          const dfloat* __restrict__ ydf, const Ctrl* ctrl, double rho_arg, double* __restrict__ part,
-         const Ctrl* gate, int ph, int pf) {
+         const Ctrl* gate, int ph) {
     if (gated_off(gate, ph)) return;
-    k_spmm_c_body<TX, TO, TR, CPL, EPI>(p, X, out, ld, L, Q, v, write_out, R, y, zrow_v, ydf, ctrl, rho_arg, part, hw_grid(),
-                                        pf);
+    k_spmm_c_body<TX, TO, TR, CPL, EPI, DENSE, PF>(p, X, out, ld, L, Q, v, write_out, R, y, zrow_v, ydf, ctrl, rho_arg,
+                                                   part, hw_grid());
 }
 
 template <typename TX, typename TO, int CPL, bool VDF>
@@ -1164,7 +1205,7 @@ k_cons(ProbDev p, int64_t k0, int64_t k1, const TU* __restrict__ U, const TV* __
 
 template <typename TD, typename TDIR = TD>
 __global__ void __launch_bounds__(kThreads)
-k_dir(int64_t nunits, const TD* __restrict__ G, TDIR* __restrict__ D, const TD* __restrict__ hist,
+k_dir(int64_t nunits, const TD* __restrict__ G, TDIR* __restrict__ D, const TDIR* __restrict__ hist,
       int64_t slot_stride, const Ctrl* ctrl, double* __restrict__ part, const Ctrl* gate, int ph) {
     if (gated_off(gate, ph)) return;
     k_dir_body<TD, TDIR>(nunits, G, D, hist, slot_stride, ctrl, part, hw_grid());
@@ -1182,7 +1223,7 @@ template <typename TR, typename TD, int CPL, bool STEP, bool HIST, typename TDIR
 __global__ void __launch_bounds__(kThreads, (update_min_blocks<TR, TD, CPL>()))
 k_update(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __restrict__ D,
          const TD* __restrict__ CD, TD* __restrict__ G, const TD* __restrict__ W,
-         TD* __restrict__ hist, int64_t slot_stride, int ld, int L, int Q,
+         TDIR* __restrict__ hist, int64_t slot_stride, int ld, int L, int Q,
          const double* __restrict__ y, const dfloat* __restrict__ ydf, void* __restrict__ zrow_v,
          const Ctrl* ctrl, double* __restrict__ part, const Ctrl* gate, int ph) {
     if (gated_off(gate, ph)) return;
@@ -1191,16 +1232,17 @@ k_update(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __restr
 
 // The step update with EXTRA more resident blocks per SM (fewer registers per
 // thread, some spilled to L1): more rows in flight for the latency-bound pass.
-template <typename TR, typename TD, int CPL, int EXTRA, typename TDIR = TD>
+// DENSE: packed row groups of L = Q lanes (RowLoop).
+template <typename TR, typename TD, int CPL, int EXTRA, typename TDIR = TD, bool DENSE = false>
 __global__ void __launch_bounds__(kThreads, (update_min_blocks<TR, TD, CPL>() + EXTRA))
 k_update_step_occ(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __restrict__ D,
                   const TD* __restrict__ CD, TD* __restrict__ G, const TD* __restrict__ W,
-                  TD* __restrict__ hist, int64_t slot_stride, int ld, int L, int Q,
+                  TDIR* __restrict__ hist, int64_t slot_stride, int ld, int L, int Q,
                   const double* __restrict__ y, const dfloat* __restrict__ ydf, void* __restrict__ zrow_v,
                   const Ctrl* ctrl, double* __restrict__ part, const Ctrl* gate, int ph, int pf) {
     if (gated_off(gate, ph)) return;
-    k_update_body<TR, TD, CPL, true, true, TDIR>(p, R, CR, D, CD, G, W, hist, slot_stride, ld, L, Q, y, ydf, zrow_v, ctrl,
-                                           part, hw_grid(), pf);
+    k_update_body<TR, TD, CPL, true, true, TDIR, DENSE>(p, R, CR, D, CD, G, W, hist, slot_stride, ld, L, Q, y, ydf,
+                                                         zrow_v, ctrl, part, hw_grid(), pf);
 }
 
 }  // namespace lorads

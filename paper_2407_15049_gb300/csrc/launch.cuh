@@ -17,21 +17,33 @@ namespace lorads {
         default: break;                                                 \
     }
 
+template <typename TX, typename TO, typename TR, int CPL, int EPI, bool DENSE, int PF>
+void launch_spmm_c_one(const SpmmCArgs& a, int L) {
+    k_spmm_c<TX, TO, TR, CPL, EPI, DENSE, PF><<<a.blocks, kThreads, 0, a.stream>>>(
+        a.p, static_cast<const TX*>(a.X), static_cast<TO*>(a.out), a.ld, L, a.sh.Q, a.v, a.write_out,
+        static_cast<const TR*>(a.R), a.y, a.zrow, a.ydf, a.ctrl, a.rho, a.part, a.gate, a.ph);
+}
+
+// The line-search form takes the prefetch depth (and packed groups) as template
+// arguments; the other epilogues run without prefetch.
 template <typename TX, typename TO, typename TR>
 void launch_spmm_c(const SpmmCArgs& a) {
-    const TX* X = static_cast<const TX*>(a.X);
-    TO* out = static_cast<TO*>(a.out);
-    const TR* R = static_cast<const TR*>(a.R);
+    if (a.epi == EPI_LS && a.dense && packed_rows_gain(a.sh)) {
+        if (a.prefetch == 2) launch_spmm_c_one<TX, TO, TR, 1, EPI_LS, true, 2>(a, a.sh.Q);
+        else if (a.prefetch == 1) launch_spmm_c_one<TX, TO, TR, 1, EPI_LS, true, 1>(a, a.sh.Q);
+        else launch_spmm_c_one<TX, TO, TR, 1, EPI_LS, true, 0>(a, a.sh.Q);
+        return;
+    }
     LORADS_CPL_SWITCH(a.sh.CPL, {
-        if (a.epi == EPI_LS)
-            k_spmm_c<TX, TO, TR, CPL, EPI_LS><<<a.blocks, kThreads, 0, a.stream>>>(
-                a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.write_out, R, a.y, a.zrow, a.ydf, a.ctrl, a.rho, a.part, a.gate, a.ph, a.prefetch);
-        else if (a.epi == EPI_OBJ)
-            k_spmm_c<TX, TO, TR, CPL, EPI_OBJ><<<a.blocks, kThreads, 0, a.stream>>>(
-                a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.write_out, R, a.y, a.zrow, a.ydf, a.ctrl, a.rho, a.part, a.gate, a.ph, a.prefetch);
-        else
-            k_spmm_c<TX, TO, TR, CPL, EPI_NONE><<<a.blocks, kThreads, 0, a.stream>>>(
-                a.p, X, out, a.ld, a.sh.L, a.sh.Q, a.v, a.write_out, R, a.y, a.zrow, a.ydf, a.ctrl, a.rho, a.part, a.gate, a.ph, a.prefetch);
+        if (a.epi == EPI_LS) {
+            if (a.prefetch == 2) launch_spmm_c_one<TX, TO, TR, CPL, EPI_LS, false, 2>(a, a.sh.L);
+            else if (a.prefetch == 1) launch_spmm_c_one<TX, TO, TR, CPL, EPI_LS, false, 1>(a, a.sh.L);
+            else launch_spmm_c_one<TX, TO, TR, CPL, EPI_LS, false, 0>(a, a.sh.L);
+        } else if (a.epi == EPI_OBJ) {
+            launch_spmm_c_one<TX, TO, TR, CPL, EPI_OBJ, false, 0>(a, a.sh.L);
+        } else {
+            launch_spmm_c_one<TX, TO, TR, CPL, EPI_NONE, false, 0>(a, a.sh.L);
+        }
     })
 }
 
@@ -89,7 +101,7 @@ void launch_cons(const ConsArgs& a) {
 template <typename TD, typename TDIR>
 void launch_dir(const DirArgs& a) {
     k_dir<TD, TDIR><<<a.blocks, kThreads, 0, a.stream>>>(
-        a.nunits, static_cast<const TD*>(a.G), static_cast<TDIR*>(a.D), static_cast<const TD*>(a.hist),
+        a.nunits, static_cast<const TD*>(a.G), static_cast<TDIR*>(a.D), static_cast<const TDIR*>(a.hist),
         a.slot_stride, a.ctrl, a.part, a.gate, a.ph);
 }
 
@@ -108,7 +120,13 @@ void launch_update(const UpdateArgs& a) {
     const TD* CD = static_cast<const TD*>(a.CD);
     TD* G = static_cast<TD*>(a.G);
     const TD* W = static_cast<const TD*>(a.W);
-    TD* H = static_cast<TD*>(a.hist);
+    TDIR* H = static_cast<TDIR*>(a.hist);          // pairs stored in the direction's type
+    if (a.step && a.hist_on && a.extra_blocks == 1 && a.dense && packed_rows_gain(a.sh)) {
+        k_update_step_occ<TR, TD, 1, 1, TDIR, true><<<a.blocks, kThreads, 0, a.stream>>>(
+            a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.Q, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate,
+            a.ph, a.prefetch);
+        return;
+    }
     LORADS_CPL_SWITCH(a.sh.CPL, {
         if (a.step && a.hist_on && a.extra_blocks == 1)
             k_update_step_occ<TR, TD, CPL, 1, TDIR><<<a.blocks, kThreads, 0, a.stream>>>(

@@ -18,6 +18,7 @@ struct SpmmCArgs {
     int blocks; const Ctrl* gate; int ph; cudaStream_t stream;
     int prefetch = 0;   // 1: carry the next row's bounds and prefetch its entries and row terms into L2;
                         // 2: also the bounds of the row after next and one neighbour row of the next row
+    int dense = 0;      // line-search epilogue: packed row groups of Q lanes (one unit per lane)
 };
 
 // v: double[m], or double-float[m] when v_df (weights then formed without FP64)
@@ -57,6 +58,7 @@ struct UpdateArgs {
     int blocks; const Ctrl* gate; int ph; cudaStream_t stream;
     int extra_blocks;   // step update: 0, or the variant with 1 or 2 more resident blocks per SM
     int prefetch = 0;   // step update with extra blocks: 1 = L2 prefetch of each group's next row
+    int dense = 0;      // step update with extra blocks: packed row groups of Q lanes (one unit per lane)
 };
 
 template <typename TX, typename TO, typename TR> void launch_spmm_c(const SpmmCArgs& a);

@@ -73,3 +73,21 @@ def test_default_run_fits_the_driver_limit():
     slow = bench.plan_seconds(20, 5, 2 * per, budget)
     assert slow["total_s"] <= bench.DRIVER_LIMIT_S, slow
     assert bench.plan_seconds(20, 5, 40.0, budget)["timed_steps"] == 20
+
+
+def test_scale_run_fits_and_refuses_without_memory(monkeypatch, capsys):
+    """The n = 1.7e8, r = 28 mixed solve at T = 2 fits a GB300's HBM with room for
+    the err2 vectors, and the scale leg prints an unavailable line, without
+    touching the GPU, when the host lacks the memory to build the instance."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench", ROOT / "bench.py")
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    cfg = bench.WORKLOADS["maxcut_er_1p7e8"]
+    need = bench.scale_device_bytes(cfg["n"], cfg["n"] + 2 * cfg["edges"], 28, cfg["lbfgs_mem"])
+    assert 2.4e11 < need < 2.8e11
+    monkeypatch.setattr(bench, "_host_available_gb", lambda: 1.0)
+    args = bench._args(["--workload", "maxcut_er_1p7e8"])
+    assert bench.run_scale(args) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert "unavailable" in line and "host memory" in line["unavailable"]

@@ -258,14 +258,19 @@ def test_prefetch_variants_are_bit_identical(prec):
     assert np.array_equal(Ra, Rc) and np.array_equal(ya, yc)
 
 
-@pytest.mark.parametrize("kv", [2 | 8 | 32])
-def test_kernel_variants_follow_oracle_trajectory(kv):
+@pytest.mark.parametrize("kv,r", [(2 | 8 | 32, 24), (2 | 8 | 128, 24), (2 | 8 | 128, 20), (2 | 8 | 128, 12),
+                                  (2 | 8 | 256, 24), (2 | 8 | 64 | 128 | 256, 20)])
+def test_kernel_variants_follow_oracle_trajectory(kv, r):
     """Narrow lane groups in the line-search SpMM (bit 5: another reduction order
-    of the epilogue sums): FP64 iterates after 5 steps equal the oracle's; in the
-    mixed form a capped solve stays within 1e-6 of the default."""
+    of the epilogue sums) and packed row groups in the step update and the
+    line-search SpMM (bits 7, 8: 5, 6 or 10 rows per warp at ld = 24, 20, 12;
+    another order of the row sums and partial sums; 60 000 rows are not a
+    multiple of the rows one grid pass takes): FP64
+    iterates after 5 steps equal the oracle's; in the mixed form a capped solve
+    stays within 1e-6 of the default."""
     n = 60_000
     inst = W.maxcut_instance(n, W.er_graph(n, 2 * n, 3, "pm1"))
-    R0 = W.initial_factor(inst, 24, 5)
+    R0 = W.initial_factor(inst, r, 5)
     caps = dict(max_outer=1, max_inner=5, tol=1e-300)
     ref = O.solve(O.Problem(inst), R0, O.Params(**caps))
     res, R, y = _gpu_solve(inst, R0, prec="fp64", kernel_variant=kv, **caps)
