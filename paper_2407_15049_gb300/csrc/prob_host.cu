@@ -1,11 +1,55 @@
 // Host-side validation and layout of one problem instance (see prob_host.h).
 #include <algorithm>
 #include <cmath>
+#include <thread>
 #include <utility>
 
 #include "prob_host.h"
 
 namespace lorads {
+
+namespace {
+
+// Symmetry of C: every stored (i, j, v) has a stored (j, i, v).  The lookups jump
+// across the whole column array (a cache miss each on large graphs), so the rows are
+// checked in contiguous ranges by several threads; each range reports its first
+// failure and the lowest failing row is returned (-1: symmetric), whatever the
+// thread count.
+int64_t first_asymmetric_row(int64_t n, const int64_t* rp, const int32_t* ci, const double* cv, int32_t* bad_col) {
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = std::max(1u, std::min(nt, 32u));
+    if (rp[n] < (int64_t(1) << 22)) nt = 1;
+    std::vector<int64_t> first(nt, -1);
+    std::vector<int32_t> col(nt, -1);
+    auto check = [&](unsigned t) {
+        const int64_t r0 = n * (int64_t)t / nt, r1 = n * (int64_t)(t + 1) / nt;
+        for (int64_t i = r0; i < r1; ++i) {
+            for (int64_t s = rp[i]; s < rp[i + 1]; ++s) {
+                const int32_t j = ci[s];
+                const int32_t* lo = ci + rp[j];
+                const int32_t* hi = ci + rp[j + 1];
+                const int32_t* f = std::lower_bound(lo, hi, (int32_t)i);
+                if (f == hi || *f != i || cv[f - ci] != cv[s]) {
+                    first[t] = i;
+                    col[t] = j;
+                    return;
+                }
+            }
+        }
+    };
+    std::vector<std::thread> pool;
+    for (unsigned t = 1; t < nt; ++t) pool.emplace_back(check, t);
+    check(0);
+    for (auto& th : pool) th.join();
+    for (unsigned t = 0; t < nt; ++t)
+        if (first[t] >= 0) {
+            *bad_col = col[t];
+            return first[t];
+        }
+    return -1;
+}
+
+}  // namespace
 
 lorads_status build_host_prob(HostProb* hp, std::string* err, int64_t n, const int64_t* rp, const int32_t* ci,
                               const double* cv, int64_t m, int64_t nnz_a, const int32_t* acon, const int32_t* arow,
@@ -33,16 +77,12 @@ lorads_status build_host_prob(HostProb* hp, std::string* err, int64_t n, const i
         }
     }
     // symmetry: (i, j, v) needs (j, i, v)
-    for (int64_t i = 0; i < n; ++i) {
-        for (int64_t s = rp[i]; s < rp[i + 1]; ++s) {
-            const int32_t j = ci[s];
-            const int32_t* lo = ci + rp[j];
-            const int32_t* hi = ci + rp[j + 1];
-            const int32_t* f = std::lower_bound(lo, hi, (int32_t)i);
-            if (f == hi || *f != i || cv[f - ci] != cv[s])
-                return set_err("C is not symmetric at (" + std::to_string(i) + "," + std::to_string(j) + ")"),
-                       LORADS_ERR_NOT_SYMMETRIC;
-        }
+    {
+        int32_t j = -1;
+        const int64_t i = first_asymmetric_row(n, rp, ci, cv, &j);
+        if (i >= 0)
+            return set_err("C is not symmetric at (" + std::to_string(i) + "," + std::to_string(j) + ")"),
+                   LORADS_ERR_NOT_SYMMETRIC;
     }
     hp->cnorm1 = sum_abs;
     hp->mean_abs_c = cnt_nz ? sum_abs / (double)cnt_nz : 1.0;

@@ -67,6 +67,25 @@ def test_rejects_asymmetric_C(lib):
     _expect("LORADS_ERR_NOT_SYMMETRIC", inst)
 
 
+def test_asymmetry_reports_the_lowest_row_on_a_large_C(lib):
+    """C large enough for the threaded symmetry check: with two broken entries in
+    different row ranges, the message names the lowest row that sees a mismatch
+    (a broken (i, j) is seen from row i and from row j), as a sequential scan would."""
+    n = 1_200_000
+    inst = W.maxcut_instance(n, W.er_graph(n, 2 * n, 9, "pm1"))
+    assert inst.nnz >= 1 << 22
+    inst.val = inst.val.copy()
+    seen = []
+    for row in (1_000_003, 400_001):
+        s = inst.rowptr[row]
+        if inst.colind[s] == row:
+            s += 1
+        inst.val[s] += 0.5
+        seen += [row, int(inst.colind[s])]
+    msg = _expect("LORADS_ERR_NOT_SYMMETRIC", inst)
+    assert f"at ({min(seen)}," in msg, msg
+
+
 def test_rejects_out_of_range_index(lib):
     inst = _maxcut()
     inst.colind = inst.colind.copy()
