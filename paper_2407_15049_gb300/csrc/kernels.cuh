@@ -1167,11 +1167,13 @@ k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __
 
 // Resident blocks per SM the SpMM over C is compiled for: for float rows 4 (64
 // registers, no spills) with one unit per lane and 3 (85 registers) with more,
-// where the pass is bound by the latency of its dependent loads; otherwise left
-// to the compiler.
+// for bf16 rows 3 (their conversions take more registers), where the pass is
+// bound by the latency of its dependent loads; otherwise left to the compiler.
 template <typename TX, typename TO, int CPL>
 constexpr int spmm_min_blocks() {
-    return (std::is_same_v<TX, float> && std::is_same_v<TO, float>) ? (CPL == 1 ? 4 : 3) : 1;
+    if constexpr (std::is_same_v<TX, float> && std::is_same_v<TO, float>) return CPL == 1 ? 4 : 3;
+    else if constexpr (std::is_same_v<TX, __nv_bfloat16> && std::is_same_v<TO, float>) return 3;
+    else return 1;
 }
 
 template <typename TX, typename TO, typename TR, int CPL, int EPI, bool DENSE = false, int PF = 0>
