@@ -121,7 +121,8 @@ typedef struct {
                                   Bits 3, 4 and 6 change no arithmetic, bit 5 only the order of the
                                   epilogue's sums, bits 7 and 8 the order of the row sums and of the
                                   partial sums.
-                                  Default 10 = bits 1 and 3. */
+                                  Default 394 = bits 1, 3, 7 and 8 (at n = 1e7, ld = 24: step update 4.09 ->
+                                  3.81 ms, line-search SpMM 2.58 -> 2.46 ms). */
     int32_t inner_scale;       /* inner stop ||G||_F <= thr, z = A(RR^T) - b, e = tol (1 + ||b||_inf):
                                   0: thr = inner_rel max(||z||, e);  1: thr = inner_rel max(rho ||z||, e);
                                   2 (default): thr = max(e, min(inner_rel rho ||z||, inner_progress ||G_0||)) */

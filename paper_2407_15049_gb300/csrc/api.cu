@@ -259,7 +259,7 @@ extern "C" void lorads_default_params(lorads_params* p) {
     p->lbfgs_scaling = 1;
     p->rho_policy = 2;
     p->inner_scale = 2;
-    p->kernel_variant = 10;
+    p->kernel_variant = 2 | 8 | 128 | 256;
     p->admm_switch = 0.0;
     p->cg_rel = 1e-2;
     p->cg_max = 50;
