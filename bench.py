@@ -293,14 +293,18 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str, prec: str):
-    """DRAM bytes of the committed ncu capture, if the kernels are unchanged and
-    the capture ran in the same precision form."""
+def ncu_traffic(kernel: str, prec: str, lbfgs_mem: int = 4, kernel_variant: int | None = None):
+    """DRAM bytes of the committed ncu capture, if the kernels are unchanged and the
+    capture ran the same precision form, number of stored pairs and kernel forms."""
     p = ROOT / "profiles" / "traffic.json"
     if not p.exists():
         return None
     d = json.loads(p.read_text())
     if d.get("source_hash") != kernel_source_hash() or d.get("prec", "mixed") != prec:
+        return None
+    if d.get("lbfgs_mem", 4) != lbfgs_mem:
+        return None
+    if kernel_variant is not None and d.get("kernel_variant") not in (None, kernel_variant):
         return None
     return d.get("kernels", {}).get(kernel)
 
@@ -672,7 +676,7 @@ def run_native(args):
     if hot:
         dom = max(hot, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["solve_launches"])
         ach = kernels[dom]["GBps"]
-        tr = ncu_traffic(dom, args.prec)
+        tr = ncu_traffic(dom, args.prec, args.lbfgs_mem, params.kernel_variant)
         roofline = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                     "frac": ach / peak, "peak_kind": peak_kind,
                     # DRAM bytes per unit from the committed capture, times this workload's units
