@@ -671,7 +671,8 @@ struct Driver {
         UpdateArgs u{p(), c->m_off == 0, true, st.R, st.CR, st.D, st.CD, st.G, c->m_off ? st.W : nullptr, st.hist,
                      st.slot_stride, st.ld, st.sh, st.y, st.ydf, st.zrow, c->ctrl, part_of(c, PART_UPD), nb_rows, c->ctrl, PH_STEP, s,
                      (c->prm.kernel_variant & 4) ? 2 : ((c->prm.kernel_variant & 2) ? 1 : 0),
-                     (c->prm.kernel_variant & 16) ? 1 : 0, (c->prm.kernel_variant & 128) ? 1 : 0};
+                     (c->prm.kernel_variant & 16) ? 1 : 0, (c->prm.kernel_variant & 128) ? 1 : 0,
+                     c->prm.lbfgs_mem - 1};
         timed(FAM_UPDATE, [&] { launch_update<TR, TD, TDIR>(u); });
         timed(FAM_HIST, [&] {
             ctrl_hist(s, c->ctrl, HIST_STEP, part_of(c, PART_UPD), nb_rows,

@@ -984,7 +984,11 @@ constexpr int update_min_blocks() {
     return (CPL == 1 && !std::is_same_v<arith_t<TR>, double>) ? 3 : 2;
 }
 
-template <typename TR, typename TD, int CPL, bool STEP, bool HIST, typename TDIR = TD, bool DENSE = false>
+// MAXOLD: most stored pairs besides the new one (T - 1 of Algorithm 1) the pass is
+// compiled for; the Gram accumulators of the others are compile-time zeros, which
+// frees their registers (T = 2: 8 partial sums instead of 14).
+template <typename TR, typename TD, int CPL, bool STEP, bool HIST, typename TDIR = TD, bool DENSE = false,
+          int MAXOLD = kMaxMem - 1>
 __device__ __forceinline__ void
 k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __restrict__ D,
          const TD* __restrict__ CD, TD* __restrict__ G, const TD* __restrict__ W,
@@ -1007,15 +1011,16 @@ k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __
     int nold = 0;
     TDIR* Snew = nullptr;                       // pairs stored in the direction's type
     TDIR* Ynew = nullptr;
-    const TDIR* So[kMaxMem - 1];
-    const TDIR* Yo[kMaxMem - 1];
+    static_assert(MAXOLD >= 1 && MAXOLD <= kMaxMem - 1, "stored pairs");
+    const TDIR* So[MAXOLD];
+    const TDIR* Yo[MAXOLD];
     if constexpr (HIST) {
         nold = ctrl->old_count;
         const int ns = ctrl->new_slot;
         Snew = hist + (int64_t)(2 * ns) * slot_stride;
         Ynew = hist + (int64_t)(2 * ns + 1) * slot_stride;
 #pragma unroll
-        for (int t = 0; t < kMaxMem - 1; ++t) {
+        for (int t = 0; t < MAXOLD; ++t) {
             const int s = ctrl->old_slots[t < nold ? t : 0];
             So[t] = hist + (int64_t)(2 * s) * slot_stride;
             Yo[t] = hist + (int64_t)(2 * s + 1) * slot_stride;
@@ -1041,7 +1046,7 @@ k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __
                 if constexpr (HIST) {
                     prefetch_row<TD, CPL>(G, nx, ld, L, Q, rl.lig);
 #pragma unroll
-                    for (int t = 0; t < kMaxMem - 1; ++t)
+                    for (int t = 0; t < MAXOLD; ++t)
                         if (t < nold) {
                             prefetch_row<TDIR, CPL>(So[t], nx, ld, L, Q, rl.lig);
                             prefetch_row<TDIR, CPL>(Yo[t], nx, ld, L, Q, rl.lig);
@@ -1132,7 +1137,7 @@ k_update_body(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __
                 accq[PU_SYN] += dot_units<AD>(sn, yn);
                 accq[PU_YYN] += dot_units<AD>(yn, yn);
 #pragma unroll
-                for (int t = 0; t < kMaxMem - 1; ++t) {
+                for (int t = 0; t < MAXOLD; ++t) {
                     if (t < nold) {
                         Unit<TDIR> so[CPL], yo[CPL];
                         load_row_stream<TDIR, CPL>(so, So[t], i, ld, L, Q, rl.lig);
@@ -1234,8 +1239,9 @@ k_update(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __restr
 
 // The step update with EXTRA more resident blocks per SM (fewer registers per
 // thread, some spilled to L1): more rows in flight for the latency-bound pass.
-// DENSE: packed row groups of L = Q lanes (RowLoop).
-template <typename TR, typename TD, int CPL, int EXTRA, typename TDIR = TD, bool DENSE = false>
+// DENSE: packed row groups of L = Q lanes (RowLoop).  MAXOLD: see k_update_body.
+template <typename TR, typename TD, int CPL, int EXTRA, typename TDIR = TD, bool DENSE = false,
+          int MAXOLD = kMaxMem - 1>
 __global__ void __launch_bounds__(kThreads, (update_min_blocks<TR, TD, CPL>() + EXTRA))
 k_update_step_occ(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR* __restrict__ D,
                   const TD* __restrict__ CD, TD* __restrict__ G, const TD* __restrict__ W,
@@ -1243,8 +1249,8 @@ k_update_step_occ(ProbDev p, TR* __restrict__ R, TR* __restrict__ CR, const TDIR
                   const double* __restrict__ y, const dfloat* __restrict__ ydf, void* __restrict__ zrow_v,
                   const Ctrl* ctrl, double* __restrict__ part, const Ctrl* gate, int ph, int pf) {
     if (gated_off(gate, ph)) return;
-    k_update_body<TR, TD, CPL, true, true, TDIR, DENSE>(p, R, CR, D, CD, G, W, hist, slot_stride, ld, L, Q, y, ydf,
-                                                         zrow_v, ctrl, part, hw_grid(), pf);
+    k_update_body<TR, TD, CPL, true, true, TDIR, DENSE, MAXOLD>(p, R, CR, D, CD, G, W, hist, slot_stride, ld, L, Q, y,
+                                                                 ydf, zrow_v, ctrl, part, hw_grid(), pf);
 }
 
 }  // namespace lorads

@@ -112,6 +112,28 @@ void launch_step(const StepArgs& a) {
         static_cast<const TD*>(a.CD), a.ctrl, a.gate, a.ph);
 }
 
+template <typename TR, typename TD, typename TDIR, int CPL, int EXTRA, bool DENSE, int MAXOLD>
+void launch_update_occ(const UpdateArgs& a, int L) {
+    k_update_step_occ<TR, TD, CPL, EXTRA, TDIR, DENSE, MAXOLD><<<a.blocks, kThreads, 0, a.stream>>>(
+        a.p, static_cast<TR*>(a.R), static_cast<TR*>(a.CR), static_cast<const TDIR*>(a.D),
+        static_cast<const TD*>(a.CD), static_cast<TD*>(a.G), static_cast<const TD*>(a.W), static_cast<TDIR*>(a.hist),
+        a.slot_stride, a.ld, L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph, a.prefetch);
+}
+
+// The step update with more resident blocks: one instantiation per lane shape and
+// per bound on the stored pairs (T <= 2, or up to 4).
+template <typename TR, typename TD, typename TDIR, int CPL, int EXTRA>
+void launch_update_occ_shape(const UpdateArgs& a) {
+    const bool dense = CPL == 1 && a.dense && packed_rows_gain(a.sh);
+    if (dense) {
+        if (a.max_old <= 1) launch_update_occ<TR, TD, TDIR, 1, EXTRA, true, 1>(a, a.sh.Q);
+        else launch_update_occ<TR, TD, TDIR, 1, EXTRA, true, kMaxMem - 1>(a, a.sh.Q);
+    } else {
+        if (a.max_old <= 1) launch_update_occ<TR, TD, TDIR, CPL, EXTRA, false, 1>(a, a.sh.L);
+        else launch_update_occ<TR, TD, TDIR, CPL, EXTRA, false, kMaxMem - 1>(a, a.sh.L);
+    }
+}
+
 template <typename TR, typename TD, typename TDIR>
 void launch_update(const UpdateArgs& a) {
     TR* R = static_cast<TR*>(a.R);
@@ -121,19 +143,11 @@ void launch_update(const UpdateArgs& a) {
     TD* G = static_cast<TD*>(a.G);
     const TD* W = static_cast<const TD*>(a.W);
     TDIR* H = static_cast<TDIR*>(a.hist);          // pairs stored in the direction's type
-    if (a.step && a.hist_on && a.extra_blocks == 1 && a.dense && packed_rows_gain(a.sh)) {
-        k_update_step_occ<TR, TD, 1, 1, TDIR, true><<<a.blocks, kThreads, 0, a.stream>>>(
-            a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.Q, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate,
-            a.ph, a.prefetch);
-        return;
-    }
     LORADS_CPL_SWITCH(a.sh.CPL, {
         if (a.step && a.hist_on && a.extra_blocks == 1)
-            k_update_step_occ<TR, TD, CPL, 1, TDIR><<<a.blocks, kThreads, 0, a.stream>>>(
-                a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph, a.prefetch);
+            launch_update_occ_shape<TR, TD, TDIR, CPL, 1>(a);
         else if (a.step && a.hist_on && a.extra_blocks == 2)
-            k_update_step_occ<TR, TD, CPL, 2, TDIR><<<a.blocks, kThreads, 0, a.stream>>>(
-                a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph, a.prefetch);
+            launch_update_occ_shape<TR, TD, TDIR, CPL, 2>(a);
         else if (a.step && a.hist_on)
             k_update<TR, TD, CPL, true, true, TDIR><<<a.blocks, kThreads, 0, a.stream>>>(
                 a.p, R, CR, D, CD, G, W, H, a.slot_stride, a.ld, a.sh.L, a.sh.Q, a.y, a.ydf, a.zrow, a.ctrl, a.part, a.gate, a.ph);

@@ -59,6 +59,7 @@ struct UpdateArgs {
     int extra_blocks;   // step update: 0, or the variant with 1 or 2 more resident blocks per SM
     int prefetch = 0;   // step update with extra blocks: 1 = L2 prefetch of each group's next row
     int dense = 0;      // step update with extra blocks: packed row groups of Q lanes (one unit per lane)
+    int max_old = 3;    // step update with extra blocks: stored pairs besides the new one (T - 1) at most
 };
 
 template <typename TX, typename TO, typename TR> void launch_spmm_c(const SpmmCArgs& a);

@@ -281,6 +281,23 @@ def test_kernel_variants_follow_oracle_trajectory(kv, r):
     assert np.max(np.abs(Rm - Rd)) <= 1e-6 * np.abs(Rd).max()
 
 
+@pytest.mark.parametrize("kv", [2 | 8 | 128 | 256, 4 | 8 | 128 | 256])
+@pytest.mark.parametrize("mem", [1, 2, 3])
+def test_short_memory_update_follows_oracle_trajectory(mem, kv):
+    """With T <= 2 the step update is compiled for one old pair (its other Gram
+    accumulators are compile-time zeros); with 4 or 5 resident blocks per SM
+    (bits 1 / 2): FP64 iterates after 30 steps (the memory fills and cycles) equal
+    the oracle's with the same T."""
+    n = 60_000
+    inst = W.maxcut_instance(n, W.er_graph(n, 2 * n, 3, "pm1"))
+    R0 = W.initial_factor(inst, 24, 5)
+    caps = dict(max_outer=1, max_inner=30, tol=1e-300, lbfgs_mem=mem)
+    ref = O.solve(O.Problem(inst), R0, O.Params(**caps))
+    res, R, y = _gpu_solve(inst, R0, prec="fp64", kernel_variant=kv, **caps)
+    assert res["inner_iters"] == ref["inner"]
+    assert np.max(np.abs(R - ref["R"])) <= 1e-8 * np.abs(ref["R"]).max()
+
+
 def test_prefetch_variant_follows_oracle_trajectory():
     """FP64 with both prefetch forms, several grid passes per kernel: the iterate
     after 5 L-BFGS steps equals the oracle's."""
