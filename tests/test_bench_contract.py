@@ -58,9 +58,9 @@ def _bench():
     return bench
 
 
-def test_default_run_fits_the_driver_limit():
-    """The driver runs `bench.py --gpus 1 --steps 20 --warmup 5` under an 1800 s
-    limit.  From the last measured solve time, the fixed legs, the capped warm-up
+def test_default_run_fits_the_time_limit():
+    """`bench.py --gpus 1 --steps 20 --warmup 5` must end within 1800 s.
+    From the last measured solve time, the fixed legs, the capped warm-up
     solves, the timed solves the budget admits and the e2e solve stay well inside
     it; and even a solve twice as slow cannot push the run past the limit, because
     the timed loop starts no solve that would end past its budget."""
@@ -68,10 +68,10 @@ def test_default_run_fits_the_driver_limit():
     per = bench.MEASURED_SOLVE_S["maxcut_er_1e7"]
     budget = bench.DEFAULT_TIME_BUDGET_S
     plan = bench.plan_seconds(20, 5, per, budget)
-    assert plan["fits_in_driver_run"], plan
+    assert plan["fits_in_limit"], plan
     assert plan["timed_steps"] >= 10
     slow = bench.plan_seconds(20, 5, 2 * per, budget)
-    assert slow["total_s"] <= bench.DRIVER_LIMIT_S, slow
+    assert slow["total_s"] <= bench.RUN_LIMIT_S, slow
     assert bench.plan_seconds(20, 5, 40.0, budget)["timed_steps"] == 20
 
 

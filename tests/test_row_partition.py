@@ -5,8 +5,8 @@ Each rank owns a contiguous row block of C and R, receives its halo rows of R
 from their owners through the plan's send/receive lists, multiplies its own
 rows of C by [own rows; halo rows] and must obtain exactly its rows of the FP64
 oracle's C R; the all-reduce of the per-rank partial <C R, R> must equal the
-oracle's objective.  Unmeasured on hardware: every box of this build has one
-GPU; this covers the host-side logic of the multi-GPU design.
+oracle's objective.  Unmeasured on hardware (the library runs on one GPU);
+this covers the host-side logic of the multi-GPU design.
 """
 import os
 import socket
