@@ -152,6 +152,9 @@ def _args(argv=None):
     ap.add_argument("--kernel-probe", type=int, default=0, metavar="ITERS",
                     help="print the CUDA-event time of every kernel family over the first ITERS L-BFGS iterations "
                          "of a host-stepped solve of the workload (twice) and exit: the target of ncu captures")
+    ap.add_argument("--l2-fetch-limit", type=int, default=0, metavar="BYTES",
+                    help="with --kernel-probe: set the context's L2 fetch granularity limit (a hint, 0-128 bytes; "
+                         "it lasts until the process exits) before timing, and report the limit in force")
     ap.add_argument("--spmm-vs-cusparse", type=int, default=0, metavar="N",
                     help="informational: time C D of the library's SpMM and of cuSPARSE (torch CSR @ dense) "
                          "on the ER graph with N vertices (degree 4, r = 24, FP32) and exit")
@@ -706,7 +709,7 @@ def run_native(args):
         "vs_baseline": None,
         "dtype": {"fp64": "f64", "mixed": "f32 (+double-float R, CR)", "df64": "double-float (2xf32)",
                   "fp32": "f32"}[args.prec],
-        "data": "synthetic", "config": _config(args),
+        "data": "synthetic", "config": {**_config(args), "l2_fetch_limit_bytes": l2_fetch_limit()},
         "e2e": {"value": e2e_mean, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "parts": e2e_parts, "start": "the first timed step's (seed 1), from pinned host memory"},
         "gpu_launches": int(launches),
@@ -972,6 +975,27 @@ def spmm_vs_cusparse(n: int) -> int:
     return 0
 
 
+def l2_fetch_limit(set_bytes: int = 0) -> int | None:
+    """The current context's L2 fetch granularity limit in bytes (the driver API's
+    CU_LIMIT_MAX_L2_FETCH_GRANULARITY), after setting it to set_bytes when that is
+    nonzero; None when the driver library cannot be queried."""
+    import ctypes
+    import torch
+    torch.zeros(1, device="cuda")                 # the primary context, current on this thread
+    torch.cuda.synchronize()
+    try:
+        cu = ctypes.CDLL("libcuda.so.1")
+    except OSError:
+        return None
+    limit_id = ctypes.c_int(5)                    # CU_LIMIT_MAX_L2_FETCH_GRANULARITY
+    if set_bytes:
+        rc = cu.cuCtxSetLimit(limit_id, ctypes.c_size_t(set_bytes))
+        if rc != 0:
+            raise RuntimeError(f"cuCtxSetLimit(L2 fetch granularity, {set_bytes}) failed: CUresult {rc}")
+    v = ctypes.c_size_t(0)
+    return int(v.value) if cu.cuCtxGetLimit(ctypes.byref(v), limit_id) == 0 else None
+
+
 def kernel_probe(args) -> int:
     """Per-kernel CUDA-event times of the first ITERS iterations of a host-stepped solve
     (the same kernels and decisions as the graph path), twice; one JSON line each."""
@@ -981,6 +1005,7 @@ def kernel_probe(args) -> int:
     code = {"fp64": L.LORADS_FP64, "mixed": L.LORADS_MIXED, "df64": L.LORADS_DF64, "fp32": L.LORADS_FP32}[args.prec]
     inst, R0, _ = build_instance(args.workload)
     R0d = torch.as_tensor(R0, device="cuda")
+    limit = l2_fetch_limit(args.l2_fetch_limit)
     for rep in range(2):
         ctx = L.lorads_create(inst, L.default_params(prec=code, verbose=2, max_outer=10**6, max_inner=args.kernel_probe,
                                                      rank_update_threshold=10**6, lbfgs_mem=args.lbfgs_mem))
@@ -988,7 +1013,7 @@ def kernel_probe(args) -> int:
         t = L.lorads_kernel_times(ctx)
         L.lorads_destroy(ctx)
         print(json.dumps({"workload": args.workload, "prec": args.prec, "lbfgs_mem": args.lbfgs_mem, "rep": rep,
-                          "iters": res["inner_iters"],
+                          "iters": res["inner_iters"], "l2_fetch_limit": limit,
                           "kernels_ms": {k: v[0] for k, v in t.items()}}), flush=True)
     return 0
 
