@@ -312,6 +312,16 @@ def ncu_traffic(kernel: str, prec: str, lbfgs_mem: int = 4, kernel_variant: int 
     return d.get("kernels", {}).get(kernel)
 
 
+def dram_rate(traffic_rec, n: int, ld: int, avg_ms: float):
+    """DRAM bytes of one launch at this workload (the committed capture's bytes per
+    element of the n x ld factor, times n * ld) and the rate in GB/s at which a launch
+    of avg_ms moves them; (None, None) without a usable record."""
+    if not traffic_rec or not traffic_rec.get("measured_units") or not avg_ms or avg_ms <= 0:
+        return None, None
+    b = traffic_rec["dram_bytes_measured"] / traffic_rec["measured_units"] * n * ld
+    return b, b / (avg_ms * 1e-3) / 1e9
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 
 def host_cpu() -> str:
@@ -680,18 +690,24 @@ def run_native(args):
         dom = max(hot, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["solve_launches"])
         ach = kernels[dom]["GBps"]
         tr = ncu_traffic(dom, args.prec, args.lbfgs_mem, params.kernel_variant)
+        # DRAM bytes per unit from the committed capture, times this workload's units
+        # (the streaming passes move every operand once: traffic grows with n * ld)
+        traffic, dram_gbps = dram_rate(tr, cfg["n"], ld, kernels[dom]["avg_ms"])
         roofline = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                    "frac": ach / peak, "peak_kind": peak_kind,
-                    # DRAM bytes per unit from the committed capture, times this workload's units
-                    # (the streaming passes move every operand once: traffic grows with n * ld)
-                    "traffic": (None if tr is None or not tr.get("measured_units")
-                                else tr["dram_bytes_measured"] / tr["measured_units"] * cfg["n"] * ld),
+                    "frac": ach / peak, "peak_kind": peak_kind, "frac_of_8TBps": ach / 8000.0,
+                    "traffic": traffic, "dram_GBps": dram_gbps,
                     "algorithmic_bytes_per_launch": kernels[dom]["algorithmic_bytes"],
                     "avg_launch_ms": kernels[dom]["avg_ms"]}
         spmm = kernels.get("k_spmm_c(CD,ls)")
         if spmm:
+            # the neighbour gathers read each row of D once per stored entry: DRAM bytes
+            # (lower bound when scaled from the smaller capture) above the algorithmic ones
+            s_tr, s_gbps = dram_rate(ncu_traffic("k_spmm_c(CD,ls)", args.prec, args.lbfgs_mem, params.kernel_variant),
+                                     cfg["n"], ld, spmm["avg_ms"])
             roofline["spmm"] = {"achieved": spmm["GBps"], "frac": spmm["GBps"] / peak,
-                                "frac_of_8TBps": spmm["GBps"] / 8000.0, "avg_launch_ms": spmm["avg_ms"]}
+                                "frac_of_8TBps": spmm["GBps"] / 8000.0, "avg_launch_ms": spmm["avg_ms"],
+                                "traffic": s_tr, "dram_GBps": s_gbps,
+                                "dram_frac": None if s_gbps is None else s_gbps / peak}
     iters_mean = statistics.mean(r["inner_iters"] for r in timed)
     cpu = None
     if not args.no_cpu_baseline:

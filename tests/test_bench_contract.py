@@ -91,3 +91,23 @@ def test_scale_run_fits_and_refuses_without_memory(monkeypatch, capsys):
     assert bench.run_scale(args) == 0
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert "unavailable" in line and "host memory" in line["unavailable"]
+
+
+def test_dram_rate_scales_the_committed_capture():
+    """The bench line's DRAM figures: the capture's bytes per element of the n x ld
+    factor times this workload's elements, over the launch time; no figure without a
+    record.  The committed record at HEAD matches the kernel sources (its hash) and
+    gives the step update DRAM bytes within 1% of its algorithmic bytes."""
+    bench = _bench()
+    rec = {"dram_bytes_measured": 6.0e9, "measured_units": 96_000_000}
+    b, gbps = bench.dram_rate(rec, 10_000_000, 24, 3.0)
+    assert b == 6.0e9 / 96_000_000 * 240_000_000 == 15.0e9
+    assert gbps == 15.0e9 / 3.0e-3 / 1e9 == 5000.0
+    assert bench.dram_rate(None, 10, 4, 1.0) == (None, None)
+    assert bench.dram_rate({"dram_bytes_measured": 1.0}, 10, 4, 1.0) == (None, None)
+    assert bench.dram_rate(rec, 10, 4, 0.0) == (None, None)
+    tr = bench.ncu_traffic("k_update(step)", "mixed", 2, 394)
+    assert tr is not None, "profiles/traffic.json does not match the kernel sources"
+    alg = bench.kernel_bytes("k_update(step)", 4_000_000, 24, 20_000_000, 4_000_000, 8, 4, 2)
+    assert abs(tr["dram_bytes_measured"] / alg - 1.0) < 0.01
+    assert bench.ncu_traffic("k_spmm_c(CD,ls)", "mixed", 2, 394) is not None
