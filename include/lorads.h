@@ -308,10 +308,11 @@ int32_t lorads_kernel_counts(const lorads_ctx* ctx, const char** names, int64_t*
 
 /* Exact line-search coefficients for callers that cannot allocate device memory.
  * The paper has no counterpart: this is a deployment variant of
- * lorads_linesearch_coeffs (FP64) that needs no context.  It is meant for code that
- * must not call cudaMalloc where it needs the step -- work recorded while a stream is
- * captured into a CUDA graph, frameworks whose allocator owns all device memory, or
- * latency-critical loops that cannot take cudaMalloc's implicit synchronisation.
+ * lorads_linesearch_coeffs (FP64) that needs no context and allocates nothing.  It is
+ * for callers that cannot call cudaMalloc where they need the step: frameworks whose
+ * caching allocator owns the device memory (an allocation outside it can fail or
+ * fragment what the framework holds), and latency-critical loops that cannot take the
+ * device-wide synchronisation cudaMalloc and cudaFree may imply.
  *   n, c_rowptr[n+1] (int64), c_colind, c_val   C as full symmetric CSR, device.
  *   m, a_con, a_row, a_col, a_val (m triplets, one per constraint, row <= col), b[m]:
  *                     device; a_con is the constraint index of each triplet.
@@ -329,9 +330,9 @@ int32_t lorads_kernel_counts(const lorads_ctx* ctx, const char** names, int64_t*
  * caller; nothing needs clearing between calls.  The first call on each device looks
  * up the array's device address (cudaGetSymbolAddress, with that device current) and
  * caches it per device ordinal; make that first call before starting any stream
- * capture.  The library's kernels load on their first launch, one variant per row
- * width: a caller that captures the call should make one call with each ld it will use
- * beforehand.  After cudaDeviceReset on a device the cached address is stale: do not
+ * capture.  The kernels it launches are loaded on their first launch, one variant per
+ * row width, so the first call with each ld takes longer than the calls after it.
+ * After cudaDeviceReset on a device the cached address is stale: do not
  * call this entry point on that device again in the same process.  Sizes beyond the
  * limits above return LORADS_ERR_INVALID_ARG; the message is in lorads_noalloc_error().
  * Calls no allocation routine. */

@@ -2,14 +2,14 @@
 // a context and without any device allocation.
 //
 // Some callers cannot allocate device memory at the point where they need the
-// step: code that runs while a stream is being captured into a CUDA graph,
-// frameworks whose allocator owns all device memory, or latency-critical loops
-// that cannot afford the implicit synchronisation of cudaMalloc.  This entry
-// point takes every input as caller-owned device memory and keeps its only
-// scratch (the per-block partial sums of its two reductions) in one
-// file-scope device array of fixed size: 2 x 1024 blocks x 7 doubles, 114,688
-// bytes.  Launch grids are capped at 1024 blocks, so the scratch never grows
-// with the problem.
+// step: frameworks whose caching allocator owns the device memory (a cudaMalloc
+// beside it can fail or fragment what the framework holds), and latency-critical
+// loops that cannot afford the device-wide synchronisation cudaMalloc and
+// cudaFree may imply.  This entry point takes every input as caller-owned device
+// memory and keeps its only scratch (the per-block partial sums of its two
+// reductions) in one file-scope device array of fixed size: 2 x 1024 blocks x 7
+// doubles, 114,688 bytes.  Launch grids are capped at 1024 blocks, so the
+// scratch never grows with the problem.
 //
 // That array is a single region shared by every call on a device: calls that
 // overlap on the GPU (different streams or threads without ordering) race on

@@ -1,6 +1,7 @@
 """lorads_linesearch_coeffs_noalloc: the context-free line-search entry point for
-callers that cannot allocate device memory (graph capture, foreign allocators,
-latency-critical loops).  Its scratch is a fixed device array inside the
+callers that cannot allocate device memory (a framework's caching allocator
+owns it, or a latency-critical loop cannot take cudaMalloc's synchronisation).
+Its scratch is a fixed device array inside the
 library, so the test checks it against the context entry point and against
 the FP64 oracle's coefficients of App. A.2 on two calls in a row (the second
 sees the first call's leftovers in that array), on small instances and on one
