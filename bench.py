@@ -873,7 +873,8 @@ def run_batch(args):
     barrier()
     t = time.perf_counter()
     b2 = L.lorads_batch_create(B, params)
-    L.lorads_batch_set_shape(b2, shape["ctas_per_sm"], shape["rows_per_warp"], shape["order"], shape["threads"])
+    L.lorads_batch_set_shape(b2, shape["ctas_per_sm"], shape["rows_per_warp"], shape["order"], shape["threads"],
+                             shape["cluster"], shape["team_count"])
     res2, st2 = L.lorads_batch_solve(b2, count)
     d2h = 0
     for i, inst in enumerate(B):
