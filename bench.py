@@ -155,6 +155,9 @@ def _args(argv=None):
     ap.add_argument("--l2-fetch-limit", type=int, default=0, metavar="BYTES",
                     help="with --kernel-probe: set the context's L2 fetch granularity limit (a hint, 0-128 bytes; "
                          "it lasts until the process exits) before timing, and report the limit in force")
+    ap.add_argument("--gather-locality", type=int, default=0, metavar="N",
+                    help="informational, CPU only: L2 reuse of the SpMM's neighbour gathers on the ER graph with "
+                         "N vertices, natural vs reverse Cuthill-McKee order, and exit")
     ap.add_argument("--spmm-vs-cusparse", type=int, default=0, metavar="N",
                     help="informational: time C D of the library's SpMM and of cuSPARSE (torch CSR @ dense) "
                          "on the ER graph with N vertices (degree 4, r = 24, FP32) and exit")
@@ -944,6 +947,61 @@ def run_batch(args):
     return 0
 
 
+def gather_reuse(indptr, indices, windows, row_bytes: int = 96, chunk: int = 64) -> dict:
+    """Fraction of the SpMM's neighbour-row fetches that an L2 holding the last W
+    processed rows' traffic could serve: rows are processed in index order (time =
+    row), each stored entry (i, j) fetches the `chunk`-byte pieces of row j of the
+    gathered operand (row_bytes each), and a fetch counts as reused when the same
+    piece was fetched at most W rows earlier.  Returns {W: fraction} and the number
+    of fetches."""
+    import numpy as np
+    indptr = np.asarray(indptr, dtype=np.int64)
+    col = np.asarray(indices, dtype=np.int64)
+    t = np.repeat(np.arange(len(indptr) - 1, dtype=np.int64), np.diff(indptr))
+    first = col * row_bytes // chunk
+    last = (col * row_bytes + row_bytes - 1) // chunk
+    span = last - first
+    pieces, times = [first], [t]
+    for k in range(1, int(span.max(initial=0)) + 1):
+        sel = span >= k
+        pieces.append(first[sel] + k)
+        times.append(t[sel])
+    pc, tm = np.concatenate(pieces), np.concatenate(times)
+    order = np.lexsort((tm, pc))
+    pc, tm = pc[order], tm[order]
+    same = np.r_[False, pc[1:] == pc[:-1]]
+    gap = np.r_[np.inf, (tm[1:] - tm[:-1]).astype(float)]
+    gap[~same] = np.inf
+    return {"reuse": {int(w): float(np.mean(gap <= w)) for w in windows}, "fetches": int(len(pc))}
+
+
+def gather_locality(n: int) -> int:
+    """Informational (CPU only): how much a one-time vertex relabelling would let L2
+    serve the line-search SpMM's neighbour gathers on the benchmark's graph family
+    (Erdos-Renyi, average degree 4): reuse fractions of gather_reuse for the natural
+    order and for reverse Cuthill-McKee (scipy), D rows of 96 bytes (ld 24, FP32),
+    64-byte fetches."""
+    import numpy as np
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import reverse_cuthill_mckee
+    import workloads as W
+    i, j, _ = W.er_graph(n, 2 * n, 0, "pm1")
+    A = sp.coo_matrix((np.ones(len(i)), (i, j)), shape=(n, n))
+    A = (A + A.T).tocsr()
+    windows = [20_000, 50_000, 100_000, 200_000]
+    out = {}
+    for name in ("natural", "rcm"):
+        t = time.perf_counter()
+        B = A
+        if name == "rcm":
+            perm = reverse_cuthill_mckee(A, symmetric_mode=True)
+            B = A[perm][:, perm].tocsr()
+        out[name] = {**gather_reuse(B.indptr, B.indices, windows), "seconds": time.perf_counter() - t}
+    print(json.dumps({"analysis": "gather_locality", "n": n, "edges": 2 * n, "row_bytes": 96, "fetch_bytes": 64,
+                      "window_unit": "rows processed", **out}), flush=True)
+    return 0
+
+
 def spmm_vs_cusparse(n: int) -> int:
     """C D with the library's SpMM entry point and with cuSPARSE (torch's CSR
     matmul) on the same CSR and D: CUDA events over 20 calls after 3, outputs
@@ -1154,6 +1212,8 @@ def main():
         return run_scale(args)
     if args.spmm_vs_cusparse:
         return spmm_vs_cusparse(args.spmm_vs_cusparse)
+    if args.gather_locality:
+        return gather_locality(args.gather_locality)
     if args.workload in BATCH_WORKLOADS:
         return run_batch(args)
     if args.impl == "reference":

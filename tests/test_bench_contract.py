@@ -111,3 +111,23 @@ def test_dram_rate_scales_the_committed_capture():
     alg = bench.kernel_bytes("k_update(step)", 4_000_000, 24, 20_000_000, 4_000_000, 8, 4, 2)
     assert abs(tr["dram_bytes_measured"] / alg - 1.0) < 0.01
     assert bench.ncu_traffic("k_spmm_c(CD,ls)", "mixed", 2, 394) is not None
+
+
+def test_gather_reuse_on_a_path():
+    """Path 0-1-2-3 with one 64-byte piece per row: the fetches are row 1 at time 0,
+    rows 0 and 2 at time 1, rows 1 and 3 at time 2, row 2 at time 3; rows 1 and 2 are
+    fetched again two rows later, so 2 of 6 fetches are reused within a window of 2
+    and none within 1.  With 96-byte rows each row spans two 64-byte pieces and
+    neighbouring rows share one."""
+    bench = _bench()
+    indptr, indices = [0, 1, 3, 5, 6], [1, 0, 2, 1, 3, 2]
+    r = bench.gather_reuse(indptr, indices, [1, 2], row_bytes=64, chunk=64)
+    assert r["fetches"] == 6
+    assert r["reuse"] == {1: 0.0, 2: 2 / 6}
+    r96 = bench.gather_reuse(indptr, indices, [1, 2, 3], row_bytes=96, chunk=64)
+    assert r96["fetches"] == 12
+    # pieces: row0 {0,1}, row1 {1,2}, row2 {3,4}, row3 {4,5}; times: row1@0, row0@1,
+    # row2@1, row1@2, row3@2, row2@3.  Piece 1 at 0,1,2; piece 2 at 0,2; piece 3 at
+    # 1,3; piece 4 at 1,2,3; pieces 0 and 5 once -> gaps 1,1 | 2 | 2 | 1,1: 4 within
+    # 1, 6 within 2.
+    assert r96["reuse"] == {1: 4 / 12, 2: 6 / 12, 3: 6 / 12}
