@@ -15,11 +15,15 @@
  * and the multiplier step of Sec. 2.1 is y <- y~.  The error measures of
  * Sec. 4.2 (err1, err2, err3) are written with the dual slack C - A*(y).
  *
- * Constraint convention (single-entry constraints).  Constraint k is one
- * triplet (i <= j, a):  <A_k, X> = a X_ii  (i == j)  or  2 a X_ij  (i < j).
- * This covers the MaxCut SDP of Sec. 4.3 (X_ii = 1) and the matrix-completion
- * SDP of Sec. 4.4.  Constraints with several triplets (general SDPs, Sec. 4.5)
- * are rejected with LORADS_ERR_UNSUPPORTED.
+ * Constraint convention (SDPA-style triplets).  Constraint k is the sum of
+ * its triplets (i <= j, a), each contributing a X_ii (i == j) or 2 a X_ij
+ * (i < j) to <A_k, X>.  One triplet per constraint covers the MaxCut SDP of
+ * Sec. 4.3 (X_ii = 1) and the matrix-completion SDP of Sec. 4.4.  Constraints
+ * with several triplets, and several constraints on one entry (the general
+ * sparse SDPs of Sec. 4.5), are accepted by lorads_create and every
+ * single-instance entry point except lorads_admm_operator, which returns
+ * LORADS_ERR_UNSUPPORTED for them; the batched solve and
+ * lorads_linesearch_coeffs_noalloc take one triplet per constraint.
  *
  * Layout.  Every n x r factor (R, D, U, V, outputs) is row-major with a
  * leading dimension `ld` (elements): element (i, c) lives at p[i*ld + c].
@@ -80,7 +84,15 @@ typedef enum {
 
 /* Solver constants.  The paper fixes tol (Sec. 4.2), the time limit (Sec. 4.2)
  * and the rank rule (App. A.1); the remaining values are this library's
- * readings of what the paper leaves open. */
+ * readings of what the paper leaves open.  lorads_create and lorads_batch_create
+ * refuse (LORADS_ERR_INVALID_ARG, message naming the field): tol not finite and
+ * > 0; time_limit not > 0; lbfgs_mem outside [1, 4]; max_inner, max_outer,
+ * rank_update_threshold or lanczos_steps below 1; rho0 not finite; rho_growth
+ * not finite and >= 1; rho_max not > 0; infeas_decrease not finite and >= 0;
+ * inner_rel or inner_progress not finite and > 0; lbfgs_scaling outside {0, 1};
+ * rho_policy or inner_scale outside {0, 1, 2}; admm_switch < 0; cg_rel outside
+ * (0, 1); cg_max < 1; admm_max_iter < 0; reopt_level outside [0, 2];
+ * max_reopt < 0; reopt_factor outside (0, 1). */
 typedef struct {
     double  tol;               /* 1e-5: err1 (1+||b||_inf normalisation) and |err3| */
     double  time_limit;        /* seconds, 1e4 */
@@ -172,10 +184,11 @@ void lorads_default_params(lorads_params* p);
  *                              distinct within each row, values finite; C must equal C^T.
  *   m                          number of constraints (>= 1)
  *   nnz_a, a_con, a_row, a_col, a_val          constraint triplets, host; a_con in [0,m),
- *                              a_row <= a_col < n, exactly one triplet per constraint and
- *                              at most one constraint per entry (i, j).
+ *                              a_row <= a_col < n, every constraint at least one triplet,
+ *                              no entry (i, j) twice in one constraint.
  *   b[m]                       right-hand side, host.
- *   p                          parameters (NULL = defaults), copied.
+ *   p                          parameters (NULL = defaults), copied; a value outside the
+ *                              ranges listed with lorads_params is refused (INVALID_ARG).
  *   cuda_stream                cudaStream_t the context uses (NULL = default stream).
  * On success *out receives a new context (free with lorads_destroy).  On failure *out
  * is NULL and the status says why (INVALID_ARG, NOT_SYMMETRIC, UNSUPPORTED, OOM, CUDA). */

@@ -414,20 +414,13 @@ extern "C" lorads_status lorads_create(lorads_ctx** out, int64_t n, const int64_
     }
     lorads_default_params(&ctx->prm);
     if (p) ctx->prm = *p;
-    if (ctx->prm.lbfgs_mem < 1 || ctx->prm.lbfgs_mem > kMaxMem) {
-        g_create_error = "lbfgs_mem must be in [1, 4]";
+    const std::string perr = solver_params_error(ctx->prm);
+    if (!perr.empty()) {
+        g_create_error = perr;
         delete ctx;
         return LORADS_ERR_INVALID_ARG;
     }
     if (ctx->prm.check_every < 1) ctx->prm.check_every = 1;
-    if (!(ctx->prm.admm_switch >= 0.0) || !(ctx->prm.cg_rel > 0.0 && ctx->prm.cg_rel < 1.0) ||
-        ctx->prm.cg_max < 1 || ctx->prm.admm_max_iter < 0 || ctx->prm.reopt_level < 0 || ctx->prm.reopt_level > 2 ||
-        ctx->prm.max_reopt < 0 || !(ctx->prm.reopt_factor > 0.0 && ctx->prm.reopt_factor < 1.0)) {
-        g_create_error = "need admm_switch >= 0, 0 < cg_rel < 1, cg_max >= 1, admm_max_iter >= 0, reopt_level in "
-                         "[0, 2], max_reopt >= 0 and 0 < reopt_factor < 1";
-        delete ctx;
-        return LORADS_ERR_INVALID_ARG;
-    }
     ctx->stream = static_cast<cudaStream_t>(cuda_stream);
     lorads_status s = validate_and_build(ctx, n, c_rowptr, c_colind, c_val, m, nnz_a, a_con, a_row, a_col, a_val, b);
     if (s == LORADS_OK) s = dalloc(ctx, &ctx->part, (size_t)NPART * ctx->max_blocks * kPartStride);

@@ -351,8 +351,10 @@ extern "C" lorads_status lorads_batch_create(lorads_batch** out, int32_t count, 
     else lorads_default_params(&P);
     if (P.prec != LORADS_FP64 && P.prec != LORADS_MIXED && P.prec != LORADS_FP32)
         return fail(LORADS_ERR_INVALID_ARG, "batch prec must be LORADS_FP64, LORADS_MIXED or LORADS_FP32");
-    if (P.lbfgs_mem < 1 || P.lbfgs_mem > kMaxMem || P.max_inner < 1 || P.max_outer < 1 || !(P.tol > 0))
-        return fail(LORADS_ERR_INVALID_ARG, "lbfgs_mem must be in [1,4], max_inner/max_outer >= 1, tol > 0");
+    {
+        const std::string perr = solver_params_error(P);
+        if (!perr.empty()) return fail(LORADS_ERR_INVALID_ARG, perr);
+    }
     const size_t esR = P.prec == LORADS_FP64 ? 8 : (P.prec == LORADS_MIXED ? 8 : 4);
     const size_t esD = P.prec == LORADS_FP64 ? 8 : 4;
     const bool fp64 = P.prec == LORADS_FP64;

@@ -4,6 +4,7 @@
 #include <thread>
 #include <utility>
 
+#include "common.cuh"
 #include "prob_host.h"
 
 namespace lorads {
@@ -273,6 +274,30 @@ lorads_status build_host_prob(HostProb* hp, std::string* err, int64_t n, const i
     hp->a_adf.resize(hp->a_a.size());
     for (size_t q = 0; q < hp->a_a.size(); ++q) hp->a_adf[q] = split(hp->a_a[q]);
     return LORADS_OK;
+}
+
+std::string solver_params_error(const lorads_params& p) {
+    auto finite = [](double v) { return std::isfinite(v); };
+    if (p.lbfgs_mem < 1 || p.lbfgs_mem > kMaxMem) return "lbfgs_mem must be in [1, 4]";
+    if (!(p.tol > 0.0) || !finite(p.tol)) return "tol must be finite and > 0";
+    if (!(p.time_limit > 0.0)) return "time_limit must be > 0";
+    if (p.max_inner < 1 || p.max_outer < 1) return "max_inner and max_outer must be >= 1";
+    if (p.rank_update_threshold < 1) return "rank_update_threshold must be >= 1";
+    if (!finite(p.rho0)) return "rho0 must be finite (<= 0 selects the automatic value)";
+    if (!(p.rho_growth >= 1.0) || !finite(p.rho_growth)) return "rho_growth must be finite and >= 1";
+    if (!(p.rho_max > 0.0)) return "rho_max must be > 0";
+    if (!(p.infeas_decrease >= 0.0) || !finite(p.infeas_decrease)) return "infeas_decrease must be finite and >= 0";
+    if (!(p.inner_rel > 0.0) || !finite(p.inner_rel) || !(p.inner_progress > 0.0) || !finite(p.inner_progress))
+        return "inner_rel and inner_progress must be finite and > 0";
+    if (p.lanczos_steps < 1) return "lanczos_steps must be >= 1";
+    if (p.lbfgs_scaling < 0 || p.lbfgs_scaling > 1) return "lbfgs_scaling must be 0 or 1";
+    if (p.rho_policy < 0 || p.rho_policy > 2) return "rho_policy must be 0, 1 or 2";
+    if (p.inner_scale < 0 || p.inner_scale > 2) return "inner_scale must be 0, 1 or 2";
+    if (!(p.admm_switch >= 0.0) || !(p.cg_rel > 0.0 && p.cg_rel < 1.0) || p.cg_max < 1 || p.admm_max_iter < 0)
+        return "need admm_switch >= 0, 0 < cg_rel < 1, cg_max >= 1 and admm_max_iter >= 0";
+    if (p.reopt_level < 0 || p.reopt_level > 2 || p.max_reopt < 0 || !(p.reopt_factor > 0.0 && p.reopt_factor < 1.0))
+        return "need reopt_level in [0, 2], max_reopt >= 0 and 0 < reopt_factor < 1";
+    return std::string();
 }
 
 }  // namespace lorads

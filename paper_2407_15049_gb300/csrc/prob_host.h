@@ -50,4 +50,8 @@ lorads_status build_host_prob(HostProb* hp, std::string* err, int64_t n, const i
                               const double* cv, int64_t m, int64_t nnz_a, const int32_t* acon, const int32_t* arow,
                               const int32_t* acol, const double* aval, const double* b);
 
+// Checks the solver constants of `p` against their documented ranges.  Returns an
+// empty string when every value is usable, else a message naming the first bad one.
+std::string solver_params_error(const lorads_params& p);
+
 }  // namespace lorads

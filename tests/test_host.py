@@ -164,6 +164,26 @@ def test_rejects_bad_lbfgs_memory(lib):
     _expect("LORADS_ERR_INVALID_ARG", _maxcut(), params=N.default_params(lbfgs_mem=9))
 
 
+@pytest.mark.parametrize("field,value,word", [
+    ("tol", float("nan"), "tol"), ("tol", 0.0, "tol"), ("time_limit", 0.0, "time_limit"),
+    ("max_inner", 0, "max_inner"), ("max_outer", 0, "max_outer"),
+    ("rank_update_threshold", 0, "rank_update_threshold"), ("rho0", float("inf"), "rho0"),
+    ("rho_growth", 0.5, "rho_growth"), ("rho_max", float("nan"), "rho_max"),
+    ("infeas_decrease", -0.1, "infeas_decrease"), ("inner_rel", 0.0, "inner_rel"),
+    ("inner_progress", float("inf"), "inner_progress"), ("lanczos_steps", 0, "lanczos_steps"),
+    ("lbfgs_scaling", 2, "lbfgs_scaling"), ("rho_policy", 3, "rho_policy"), ("inner_scale", -1, "inner_scale"),
+    ("cg_rel", 1.0, "cg_rel"), ("reopt_factor", 1.0, "reopt_factor"),
+])
+def test_rejects_solver_constants_out_of_range(lib, field, value, word):
+    """Each solver constant outside its documented range is refused by lorads_create
+    and by lorads_batch_create, with a message that names it; the defaults and the
+    values the tests and the bench use pass."""
+    msg = _expect("LORADS_ERR_INVALID_ARG", _maxcut(), params=N.default_params(**{field: value}))
+    assert word in msg, msg
+    msg = _expect_batch("LORADS_ERR_INVALID_ARG", [_maxcut()], params=N.default_params(**{field: value}))
+    assert word in msg, msg
+
+
 def _expect_batch(status_name, insts, **kw):
     with pytest.raises(N.LoradsError) as ei:
         N.lorads_batch_create(insts, **kw)
