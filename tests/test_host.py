@@ -260,3 +260,23 @@ def test_unsorted_pairs_take_the_sparse_conversion():
     b = W.maxcut_instance(100, (i[perm], j[perm], w[perm]))
     assert np.array_equal(a.rowptr, b.rowptr) and np.array_equal(a.colind, b.colind)
     assert np.allclose(a.val, b.val, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("overrides", [
+    {}, dict(prec=N.LORADS_MIXED, compute_err2=1, admm_switch=3e-4, lbfgs_mem=2),
+    dict(max_outer=10**6, max_inner=200, rank_update_threshold=10**6, verbose=2),
+    dict(max_outer=1, max_inner=5, tol=1e-300), dict(time_limit=1e-9), dict(reopt_level=2, lanczos_steps=300),
+    dict(lbfgs_scaling=0, rank_update_threshold=1), dict(infeas_decrease=0.0, rho_growth=1.0),
+])
+def test_accepts_the_solver_constants_in_use(lib, overrides):
+    """The parameter sets of the bench, smoke() and the GPU tests pass the range checks:
+    without a GPU the call gets as far as the first device call, with one it succeeds."""
+    pairs = ((lambda p: N.lorads_create(_maxcut(), p), N.lorads_destroy),
+             (lambda p: N.lorads_batch_create([_maxcut()], p), N.lorads_batch_destroy))
+    for create, destroy in pairs:
+        try:
+            handle = create(N.default_params(**overrides))
+        except N.LoradsError as e:
+            assert N.STATUS_NAMES[e.status] in ("LORADS_ERR_CUDA", "LORADS_ERR_OOM"), str(e)
+        else:
+            destroy(handle)
