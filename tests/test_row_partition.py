@@ -8,6 +8,7 @@ oracle's C R; the all-reduce of the per-rank partial <C R, R> must equal the
 oracle's objective.  Unmeasured on hardware (the library runs on one GPU);
 this covers the host-side logic of the multi-GPU design.
 """
+import math
 import os
 import socket
 
@@ -93,3 +94,137 @@ def test_plan_of_a_single_rank_has_no_halo():
     plan = PT.build_plan(inst.rowptr, inst.colind, inst.val, inst.n, 1, 0)
     assert plan.n_halo == 0 and plan.send == {} and plan.n_own == inst.n
     assert np.array_equal(plan.col, inst.colind)
+
+
+def _partitioned_inner_loop(rank: int, world: int, port: int, k: int, out):
+    """Algorithm 1 on row-partitioned ranks for the MaxCut SDP (constraint i on row i):
+    k L-BFGS iterations of the first ALM outer step, then its multiplier step, with
+    the oracle's inner-loop control (stop test, gamma-scaled two-loop, exact line
+    search of App. A.2, pair acceptance).  Per iteration the ranks exchange the halo
+    rows of D for C D, and every global sum is an all-reduce of per-rank partial
+    sums; the seven line-search sums travel in one all-reduce."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import scipy.sparse as sp
+        import workloads as W
+        from oracle import lorads_oracle as O
+        from paper_2407_15049_gb300 import partition as PT
+        inst = _instance("er")
+        r = 7
+        R0 = W.initial_factor(inst, r, 3)
+        plan = PT.build_plan(inst.rowptr, inst.colind, inst.val, inst.n, world, rank)
+        C_loc = sp.csr_matrix((plan.val, plan.col, plan.rowptr), shape=(plan.n_own, plan.n_own + plan.n_halo))
+
+        def allsum(*vals):
+            t = torch.tensor([float(v) for v in vals], dtype=torch.float64)
+            dist.all_reduce(t)
+            return t.tolist()
+
+        def cmul(X_own):                           # own rows of C X
+            halo = PT.exchange(plan, torch.as_tensor(X_own), dist).numpy()
+            return C_loc @ np.vstack([X_own, halo])
+
+        def dot(a, b):
+            return allsum(np.sum(a * b))[0]
+
+        nz = np.abs(plan.val[plan.val != 0])
+        s_abs, cnt = allsum(nz.sum(), nz.size)
+        rho = cnt / s_abs                           # 1 / mean |C_ij| over the stored entries
+        R = R0[plan.lo:plan.hi].copy()
+        y = np.zeros(plan.n_own)
+        b = np.ones(plan.n_own)
+        tol_e = 1e-300 * 2.0                        # tol (1 + ||b||_inf), b = 1
+
+        def grad(Rx, CRx):
+            z = np.sum(Rx * Rx, axis=1) - b
+            return 2.0 * (CRx - (y - rho * z)[:, None] * Rx)
+
+        CR = cmul(R)
+        G = grad(R, CR)
+        g0 = math.sqrt(dot(G, G))
+        S, Yh, it = [], [], 0
+        while it < k:
+            zc = math.sqrt(dot(*(2 * [np.sum(R * R, axis=1) - b])))
+            thr = max(tol_e, min(1.0 * rho * zc, 0.1 * g0))
+            if math.sqrt(dot(G, G)) <= thr:
+                break
+            # two-loop recursion, gamma I initial matrix (the oracle's default)
+            D = -G.copy()
+            T = len(S)
+            alpha = [0.0] * T
+            beta = [1.0 / dot(Yh[t], S[t]) for t in range(T)]
+            for t in range(T - 1, -1, -1):
+                alpha[t] = beta[t] * dot(S[t], D)
+                D = D - alpha[t] * Yh[t]
+            if T:
+                D = D * (dot(S[-1], Yh[-1]) / dot(Yh[-1], Yh[-1]))
+            for t in range(T):
+                D = D + (alpha[t] - beta[t] * dot(Yh[t], D)) * S[t]
+            it += 1
+            CD = cmul(D)
+            q0 = b - np.sum(R * R, axis=1)
+            q1 = 2.0 * np.sum(R * D, axis=1)
+            q2 = np.sum(D * D, axis=1)
+            w = y + rho * q0
+            p1, p2, s22, s12, sw2, s11, sw1 = allsum(
+                np.sum(CR * D) + np.sum(CD * R), np.sum(CD * D), q2 @ q2, q1 @ q2, w @ q2, q1 @ q1, w @ q1)
+            a = np.array([0.5 * rho * s22, rho * s12, p2 - sw2 + 0.5 * rho * s11, p1 - sw1])
+            tau = O.quartic_step(a)
+            if tau <= 0.0:
+                if S:
+                    S.clear()
+                    Yh.clear()
+                    continue
+                break
+            R_new = R + tau * D
+            CR_new = CR + tau * CD
+            G_new = grad(R_new, CR_new)
+            s, yv = tau * D, G_new - G
+            ys, yy, ss = allsum(np.sum(yv * s), np.sum(yv * yv), np.sum(s * s))
+            if ys > 1e-16 * math.sqrt(yy) * math.sqrt(ss):
+                S.append(s)
+                Yh.append(yv)
+                if len(S) > 4:
+                    S.pop(0)
+                    Yh.pop(0)
+            else:
+                S.clear()
+                Yh.clear()
+            R, G, CR = R_new, G_new, CR_new
+        y = y - rho * (np.sum(R * R, axis=1) - b)      # multiplier step of the outer loop
+        out[rank] = (plan.lo, plan.hi, R, y, it, rho)
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("k", [1, 5])
+def test_row_partitioned_inner_loop_follows_the_oracle(world, k):
+    """After k row-partitioned L-BFGS iterations and the multiplier step, every rank's
+    rows of R and y equal the FP64 oracle's single-process iterate (O.solve with one
+    outer step of k inner iterations) up to the summation order of the global sums."""
+    import workloads as W
+    from oracle import lorads_oracle as O
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_partitioned_inner_loop, args=(r, world, port, k, out)) for r in range(world)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=180)
+            assert p.exitcode == 0
+        res = dict(out)
+    inst = _instance("er")
+    P = O.Problem(inst)
+    ref = O.solve(P, W.initial_factor(inst, 7, 3), O.Params(max_outer=1, max_inner=k, tol=1e-300))
+    assert ref["inner"] == k
+    R = np.vstack([res[q][2] for q in range(world)])
+    y = np.concatenate([res[q][3] for q in range(world)])
+    assert all(res[q][4] == k for q in range(world))
+    assert res[0][5] == pytest.approx(O.auto_rho(P), rel=1e-14)
+    assert np.max(np.abs(R - ref["R"])) <= 1e-10 * np.max(np.abs(ref["R"]))
+    assert np.max(np.abs(y - ref["y"])) <= 1e-10 * np.max(np.abs(ref["y"]))
