@@ -228,3 +228,175 @@ def test_row_partitioned_inner_loop_follows_the_oracle(world, k):
     assert res[0][5] == pytest.approx(O.auto_rho(P), rel=1e-14)
     assert np.max(np.abs(R - ref["R"])) <= 1e-10 * np.max(np.abs(ref["R"]))
     assert np.max(np.abs(y - ref["y"])) <= 1e-10 * np.max(np.abs(ref["y"]))
+
+
+def _partitioned_triplet_loop(rank: int, world: int, port: int, k: int, out):
+    """The partitioned inner loop for constraints of one triplet each, on the
+    matrix-completion SDP (constraint k couples row i of U with row n1 + j of V,
+    often on another rank).  The halo plan is built on the pattern of
+    S~ = C - A*(y~), so both ends of every constraint that touches an own row are on
+    the rank.  A constraint whose rows lie on two ranks is evaluated on both, from
+    the same two rows: the replicated multipliers stay identical.  Global sums
+    count each constraint once, on the owner of its lower row."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import scipy.sparse as sp
+        import workloads as W
+        from oracle import lorads_oracle as O
+        from paper_2407_15049_gb300 import partition as PT
+        inst = _mc_instance()
+        n = inst.n
+        R0 = W.initial_factor(inst, 5, 4)
+        C = sp.csr_matrix((inst.val, inst.colind, inst.rowptr), shape=(n, n))
+        A = sp.csr_matrix((np.ones(inst.m), (inst.row, inst.col)), shape=(n, n))
+        pat = (abs(C) + A + A.T).tocsr()
+        pat.sort_indices()
+        plan = PT.build_plan(pat.indptr, pat.indices, pat.data, n, world, rank)
+        lo, hi, n_own = plan.lo, plan.hi, plan.n_own
+        halo_rows = np.concatenate([plan.recv[q] for q in sorted(plan.recv)]) if plan.recv else np.zeros(0, int)
+        loc = np.full(n, -1, dtype=np.int64)
+        loc[lo:hi] = np.arange(n_own)
+        loc[halo_rows] = n_own + np.arange(len(halo_rows))
+        row, col, av = inst.row.astype(np.int64), inst.col.astype(np.int64), inst.aval
+        touch = np.nonzero(((row >= lo) & (row < hi)) | ((col >= lo) & (col < hi)))[0]
+        ui, vj, ak, bk = loc[row[touch]], loc[col[touch]], av[touch], inst.b[touch]
+        assert np.all(ui >= 0) and np.all(vj >= 0)
+        diag = row[touch] == col[touch]
+        canon = PT.owner_of(row[touch], PT.row_ranges(n, world)) == rank
+        own_i, own_j = (row[touch] >= lo) & (row[touch] < hi), (col[touch] >= lo) & (col[touch] < hi)
+        Cl = C[lo:hi].tocoo()
+        C_loc = sp.csr_matrix((Cl.data, (Cl.row, loc[Cl.col])), shape=(n_own, n_own + plan.n_halo))
+
+        def allsum(*vals):
+            t = torch.tensor([float(v) for v in vals], dtype=torch.float64)
+            dist.all_reduce(t)
+            return t.tolist()
+
+        def full(X_own):
+            return np.vstack([X_own, PT.exchange(plan, torch.as_tensor(X_own), dist).numpy()])
+
+        def amap(Xu, Xv):                          # A(U V^T) on the touching constraints
+            uv = np.sum(Xu[ui] * Xv[vj], axis=1)
+            vu = np.sum(Xu[vj] * Xv[ui], axis=1)
+            return np.where(diag, ak * uv, ak * (uv + vu))
+
+        def astar(v, Xf):                          # own rows of A*(v) X
+            res = np.zeros((n_own, Xf.shape[1]))
+            w = v * ak
+            np.add.at(res, ui[own_i], (w[own_i])[:, None] * Xf[vj[own_i]])
+            off = own_j & ~diag
+            np.add.at(res, vj[off], (w[off])[:, None] * Xf[ui[off]])
+            return res
+
+        def dot(a, b):
+            return allsum(np.sum(a * b))[0]
+
+        cabs = np.abs(Cl.data[Cl.data != 0])
+        s_abs, cnt = allsum(cabs.sum(), cabs.size)
+        rho = cnt / s_abs
+        bmax = torch.tensor([float(np.max(np.abs(bk))) if bk.size else 0.0], dtype=torch.float64)
+        dist.all_reduce(bmax, op=dist.ReduceOp.MAX)
+        tol_e = 1e-300 * (1.0 + float(bmax[0]))
+        R = R0[lo:hi].copy()
+        y = np.zeros(len(touch))
+
+        def grad(Rf):
+            y_t = y - rho * (amap(Rf, Rf) - bk)
+            return 2.0 * (C_loc @ Rf - astar(y_t, Rf))
+
+        Rf = full(R)
+        G = grad(Rf)
+        g0 = math.sqrt(dot(G, G))
+        S, Yh, it = [], [], 0
+        while it < k:
+            zc = math.sqrt(allsum(np.sum(((amap(Rf, Rf) - bk) ** 2)[canon]))[0])
+            if math.sqrt(dot(G, G)) <= max(tol_e, min(rho * zc, 0.1 * g0)):
+                break
+            D = -G.copy()
+            T = len(S)
+            alpha = [0.0] * T
+            beta = [1.0 / dot(Yh[t], S[t]) for t in range(T)]
+            for t in range(T - 1, -1, -1):
+                alpha[t] = beta[t] * dot(S[t], D)
+                D = D - alpha[t] * Yh[t]
+            if T:
+                D = D * (dot(S[-1], Yh[-1]) / dot(Yh[-1], Yh[-1]))
+            for t in range(T):
+                D = D + (alpha[t] - beta[t] * dot(Yh[t], D)) * S[t]
+            it += 1
+            Df = full(D)
+            CR, CD = C_loc @ Rf, C_loc @ Df
+            q0 = bk - amap(Rf, Rf)
+            q1 = amap(Rf, Df) + amap(Df, Rf)
+            q2 = amap(Df, Df)
+            w = y + rho * q0
+            c = canon
+            p1, p2, s22, s12, sw2, s11, sw1 = allsum(
+                np.sum(CR * D) + np.sum(CD * R), np.sum(CD * D), q2[c] @ q2[c], q1[c] @ q2[c], w[c] @ q2[c],
+                q1[c] @ q1[c], w[c] @ q1[c])
+            a = np.array([0.5 * rho * s22, rho * s12, p2 - sw2 + 0.5 * rho * s11, p1 - sw1])
+            tau = O.quartic_step(a)
+            if tau <= 0.0:
+                if S:
+                    S.clear()
+                    Yh.clear()
+                    continue
+                break
+            R_new = R + tau * D
+            Rf_new = full(R_new)
+            G_new = grad(Rf_new)
+            s, yv = tau * D, G_new - G
+            ys, yy, ss = allsum(np.sum(yv * s), np.sum(yv * yv), np.sum(s * s))
+            if ys > 1e-16 * math.sqrt(yy) * math.sqrt(ss):
+                S.append(s)
+                Yh.append(yv)
+                if len(S) > 4:
+                    S.pop(0)
+                    Yh.pop(0)
+            else:
+                S.clear()
+                Yh.clear()
+            R, Rf, G = R_new, Rf_new, G_new
+        y = y - rho * (amap(Rf, Rf) - bk)
+        out[rank] = (lo, hi, R, touch[canon], y[canon], it, len(halo_rows))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def _mc_instance():
+    import workloads as W
+    return W.mc_instance(40, 50, 3, 600, seed=3)
+
+
+@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("k", [1, 5])
+def test_row_partitioned_matrix_completion_follows_the_oracle(world, k):
+    """Matrix completion on the row partition: every rank's rows of R and the
+    multipliers of the constraints it owns equal the FP64 oracle's iterate after k
+    L-BFGS iterations and the multiplier step, and the constraints couple ranks
+    (the halo is not empty)."""
+    import workloads as W
+    from oracle import lorads_oracle as O
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_partitioned_triplet_loop, args=(r, world, port, k, out)) for r in range(world)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=180)
+            assert p.exitcode == 0
+        res = dict(out)
+    inst = _mc_instance()
+    ref = O.solve(O.Problem(inst), W.initial_factor(inst, 5, 4), O.Params(max_outer=1, max_inner=k, tol=1e-300))
+    assert ref["inner"] == k
+    R = np.vstack([res[q][2] for q in range(world)])
+    owned = np.concatenate([res[q][3] for q in range(world)])
+    y = np.concatenate([res[q][4] for q in range(world)])
+    assert np.array_equal(np.sort(owned), np.arange(inst.m))          # every constraint owned once
+    assert all(res[q][5] == k for q in range(world)) and all(res[q][6] > 0 for q in range(world))
+    assert np.max(np.abs(R - ref["R"])) <= 1e-10 * np.max(np.abs(ref["R"]))
+    assert np.max(np.abs(y - ref["y"][owned])) <= 1e-10 * np.max(np.abs(ref["y"]))
