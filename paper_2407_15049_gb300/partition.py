@@ -58,6 +58,31 @@ class HaloPlan:
     def n_halo(self) -> int:
         return int(sum(len(v) for v in self.recv.values()))
 
+    @property
+    def halo_rows(self) -> np.ndarray:
+        """Global rows of the halo, in the order `exchange` returns them."""
+        if not self.recv:
+            return np.zeros(0, dtype=np.int64)
+        return np.concatenate([np.asarray(self.recv[q], dtype=np.int64) for q in sorted(self.recv)])
+
+    def local_index(self, rows) -> np.ndarray:
+        """Position of each global row in [own rows; halo rows] (the row order of the
+        local column numbering), or -1 for a row the rank neither owns nor receives."""
+        rows = np.asarray(rows, dtype=np.int64)
+        out = np.full(rows.shape, -1, dtype=np.int64)
+        own = (rows >= self.lo) & (rows < self.hi)
+        out[own] = rows[own] - self.lo
+        halo = self.halo_rows
+        if halo.size:
+            order = np.argsort(halo, kind="stable")
+            pos = np.searchsorted(halo[order], rows[~own])
+            pos = np.minimum(pos, halo.size - 1)
+            hit = halo[order][pos] == rows[~own]
+            sub = np.full(pos.shape, -1, dtype=np.int64)
+            sub[hit] = self.n_own + order[pos[hit]]
+            out[~own] = sub
+        return out
+
 
 def build_plan(rowptr: np.ndarray, colind: np.ndarray, val: np.ndarray, n: int, world: int,
                rank: int) -> HaloPlan:

@@ -254,10 +254,8 @@ def _partitioned_triplet_loop(rank: int, world: int, port: int, k: int, out):
         pat.sort_indices()
         plan = PT.build_plan(pat.indptr, pat.indices, pat.data, n, world, rank)
         lo, hi, n_own = plan.lo, plan.hi, plan.n_own
-        halo_rows = np.concatenate([plan.recv[q] for q in sorted(plan.recv)]) if plan.recv else np.zeros(0, int)
-        loc = np.full(n, -1, dtype=np.int64)
-        loc[lo:hi] = np.arange(n_own)
-        loc[halo_rows] = n_own + np.arange(len(halo_rows))
+        halo_rows = plan.halo_rows
+        loc = plan.local_index(np.arange(n))
         row, col, av = inst.row.astype(np.int64), inst.col.astype(np.int64), inst.aval
         touch = np.nonzero(((row >= lo) & (row < hi)) | ((col >= lo) & (col < hi)))[0]
         ui, vj, ak, bk = loc[row[touch]], loc[col[touch]], av[touch], inst.b[touch]
@@ -400,3 +398,21 @@ def test_row_partitioned_matrix_completion_follows_the_oracle(world, k):
     assert all(res[q][5] == k for q in range(world)) and all(res[q][6] > 0 for q in range(world))
     assert np.max(np.abs(R - ref["R"])) <= 1e-10 * np.max(np.abs(ref["R"]))
     assert np.max(np.abs(y - ref["y"][owned])) <= 1e-10 * np.max(np.abs(ref["y"]))
+
+
+def test_local_index_follows_the_halo_order():
+    """local_index maps own rows to 0..n_own-1 and halo rows to n_own + their position
+    in the exchange order (owner rank, then row), and every other row to -1; the
+    local column numbering of the plan's CSR uses the same map."""
+    from paper_2407_15049_gb300 import partition as PT
+    inst = _instance("er")
+    for world in (2, 3):
+        for rank in range(world):
+            plan = PT.build_plan(inst.rowptr, inst.colind, inst.val, inst.n, world, rank)
+            loc = plan.local_index(np.arange(inst.n))
+            assert np.array_equal(loc[plan.lo:plan.hi], np.arange(plan.n_own))
+            assert np.array_equal(loc[plan.halo_rows], plan.n_own + np.arange(plan.n_halo))
+            others = np.setdiff1d(np.setdiff1d(np.arange(inst.n), np.arange(plan.lo, plan.hi)), plan.halo_rows)
+            assert np.all(loc[others] == -1)
+            s0, s1 = inst.rowptr[plan.lo], inst.rowptr[plan.hi]
+            assert np.array_equal(plan.col, loc[inst.colind[s0:s1]])
