@@ -111,6 +111,31 @@ def build_plan(rowptr: np.ndarray, colind: np.ndarray, val: np.ndarray, n: int, 
                     val=np.asarray(val[s0:s1]), recv=recv, send=send)
 
 
+def sdp_pattern_plan(n: int, rowptr, colind, val, con_row, con_col, world: int, rank: int):
+    """Plan of `rank` for an SDP with constraints of one triplet each (constraint k on
+    entry (con_row[k], con_col[k]), row <= col): the halo plan of the pattern of
+    S~ = C - A*(y~) (C's stored entries and both triangles of every constraint entry),
+    so that both rows of every constraint touching an own row are on the rank, and
+    the constraint bookkeeping.  Returns (plan, touch, canonical): `touch` lists the
+    constraints with a row on this rank (each is evaluated here, from the same two
+    rows as on the other rank, so replicated multipliers stay identical) and
+    `canonical` marks those this rank counts in global sums (the owner of the
+    constraint's lower row), so every constraint is counted once."""
+    import scipy.sparse as sp
+    con_row = np.asarray(con_row, dtype=np.int64)
+    con_col = np.asarray(con_col, dtype=np.int64)
+    C = sp.csr_matrix((np.abs(np.asarray(val, dtype=np.float64)) + 1.0, np.asarray(colind), np.asarray(rowptr)),
+                      shape=(n, n))
+    A = sp.csr_matrix((np.ones(len(con_row)), (con_row, con_col)), shape=(n, n))
+    pat = (C + A + A.T).tocsr()
+    pat.sort_indices()
+    plan = build_plan(pat.indptr, pat.indices, pat.data, n, world, rank)
+    lo, hi = plan.lo, plan.hi
+    touch = np.nonzero(((con_row >= lo) & (con_row < hi)) | ((con_col >= lo) & (con_col < hi)))[0]
+    canonical = owner_of(con_row[touch], row_ranges(n, world)) == rank
+    return plan, touch, canonical
+
+
 def exchange(plan: HaloPlan, X_own, dist) -> "object":
     """Halo rows of X (a torch tensor holding this rank's rows, n_own x ld) in the
     plan's halo order, by one send/receive per neighbouring rank (torch.distributed

@@ -249,19 +249,15 @@ def _partitioned_triplet_loop(rank: int, world: int, port: int, k: int, out):
         n = inst.n
         R0 = W.initial_factor(inst, 5, 4)
         C = sp.csr_matrix((inst.val, inst.colind, inst.rowptr), shape=(n, n))
-        A = sp.csr_matrix((np.ones(inst.m), (inst.row, inst.col)), shape=(n, n))
-        pat = (abs(C) + A + A.T).tocsr()
-        pat.sort_indices()
-        plan = PT.build_plan(pat.indptr, pat.indices, pat.data, n, world, rank)
+        plan, touch, canon = PT.sdp_pattern_plan(n, inst.rowptr, inst.colind, inst.val, inst.row, inst.col,
+                                                 world, rank)
         lo, hi, n_own = plan.lo, plan.hi, plan.n_own
         halo_rows = plan.halo_rows
         loc = plan.local_index(np.arange(n))
         row, col, av = inst.row.astype(np.int64), inst.col.astype(np.int64), inst.aval
-        touch = np.nonzero(((row >= lo) & (row < hi)) | ((col >= lo) & (col < hi)))[0]
         ui, vj, ak, bk = loc[row[touch]], loc[col[touch]], av[touch], inst.b[touch]
         assert np.all(ui >= 0) and np.all(vj >= 0)
         diag = row[touch] == col[touch]
-        canon = PT.owner_of(row[touch], PT.row_ranges(n, world)) == rank
         own_i, own_j = (row[touch] >= lo) & (row[touch] < hi), (col[touch] >= lo) & (col[touch] < hi)
         Cl = C[lo:hi].tocoo()
         C_loc = sp.csr_matrix((Cl.data, (Cl.row, loc[Cl.col])), shape=(n_own, n_own + plan.n_halo))
@@ -416,3 +412,22 @@ def test_local_index_follows_the_halo_order():
             assert np.all(loc[others] == -1)
             s0, s1 = inst.rowptr[plan.lo], inst.rowptr[plan.hi]
             assert np.array_equal(plan.col, loc[inst.colind[s0:s1]])
+
+
+def test_sdp_pattern_plan_counts_every_constraint_once():
+    """On every rank, the constraints it evaluates are exactly those with a row it
+    owns, both rows of each are own or halo rows, and over the ranks each
+    constraint is counted (canonical) exactly once."""
+    from paper_2407_15049_gb300 import partition as PT
+    inst = _mc_instance()
+    for world in (1, 2, 3):
+        counted = np.zeros(inst.m, dtype=int)
+        for rank in range(world):
+            plan, touch, canon = PT.sdp_pattern_plan(inst.n, inst.rowptr, inst.colind, inst.val, inst.row,
+                                                     inst.col, world, rank)
+            row, col = inst.row.astype(np.int64), inst.col.astype(np.int64)
+            mine = ((row >= plan.lo) & (row < plan.hi)) | ((col >= plan.lo) & (col < plan.hi))
+            assert np.array_equal(touch, np.nonzero(mine)[0])
+            assert np.all(plan.local_index(row[touch]) >= 0) and np.all(plan.local_index(col[touch]) >= 0)
+            counted[touch[canon]] += 1
+        assert np.all(counted == 1)
